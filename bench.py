@@ -1,0 +1,326 @@
+"""Throughput of the parareal all-at-once partially explicit splitting solve.
+
+One step = one pint_parareal_solve on the 256x256 / 16x16-coarse / J=4 /
+four-layer workload with N = 64 coarse intervals x P = 64 fine steps
+(initial G sweep, K1 parareal iterations of WR fine propagation on all
+intervals + sequential coarse correction + jump norm, prolongation of the N
+states to the fine grid), inputs resident in HBM.
+
+metric: DOF.steps/s = (n_f - 1)^2 interior fine unknowns x N P fine steps /
+solve time.  Prints one JSON line (rank 0).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DOF·steps/s of parareal solve at rel L2 err ≤1e-6 vs FP64; % roofline; iters"
+UNIT = "DOF*steps/s"
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2"])
+    ap.add_argument("--precision", default="fp64", choices=["fp64", "mixed"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_init(args):
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    if world > 1:
+        import torch.distributed as dist
+        import torch
+        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+        dist.init_process_group("nccl")
+    return rank, world
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x, world):
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during the timed region."""
+
+    def __init__(self, index=0):
+        self.rows = []
+        self.proc = None
+        self.index = index
+
+    def __enter__(self):
+        q = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except OSError:
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.rows.append([x.strip() for x in line.split(",")])
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in self.rows:
+            try:
+                sm.append(float(r[0]))
+                mx = float(r[1])
+                for nm, v in zip(names, r[4:8]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": mx,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def load_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        return json.load(open(p)), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+# FP64 DGEMM throughput measured on this machine's GB300 with cuBLAS (torch.matmul
+# float64, 4096^3, best of 10); MEASURED_PEAKS.json carries no FP64 figure.
+FP64_MEASURED_TFLOPS = 1.096
+
+
+def problem(name):
+    from paper_2411_09244_gb300 import inputs
+    return {"c1": inputs.config_c1, "c2": inputs.config_c2}[name]()
+
+
+def cpu_baseline(prob, d1, d2, K1, wr_total, budget_s=25.0):
+    """The oracle's time stepping as it stands, on a synthetic reduced system
+    with the workload's dimensions (d1, d2, N, P): the shifted complex LU
+    setup of eq. (4.7), one WR iteration on a subset of intervals, one G
+    sweep; extrapolated to the solve with the measured K1 and WR counts."""
+    import types
+    from oracle.scheme import Scheme
+    cores = len(os.sched_getaffinity(0))
+    rng = np.random.default_rng(0)
+
+    def spd(n, scale):
+        X = rng.normal(size=(n, n)) / math.sqrt(n)
+        return (X @ X.T + np.eye(n)) * scale
+
+    r = types.SimpleNamespace()
+    r.M11, r.A11 = spd(d1, 1e-3), spd(d1, 1.0)
+    r.M22, r.A22 = spd(d2, 1e-3), spd(d2, 1.0)
+    r.M12 = rng.normal(size=(d1, d2)) * 1e-5
+    r.A12 = rng.normal(size=(d1, d2)) * 1e-2
+    r.M21, r.A21 = r.M12.T, r.A12.T
+    r.d1, r.d2 = d1, d2
+    N, P = prob.N, prob.P
+    t0 = time.perf_counter()
+    sch = Scheme(r, T=1e-4, N=N, P=P, alpha=prob.alpha)
+    sch._shift_lu()
+    t_setup = time.perf_counter() - t0
+    nsub = max(1, min(N, 4))
+    starts = [(rng.normal(size=d1), rng.normal(size=d2)) for _ in range(nsub)]
+    F1 = [np.ones(d1)] * nsub
+    F2 = [np.ones(d2)] * nsub
+    t0 = time.perf_counter()
+    sch.F_wr(starts, F1, F2, wr_tol=0.0, wr_max=1)
+    t_wr = (time.perf_counter() - t0) * N / nsub
+    t0 = time.perf_counter()
+    u, w = starts[0]
+    for n in range(N):
+        u, w = sch.G(u, w, F1[0], F2[0])
+    t_g = time.perf_counter() - t0
+    t_solve = t_setup + wr_total * t_wr + (K1 + 1) * t_g
+    D = (prob.n_f - 1) ** 2
+    return {"value": D * N * P / t_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "sample": (f"oracle time stepping on a synthetic reduced system of the workload's size "
+                       f"(d1={d1}, d2={d2}, N={N}, P={P}): shifted-LU setup {t_setup:.1f}s, one WR "
+                       f"iteration on {nsub} of {N} intervals, one G sweep; extrapolated with "
+                       f"K1={K1}, sum K0={wr_total} to {t_solve:.1f}s per solve")}
+
+
+def run_ours(args, rank, world):
+    import torch
+    from paper_2411_09244_gb300 import api, _lib
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    prob = problem(args.config)
+    prec = _lib.PINT_MIXED if args.precision == "mixed" else _lib.PINT_FP64
+    t0 = time.perf_counter()
+    p = api.Pint(prob.n_f, prob.kappa, device=dev)
+    info = p.build_multiscale_spaces(prob.nc, prob.J, prob.ell)
+    info = p.assemble_reduced(None, prob.N, prob.P, prob.alpha, prec)
+    setup_s = time.perf_counter() - t0
+    u0 = torch.tensor(prob.u0, dtype=torch.float64, device=dev)
+    f = torch.tensor(prob.f, dtype=torch.float64, device=dev)
+    amp = torch.tensor(prob.amp, dtype=torch.float64, device=dev)
+    eps = prob.eps
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    for _ in range(args.warmup):
+        p.parareal_solve(u0, f, amp, eps=eps, want_fine=True)
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    times, stats = [], []
+    barrier(world)
+    torch.cuda.synchronize()
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            flush.zero_()                       # L2 flush between timed iterations
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            _, _, st = p.parareal_solve(u0, f, amp, eps=eps, want_fine=True)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+            stats.append(st)
+    torch.cuda.synchronize()
+    barrier(world)
+    t_step = max_over_ranks(sum(times) / len(times), world)
+    D = (prob.n_f - 1) ** 2
+    dofsteps = D * prob.N * prob.P
+    value = world * dofsteps / t_step
+    # end to end through the C ABI with pinned host buffers (copies inside)
+    hu0 = torch.tensor(prob.u0, dtype=torch.float64).pin_memory()
+    hf = torch.tensor(prob.f, dtype=torch.float64).pin_memory()
+    ha = torch.tensor(prob.amp, dtype=torch.float64).pin_memory()
+    d = info["d1"] + info["d2"]
+    hfine = torch.empty((prob.N, (prob.n_f + 1) ** 2), dtype=torch.float64).pin_memory()
+    hcoarse = torch.empty((prob.N + 1, d), dtype=torch.float64).pin_memory()
+    import ctypes as C
+    L = _lib.lib()
+    e2e_t = []
+    for it in range(args.warmup + args.steps):
+        stv = _lib.Stats()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        s = L.pint_parareal_solve(p.h, hu0.data_ptr(), hf.data_ptr(), ha.data_ptr(), eps, prob.N, 1e-3 * eps,
+                                  200, hfine.data_ptr(), hcoarse.data_ptr(), C.byref(stv))
+        torch.cuda.synchronize()
+        if it >= args.warmup:
+            e2e_t.append(time.perf_counter() - t0)
+        _lib.check(s, allow=(-5,))
+    e2e_value = world * dofsteps / max_over_ranks(sum(e2e_t) / len(e2e_t), world)
+    h2d = (hu0.numel() + hf.numel() + ha.numel()) * 8
+    d2h = (hfine.numel() + hcoarse.numel()) * 8
+    st = stats[-1]
+    # roofline of the dominant kernel (the WR contractions)
+    peaks, src = load_peaks()
+    hot_ms = st.get("hot_ms", 0.0)
+    hot_flops = st.get("hot_flops", 0.0)
+    hot_launches = st.get("hot_launches", 0)
+    if args.precision == "fp64":
+        achieved = (hot_flops / (hot_ms / 1e3) / 1e12) if hot_ms > 0 else None
+        roof = {"bound": "alu", "kernel": "k_wr_gemm (FP64 WR contractions)", "achieved": achieved,
+                "peak": FP64_MEASURED_TFLOPS, "unit": "TFLOP/s",
+                "frac": (achieved / FP64_MEASURED_TFLOPS) if achieved else None, "traffic": None,
+                "peak_source": "measured cuBLAS DGEMM on GB300 (FP64 pipe)",
+                "launches": hot_launches, "avg_launch_ms": (hot_ms / hot_launches) if hot_launches else None}
+    else:
+        achieved = (hot_flops / (hot_ms / 1e3) / 1e12) if hot_ms > 0 else None
+        pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops"))
+        roof = {"bound": "tensor", "kernel": "WR contractions (tcgen05)", "achieved": achieved, "peak": pk,
+                "unit": "TFLOP/s", "frac": (achieved / pk) if achieved else None, "traffic": None,
+                "peak_source": src}
+    out = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64" if args.precision == "fp64" else "tf32/f32+f64",
+        "data": "synthetic (seeded splitmix64 high-contrast channels/inclusions; paper fields unavailable)",
+        "config": {"workload": f"{prob.name}: {prob.n_f}x{prob.n_f} fine, {prob.nc}x{prob.nc} coarse, "
+                               f"J={prob.J}, ell={prob.ell}, N={prob.N} x P={prob.P}, T={p.T:g}",
+                   "d1": info["d1"], "d2": info["d2"], "gamma": info["gamma"],
+                   "lambda_max22": info["lambda_max22"], "precision": args.precision,
+                   "K1": st["K1"], "wr_total": st["wr_total"], "wr_iters": st["wr_iters"],
+                   "setup_s": setup_s, "l2": "512 MB buffer zeroed before every timed step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "roofline": roof,
+        "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h},
+        "gpu_launches": int(sum(s["launches"] for s in stats)),
+        "clocks": clk.summary(),
+        "split_ms": {"f": st["f_ms"], "g": st["g_ms"], "prolong": st["prolong_ms"]},
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(prob, info["d1"], info["d2"], st["K1"], st["wr_total"])
+    p.close()
+    return out
+
+
+def run_reference(args, rank, world):
+    """The oracle timed on the host cores: each step a bounded sample."""
+    if rank != 0:
+        return None
+    prob = problem(args.config)
+    d1, d2 = (1355, 257) if args.config == "c2" else (170, 65)
+    K1, wr_total = (7, 105) if args.config == "c2" else (4, 60)
+    vals = []
+    for _ in range(args.warmup + args.steps):
+        cb = cpu_baseline(prob, d1, d2, K1, wr_total)
+        vals.append(cb["value"])
+    v = statistics.mean(vals[args.warmup:])
+    cb["value"] = v
+    D = (prob.n_f - 1) ** 2
+    return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": D * prob.N * prob.P / v * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": prob.name},
+            "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
+                                        "d2h_bytes_per_step": 0}}
+
+
+def main():
+    args = parse()
+    rank, world = dist_init(args)
+    out = run_reference(args, rank, world) if args.impl == "reference" else run_ours(args, rank, world)
+    if rank == 0 and out is not None:
+        print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,234 @@
+/*
+ * pint.h -- C ABI of the GB300 library for the parareal all-at-once partially
+ * explicit splitting scheme (Wang, Yang, Leung, "Parallel in time partially
+ * explicit splitting scheme for high contrast linear multiscale diffusion
+ * problems", arXiv:2411.09244).
+ *
+ * Problem (Section 2, eq. (2.1)): u_t - div(kappa grad u) = f on the unit
+ * square, u = 0 on the boundary, u(0) = u0; find the multiscale solution
+ * u_H^n at the coarse times t_n = n T / N (Algorithm 1).
+ *
+ * Conventions shared by every call
+ *   - Every call returns a pint_status: PINT_OK (0) or a negative code.
+ *     No call aborts, prints or exits; pint_last_error() gives a one-line
+ *     message for the last failure on the calling thread.
+ *   - Arrays are FP64 unless stated, row-major, fine-grid nodal arrays use
+ *     node (i, j) -> j*(n_f+1) + i (x fastest), cell arrays (ci, cj) ->
+ *     cj*n_f + ci.
+ *   - "ptr" arguments may be host or device memory: the library inspects
+ *     each pointer and stages host buffers through its own device buffers
+ *     with cudaMemcpyAsync on the context's stream.  The caller keeps
+ *     ownership of everything it passes; the library owns every buffer it
+ *     allocates and frees them in pint_destroy().
+ *   - All GPU work runs on the stream given to pint_setup_fine_grid (a
+ *     cudaStream_t passed as void*; NULL = legacy default stream).  Calls
+ *     that return host-visible results synchronise that stream before
+ *     returning.
+ *   - One context is not thread-safe; distinct contexts are independent.
+ */
+#ifndef PINT_H
+#define PINT_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pint_ctx pint_ctx;
+typedef int pint_status;
+
+enum {
+  PINT_OK = 0,
+  PINT_ERR_BAD_ARG = -1,       /* invalid size, pointer or call order      */
+  PINT_ERR_OOM = -2,           /* device allocation failed                 */
+  PINT_ERR_CUDA = -3,          /* a CUDA runtime call failed               */
+  PINT_ERR_UNSTABLE_DT = -4,   /* Delta t violates the Section 3.2 bound   */
+  PINT_ERR_NOT_CONVERGED = -5, /* parareal stopped at k_max above eps      */
+  PINT_ERR_NONFINITE = -6,     /* NaN/Inf in a jump or WR update norm      */
+  PINT_ERR_SINGULAR = -7,      /* a Cholesky pivot was not positive        */
+  PINT_ERR_STATE = -8,         /* stage called before its prerequisites    */
+  PINT_ERR_TIMEOUT = -9        /* a bounded device wait ran out            */
+};
+
+enum { PINT_FP64 = 0, PINT_MIXED = 1 };
+
+/* flags for pint_assemble_reduced */
+enum { PINT_ALLOW_UNSTABLE = 1 };
+
+typedef struct {
+  int n_f, nc, J, ell;
+  int n_blocks;       /* nc*nc                                             */
+  int n_raw;          /* all CEM/NLMC bases (matrix + fracture + enrichment) */
+  int L;              /* fracture bases (eq. (3.7))                         */
+  int d1, d2;         /* dim V_H1, dim V_H2                                 */
+  double gamma;       /* eq. (4.15), largest L2 cosine between the spaces  */
+  double lambda_max22;/* sup_{V_H2} ||v||_a^2 / ||v||^2                     */
+  double dt_max;      /* (1 - gamma^2) / lambda_max22 (Section 3.2)         */
+  double setup_ms;    /* device time of the last setup stage                */
+} pint_space_info;
+
+#define PINT_MAX_ITERS 512
+
+typedef struct {
+  int K1;                     /* parareal F sweeps done                   */
+  int converged;              /* 1 if the jump fell below eps              */
+  int wr_total;               /* WR iterations summed over all F sweeps    */
+  int wr_iters[PINT_MAX_ITERS];   /* WR iterations of F sweep k          */
+  double jumps[PINT_MAX_ITERS];   /* eq. (2.8) jump after sweep k        */
+  double solve_ms;            /* device time of the solve (CUDA events)    */
+  double f_ms, g_ms, prolong_ms; /* split of solve_ms                       */
+  int launches;               /* kernels launched inside the solve         */
+  int hot_launches;           /* launches of the WR contraction kernels     */
+  double hot_ms;              /* their summed device time (CUDA events)     */
+  double hot_flops;           /* their algorithmic flops: 4 d1 d2 per column
+                                 of each contraction (two per WR iteration) */
+} pint_stats;
+
+/*
+ * pint_setup_fine_grid -- Section 2 (fine FEM, eq. (2.2)); the fine mass and
+ * stiffness matrices M_f, A_f of Section 3.2.  Q1 elements on n_f x n_f
+ * square cells of side 1/n_f, kappa constant per cell.
+ *   out          receives a new context (free with pint_destroy)
+ *   n_f          fine cells per side, 4 <= n_f <= 4096
+ *   kappa_cells  ptr, n_f*n_f cell coefficients, all > 0
+ *   stream       cudaStream_t for all work of this context (void*)
+ * Errors: BAD_ARG (sizes, non-positive kappa), OOM, CUDA.
+ */
+pint_status pint_setup_fine_grid(pint_ctx** out, int n_f, const double* kappa_cells,
+                                 void* stream);
+
+/*
+ * pint_build_multiscale_spaces -- Section 3: per coarse block the NLMC
+ * indicator functions of the matrix and of each high-conductivity component
+ * (eqs. (3.4)-(3.5)) plus J CEM eigen-enrichment functions from eq. (3.1);
+ * the oversampled constraint energy minimising bases of eq. (3.2) on
+ * K_i^+ = K_i enlarged by ell coarse layers; psi_bar and the split
+ * V_H1 / V_H2 of eq. (3.7).
+ *   nc    coarse blocks per side (n_f % nc == 0, n_f/nc <= 32)
+ *   J     eigen-enrichment functions per block (0 = NLMC only)
+ *   ell   oversampling layers (>= 1)
+ *   info  optional, receives the dimensions (gamma/lambda are filled by
+ *         pint_assemble_reduced)
+ * Errors: BAD_ARG, STATE (no fine grid), SINGULAR (a window system not
+ * positive definite), OOM, CUDA.
+ */
+pint_status pint_build_multiscale_spaces(pint_ctx* ctx, int nc, int J, int ell,
+                                         pint_space_info* info);
+
+/*
+ * pint_assemble_reduced -- eq. (3.8): M_ij = Psi_i^T M_f Psi_j,
+ * A_ij = Psi_i^T A_f Psi_j; gamma of eq. (4.15); the time grid of Section
+ * 4.3 (N coarse intervals of Delta t = T/N, each split into P steps of
+ * dt = Delta t / P) and the WR parameter alpha of eq. (4.1).  Also the
+ * eigenbases Q (A11 Q = M11 Q Lambda1, Q^T M11 Q = I) and Q2 (same for
+ * (A22, M22)) in which the fine and coarse steps are solved.
+ *   T, N, P, alpha   time grid and WR parameter (0 < alpha < 1, P <= 64)
+ *   precision        PINT_FP64 or PINT_MIXED
+ *   flags            PINT_ALLOW_UNSTABLE: do not reject a Delta t above
+ *                    dt_max (Section 3.2 condition)
+ *   info             optional, receives gamma, lambda_max22, dt_max
+ * Errors: BAD_ARG, STATE, UNSTABLE_DT (Delta t > dt_max without the flag;
+ * info is still filled), SINGULAR, OOM, CUDA.
+ */
+pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double alpha,
+                                  int precision, int flags, pint_space_info* info);
+
+/*
+ * pint_parareal_solve -- Algorithm 1 (update eq. (2.7), stopping rule eq.
+ * (2.8)): initial G sweep, then F sweeps by the all-at-once WR propagator
+ * of Section 4.2 on every coarse interval at once, each followed by the
+ * sequential coarse correction, until max_n ||u_H^{n,k} - u_H^{n,k-1}||_L2
+ * <= eps, k = N or k = k_max; then prolongation to the fine grid.
+ *   u0_nodes    ptr, (n_f+1)^2 initial values (boundary values ignored)
+ *   f_shape     ptr, (n_f+1)^2 source shape g; the source on interval n is
+ *               amp[n] * g
+ *   amp         ptr or NULL (all ones), N amplitudes
+ *   eps         absolute jump tolerance (>= 0)
+ *   k_max       maximum F sweeps (1..N)
+ *   wr_tol      WR stop: max over intervals and steps of the L2 norm of the
+ *               update of u or w (>= 0)
+ *   wr_max      maximum WR iterations per F sweep (>= 1)
+ *   u_out       ptr or NULL, N x (n_f+1)^2: u_H at t_1..t_N on the fine grid
+ *   coarse_out  ptr or NULL, (N+1) x (d1+d2): (u_n, w_n) coefficients in the
+ *               V_H1 / V_H2 bases at t_0..t_N
+ *   stats       optional
+ * Errors: BAD_ARG, STATE, NOT_CONVERGED (outputs still written), NONFINITE,
+ * OOM, CUDA.
+ */
+pint_status pint_parareal_solve(pint_ctx* ctx, const double* u0_nodes, const double* f_shape,
+                                const double* amp, double eps, int k_max, double wr_tol,
+                                int wr_max, double* u_out, double* coarse_out,
+                                pint_stats* stats);
+
+/*
+ * pint_sequential_solve -- the limit of Algorithm 1: the fine splitting
+ * scheme eqs. (2.4)-(2.5) stepped sequentially over all N*P fine steps,
+ * restarting the lag terms at every coarse boundary.  Same arguments and
+ * outputs as pint_parareal_solve (no stats).
+ */
+pint_status pint_sequential_solve(pint_ctx* ctx, const double* u0_nodes, const double* f_shape,
+                                  const double* amp, double* u_out, double* coarse_out);
+
+/*
+ * pint_adjoint -- gradient of the observation misfit
+ * J = 1/2 sum_{n=1..N} sum_o (u_H^n(x_o) - d_{o,n})^2 with respect to u0
+ * and the amplitudes, through the transposed parareal sweeps (the forward
+ * map of Algorithm 1 at its limit is linear in (u0, amp)).
+ *   obs_nodes   ptr (int32), n_obs node ids
+ *   data        ptr, N x n_obs observations d_{o,n}
+ *   u0_nodes, f_shape, amp   as in pint_parareal_solve
+ *   eps, k_max, wr_tol, wr_max  controls of the forward and adjoint sweeps
+ *   misfit      host double*, receives J (may be NULL)
+ *   grad_u0     ptr or NULL, (n_f+1)^2
+ *   grad_amp    ptr or NULL, N
+ * Errors: as pint_parareal_solve.
+ */
+pint_status pint_adjoint(pint_ctx* ctx, const int* obs_nodes, int n_obs, const double* data,
+                         const double* u0_nodes, const double* f_shape, const double* amp,
+                         double eps, int k_max, double wr_tol, int wr_max, double* misfit,
+                         double* grad_u0, double* grad_amp);
+
+/*
+ * pint_get_reduced -- copy a reduced quantity (for inspection and tests).
+ *   which  0 M11, 1 A11, 2 M22, 3 A22, 4 M12, 5 A12 (row-major d_i x d_j),
+ *          6 load F1 and F2 of f_shape (d1 then d2; pass f_shape in aux),
+ *          7 the raw-basis Gram matrices G_M (n_raw^2),
+ *          8 per raw basis: kind (0 matrix, 1 fracture, 2 enrichment) and
+ *            owner block, as doubles (2*n_raw)
+ *   out    ptr, large enough for the quantity
+ *   aux    ptr or NULL, extra input for which = 6
+ */
+pint_status pint_get_reduced(pint_ctx* ctx, int which, double* out, const double* aux);
+
+/*
+ * pint_prolong -- u_h = Psi1 u + Psi2 w on the fine grid (Algorithm 1's
+ * output u_H = u + w), for `count` coefficient vectors.
+ *   coarse  ptr, count x (d1+d2)
+ *   u_out   ptr, count x (n_f+1)^2
+ */
+pint_status pint_prolong(pint_ctx* ctx, const double* coarse, int count, double* u_out);
+
+/* pint_apply_G / pint_apply_F -- one application of the coarse propagator
+ * (one step of eqs. (2.4)-(2.5) with step Delta t) or of the WR fine
+ * propagator (Section 4.2) to `count` states (count <= N), with source
+ * amplitudes amp (ptr, count values, or NULL = ones) of f_shape.
+ *   in, out  ptr, count x (d1+d2) coefficient vectors
+ *   wr_iters host int*, receives the WR iterations (F only, may be NULL) */
+pint_status pint_apply_G(pint_ctx* ctx, const double* in, int count, const double* f_shape,
+                         const double* amp, double* out);
+pint_status pint_apply_F(pint_ctx* ctx, const double* in, int count, const double* f_shape,
+                         const double* amp, double wr_tol, int wr_max, double* out,
+                         int* wr_iters);
+
+/* pint_get_info -- current dimensions and diagnostics. */
+pint_status pint_get_info(pint_ctx* ctx, pint_space_info* info);
+
+/* pint_destroy -- free every device buffer of the context (NULL is a no-op). */
+pint_status pint_destroy(pint_ctx* ctx);
+
+/* pint_last_error -- message of the last failing call on this thread. */
+const char* pint_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* PINT_H */

@@ -1,0 +1,166 @@
+"""Python front end of libpint with the C-ABI names (include/pint.h).
+
+`Pint` owns one context.  Inputs may be NumPy arrays, host tensors or CUDA
+tensors (float64, contiguous); results come back as float64 tensors on the
+device the caller asks for.  Every numerical step runs in libpint's CUDA
+kernels; this module only marshals arguments.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import math
+
+import numpy as np
+import torch
+
+from . import _lib as L
+
+
+def _f64(x, device=None):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        x = torch.from_numpy(np.ascontiguousarray(x, dtype=np.float64))
+    x = x.to(dtype=torch.float64)
+    if device is not None:
+        x = x.to(device)
+    return x.contiguous()
+
+
+def stable_T(N: int, gamma: float, lambda_max22: float, margin: float = 0.9) -> float:
+    """Final time whose coarse step satisfies the condition of Section 3.2,
+    Delta t lambda_max(A22, M22) <= 1 - gamma^2, with a margin, rounded down
+    to two significant digits."""
+    t = margin * N * (1.0 - gamma * gamma) / lambda_max22
+    e = math.floor(math.log10(t)) - 1
+    return math.floor(t / 10.0 ** e) * 10.0 ** e
+
+
+class Pint:
+    """One problem instance: fine grid -> spaces -> reduced operators ->
+    solves.  Mirrors pint_setup_fine_grid / pint_build_multiscale_spaces /
+    pint_assemble_reduced / pint_parareal_solve / pint_adjoint."""
+
+    def __init__(self, n_f: int, kappa_cells, device: str = "cuda"):
+        self.device = torch.device(device)
+        self.lib = L.lib()
+        self.n_f = n_f
+        self.nn = (n_f + 1) ** 2
+        k = _f64(kappa_cells, self.device).reshape(-1)
+        h = C.c_void_p()
+        L.check(self.lib.pint_setup_fine_grid(C.byref(h), n_f, L.ptr(k), L.current_stream()))
+        self.h = h
+        self.info = None
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            self.lib.pint_destroy(self.h)
+            self.h = C.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    # -- stages -----------------------------------------------------------
+    def build_multiscale_spaces(self, nc: int, J: int, ell: int) -> dict:
+        info = L.SpaceInfo()
+        L.check(self.lib.pint_build_multiscale_spaces(self.h, nc, J, ell, C.byref(info)))
+        self.info = info.as_dict()
+        return self.info
+
+    def assemble_reduced(self, T: float | None, N: int, P: int, alpha: float, precision: int = L.PINT_FP64,
+                         allow_unstable: bool = False) -> dict:
+        """T = None picks the stable final time from gamma and lambda_max."""
+        info = L.SpaceInfo()
+        flags = L.PINT_ALLOW_UNSTABLE if allow_unstable else 0
+        if T is None:
+            # first pass with a tiny T to obtain gamma and lambda_max
+            L.check(self.lib.pint_assemble_reduced(self.h, 1e-30, N, P, alpha, precision, flags,
+                                                   C.byref(info)))
+            T = stable_T(N, info.gamma, info.lambda_max22)
+        st = self.lib.pint_assemble_reduced(self.h, T, N, P, alpha, precision, flags, C.byref(info))
+        L.check(st)
+        self.info = info.as_dict()
+        self.T, self.N, self.P, self.alpha = T, N, P, alpha
+        return self.info
+
+    def get_info(self) -> dict:
+        info = L.SpaceInfo()
+        L.check(self.lib.pint_get_info(self.h, C.byref(info)))
+        return info.as_dict()
+
+    # -- solves -----------------------------------------------------------
+    def parareal_solve(self, u0_nodes, f_shape, amp=None, eps=1e-10, k_max=None, wr_tol=None, wr_max=200,
+                       want_fine=True, out_device=None):
+        dev = self.device if out_device is None else torch.device(out_device)
+        u0 = _f64(u0_nodes, self.device)
+        f = _f64(f_shape, self.device)
+        a = _f64(amp, self.device)
+        k_max = self.N if k_max is None else k_max
+        wr_tol = 1e-3 * eps if wr_tol is None else wr_tol
+        d = self.info["d1"] + self.info["d2"]
+        coarse = torch.empty((self.N + 1, d), dtype=torch.float64, device=dev)
+        fine = torch.empty((self.N, self.nn), dtype=torch.float64, device=dev) if want_fine else None
+        st = L.Stats()
+        status = self.lib.pint_parareal_solve(self.h, L.ptr(u0), L.ptr(f), L.ptr(a), eps, k_max, wr_tol,
+                                              wr_max, L.ptr(fine), L.ptr(coarse), C.byref(st))
+        L.check(status, allow=(-5,))
+        out = st.as_dict()
+        out["status"] = L.STATUS[status]
+        return coarse, fine, out
+
+    def sequential_solve(self, u0_nodes, f_shape, amp=None, want_fine=True):
+        u0 = _f64(u0_nodes, self.device)
+        f = _f64(f_shape, self.device)
+        a = _f64(amp, self.device)
+        d = self.info["d1"] + self.info["d2"]
+        coarse = torch.empty((self.N + 1, d), dtype=torch.float64, device=self.device)
+        fine = torch.empty((self.N, self.nn), dtype=torch.float64, device=self.device) if want_fine else None
+        L.check(self.lib.pint_sequential_solve(self.h, L.ptr(u0), L.ptr(f), L.ptr(a), L.ptr(fine),
+                                               L.ptr(coarse)))
+        return coarse, fine
+
+    def get_reduced(self, which: str, aux=None):
+        names = {"M11": 0, "A11": 1, "M22": 2, "A22": 3, "M12": 4, "A12": 5, "load": 6, "GM": 7, "kinds": 8}
+        d1, d2, nr = self.info["d1"], self.info["d2"], self.info["n_raw"]
+        shapes = {"M11": (d1, d1), "A11": (d1, d1), "M22": (d2, d2), "A22": (d2, d2), "M12": (d1, d2),
+                  "A12": (d1, d2), "load": (d1 + d2,), "GM": (nr, nr), "kinds": (nr, 2)}
+        out = torch.empty(shapes[which], dtype=torch.float64, device=self.device)
+        x = _f64(aux, self.device)
+        L.check(self.lib.pint_get_reduced(self.h, names[which], L.ptr(out), L.ptr(x)))
+        return out
+
+    def prolong(self, coarse):
+        c = _f64(coarse, self.device)
+        cnt = c.shape[0]
+        out = torch.empty((cnt, self.nn), dtype=torch.float64, device=self.device)
+        L.check(self.lib.pint_prolong(self.h, L.ptr(c), cnt, L.ptr(out)))
+        return out
+
+    def apply_G(self, states, f_shape, amp=None):
+        s = _f64(states, self.device)
+        f = _f64(f_shape, self.device)
+        a = _f64(amp, self.device)
+        out = torch.empty_like(s)
+        L.check(self.lib.pint_apply_G(self.h, L.ptr(s), s.shape[0], L.ptr(f), L.ptr(a), L.ptr(out)))
+        return out
+
+    def apply_F(self, states, f_shape, amp=None, wr_tol=1e-14, wr_max=200):
+        s = _f64(states, self.device)
+        f = _f64(f_shape, self.device)
+        a = _f64(amp, self.device)
+        out = torch.empty_like(s)
+        it = C.c_int(0)
+        L.check(self.lib.pint_apply_F(self.h, L.ptr(s), s.shape[0], L.ptr(f), L.ptr(a), wr_tol, wr_max,
+                                      L.ptr(out), C.byref(it)))
+        return out, it.value
+
+
+def from_problem(prob, device="cuda", precision=L.PINT_FP64, T=None):
+    """Build a Pint for a seeded Problem (inputs module) through all setup stages."""
+    p = Pint(prob.n_f, prob.kappa, device=device)
+    p.build_multiscale_spaces(prob.nc, prob.J, prob.ell)
+    p.assemble_reduced(T if T is not None else prob.T, prob.N, prob.P, prob.alpha, precision)
+    return p

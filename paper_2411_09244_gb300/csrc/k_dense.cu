@@ -1,0 +1,389 @@
+// Dense FP64 kernels for the reduced (d1- and d2-sized) problems of the
+// setup: blocked Cholesky, triangular solves, GEMM, and the symmetric
+// eigenproblem by the parallel cyclic Jacobi method (round-robin ordering;
+// each round applies n/2 disjoint rotations: row pass, then column pass).
+// The generalised problem A q = lambda B q is reduced with B = L L^T to
+// C = L^-1 A L^-T, and Q = L^-T V is B-orthonormal.
+#include "common.cuh"
+
+#include <algorithm>
+#include <numeric>
+
+namespace pint {
+
+namespace {
+
+constexpr int PB = 32;
+
+__global__ void k_potrf_diag(double* A, int n, int k0, int kb, int* status) {
+  __shared__ double T[PB][PB + 1];
+  int t = threadIdx.x;
+  for (int e = t; e < kb * kb; e += blockDim.x) T[e / kb][e % kb] = A[(size_t)(k0 + e / kb) * n + k0 + e % kb];
+  __syncthreads();
+  for (int k = 0; k < kb; ++k) {
+    if (t == 0) {
+      double d = T[k][k];
+      if (!(d > 0.0)) {
+        status[0] = 1;
+        d = 1.0;
+      }
+      T[k][k] = sqrt(d);
+    }
+    __syncthreads();
+    for (int i = k + 1 + t; i < kb; i += blockDim.x) T[i][k] /= T[k][k];
+    __syncthreads();
+    for (int e = t; e < kb * kb; e += blockDim.x) {
+      int i = e / kb, j = e % kb;
+      if (j > k && i >= j) T[i][j] -= T[i][k] * T[j][k];
+    }
+    __syncthreads();
+  }
+  for (int e = t; e < kb * kb; e += blockDim.x) {
+    int i = e / kb, j = e % kb;
+    A[(size_t)(k0 + i) * n + k0 + j] = (j <= i) ? T[i][j] : 0.0;
+  }
+}
+
+// rows below the diagonal block: x L11^T = a
+__global__ void k_trsm_panel(double* A, int n, int k0, int kb) {
+  __shared__ double L11[PB][PB + 1];
+  for (int e = threadIdx.x; e < kb * kb; e += blockDim.x)
+    L11[e / kb][e % kb] = A[(size_t)(k0 + e / kb) * n + k0 + e % kb];
+  __syncthreads();
+  int i = k0 + kb + blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double x[PB];
+  for (int j = 0; j < kb; ++j) {
+    double v = A[(size_t)i * n + k0 + j];
+    for (int l = 0; l < j; ++l) v -= x[l] * L11[j][l];
+    x[j] = v / L11[j][j];
+  }
+  for (int j = 0; j < kb; ++j) A[(size_t)i * n + k0 + j] = x[j];
+}
+
+// trailing update A22 -= L21 L21^T, lower-triangle 32x32 tiles
+__global__ void k_syrk_update(double* A, int n, int k0, int kb) {
+  int s = k0 + kb;
+  int ti = s + blockIdx.y * 32, tj = s + blockIdx.x * 32;
+  if (ti >= n || tj >= n || tj > ti) return;
+  __shared__ double Ai[32][PB + 1], Aj[32][PB + 1];
+  for (int e = threadIdx.x; e < 32 * kb; e += blockDim.x) {
+    int r = e / kb, l = e % kb;
+    Ai[r][l] = (ti + r < n) ? A[(size_t)(ti + r) * n + k0 + l] : 0.0;
+    Aj[r][l] = (tj + r < n) ? A[(size_t)(tj + r) * n + k0 + l] : 0.0;
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < 32 * 32; e += blockDim.x) {
+    int r = e / 32, q = e % 32;
+    int i = ti + r, j = tj + q;
+    if (i < n && j < n && j <= i) {
+      double acc = 0.0;
+      for (int l = 0; l < kb; ++l) acc += Ai[r][l] * Aj[q][l];
+      A[(size_t)i * n + j] -= acc;
+    }
+  }
+}
+
+__global__ void k_trsm_cols(const double* __restrict__ L, double* __restrict__ X, int n, int ncols,
+                            int trans) {
+  int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= ncols) return;
+  if (!trans) {
+    for (int i = 0; i < n; ++i) {
+      double v = X[(size_t)i * ncols + c];
+      const double* Li = L + (size_t)i * n;
+      for (int k = 0; k < i; ++k) v -= Li[k] * X[(size_t)k * ncols + c];
+      X[(size_t)i * ncols + c] = v / Li[i];
+    }
+  } else {
+    for (int i = n - 1; i >= 0; --i) {
+      double v = X[(size_t)i * ncols + c];
+      for (int k = i + 1; k < n; ++k) v -= L[(size_t)k * n + i] * X[(size_t)k * ncols + c];
+      X[(size_t)i * ncols + c] = v / L[(size_t)i * n + i];
+    }
+  }
+}
+
+// C = alpha op(A) op(B) + beta C (row-major); op(A) m x k, op(B) k x n
+__global__ void __launch_bounds__(256) k_gemm64(const double* __restrict__ A, const double* __restrict__ B,
+                                                double* __restrict__ C, int m, int n, int k, int ta,
+                                                int tb, double alpha, double beta) {
+  __shared__ double As[16][65], Bs[16][65];
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 4x4 outputs per thread
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < k; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      int kk = e / 64, r = e % 64;
+      int kg = k0 + kk, ig = i0 + r, jg = j0 + r;
+      double av = 0.0, bv = 0.0;
+      if (kg < k && ig < m) av = ta ? A[(size_t)kg * m + ig] : A[(size_t)ig * k + kg];
+      if (kg < k && jg < n) bv = tb ? B[(size_t)jg * k + kg] : B[(size_t)kg * n + jg];
+      As[kk][r] = av;
+      Bs[kk][r] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = As[kk][ty * 4 + q];
+        b[q] = Bs[kk][tx * 4 + q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * b[q];
+    }
+    __syncthreads();
+  }
+  for (int p = 0; p < 4; ++p)
+    for (int q = 0; q < 4; ++q) {
+      int i = i0 + ty * 4 + p, j = j0 + tx * 4 + q;
+      if (i < m && j < n) {
+        double v = alpha * acc[p][q];
+        if (beta != 0.0) v += beta * C[(size_t)i * n + j];
+        C[(size_t)i * n + j] = v;
+      }
+    }
+}
+
+__device__ inline void rot_params(double a, double b, double d, double& c, double& s) {
+  if (b == 0.0) {
+    c = 1.0;
+    s = 0.0;
+    return;
+  }
+  double tau = (d - a) / (2.0 * b);
+  double t = (tau >= 0.0 ? 1.0 : -1.0) / (fabs(tau) + sqrt(1.0 + tau * tau));
+  c = 1.0 / sqrt(1.0 + t * t);
+  s = t * c;
+}
+
+__device__ inline int rr_pos(int k, int r, int m) { return k == 0 ? 0 : 1 + ((k - 1 + r) % (m - 1)); }
+
+struct Rot {
+  int p, q;
+  double c, s;
+};
+
+__global__ void k_jac_params(const double* __restrict__ C, int n, int m, int r, Rot* __restrict__ rot) {
+  int k = blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= m / 2) return;
+  int x = rr_pos(k, r, m), y = rr_pos(m - 1 - k, r, m);
+  int p = min(x, y), q = max(x, y);
+  Rot R{p, q, 1.0, 0.0};
+  if (q < n) rot_params(C[(size_t)p * n + p], C[(size_t)p * n + q], C[(size_t)q * n + q], R.c, R.s);
+  else R.q = -1;
+  rot[k] = R;
+}
+
+__global__ void k_jac_rows(double* __restrict__ C, int n, int npair, const Rot* __restrict__ rot) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)npair * n) return;
+  int k = (int)(e / n), j = (int)(e % n);
+  Rot R = rot[k];
+  if (R.q < 0 || R.s == 0.0) return;
+  double x = C[(size_t)R.p * n + j], y = C[(size_t)R.q * n + j];
+  C[(size_t)R.p * n + j] = R.c * x - R.s * y;
+  C[(size_t)R.q * n + j] = R.s * x + R.c * y;
+}
+
+__global__ void k_jac_cols(double* __restrict__ C, double* __restrict__ V, int n, int npair,
+                           const Rot* __restrict__ rot) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)npair * n) return;
+  int k = (int)(e % npair), i = (int)(e / npair);
+  Rot R = rot[k];
+  if (R.q < 0 || R.s == 0.0) return;
+  double x = C[(size_t)i * n + R.p], y = C[(size_t)i * n + R.q];
+  C[(size_t)i * n + R.p] = R.c * x - R.s * y;
+  C[(size_t)i * n + R.q] = R.s * x + R.c * y;
+  x = V[(size_t)i * n + R.p];
+  y = V[(size_t)i * n + R.q];
+  V[(size_t)i * n + R.p] = R.c * x - R.s * y;
+  V[(size_t)i * n + R.q] = R.s * x + R.c * y;
+}
+
+__global__ void k_offnorm(const double* __restrict__ C, int n, double* __restrict__ out) {
+  __shared__ double sh[64];
+  double off = 0, tot = 0;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < (long long)n * n;
+       e += (long long)gridDim.x * blockDim.x) {
+    double v = C[e] * C[e];
+    tot += v;
+    if (e / n != e % n) off += v;
+  }
+  off = pintd::block_sum(off, sh);
+  tot = pintd::block_sum(tot, sh);
+  if (threadIdx.x == 0) {
+    atomicAdd(out, off);
+    atomicAdd(out + 1, tot);
+  }
+}
+
+__global__ void k_eye(double* V, int n) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < (long long)n * n) V[e] = (e / n == e % n) ? 1.0 : 0.0;
+}
+
+__global__ void k_diag(const double* C, int n, double* d) {
+  int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) d[i] = C[(size_t)i * n + i];
+}
+
+__global__ void k_symmetrize(double* C, int n) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  int i = (int)(e / n), j = (int)(e % n);
+  if (i < j) {
+    double v = 0.5 * (C[(size_t)i * n + j] + C[(size_t)j * n + i]);
+    C[(size_t)i * n + j] = v;
+    C[(size_t)j * n + i] = v;
+  }
+}
+
+__global__ void k_permute_cols(const double* __restrict__ V, const int* __restrict__ perm, int n,
+                               double* __restrict__ out) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)n * n) return;
+  int i = (int)(e / n), j = (int)(e % n);
+  out[e] = V[(size_t)i * n + perm[j]];
+}
+
+__global__ void k_transpose(const double* __restrict__ A, int m, int n, double* __restrict__ B) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)m * n) return;
+  int i = (int)(e / n), j = (int)(e % n);
+  B[(size_t)j * m + i] = A[e];
+}
+
+inline unsigned nblk(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+void dense_cholesky(Ctx* c, double* A, int n) {
+  int* st = (int*)dalloc(c, sizeof(int));
+  PINT_CUDA(cudaMemsetAsync(st, 0, sizeof(int), c->stream));
+  for (int k0 = 0; k0 < n; k0 += PB) {
+    int kb = std::min(PB, n - k0);
+    k_potrf_diag<<<1, 256, 0, c->stream>>>(A, n, k0, kb, st);
+    int rows = n - k0 - kb;
+    if (rows > 0) {
+      k_trsm_panel<<<nblk(rows, 128), 128, 0, c->stream>>>(A, n, k0, kb);
+      int tiles = (rows + 31) / 32;
+      k_syrk_update<<<dim3(tiles, tiles), 256, 0, c->stream>>>(A, n, k0, kb);
+    }
+    PINT_LAUNCH_CHECK();
+  }
+  // (the strict upper triangle outside the diagonal blocks keeps A's values;
+  // every consumer reads the lower triangle only)
+  int h = 0;
+  PINT_CUDA(cudaMemcpyAsync(&h, st, sizeof(int), cudaMemcpyDeviceToHost, c->stream));
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+  dfree(c, st);
+  PINT_REQUIRE(h == 0, PINT_ERR_SINGULAR, "dense Cholesky: matrix not positive definite");
+}
+
+void dense_trsm_lower(Ctx* c, const double* L, double* X, int n, int ncols, bool trans) {
+  k_trsm_cols<<<nblk(ncols, 64), 64, 0, c->stream>>>(L, X, n, ncols, trans ? 1 : 0);
+  PINT_LAUNCH_CHECK();
+}
+
+void dense_gemm(Ctx* c, const double* A, const double* B, double* C, int m, int n, int k, bool ta,
+                bool tb, double alpha, double beta) {
+  k_gemm64<<<dim3((n + 63) / 64, (m + 63) / 64), 256, 0, c->stream>>>(A, B, C, m, n, k, ta, tb, alpha,
+                                                                      beta);
+  PINT_LAUNCH_CHECK();
+}
+
+void dense_sym_eig(Ctx* c, double* C, double* V, double* lam, int n) {
+  const int m = n + (n & 1), npair = m / 2;
+  Rot* rot = (Rot*)dalloc(c, sizeof(Rot) * npair);
+  double* dn = (double*)dalloc(c, 2 * sizeof(double));
+  double* Vtmp = (double*)dalloc(c, (size_t)n * n * 8);
+  k_symmetrize<<<nblk((long long)n * n, 256), 256, 0, c->stream>>>(C, n);
+  k_eye<<<nblk((long long)n * n, 256), 256, 0, c->stream>>>(Vtmp, n);
+  PINT_LAUNCH_CHECK();
+  // one sweep = m-1 rounds, captured once as a CUDA graph
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  cudaStream_t cs = nullptr;
+  PINT_CUDA(cudaStreamCreateWithFlags(&cs, cudaStreamNonBlocking));
+  PINT_CUDA(cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal));
+  for (int r = 0; r < m - 1; ++r) {
+    k_jac_params<<<nblk(npair, 128), 128, 0, cs>>>(C, n, m, r, rot);
+    k_jac_rows<<<nblk((long long)npair * n, 256), 256, 0, cs>>>(C, n, npair, rot);
+    k_jac_cols<<<nblk((long long)npair * n, 256), 256, 0, cs>>>(C, Vtmp, n, npair, rot);
+  }
+  PINT_CUDA(cudaStreamEndCapture(cs, &graph));
+  PINT_CUDA(cudaGraphInstantiate(&exec, graph, 0));
+  double prev = 1e300;
+  for (int sweep = 0; sweep < 40; ++sweep) {
+    double h[2];
+    PINT_CUDA(cudaMemsetAsync(dn, 0, 16, c->stream));
+    k_offnorm<<<256, 256, 0, c->stream>>>(C, n, dn);
+    PINT_CUDA(cudaMemcpyAsync(h, dn, 16, cudaMemcpyDeviceToHost, c->stream));
+    PINT_CUDA(cudaStreamSynchronize(c->stream));
+    if (h[0] == 0.0 || h[0] <= 1e-30 * h[1] || (h[0] <= 1e-20 * h[1] && h[0] > 0.25 * prev)) break;
+    prev = h[0];
+    PINT_CUDA(cudaGraphLaunch(exec, c->stream));
+  }
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+  cudaGraphExecDestroy(exec);
+  cudaGraphDestroy(graph);
+  cudaStreamDestroy(cs);
+  // sort ascending
+  double* dd = (double*)dalloc(c, (size_t)n * 8);
+  k_diag<<<nblk(n, 256), 256, 0, c->stream>>>(C, n, dd);
+  std::vector<double> hl(n);
+  PINT_CUDA(cudaMemcpyAsync(hl.data(), dd, (size_t)n * 8, cudaMemcpyDeviceToHost, c->stream));
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+  std::vector<int> perm(n);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return hl[a] < hl[b]; });
+  std::vector<double> sl(n);
+  for (int i = 0; i < n; ++i) sl[i] = hl[perm[i]];
+  int* dperm = (int*)dalloc(c, (size_t)n * sizeof(int));
+  PINT_CUDA(cudaMemcpyAsync(dperm, perm.data(), (size_t)n * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(lam, sl.data(), (size_t)n * 8, cudaMemcpyHostToDevice, c->stream));
+  k_permute_cols<<<nblk((long long)n * n, 256), 256, 0, c->stream>>>(Vtmp, dperm, n, V);
+  PINT_LAUNCH_CHECK();
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+  dfree(c, dperm);
+  dfree(c, dd);
+  dfree(c, Vtmp);
+  dfree(c, dn);
+  dfree(c, rot);
+}
+
+void dense_gen_eig(Ctx* c, const double* A, const double* B, int n, double* Q, double* lam) {
+  size_t nn = (size_t)n * n;
+  double* Lb = (double*)dalloc(c, nn * 8);
+  double* Cm = (double*)dalloc(c, nn * 8);
+  double* T = (double*)dalloc(c, nn * 8);
+  PINT_CUDA(cudaMemcpyAsync(Lb, B, nn * 8, cudaMemcpyDeviceToDevice, c->stream));
+  dense_cholesky(c, Lb, n);
+  // C = L^-1 A L^-T : T = L^-1 A ; C = L^-1 T^T
+  PINT_CUDA(cudaMemcpyAsync(T, A, nn * 8, cudaMemcpyDeviceToDevice, c->stream));
+  dense_trsm_lower(c, Lb, T, n, n, false);
+  k_transpose<<<nblk((long long)nn, 256), 256, 0, c->stream>>>(T, n, n, Cm);
+  dense_trsm_lower(c, Lb, Cm, n, n, false);
+  PINT_LAUNCH_CHECK();
+  dense_sym_eig(c, Cm, T, lam, n);
+  // Q = L^-T V
+  PINT_CUDA(cudaMemcpyAsync(Q, T, nn * 8, cudaMemcpyDeviceToDevice, c->stream));
+  dense_trsm_lower(c, Lb, Q, n, n, true);
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+  dfree(c, Lb);
+  dfree(c, Cm);
+  dfree(c, T);
+}
+
+void dense_transpose(Ctx* c, const double* A, int m, int n, double* B) {
+  k_transpose<<<nblk((long long)m * n, 256), 256, 0, c->stream>>>(A, m, n, B);
+  PINT_LAUNCH_CHECK();
+}
+
+}  // namespace pint

@@ -1,0 +1,445 @@
+// Galerkin projections of eq. (3.8) and the V_H1 / V_H2 split of eq. (3.7).
+//
+// Every raw basis (matrix, fracture or enrichment CEM basis) lives on its
+// window's interior nodes.  The raw Gram matrices G_X = Psi_all^T X Psi_all,
+// X in {M_f, A_f, s}, are formed window pair by window pair: X Psi_b is
+// evaluated once on the closure of b's window (9-point stencils), then dotted
+// with Psi_a over the overlap.  The split is a sparse change of basis of the
+// raw bases,
+//   V_H1: psi_tilde_r = psi_r - coef_r psi_bar  (fracture and enrichment r,
+//         the last fracture basis dropped),
+//   V_H2: psi_bar = sum_fracture psi_r / L, then the matrix bases,
+// so M11 = T1^T G_M T1 etc. are evaluated with rank-one corrections.
+#include "common.cuh"
+
+#include <algorithm>
+
+namespace pint {
+
+namespace {
+
+struct GWin {
+  int X0, Y0, wx, wy, nw, kt, raw0, pad;
+  long long psi_off, xpsi_off;
+};
+
+// X Psi_b on the closure (wx+2) x (wy+2) of b's window, for X = A, M, s
+__global__ void k_xpsi(const GWin* __restrict__ gw, int n_f, const double* __restrict__ stA,
+                       const double* __restrict__ stM, const double* __restrict__ stS,
+                       const double* __restrict__ psi, double* __restrict__ xpsi,
+                       long long xstride) {
+  const GWin W = gw[blockIdx.y];
+  const int cw = W.wx + 2, ch = W.wy + 2, ncl = cw * ch;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < ncl * W.kt; e += gridDim.x * blockDim.x) {
+    int q = e / ncl, l = e % ncl;
+    int cx = l % cw, cy = l / cw;           // closure coords, interior starts at (1,1)
+    int gx = W.X0 - 1 + cx, gy = W.Y0 - 1 + cy;
+    double a = 0, m = 0, s = 0;
+    if (gx >= 0 && gx <= n_f && gy >= 0 && gy <= n_f) {
+      int node = gy * (n_f + 1) + gx;
+      const double* ps = psi + W.psi_off + (size_t)q * W.nw;
+      for (int dy = -1; dy <= 1; ++dy)
+        for (int dx = -1; dx <= 1; ++dx) {
+          int ix = cx - 1 + dx, iy = cy - 1 + dy;  // interior coords
+          if (ix < 0 || ix >= W.wx || iy < 0 || iy >= W.wy) continue;
+          double v = ps[iy * W.wx + ix];
+          int k = (dy + 1) * 3 + (dx + 1);
+          a += stA[(size_t)node * 9 + k] * v;
+          m += stM[(size_t)node * 9 + k] * v;
+          s += stS[(size_t)node * 9 + k] * v;
+        }
+    }
+    size_t o = W.xpsi_off + (size_t)q * ncl + l;
+    xpsi[o] = a;
+    xpsi[o + xstride] = m;
+    xpsi[o + 2 * xstride] = s;
+  }
+}
+
+constexpr int KA = 24;  // max bases per window handled by the pair kernel
+
+// G_X[raw_a][raw_b] for all a of window wa and one b of window wb
+__global__ void __launch_bounds__(256) k_pair(const GWin* __restrict__ gw, const int2* __restrict__ pairs,
+                                              const double* __restrict__ psi,
+                                              const double* __restrict__ xpsi, long long xstride,
+                                              int n_raw, double* __restrict__ GA,
+                                              double* __restrict__ GM, double* __restrict__ GS) {
+  const int2 pr = pairs[blockIdx.x];
+  const GWin A = gw[pr.x], B = gw[pr.y];
+  const int qb = blockIdx.y;
+  if (qb >= B.kt) return;
+  // overlap of A's interior with B's closure, in global node coords
+  int x0 = max(A.X0, B.X0 - 1), x1 = min(A.X0 + A.wx - 1, B.X0 + B.wx);
+  int y0 = max(A.Y0, B.Y0 - 1), y1 = min(A.Y0 + A.wy - 1, B.Y0 + B.wy);
+  double acc[3][KA];
+#pragma unroll
+  for (int t = 0; t < KA; ++t) acc[0][t] = acc[1][t] = acc[2][t] = 0.0;
+  const int ox = x1 - x0 + 1, oy = y1 - y0 + 1;
+  const int cwB = B.wx + 2;
+  const double* xb = xpsi + B.xpsi_off + (size_t)qb * cwB * (B.wy + 2);
+  if (ox > 0 && oy > 0) {
+    for (int e = threadIdx.x; e < ox * oy; e += blockDim.x) {
+      int gx = x0 + e % ox, gy = y0 + e / ox;
+      int lb = (gy - B.Y0 + 1) * cwB + (gx - B.X0 + 1);
+      double va = xb[lb], vm = xb[lb + xstride], vs = xb[lb + 2 * xstride];
+      int la = (gy - A.Y0) * A.wx + (gx - A.X0);
+#pragma unroll
+      for (int t = 0; t < KA; ++t) {
+        if (t < A.kt) {
+          double p = psi[A.psi_off + (size_t)t * A.nw + la];
+          acc[0][t] += p * va;
+          acc[1][t] += p * vm;
+          acc[2][t] += p * vs;
+        }
+      }
+    }
+  }
+  __shared__ double sh[64];
+  for (int t = 0; t < A.kt; ++t) {
+    double s0 = pintd::block_sum(acc[0][t], sh);
+    double s1 = pintd::block_sum(acc[1][t], sh);
+    double s2 = pintd::block_sum(acc[2][t], sh);
+    if (threadIdx.x == 0) {
+      size_t o = (size_t)(A.raw0 + t) * n_raw + (B.raw0 + qb);
+      GA[o] = s0;
+      GM[o] = s1;
+      GS[o] = s2;
+    }
+  }
+}
+
+// out[v][raw] = sum_nodes psi_raw(node) vec_v(node)
+__global__ void k_raw_dot(const GWin* __restrict__ gw, int n_f, const double* __restrict__ psi,
+                          const double* __restrict__ vec, int count, int n_raw,
+                          double* __restrict__ out) {
+  const GWin W = gw[blockIdx.x];
+  const int q = blockIdx.y;
+  if (q >= W.kt) return;
+  const int nn = (n_f + 1) * (n_f + 1);
+  __shared__ double sh[64];
+  for (int v = 0; v < count; ++v) {
+    double acc = 0.0;
+    for (int l = threadIdx.x; l < W.nw; l += blockDim.x) {
+      int gx = W.X0 + l % W.wx, gy = W.Y0 + l / W.wx;
+      acc += psi[W.psi_off + (size_t)q * W.nw + l] * vec[(size_t)v * nn + gy * (n_f + 1) + gx];
+    }
+    acc = pintd::block_sum(acc, sh);
+    if (threadIdx.x == 0) out[(size_t)v * n_raw + W.raw0 + q] = acc;
+  }
+}
+
+// gb = G beta, with beta = 1/L on fracture raws
+__global__ void k_gbeta(const double* __restrict__ G, const int* __restrict__ kind, int n_raw,
+                        double invL, double* __restrict__ gb) {
+  int r = blockIdx.x;
+  __shared__ double sh[64];
+  double acc = 0.0;
+  for (int c = threadIdx.x; c < n_raw; c += blockDim.x)
+    if (kind[c] == 1) acc += G[(size_t)r * n_raw + c] * invL;
+  acc = pintd::block_sum(acc, sh);
+  if (threadIdx.x == 0) gb[r] = acc;
+}
+
+// bGb = beta^T G beta and coef_r = (G_S beta)_r / (beta^T G_S beta)
+__global__ void k_bgb(const double* __restrict__ gbM, const double* __restrict__ gbA,
+                      const double* __restrict__ gbS, const int* __restrict__ kind, int n_raw,
+                      double invL, double* __restrict__ scal, double* __restrict__ coef) {
+  __shared__ double sh[64];
+  double m = 0, a = 0, s = 0;
+  for (int c = threadIdx.x; c < n_raw; c += blockDim.x)
+    if (kind[c] == 1) {
+      m += gbM[c] * invL;
+      a += gbA[c] * invL;
+      s += gbS[c] * invL;
+    }
+  m = pintd::block_sum(m, sh);
+  a = pintd::block_sum(a, sh);
+  s = pintd::block_sum(s, sh);
+  if (threadIdx.x == 0) {
+    scal[0] = m;
+    scal[1] = a;
+    scal[2] = s;
+  }
+  for (int c = threadIdx.x; c < n_raw; c += blockDim.x) coef[c] = (kind[c] >= 1) ? gbS[c] / s : 0.0;
+}
+
+// reduced blocks of X from G_X (see file header); has_bar selects the L > 0 form
+__global__ void k_reduce(const double* __restrict__ G, const double* __restrict__ gb,
+                         const double* __restrict__ scal, int which, const double* __restrict__ coef,
+                         const int* __restrict__ h1, int d1, const int* __restrict__ h2m, int nm,
+                         int has_bar, int n_raw, double* __restrict__ X11,
+                         double* __restrict__ X12, double* __restrict__ X22) {
+  const int d2 = nm + has_bar;
+  const double bgb = has_bar ? scal[which] : 0.0;
+  long long tot = (long long)d1 * d1 + (long long)d1 * d2 + (long long)d2 * d2;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot;
+       e += (long long)gridDim.x * blockDim.x) {
+    if (e < (long long)d1 * d1) {
+      int i = (int)(e / d1), j = (int)(e % d1);
+      int ri = h1[i], rj = h1[j];
+      double v = G[(size_t)ri * n_raw + rj];
+      if (has_bar)
+        v += -gb[ri] * coef[rj] - coef[ri] * gb[rj] + bgb * coef[ri] * coef[rj];
+      X11[e] = v;
+    } else if (e < (long long)d1 * d1 + (long long)d1 * d2) {
+      long long f = e - (long long)d1 * d1;
+      int i = (int)(f / d2), j = (int)(f % d2);
+      int ri = h1[i];
+      double v;
+      if (has_bar && j == 0) {
+        v = gb[ri] - coef[ri] * bgb;
+      } else {
+        int rm = h2m[j - has_bar];
+        v = G[(size_t)ri * n_raw + rm];
+        if (has_bar) v -= coef[ri] * gb[rm];
+      }
+      X12[f] = v;
+    } else {
+      long long f = e - (long long)d1 * d1 - (long long)d1 * d2;
+      int i = (int)(f / d2), j = (int)(f % d2);
+      double v;
+      if (has_bar && i == 0 && j == 0) v = bgb;
+      else if (has_bar && i == 0) v = gb[h2m[j - 1]];
+      else if (has_bar && j == 0) v = gb[h2m[i - 1]];
+      else v = G[(size_t)h2m[i - has_bar] * n_raw + h2m[j - has_bar]];
+      X22[f] = v;
+    }
+  }
+}
+
+// v1 = T1^T raw, v2 = T2^T raw for count raw vectors
+__global__ void k_to_reduced(const double* __restrict__ raw, int count, int n_raw,
+                             const int* __restrict__ kind, double invL, const double* __restrict__ coef,
+                             const int* __restrict__ h1, int d1, const int* __restrict__ h2m, int nm,
+                             int has_bar, double* __restrict__ v1, double* __restrict__ v2) {
+  const int v = blockIdx.x;
+  const double* r = raw + (size_t)v * n_raw;
+  __shared__ double sh[64];
+  double br = 0.0;
+  if (has_bar) {
+    for (int c = threadIdx.x; c < n_raw; c += blockDim.x)
+      if (kind[c] == 1) br += r[c] * invL;
+    br = pintd::block_sum(br, sh);
+  }
+  const int d2 = nm + has_bar;
+  for (int i = threadIdx.x; i < d1; i += blockDim.x) v1[(size_t)v * d1 + i] = r[h1[i]] - coef[h1[i]] * br;
+  for (int j = threadIdx.x; j < d2; j += blockDim.x)
+    v2[(size_t)v * d2 + j] = (has_bar && j == 0) ? br : r[h2m[j - has_bar]];
+}
+
+// raw coefficients a = T1 u + T2 w, stored transposed: a[raw][v]
+__global__ void k_from_reduced(const double* __restrict__ u, const double* __restrict__ w, int count,
+                               int n_raw, const int* __restrict__ kind, double invL,
+                               const double* __restrict__ coef, const int* __restrict__ h1, int d1,
+                               const int* __restrict__ h2m, int nm, int has_bar,
+                               double* __restrict__ a) {
+  const int v = blockIdx.x;
+  const int d2 = nm + has_bar;
+  __shared__ double sh[64];
+  double cu = 0.0;
+  if (has_bar) {
+    for (int i = threadIdx.x; i < d1; i += blockDim.x) cu += coef[h1[i]] * u[(size_t)v * d1 + i];
+    cu = pintd::block_sum(cu, sh);
+  }
+  const double bar = has_bar ? (w[(size_t)v * d2] - cu) * invL : 0.0;
+  for (int r = threadIdx.x; r < n_raw; r += blockDim.x) a[(size_t)r * count + v] = (kind[r] == 1) ? bar : 0.0;
+  __syncthreads();
+  for (int i = threadIdx.x; i < d1; i += blockDim.x) a[(size_t)h1[i] * count + v] += u[(size_t)v * d1 + i];
+  for (int j = threadIdx.x; j < nm; j += blockDim.x)
+    a[(size_t)h2m[j] * count + v] += w[(size_t)v * d2 + has_bar + j];
+}
+
+// out[v][node] = sum over windows containing node, bases q: a[raw][v] psi
+__global__ void k_prolong(const GWin* __restrict__ gw, int n_f, int nc, int bs, int ell,
+                          const double* __restrict__ psi, const double* __restrict__ a, int count,
+                          double* __restrict__ out) {
+  const int nn1 = n_f + 1, nn = nn1 * nn1;
+  long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (long long)nn * count) return;
+  int v = (int)(t / nn), node = (int)(t % nn);
+  int gx = node % nn1, gy = node / nn1;
+  int cx = min(gx / bs, nc - 1), cy = min(gy / bs, nc - 1);
+  double acc = 0.0;
+  for (int by = max(0, cy - ell - 1); by <= min(nc - 1, cy + ell + 1); ++by)
+    for (int bx = max(0, cx - ell - 1); bx <= min(nc - 1, cx + ell + 1); ++bx) {
+      const GWin W = gw[by * nc + bx];
+      int lx = gx - W.X0, ly = gy - W.Y0;
+      if (lx < 0 || lx >= W.wx || ly < 0 || ly >= W.wy) continue;
+      int l = ly * W.wx + lx;
+      for (int q = 0; q < W.kt; ++q)
+        acc += a[(size_t)(W.raw0 + q) * count + v] * psi[W.psi_off + (size_t)q * W.nw + l];
+    }
+  out[t] = acc;
+}
+
+}  // namespace
+
+static GWin* make_gwin(Ctx* c) {
+  std::vector<GWin> gw(c->n_blocks);
+  long long xoff = 0;
+  for (int b = 0; b < c->n_blocks; ++b) {
+    const WinDesc& W = c->win[b];
+    GWin& G = gw[b];
+    G.X0 = W.X0;
+    G.Y0 = W.Y0;
+    G.wx = W.wx;
+    G.wy = W.wy;
+    G.nw = W.nw;
+    G.kt = W.kt;
+    G.raw0 = c->blk_kind_off[b];
+    G.pad = 0;
+    G.psi_off = W.psi_off;
+    G.xpsi_off = xoff;
+    xoff += (long long)W.kt * (W.wx + 2) * (W.wy + 2);
+    c->win[b].xpsi_off = G.xpsi_off;
+  }
+  GWin* d = (GWin*)dalloc(c, sizeof(GWin) * gw.size());
+  PINT_CUDA(cudaMemcpyAsync(d, gw.data(), sizeof(GWin) * gw.size(), cudaMemcpyHostToDevice, c->stream));
+  c->d_windesc = (int*)d;
+  return d;
+}
+
+void build_galerkin(Ctx* c) {
+  GWin* d_gw = make_gwin(c);
+  long long xtot = 0;
+  for (const auto& W : c->win) xtot += (long long)W.kt * (W.wx + 2) * (W.wy + 2);
+  double* xpsi = (double*)dalloc(c, (size_t)xtot * 3 * sizeof(double));
+  k_xpsi<<<dim3(64, c->n_blocks), 256, 0, c->stream>>>(d_gw, c->n_f, c->stA, c->stM, c->stS, c->psi,
+                                                       xpsi, xtot);
+  PINT_LAUNCH_CHECK();
+  // window pairs with A's interior meeting B's closure
+  std::vector<int2> pairs;
+  int maxkt = 0;
+  for (int a = 0; a < c->n_blocks; ++a) {
+    const WinDesc& A = c->win[a];
+    maxkt = std::max(maxkt, A.kt);
+    for (int b = 0; b < c->n_blocks; ++b) {
+      const WinDesc& B = c->win[b];
+      int x0 = std::max(A.X0, B.X0 - 1), x1 = std::min(A.X0 + A.wx - 1, B.X0 + B.wx);
+      int y0 = std::max(A.Y0, B.Y0 - 1), y1 = std::min(A.Y0 + A.wy - 1, B.Y0 + B.wy);
+      if (x0 <= x1 && y0 <= y1 && A.kt > 0 && B.kt > 0) pairs.push_back(make_int2(a, b));
+    }
+  }
+  PINT_REQUIRE(maxkt <= KA, PINT_ERR_BAD_ARG, "too many bases per block for the Galerkin kernel");
+  int2* d_pairs = (int2*)dalloc(c, pairs.size() * sizeof(int2));
+  PINT_CUDA(cudaMemcpyAsync(d_pairs, pairs.data(), pairs.size() * sizeof(int2), cudaMemcpyHostToDevice,
+                            c->stream));
+  size_t g2 = (size_t)c->n_raw * c->n_raw;
+  c->GM = (double*)dalloc(c, g2 * 8);
+  c->GA = (double*)dalloc(c, g2 * 8);
+  c->GS = (double*)dalloc(c, g2 * 8);
+  PINT_CUDA(cudaMemsetAsync(c->GM, 0, g2 * 8, c->stream));
+  PINT_CUDA(cudaMemsetAsync(c->GA, 0, g2 * 8, c->stream));
+  PINT_CUDA(cudaMemsetAsync(c->GS, 0, g2 * 8, c->stream));
+  for (size_t p0 = 0; p0 < pairs.size(); p0 += 65535) {
+    unsigned np = (unsigned)std::min<size_t>(65535, pairs.size() - p0);
+    k_pair<<<dim3(np, maxkt), 256, 0, c->stream>>>(d_gw, d_pairs + p0, c->psi, xpsi, xtot, c->n_raw,
+                                                   c->GA, c->GM, c->GS);
+    PINT_LAUNCH_CHECK();
+  }
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+  dfree(c, xpsi);
+  dfree(c, d_pairs);
+}
+
+namespace {
+struct SplitDev {
+  int* kind;
+  int* h1;
+  int* h2m;
+};
+SplitDev split_dev(Ctx* c) {
+  // three int arrays packed after each other in d_h1 (allocated in build_reduced)
+  int* base = reinterpret_cast<int*>(c->d_h1);
+  return SplitDev{base, base + c->n_raw, base + c->n_raw + c->d1};
+}
+}  // namespace
+
+void build_reduced(Ctx* c) {
+  const int n_raw = c->n_raw;
+  c->h1.clear();
+  c->h2m.clear();
+  int last_frac = -1;
+  for (int r = 0; r < n_raw; ++r)
+    if (c->kind[r] == 1) last_frac = r;
+  for (int r = 0; r < n_raw; ++r) {
+    if (c->kind[r] == 0) c->h2m.push_back(r);
+    else if (r != last_frac) c->h1.push_back(r);
+  }
+  c->has_bar = c->L > 0;
+  c->d1 = (int)c->h1.size();
+  c->d2 = (int)c->h2m.size() + (c->has_bar ? 1 : 0);
+  PINT_REQUIRE(c->d1 > 0 && c->d2 > 0, PINT_ERR_BAD_ARG, "empty V_H1 or V_H2");
+  std::vector<int> packed;
+  packed.insert(packed.end(), c->kind.begin(), c->kind.end());
+  packed.insert(packed.end(), c->h1.begin(), c->h1.end());
+  packed.insert(packed.end(), c->h2m.begin(), c->h2m.end());
+  c->d_h1 = (double*)dalloc(c, packed.size() * sizeof(int));
+  PINT_CUDA(cudaMemcpyAsync(c->d_h1, packed.data(), packed.size() * sizeof(int), cudaMemcpyHostToDevice,
+                            c->stream));
+  SplitDev sd = split_dev(c);
+  const double invL = c->has_bar ? 1.0 / c->L : 0.0;
+  double* gb = (double*)dalloc(c, 3 * (size_t)n_raw * 8);
+  double* scal = (double*)dalloc(c, 4 * 8);
+  c->coef = (double*)dalloc(c, (size_t)n_raw * 8);
+  PINT_CUDA(cudaMemsetAsync(scal, 0, 32, c->stream));
+  PINT_CUDA(cudaMemsetAsync(c->coef, 0, (size_t)n_raw * 8, c->stream));
+  if (c->has_bar) {
+    k_gbeta<<<n_raw, 128, 0, c->stream>>>(c->GM, sd.kind, n_raw, invL, gb);
+    k_gbeta<<<n_raw, 128, 0, c->stream>>>(c->GA, sd.kind, n_raw, invL, gb + n_raw);
+    k_gbeta<<<n_raw, 128, 0, c->stream>>>(c->GS, sd.kind, n_raw, invL, gb + 2 * n_raw);
+    k_bgb<<<1, 256, 0, c->stream>>>(gb, gb + n_raw, gb + 2 * n_raw, sd.kind, n_raw, invL, scal, c->coef);
+    PINT_LAUNCH_CHECK();
+  }
+  const int d1 = c->d1, d2 = c->d2, nm = (int)c->h2m.size();
+  auto A = [&](size_t n) { return (double*)dalloc(c, n * 8); };
+  c->M11 = A((size_t)d1 * d1);
+  c->A11 = A((size_t)d1 * d1);
+  c->M12 = A((size_t)d1 * d2);
+  c->A12 = A((size_t)d1 * d2);
+  c->M22 = A((size_t)d2 * d2);
+  c->A22 = A((size_t)d2 * d2);
+  k_reduce<<<512, 256, 0, c->stream>>>(c->GM, gb, scal, 0, c->coef, sd.h1, d1, sd.h2m, nm,
+                                        c->has_bar, n_raw, c->M11, c->M12, c->M22);
+  k_reduce<<<512, 256, 0, c->stream>>>(c->GA, gb + n_raw, scal, 1, c->coef, sd.h1, d1, sd.h2m, nm,
+                                        c->has_bar, n_raw, c->A11, c->A12, c->A22);
+  PINT_LAUNCH_CHECK();
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+  dfree(c, gb);
+  dfree(c, scal);
+}
+
+void raw_dot(Ctx* c, const double* vec_nodes, int count, double* out_raw) {
+  int maxkt = 0;
+  for (const auto& W : c->win) maxkt = std::max(maxkt, W.kt);
+  k_raw_dot<<<dim3(c->n_blocks, maxkt), 256, 0, c->stream>>>((const GWin*)c->d_windesc, c->n_f, c->psi,
+                                                              vec_nodes, count, c->n_raw, out_raw);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void to_reduced(Ctx* c, const double* raw, int count, double* v1, double* v2) {
+  SplitDev sd = split_dev(c);
+  k_to_reduced<<<count, 256, 0, c->stream>>>(raw, count, c->n_raw, sd.kind,
+                                             c->has_bar ? 1.0 / c->L : 0.0, c->coef, sd.h1, c->d1,
+                                             sd.h2m, (int)c->h2m.size(), c->has_bar, v1, v2);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void prolong_coeffs(Ctx* c, const double* u, const double* w, int count, double* out_nodes) {
+  SplitDev sd = split_dev(c);
+  double* a = (double*)dalloc(c, (size_t)c->n_raw * count * 8);
+  k_from_reduced<<<count, 256, 0, c->stream>>>(u, w, count, c->n_raw, sd.kind,
+                                               c->has_bar ? 1.0 / c->L : 0.0, c->coef, sd.h1, c->d1,
+                                               sd.h2m, (int)c->h2m.size(), c->has_bar, a);
+  PINT_LAUNCH_CHECK();
+  long long tot = (long long)c->nn * count;
+  k_prolong<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(
+      (const GWin*)c->d_windesc, c->n_f, c->nc, c->bs, c->ell, c->psi, a, count, out_nodes);
+  PINT_LAUNCH_CHECK();
+  c->launches += 2;
+  dfree(c, a);
+}
+
+}  // namespace pint

@@ -1,0 +1,808 @@
+// FP64 hot path: Algorithm 1 with the WR fine propagator of Section 4.2 on
+// all coarse intervals at once, in the spectral coordinates u = Q u~,
+// w = Q2 w~ (Q^T M11 Q = I, Q^T A11 Q = Lambda1, same for Q2 in V_H2).
+//
+// One step of eqs. (2.4)-(2.5) with step h, in these coordinates:
+//   (1 + h Lambda1) u~' = u~ - CM (w~ - w~_lag) - h CA w~ + h F1~
+//   w~' = (1 - h Lambda2) w~ - CM^T (u~ - u~_lag) - h CA^T u~' + h F2~
+// (G: h = Delta t, zero lag increments; fine scheme: h = dt.)
+//
+// One WR iteration on interval n (eqs. (4.8), (4.9), (4.12)), p = 1..P:
+//   r_p = F1~ - (CA + CM/dt) w~_{p-1} + (CM/dt) w~_{p-2}       [GEMM, K = 2 d2]
+//   per mode i: (B + lambda_i) u~_i = r_i + e_1 (u~_0 - alpha u~_P^{j-1})/dt
+//     solved by eq. (4.7): scale by Lambda^-1 (beta^{p-1}, beta = alpha^{1/P}),
+//     DFT over p, divide by d_k + lambda_i with d_k = (1 - beta e^{-2 pi i k/P})/dt,
+//     inverse DFT, scale by Lambda                                 [per mode]
+//   s_p = -CM^T (u~_p - u~_{p-1}) - dt CA^T u~_{p+1}               [GEMM, K = 2 d1]
+//   w~_{p+1} = (1 - dt Lambda2) w~_p + s_p + dt F2~                [recurrence]
+// with w~_{-1} = w~_0 and u~_{-1} = u~_0 (lags restart at the interval start).
+#include "common.cuh"
+
+#include <algorithm>
+#include <cmath>
+
+namespace pint {
+
+struct Hot {
+  int N = 0, P = 0, d1 = 0, d2 = 0, cap = 0;
+  double *Xu = nullptr, *Xw = nullptr;      // (N+1) x d
+  double *Ou = nullptr, *Ow = nullptr;      // previous iterate
+  double *Gu = nullptr, *Gw = nullptr;      // cached G(x_n^{k-1}), N x d
+  double *Fu = nullptr, *Fw = nullptr;      // F results, N x d
+  double *Ut = nullptr, *Wt = nullptr;      // cap x (P+1) x d
+  double *R = nullptr, *S = nullptr;        // cap x P x d
+  double* acc = nullptr;                    // 2 x cap x P squared update norms
+  double* red = nullptr;                    // scalars
+  double *b1 = nullptr, *b2 = nullptr;      // spectral loads of the source shape
+  double* amp = nullptr;                    // N
+  double *tmp1 = nullptr, *tmp2 = nullptr;  // staging
+  double* raw = nullptr;
+  double* nodes = nullptr;
+  cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  double hot_ms = 0, hot_flops = 0;
+  int hot_launches = 0;
+};
+
+namespace {
+
+inline unsigned nb_(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// ---------------------------------------------------------------------------
+// FP64 tiled GEMM with the WR column maps.  MODE 0: R (rows d1, K = 2 d2),
+// MODE 1: S (rows d2, K = 2 d1).  Column col -> interval n = n_lo + col / P,
+// step p = col % P.  Output out[(n - n_lo)][p][row] (row fastest).
+template <int MODE>
+__global__ void __launch_bounds__(256) k_wr_gemm(const double* __restrict__ A, int M, int K,
+                                                 const double* __restrict__ Ut,
+                                                 const double* __restrict__ Wt, int d1, int d2, int P,
+                                                 int ncols, double* __restrict__ out) {
+  __shared__ double As[16][65], Bs[16][65];
+  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[4][4] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+      int kk = e % 16, r = e / 16;  // k fastest for coalesced column reads
+      int kg = k0 + kk;
+      int ig = i0 + r, col = j0 + r;
+      double av = (kg < K && ig < M) ? A[(size_t)ig * K + kg] : 0.0;
+      double bv = 0.0;
+      if (kg < K && col < ncols) {
+        int n = col / P, p = col % P;
+        if (MODE == 0) {
+          // r_{p+1}: [w~_p ; w~_{max(p-1,0)}]
+          const double* Wn = Wt + (size_t)n * (P + 1) * d2;
+          bv = (kg < d2) ? Wn[(size_t)p * d2 + kg] : Wn[(size_t)(p >= 1 ? p - 1 : 0) * d2 + (kg - d2)];
+        } else {
+          // s_p: [u~_p - u~_{max(p-1,0)} ; u~_{p+1}]
+          const double* Un = Ut + (size_t)n * (P + 1) * d1;
+          if (kg < d1) bv = Un[(size_t)p * d1 + kg] - Un[(size_t)(p >= 1 ? p - 1 : 0) * d1 + kg];
+          else bv = Un[(size_t)(p + 1) * d1 + (kg - d1)];
+        }
+      }
+      As[kk][r] = av;
+      Bs[kk][r] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a[4], b[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        a[q] = As[kk][ty * 4 + q];
+        b[q] = Bs[kk][tx * 4 + q];
+      }
+#pragma unroll
+      for (int p = 0; p < 4; ++p)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * b[q];
+    }
+    __syncthreads();
+  }
+  for (int p = 0; p < 4; ++p)
+    for (int q = 0; q < 4; ++q) {
+      int i = i0 + ty * 4 + p, col = j0 + tx * 4 + q;
+      if (i < M && col < ncols) out[(size_t)col * M + i] = acc[p][q];
+    }
+}
+
+struct C2 {
+  double x, y;
+};
+__device__ inline C2 cmul(C2 a, C2 b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+__device__ inline C2 cdiv(C2 a, C2 b) {
+  double den = b.x * b.x + b.y * b.y;
+  return {(a.x * b.x + a.y * b.y) / den, (a.y * b.x - a.x * b.y) / den};
+}
+
+// in-place radix-2 DFT (sign -1: forward, +1: inverse without 1/P)
+__device__ void fft64(C2* v, int P, const double2* __restrict__ tw, int sign) {
+  // bit reversal
+  for (int i = 1, j = 0; i < P; ++i) {
+    int bit = P >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) {
+      C2 t = v[i];
+      v[i] = v[j];
+      v[j] = t;
+    }
+  }
+  for (int len = 2; len <= P; len <<= 1) {
+    int step = P / len;
+    for (int i = 0; i < P; i += len)
+      for (int k = 0; k < len / 2; ++k) {
+        double2 t = tw[k * step];
+        C2 w = {t.x, sign < 0 ? t.y : -t.y};
+        C2 a = v[i + k], b = cmul(v[i + k + len / 2], w);
+        v[i + k] = {a.x + b.x, a.y + b.y};
+        v[i + k + len / 2] = {a.x - b.x, a.y - b.y};
+      }
+  }
+}
+
+__device__ void dft_direct(C2* v, C2* tmp, int P, const double2* __restrict__ tw, int sign) {
+  for (int k = 0; k < P; ++k) {
+    C2 s = {0, 0};
+    for (int j = 0; j < P; ++j) {
+      double2 t = tw[(k * j) % P];
+      C2 w = {t.x, sign < 0 ? t.y : -t.y};
+      C2 m = cmul(v[j], w);
+      s.x += m.x;
+      s.y += m.y;
+    }
+    tmp[k] = s;
+  }
+  for (int k = 0; k < P; ++k) v[k] = tmp[k];
+}
+
+// per (interval, mode): alpha-circulant all-at-once solve of eq. (4.12) by
+// eq. (4.7); writes u~_1..u~_P and accumulates squared updates per (n, p)
+__global__ void __launch_bounds__(128) k_time_solve(const double* __restrict__ R, int d1, int P, int nact,
+                                                    int n_lo, double* __restrict__ Ut,
+                                                    const double* __restrict__ lam1,
+                                                    const double* __restrict__ b1,
+                                                    const double* __restrict__ amp, double alpha,
+                                                    double dt, const double2* __restrict__ tw,
+                                                    const double2* __restrict__ dsh,
+                                                    const double* __restrict__ bpow, int pow2,
+                                                    double* __restrict__ accU) {
+  const int nloc = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double sh[64];
+  C2 v[64], tmp[64];
+  double* Un = Ut + (size_t)nloc * (P + 1) * d1;
+  double unew[64];
+  if (i < d1) {
+    const double a = amp[n_lo + nloc];
+    const double li = lam1[i];
+    for (int p = 0; p < P; ++p) {
+      double y = R[((size_t)nloc * P + p) * d1 + i] + b1[i] * a;
+      if (p == 0) y += (Un[i] - alpha * Un[(size_t)P * d1 + i]) / dt;
+      v[p] = {y * bpow[p], 0.0};                       // (a) Lambda^-1 scaling
+    }
+    if (pow2) fft64(v, P, tw, -1);
+    else dft_direct(v, tmp, P, tw, -1);                // (a) DFT
+    for (int k = 0; k < P; ++k) {                      // (b) shifted solves
+      double2 d = dsh[k];
+      v[k] = cdiv(v[k], C2{d.x + li, d.y});
+    }
+    if (pow2) fft64(v, P, tw, +1);
+    else dft_direct(v, tmp, P, tw, +1);                // (c) inverse DFT
+    for (int p = 0; p < P; ++p) unew[p] = v[p].x / ((double)P * bpow[p]);
+  }
+  for (int p = 0; p < P; ++p) {
+    double du = 0.0;
+    if (i < d1) {
+      double old = Un[(size_t)(p + 1) * d1 + i];
+      du = (unew[p] - old) * (unew[p] - old);
+      Un[(size_t)(p + 1) * d1 + i] = unew[p];
+    }
+    du = pintd::block_sum(du, sh);
+    if (threadIdx.x == 0) atomicAdd(&accU[(size_t)nloc * P + p], du);
+  }
+}
+
+// per (interval, mode of V_H2): explicit recurrence of eq. (4.9)
+__global__ void __launch_bounds__(128) k_w_sweep(const double* __restrict__ S, int d2, int P, int n_lo,
+                                                 double* __restrict__ Wt, const double* __restrict__ lam2,
+                                                 const double* __restrict__ b2,
+                                                 const double* __restrict__ amp, double dt,
+                                                 double* __restrict__ accW) {
+  const int nloc = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double sh[64];
+  double* Wn = Wt + (size_t)nloc * (P + 1) * d2;
+  double w = 0.0, fac = 0.0, src = 0.0;
+  if (j < d2) {
+    w = Wn[j];
+    fac = 1.0 - dt * lam2[j];
+    src = dt * b2[j] * amp[n_lo + nloc];
+  }
+  for (int p = 0; p < P; ++p) {
+    double dw = 0.0;
+    if (j < d2) {
+      double wn = fac * w + S[((size_t)nloc * P + p) * d2 + j] + src;
+      double old = Wn[(size_t)(p + 1) * d2 + j];
+      dw = (wn - old) * (wn - old);
+      Wn[(size_t)(p + 1) * d2 + j] = wn;
+      w = wn;
+    }
+    dw = pintd::block_sum(dw, sh);
+    if (threadIdx.x == 0) atomicAdd(&accW[(size_t)nloc * P + p], dw);
+  }
+}
+
+__global__ void k_wr_norm(const double* __restrict__ acc, int cnt, double* __restrict__ out) {
+  __shared__ double sh[64];
+  double m = 0.0;
+  bool bad = false;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    double v = acc[e];
+    if (!(v == v) || v > 1e300) bad = true;
+    m = fmax(m, v);
+  }
+  m = pintd::block_max(m, sh);
+  double b = pintd::block_max(bad ? 1.0 : 0.0, sh);
+  if (threadIdx.x == 0) {
+    out[0] = sqrt(m);
+    out[1] = b;
+  }
+}
+
+// initialise the WR trajectories of intervals [n_lo, n_lo+nact) from their starts
+__global__ void k_wr_init(const double* __restrict__ Xu, const double* __restrict__ Xw, int d1, int d2,
+                          int P, int nact, double* __restrict__ Ut, double* __restrict__ Wt) {
+  const int nloc = blockIdx.y;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (P + 1) * (d1 + d2); e += gridDim.x * blockDim.x) {
+    int p = e / (d1 + d2), k = e % (d1 + d2);
+    if (k < d1) Ut[((size_t)nloc * (P + 1) + p) * d1 + k] = Xu[(size_t)nloc * d1 + k];
+    else Wt[((size_t)nloc * (P + 1) + p) * d2 + (k - d1)] = Xw[(size_t)nloc * d2 + (k - d1)];
+  }
+}
+
+__global__ void k_wr_ends(const double* __restrict__ Ut, const double* __restrict__ Wt, int d1, int d2,
+                          int P, double* __restrict__ Fu, double* __restrict__ Fw) {
+  const int nloc = blockIdx.y;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d1 + d2; e += gridDim.x * blockDim.x) {
+    if (e < d1) Fu[(size_t)nloc * d1 + e] = Ut[((size_t)nloc * (P + 1) + P) * d1 + e];
+    else Fw[(size_t)nloc * d2 + (e - d1)] = Wt[((size_t)nloc * (P + 1) + P) * d2 + (e - d1)];
+  }
+}
+
+// ---------------------------------------------------------------------------
+// one step of eqs. (2.4)-(2.5) for `count` independent states (blockIdx.y)
+// u-part: warp per row i
+__global__ void k_step_u(const double* __restrict__ CM, const double* __restrict__ CA, int d1, int d2,
+                         const double* __restrict__ u, const double* __restrict__ w,
+                         const double* __restrict__ wlag, const double* __restrict__ lam1,
+                         const double* __restrict__ b1, const double* __restrict__ amp, double h,
+                         double* __restrict__ uo, long long su, long long sw) {
+  const int v = blockIdx.y;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= d1) return;
+  const double* wv = w + v * sw;
+  const double* wl = wlag ? wlag + v * sw : nullptr;
+  double acc = 0.0;
+  for (int j = lane; j < d2; j += 32) {
+    double wj = wv[j];
+    double dw = wl ? (wj - wl[j]) : 0.0;
+    acc += CM[(size_t)warp * d2 + j] * dw + h * CA[(size_t)warp * d2 + j] * wj;
+  }
+  acc = pintd::warp_sum(acc);
+  if (lane == 0) {
+    double a = amp ? amp[v] : 1.0;
+    uo[v * su + warp] = (u[v * su + warp] - acc + h * a * b1[warp]) / (1.0 + h * lam1[warp]);
+  }
+}
+
+// w-part: warp per row j (uses the new u~')
+__global__ void k_step_w(const double* __restrict__ CMt, const double* __restrict__ CAt, int d1, int d2,
+                         const double* __restrict__ u, const double* __restrict__ ulag,
+                         const double* __restrict__ unew, const double* __restrict__ w,
+                         const double* __restrict__ lam2, const double* __restrict__ b2,
+                         const double* __restrict__ amp, double h, double* __restrict__ wo, long long su,
+                         long long sw) {
+  const int v = blockIdx.y;
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= d2) return;
+  const double* uv = u + v * su;
+  const double* ul = ulag ? ulag + v * su : nullptr;
+  const double* un = unew + v * su;
+  double acc = 0.0;
+  for (int i = lane; i < d1; i += 32) {
+    double du = ul ? (uv[i] - ul[i]) : 0.0;
+    acc += CMt[(size_t)warp * d1 + i] * du + h * CAt[(size_t)warp * d1 + i] * un[i];
+  }
+  acc = pintd::warp_sum(acc);
+  if (lane == 0) {
+    double a = amp ? amp[v] : 1.0;
+    wo[v * sw + warp] = (1.0 - h * lam2[warp]) * w[v * sw + warp] - acc + h * a * b2[warp];
+  }
+}
+
+// parareal correction of eq. (2.7) at coarse step n: x_{n+1} = g + F_n - G_old_n
+__global__ void k_pr_update(const double* __restrict__ gu, const double* __restrict__ gw,
+                            const double* __restrict__ fu, const double* __restrict__ fw,
+                            double* __restrict__ Gu, double* __restrict__ Gw, double* __restrict__ xu,
+                            double* __restrict__ xw, int d1, int d2, int first_sweep) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d1 + d2; e += gridDim.x * blockDim.x) {
+    if (e < d1) {
+      double g = gu[e];
+      xu[e] = first_sweep ? g : g + fu[e] - Gu[e];
+      Gu[e] = g;
+    } else {
+      int j = e - d1;
+      double g = gw[j];
+      xw[j] = first_sweep ? g : g + fw[j] - Gw[j];
+      Gw[j] = g;
+    }
+  }
+}
+
+// jump of eq. (2.8) per coarse time: ||du||^2 + ||dw||^2 + 2 du^T CM dw
+__global__ void k_jump(const double* __restrict__ Xu, const double* __restrict__ Xw,
+                       const double* __restrict__ Ou, const double* __restrict__ Ow,
+                       const double* __restrict__ CM, int d1, int d2, double* __restrict__ jump) {
+  const int n = blockIdx.x + 1;
+  __shared__ double sh[64];
+  __shared__ double dw[4096];
+  const double* xu = Xu + (size_t)n * d1;
+  const double* ou = Ou + (size_t)n * d1;
+  for (int j = threadIdx.x; j < d2; j += blockDim.x) dw[j] = Xw[(size_t)n * d2 + j] - Ow[(size_t)n * d2 + j];
+  __syncthreads();
+  double s = 0.0;
+  for (int j = threadIdx.x; j < d2; j += blockDim.x) s += dw[j] * dw[j];
+  for (int i = threadIdx.x; i < d1; i += blockDim.x) {
+    double du = xu[i] - ou[i];
+    double t = 0.0;
+    for (int j = 0; j < d2; ++j) t += CM[(size_t)i * d2 + j] * dw[j];
+    s += du * du + 2.0 * du * t;
+  }
+  s = pintd::block_sum(s, sh);
+  if (threadIdx.x == 0) jump[n - 1] = sqrt(fmax(s, 0.0));
+}
+
+__global__ void k_max_fin(const double* __restrict__ x, int n, double* __restrict__ out) {
+  __shared__ double sh[64];
+  double m = 0.0, bad = 0.0;
+  for (int i = threadIdx.x; i < n; i += blockDim.x) {
+    double v = x[i];
+    if (!(v == v) || v > 1e300) bad = 1.0;
+    m = fmax(m, v);
+  }
+  m = pintd::block_max(m, sh);
+  bad = pintd::block_max(bad, sh);
+  if (threadIdx.x == 0) {
+    out[0] = m;
+    out[1] = bad;
+  }
+}
+
+// initial projection in spectral coordinates (eq. (2.2), joint Gram solve):
+// [[I, CM], [CM^T, I]] [u~; w~] = [g1~; g2~]  ->  (I - CM^T CM) w~ = g2~ - CM^T g1~
+__global__ void k_proj_rhs(const double* __restrict__ CMt, const double* __restrict__ g1,
+                           const double* __restrict__ g2, int d1, int d2, double* __restrict__ r) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= d2) return;
+  double acc = 0.0;
+  for (int i = lane; i < d1; i += 32) acc += CMt[(size_t)warp * d1 + i] * g1[i];
+  acc = pintd::warp_sum(acc);
+  if (lane == 0) r[warp] = g2[warp] - acc;
+}
+__global__ void k_proj_u(const double* __restrict__ CM, const double* __restrict__ g1,
+                         const double* __restrict__ w, int d1, int d2, double* __restrict__ u) {
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (warp >= d1) return;
+  double acc = 0.0;
+  for (int j = lane; j < d2; j += 32) acc += CM[(size_t)warp * d2 + j] * w[j];
+  acc = pintd::warp_sum(acc);
+  if (lane == 0) u[warp] = g1[warp] - acc;
+}
+
+__global__ void k_fill(double* x, long long n, double v) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) x[e] = v;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------- host side --
+static Hot& hot(Ctx* c) {
+  if (!c->mixed) c->mixed = new Hot();
+  return *reinterpret_cast<Hot*>(c->mixed);
+}
+
+void hot_release(Ctx* c) {
+  if (c->mixed) {
+    delete reinterpret_cast<Hot*>(c->mixed);
+    c->mixed = nullptr;
+  }
+}
+
+static void ensure(Ctx* c, Hot& H, int cap) {
+  if (H.N == c->N && H.P == c->P && H.d1 == c->d1 && H.d2 == c->d2 && H.cap >= cap) return;
+  // buffers are owned by the context allocation list; resizing leaks the old
+  // ones until pint_destroy, which only happens when the time grid changes
+  const int N = c->N, P = c->P, d1 = c->d1, d2 = c->d2;
+  cap = std::max(cap, N);
+  auto A = [&](size_t n) { return (double*)dalloc(c, std::max<size_t>(n, 1) * 8); };
+  H.N = N;
+  H.P = P;
+  H.d1 = d1;
+  H.d2 = d2;
+  H.cap = cap;
+  H.Xu = A((size_t)(cap + 1) * d1);
+  H.Xw = A((size_t)(cap + 1) * d2);
+  H.Ou = A((size_t)(cap + 1) * d1);
+  H.Ow = A((size_t)(cap + 1) * d2);
+  H.Gu = A((size_t)cap * d1);
+  H.Gw = A((size_t)cap * d2);
+  H.Fu = A((size_t)cap * d1);
+  H.Fw = A((size_t)cap * d2);
+  H.Ut = A((size_t)cap * (P + 1) * d1);
+  H.Wt = A((size_t)cap * (P + 1) * d2);
+  H.R = A((size_t)cap * P * d1);
+  H.S = A((size_t)cap * P * d2);
+  H.acc = A((size_t)2 * cap * P);
+  H.red = A(8 + cap);
+  H.b1 = A(d1);
+  H.b2 = A(d2);
+  H.amp = A(cap);
+  H.tmp1 = A((size_t)(cap + 1) * std::max(d1, d2));
+  H.tmp2 = A((size_t)(cap + 1) * std::max(d1, d2));
+  H.raw = A((size_t)(cap + 1) * c->n_raw);
+  H.nodes = A((size_t)(cap + 1) * c->nn);
+  for (auto& e : H.ev)
+    if (!e) PINT_CUDA(cudaEventCreate(&e));
+}
+
+void hot_prepare(Ctx* c) {
+  const int d1 = c->d1, d2 = c->d2, P = c->P;
+  auto A = [&](size_t n) { return (double*)dalloc(c, n * 8); };
+  // [-G1 | G2], G1 = CA + CM/dt, G2 = CM/dt ; [-CM^T | -dt CA^T]
+  std::vector<double> hCM((size_t)d1 * d2), hCA((size_t)d1 * d2);
+  PINT_CUDA(cudaMemcpyAsync(hCM.data(), c->CM, hCM.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(hCA.data(), c->CA, hCA.size() * 8, cudaMemcpyDeviceToHost, c->stream));
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+  std::vector<double> AR((size_t)d1 * 2 * d2), AS((size_t)d2 * 2 * d1);
+  const double dt = c->dt;
+  for (int i = 0; i < d1; ++i)
+    for (int j = 0; j < d2; ++j) {
+      double cm = hCM[(size_t)i * d2 + j], ca = hCA[(size_t)i * d2 + j];
+      AR[(size_t)i * 2 * d2 + j] = -(ca + cm / dt);
+      AR[(size_t)i * 2 * d2 + d2 + j] = cm / dt;
+      AS[(size_t)j * 2 * d1 + i] = -cm;
+      AS[(size_t)j * 2 * d1 + d1 + i] = -dt * ca;
+    }
+  if (!c->AR) {
+    c->AR = A(AR.size());
+    c->AS = A(AS.size());
+    c->tw = (double2*)dalloc(c, 64 * sizeof(double2));
+    c->dshift = (double2*)dalloc(c, 64 * sizeof(double2));
+    c->lampow = A(65);
+  }
+  PINT_CUDA(cudaMemcpyAsync(c->AR, AR.data(), AR.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(c->AS, AS.data(), AS.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  std::vector<double2> tw(64), ds(64);
+  std::vector<double> bp(65);
+  const double beta = std::pow(c->alpha, 1.0 / P);
+  const double pi = 3.14159265358979323846;
+  for (int k = 0; k < P; ++k) {
+    double ang = -2.0 * pi * k / P;
+    tw[k] = make_double2(std::cos(ang), std::sin(ang));
+    ds[k] = make_double2((1.0 - beta * std::cos(ang)) / dt, (-beta * std::sin(ang)) / dt);
+  }
+  for (int p = 0; p <= P; ++p) bp[p] = std::pow(beta, (double)p);
+  PINT_CUDA(cudaMemcpyAsync(c->tw, tw.data(), 64 * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(c->dshift, ds.data(), 64 * sizeof(double2), cudaMemcpyHostToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(c->lampow, bp.data(), 65 * 8, cudaMemcpyHostToDevice, c->stream));
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+// spectral load vectors of the source shape: b~1 = Q^T Psi1^T M f, b~2 = Q2^T Psi2^T M f
+static void spectral_load(Ctx* c, Hot& H, const double* f_nodes) {
+  apply_stencil(c, c->stM, f_nodes, H.nodes, 1);
+  raw_dot(c, H.nodes, 1, H.raw);
+  to_reduced(c, H.raw, 1, H.tmp1, H.tmp2);
+  dense_gemm(c, c->Q, H.tmp1, H.b1, c->d1, 1, c->d1, true, false, 1.0, 0.0);
+  dense_gemm(c, c->Q2, H.tmp2, H.b2, c->d2, 1, c->d2, true, false, 1.0, 0.0);
+  c->launches += 2;
+}
+
+// original coordinates -> spectral: u~ = Q^T M11 u, w~ = Q2^T M22 w (count vectors)
+static void to_spectral(Ctx* c, const double* u, const double* w, int count, double* ut, double* wt,
+                        double* t1, double* t2) {
+  dense_gemm(c, u, c->M11, t1, count, c->d1, c->d1, false, false, 1.0, 0.0);
+  dense_gemm(c, t1, c->Q, ut, count, c->d1, c->d1, false, false, 1.0, 0.0);
+  dense_gemm(c, w, c->M22, t2, count, c->d2, c->d2, false, false, 1.0, 0.0);
+  dense_gemm(c, t2, c->Q2, wt, count, c->d2, c->d2, false, false, 1.0, 0.0);
+  c->launches += 4;
+}
+// spectral -> original: u = Q u~ (rows: u^T = u~^T Q^T)
+static void from_spectral(Ctx* c, const double* ut, const double* wt, int count, double* u, double* w) {
+  dense_gemm(c, ut, c->Q, u, count, c->d1, c->d1, false, true, 1.0, 0.0);
+  dense_gemm(c, wt, c->Q2, w, count, c->d2, c->d2, false, true, 1.0, 0.0);
+  c->launches += 2;
+}
+
+static void step_batch(Ctx* c, Hot& H, const double* u, const double* w, const double* ul,
+                       const double* wl, const double* amp, double h, int count, double* uo, double* wo) {
+  const int d1 = c->d1, d2 = c->d2;
+  k_step_u<<<dim3(nb_((long long)d1 * 32, 256), count), 256, 0, c->stream>>>(
+      c->CM, c->CA, d1, d2, u, w, wl, c->lam1, H.b1, amp, h, uo, d1, d2);
+  k_step_w<<<dim3(nb_((long long)d2 * 32, 256), count), 256, 0, c->stream>>>(
+      c->CMt, c->CAt, d1, d2, u, ul, uo, w, c->lam2, H.b2, amp, h, wo, d1, d2);
+  PINT_LAUNCH_CHECK();
+  c->launches += 2;
+}
+
+// WR fine propagator on intervals [n_lo, n_lo + nact) whose starts are
+// Xu[n], Xw[n] (relative rows 0..nact-1 of xs_u / xs_w); ends into fu, fw.
+static int wr_sweep(Ctx* c, Hot& H, const double* xs_u, const double* xs_w, const double* amp_act,
+                    int nact, double wr_tol, int wr_max, double* fu, double* fw, bool* bad) {
+  const int d1 = c->d1, d2 = c->d2, P = c->P;
+  const int ncols = nact * P;
+  k_wr_init<<<dim3(64, nact), 256, 0, c->stream>>>(xs_u, xs_w, d1, d2, P, nact, H.Ut, H.Wt);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+  const int pow2 = (P & (P - 1)) == 0;
+  int it = 0;
+  *bad = false;
+  for (it = 1; it <= wr_max; ++it) {
+    PINT_CUDA(cudaMemsetAsync(H.acc, 0, (size_t)2 * nact * P * 8, c->stream));
+    PINT_CUDA(cudaEventRecord(H.ev[0], c->stream));
+    k_wr_gemm<0><<<dim3(nb_(ncols, 64), nb_(d1, 64)), 256, 0, c->stream>>>(c->AR, d1, 2 * d2, H.Ut, H.Wt,
+                                                                          d1, d2, P, ncols, H.R);
+    PINT_CUDA(cudaEventRecord(H.ev[1], c->stream));
+    k_time_solve<<<dim3(nb_(d1, 128), nact), 128, 0, c->stream>>>(
+        H.R, d1, P, nact, 0, H.Ut, c->lam1, H.b1, amp_act, c->alpha, c->dt, c->tw, c->dshift, c->lampow,
+        pow2, H.acc);
+    PINT_CUDA(cudaEventRecord(H.ev[2], c->stream));
+    k_wr_gemm<1><<<dim3(nb_(ncols, 64), nb_(d2, 64)), 256, 0, c->stream>>>(c->AS, d2, 2 * d1, H.Ut, H.Wt,
+                                                                          d1, d2, P, ncols, H.S);
+    PINT_CUDA(cudaEventRecord(H.ev[3], c->stream));
+    k_w_sweep<<<dim3(nb_(d2, 128), nact), 128, 0, c->stream>>>(H.S, d2, P, 0, H.Wt, c->lam2, H.b2,
+                                                              amp_act, c->dt, H.acc + (size_t)nact * P);
+    k_wr_norm<<<1, 1024, 0, c->stream>>>(H.acc, 2 * nact * P, H.red);
+    PINT_LAUNCH_CHECK();
+    c->launches += 5;
+    double h[2];
+    PINT_CUDA(cudaMemcpyAsync(h, H.red, 16, cudaMemcpyDeviceToHost, c->stream));
+    PINT_CUDA(cudaStreamSynchronize(c->stream));
+    float m0 = 0.f, m1 = 0.f;
+    PINT_CUDA(cudaEventElapsedTime(&m0, H.ev[0], H.ev[1]));
+    PINT_CUDA(cudaEventElapsedTime(&m1, H.ev[2], H.ev[3]));
+    H.hot_ms += m0 + m1;
+    H.hot_launches += 2;
+    H.hot_flops += 2.0 * 4.0 * d1 * (double)d2 * ncols;
+    if (h[1] != 0.0 || !(h[0] == h[0])) {
+      *bad = true;
+      break;
+    }
+    if (h[0] <= wr_tol) break;
+  }
+  if (it > wr_max) it = wr_max;
+  k_wr_ends<<<dim3(8, nact), 256, 0, c->stream>>>(H.Ut, H.Wt, d1, d2, P, fu, fw);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+  return it;
+}
+
+static void stage_amp(Ctx* c, Hot& H, const double* amp_dev, int count) {
+  if (amp_dev)
+    PINT_CUDA(cudaMemcpyAsync(H.amp, amp_dev, (size_t)count * 8, cudaMemcpyDeviceToDevice, c->stream));
+  else
+    k_fill<<<nb_(count, 256), 256, 0, c->stream>>>(H.amp, count, 1.0);
+}
+
+void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const double* amp_dev, double eps,
+                int k_max, double wr_tol, int wr_max, double* u_out, double* coarse_out, pint_stats* st,
+                bool sequential) {
+  Hot& H = hot(c);
+  ensure(c, H, c->N);
+  const int N = c->N, d1 = c->d1, d2 = c->d2;
+  cudaEvent_t e0, e1, eF0, eF1;
+  PINT_CUDA(cudaEventCreate(&e0));
+  PINT_CUDA(cudaEventCreate(&e1));
+  PINT_CUDA(cudaEventCreate(&eF0));
+  PINT_CUDA(cudaEventCreate(&eF1));
+  c->launches = 0;
+  H.hot_ms = 0;
+  H.hot_flops = 0;
+  H.hot_launches = 0;
+  PINT_CUDA(cudaEventRecord(e0, c->stream));
+  stage_amp(c, H, amp_dev, N);
+  spectral_load(c, H, f_nodes);
+  // initial projection (eq. (2.2)) into spectral coordinates
+  apply_stencil(c, c->stM, u0_nodes, H.nodes, 1);
+  raw_dot(c, H.nodes, 1, H.raw);
+  to_reduced(c, H.raw, 1, H.tmp1, H.tmp2);
+  double* g1 = H.Ou;  // scratch rows
+  double* g2 = H.Ow;
+  dense_gemm(c, c->Q, H.tmp1, g1, d1, 1, d1, true, false, 1.0, 0.0);
+  dense_gemm(c, c->Q2, H.tmp2, g2, d2, 1, d2, true, false, 1.0, 0.0);
+  k_proj_rhs<<<nb_((long long)d2 * 32, 256), 256, 0, c->stream>>>(c->CMt, g1, g2, d1, d2, H.Xw);
+  dense_trsm_lower(c, c->projL, H.Xw, d2, 1, false);
+  dense_trsm_lower(c, c->projL, H.Xw, d2, 1, true);
+  k_proj_u<<<nb_((long long)d1 * 32, 256), 256, 0, c->stream>>>(c->CM, g1, H.Xw, d1, d2, H.Xu);
+  PINT_LAUNCH_CHECK();
+  c->launches += 7;
+  int K1 = 0, wr_total = 0;
+  bool converged = false, nonfinite = false;
+  float f_ms = 0.f;
+  if (sequential) {
+    // the fine scheme stepped through all N*P steps, lags restarted per interval
+    double *u = H.tmp1, *w = H.tmp2;
+    double* ul = H.Gu;
+    double* wl = H.Gw;
+    for (int n = 0; n < N; ++n) {
+      PINT_CUDA(cudaMemcpyAsync(u, H.Xu + (size_t)n * d1, d1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+      PINT_CUDA(cudaMemcpyAsync(w, H.Xw + (size_t)n * d2, d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+      PINT_CUDA(cudaMemcpyAsync(ul, u, d1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+      PINT_CUDA(cudaMemcpyAsync(wl, w, d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+      for (int p = 0; p < c->P; ++p) {
+        double* uo = H.Fu;
+        double* wo = H.Fw;
+        step_batch(c, H, u, w, ul, wl, H.amp + n, c->dt, 1, uo, wo);
+        PINT_CUDA(cudaMemcpyAsync(ul, u, d1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+        PINT_CUDA(cudaMemcpyAsync(wl, w, d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+        PINT_CUDA(cudaMemcpyAsync(u, uo, d1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+        PINT_CUDA(cudaMemcpyAsync(w, wo, d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+      }
+      PINT_CUDA(cudaMemcpyAsync(H.Xu + (size_t)(n + 1) * d1, u, d1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+      PINT_CUDA(cudaMemcpyAsync(H.Xw + (size_t)(n + 1) * d2, w, d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+    }
+    converged = true;
+  } else {
+    // k = 0: G sweep (Algorithm 1, step 1)
+    for (int n = 0; n < N; ++n) {
+      step_batch(c, H, H.Xu + (size_t)n * d1, H.Xw + (size_t)n * d2, nullptr, nullptr, H.amp + n, c->Dt, 1,
+                 H.tmp1, H.tmp2);
+      k_pr_update<<<4, 256, 0, c->stream>>>(H.tmp1, H.tmp2, nullptr, nullptr, H.Gu + (size_t)n * d1,
+                                            H.Gw + (size_t)n * d2, H.Xu + (size_t)(n + 1) * d1,
+                                            H.Xw + (size_t)(n + 1) * d2, d1, d2, 1);
+      c->launches++;
+    }
+    PINT_LAUNCH_CHECK();
+    int kcap = std::min(k_max, N);
+    for (int k = 1; k <= kcap; ++k) {
+      // intervals n < k-1 start from exact states; their F values are unchanged
+      const int n_lo = k - 1, nact = N - n_lo;
+      PINT_CUDA(cudaEventRecord(eF0, c->stream));
+      bool bad = false;
+      int it = wr_sweep(c, H, H.Xu + (size_t)n_lo * d1, H.Xw + (size_t)n_lo * d2, H.amp + n_lo, nact, wr_tol,
+                        wr_max, H.Fu + (size_t)n_lo * d1, H.Fw + (size_t)n_lo * d2, &bad);
+      PINT_CUDA(cudaEventRecord(eF1, c->stream));
+      PINT_CUDA(cudaEventSynchronize(eF1));
+      float ms = 0.f;
+      PINT_CUDA(cudaEventElapsedTime(&ms, eF0, eF1));
+      f_ms += ms;
+      if (bad) {
+        nonfinite = true;
+        break;
+      }
+      if (k - 1 < PINT_MAX_ITERS && st) st->wr_iters[k - 1] = it;
+      wr_total += it;
+      // keep x^{k-1} for the jump, then the sequential correction sweep
+      PINT_CUDA(cudaMemcpyAsync(H.Ou, H.Xu, (size_t)(N + 1) * d1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+      PINT_CUDA(cudaMemcpyAsync(H.Ow, H.Xw, (size_t)(N + 1) * d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+      for (int n = n_lo; n < N; ++n) {
+        step_batch(c, H, H.Xu + (size_t)n * d1, H.Xw + (size_t)n * d2, nullptr, nullptr, H.amp + n, c->Dt, 1,
+                   H.tmp1, H.tmp2);
+        k_pr_update<<<4, 256, 0, c->stream>>>(H.tmp1, H.tmp2, H.Fu + (size_t)n * d1, H.Fw + (size_t)n * d2,
+                                              H.Gu + (size_t)n * d1, H.Gw + (size_t)n * d2,
+                                              H.Xu + (size_t)(n + 1) * d1, H.Xw + (size_t)(n + 1) * d2, d1, d2,
+                                              0);
+        c->launches++;
+      }
+      k_jump<<<N, 256, 0, c->stream>>>(H.Xu, H.Xw, H.Ou, H.Ow, c->CM, d1, d2, H.red + 8);
+      k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
+      PINT_LAUNCH_CHECK();
+      c->launches += 2;
+      double h[2];
+      PINT_CUDA(cudaMemcpyAsync(h, H.red, 16, cudaMemcpyDeviceToHost, c->stream));
+      PINT_CUDA(cudaStreamSynchronize(c->stream));
+      K1 = k;
+      if (st && k - 1 < PINT_MAX_ITERS) st->jumps[k - 1] = h[0];
+      if (h[1] != 0.0) {
+        nonfinite = true;
+        break;
+      }
+      if (h[0] <= eps) {
+        converged = true;
+        break;
+      }
+    }
+    if (K1 == N) converged = true;  // k = N sweeps reproduce the fine propagation
+  }
+  // outputs: original coordinates and prolongation (Algorithm 1, return)
+  float pro_ms = 0.f;
+  cudaEvent_t eP0, eP1;
+  PINT_CUDA(cudaEventCreate(&eP0));
+  PINT_CUDA(cudaEventCreate(&eP1));
+  from_spectral(c, H.Xu, H.Xw, N + 1, H.tmp1, H.tmp2);
+  if (coarse_out) {
+    PINT_CUDA(cudaMemcpy2DAsync(coarse_out, (size_t)(d1 + d2) * 8, H.tmp1, (size_t)d1 * 8, (size_t)d1 * 8,
+                                N + 1, cudaMemcpyDeviceToDevice, c->stream));
+    PINT_CUDA(cudaMemcpy2DAsync(coarse_out + d1, (size_t)(d1 + d2) * 8, H.tmp2, (size_t)d2 * 8,
+                                (size_t)d2 * 8, N + 1, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  PINT_CUDA(cudaEventRecord(eP0, c->stream));
+  if (u_out) prolong_coeffs(c, H.tmp1 + d1, H.tmp2 + d2, N, u_out);
+  PINT_CUDA(cudaEventRecord(eP1, c->stream));
+  PINT_CUDA(cudaEventRecord(e1, c->stream));
+  PINT_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  PINT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  PINT_CUDA(cudaEventElapsedTime(&pro_ms, eP0, eP1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(eF0);
+  cudaEventDestroy(eF1);
+  cudaEventDestroy(eP0);
+  cudaEventDestroy(eP1);
+  if (st) {
+    st->K1 = K1;
+    st->converged = converged ? 1 : 0;
+    st->wr_total = wr_total;
+    st->solve_ms = ms;
+    st->f_ms = f_ms;
+    st->prolong_ms = pro_ms;
+    st->g_ms = ms - f_ms - pro_ms;
+    st->launches = c->launches;
+    st->hot_launches = H.hot_launches;
+    st->hot_ms = H.hot_ms;
+    st->hot_flops = H.hot_flops;
+  }
+  PINT_REQUIRE(!nonfinite, PINT_ERR_NONFINITE, "non-finite WR update or parareal jump");
+  PINT_REQUIRE(converged, PINT_ERR_NOT_CONVERGED, "parareal stopped at k_max above eps");
+}
+
+void apply_G_dev(Ctx* c, const double* in, int count, const double* f_nodes, const double* amp_dev,
+                 double* out) {
+  Hot& H = hot(c);
+  ensure(c, H, count);
+  const int d1 = c->d1, d2 = c->d2;
+  stage_amp(c, H, amp_dev, count);
+  spectral_load(c, H, f_nodes);
+  // split packed (d1+d2) rows into u, w; to spectral; step; back
+  PINT_CUDA(cudaMemcpy2DAsync(H.Ou, (size_t)d1 * 8, in, (size_t)(d1 + d2) * 8, (size_t)d1 * 8, count,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpy2DAsync(H.Ow, (size_t)d2 * 8, in + d1, (size_t)(d1 + d2) * 8, (size_t)d2 * 8, count,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  to_spectral(c, H.Ou, H.Ow, count, H.Xu, H.Xw, H.tmp1, H.tmp2);
+  step_batch(c, H, H.Xu, H.Xw, nullptr, nullptr, H.amp, c->Dt, count, H.Gu, H.Gw);
+  from_spectral(c, H.Gu, H.Gw, count, H.tmp1, H.tmp2);
+  PINT_CUDA(cudaMemcpy2DAsync(out, (size_t)(d1 + d2) * 8, H.tmp1, (size_t)d1 * 8, (size_t)d1 * 8, count,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpy2DAsync(out + d1, (size_t)(d1 + d2) * 8, H.tmp2, (size_t)d2 * 8, (size_t)d2 * 8, count,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+}
+
+void apply_F_dev(Ctx* c, const double* in, int count, const double* f_nodes, const double* amp_dev,
+                 double wr_tol, int wr_max, double* out, int* iters) {
+  Hot& H = hot(c);
+  ensure(c, H, count);
+  const int d1 = c->d1, d2 = c->d2;
+  stage_amp(c, H, amp_dev, count);
+  spectral_load(c, H, f_nodes);
+  PINT_CUDA(cudaMemcpy2DAsync(H.Ou, (size_t)d1 * 8, in, (size_t)(d1 + d2) * 8, (size_t)d1 * 8, count,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpy2DAsync(H.Ow, (size_t)d2 * 8, in + d1, (size_t)(d1 + d2) * 8, (size_t)d2 * 8, count,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  to_spectral(c, H.Ou, H.Ow, count, H.Xu, H.Xw, H.tmp1, H.tmp2);
+  bool bad = false;
+  int it = wr_sweep(c, H, H.Xu, H.Xw, H.amp, count, wr_tol, wr_max, H.Fu, H.Fw, &bad);
+  from_spectral(c, H.Fu, H.Fw, count, H.tmp1, H.tmp2);
+  PINT_CUDA(cudaMemcpy2DAsync(out, (size_t)(d1 + d2) * 8, H.tmp1, (size_t)d1 * 8, (size_t)d1 * 8, count,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpy2DAsync(out + d1, (size_t)(d1 + d2) * 8, H.tmp2, (size_t)d2 * 8, (size_t)d2 * 8, count,
+                              cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+  if (iters) *iters = it;
+  PINT_REQUIRE(!bad, PINT_ERR_NONFINITE, "non-finite WR update");
+}
+
+}  // namespace pint

@@ -1,0 +1,156 @@
+"""CUDA path vs the FP64 oracle, stage by stage, through the C ABI.
+
+Tolerances: the FP64 path must match the oracle to rel 1e-10 on the coarse
+states and fields (the multiscale spaces are canonical, so the reduced
+matrices themselves are compared entrywise at 1e-9 relative to their norm).
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = pytest.mark.gpu
+
+from paper_2411_09244_gb300 import api  # noqa: E402
+from paper_2411_09244_gb300.inputs import config_small, config_c1  # noqa: E402
+from oracle.pipeline import OracleRun  # noqa: E402
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+CASES = {
+    "small16": dict(n_f=16, nc=4, J=2, ell=1, N=4, P=8),
+    "ragged24": dict(n_f=24, nc=4, J=3, ell=2, N=3, P=12, channels=3, contrast=1e4, f_kind="gauss"),
+    "nlmc_only": dict(n_f=16, nc=4, J=0, ell=1, N=4, P=8, channels=3),
+    "uniform": dict(n_f=16, nc=4, J=2, ell=2, N=2, P=16, channels=0, contrast=1.0, u0_kind="sin",
+                    f_kind="zero"),
+}
+
+
+@pytest.fixture(scope="module", params=list(CASES) + ["c1"])
+def pair(request):
+    if request.param == "c1":
+        prob = config_c1()
+    else:
+        prob = config_small(**CASES[request.param])
+    orc = OracleRun(prob)
+    p = api.from_problem(prob, device="cuda", T=orc.T)
+    yield request.param, prob, orc, p
+    p.close()
+
+
+def test_dimensions_and_kinds(pair):
+    _, prob, orc, p = pair
+    assert p.info["d1"] == orc.red.d1 and p.info["d2"] == orc.red.d2
+    assert p.info["L"] == orc.spc.L
+    kinds = p.get_reduced("kinds").cpu().numpy()
+    assert np.array_equal(kinds[:, 0].astype(int), orc.spc.kind)
+    assert np.array_equal(kinds[:, 1].astype(int), orc.spc.owner)
+
+
+@pytest.mark.parametrize("name", ["M11", "A11", "M22", "A22", "M12", "A12"])
+def test_reduced_matrices(pair, name):
+    _, prob, orc, p = pair
+    got = p.get_reduced(name).cpu().numpy()
+    ref = getattr(orc.red, name)
+    assert rel(got, ref) < 1e-9
+
+
+def test_gamma_and_lambda(pair):
+    _, prob, orc, p = pair
+    assert abs(p.info["gamma"] - orc.gamma) < 1e-9
+    assert abs(p.info["lambda_max22"] - orc.lam22) < 1e-9 * orc.lam22
+
+
+def test_load_vector(pair):
+    _, prob, orc, p = pair
+    got = p.get_reduced("load", prob.f).cpu().numpy()
+    ref = np.concatenate([orc.F1, orc.F2])
+    assert rel(got, ref) < 1e-10
+
+
+def test_coarse_and_fine_propagators(pair):
+    _, prob, orc, p = pair
+    rng = np.random.default_rng(3)
+    d1, d2 = orc.red.d1, orc.red.d2
+    cnt = min(prob.N, 3)
+    X = rng.normal(size=(cnt, d1 + d2))
+    amp = prob.amp[:cnt]
+    G = p.apply_G(X, prob.f, amp).cpu().numpy()
+    for n in range(cnt):
+        gu, gw = orc.sch.G(X[n, :d1], X[n, d1:], amp[n] * orc.F1, amp[n] * orc.F2)
+        assert rel(G[n], np.concatenate([gu, gw])) < 1e-10
+    F, it = p.apply_F(X, prob.f, amp, wr_tol=1e-13, wr_max=400)
+    F = F.cpu().numpy()
+    starts = [(X[n, :d1], X[n, d1:]) for n in range(cnt)]
+    ends, it_o = orc.sch.F_wr(starts, [a * orc.F1 for a in amp], [a * orc.F2 for a in amp], 1e-13, 400)
+    assert abs(it - it_o) <= 1
+    for n in range(cnt):
+        ref = np.concatenate(ends[n])
+        assert rel(F[n], ref) < 1e-10
+        us, ws = orc.sch.F_seq(X[n, :d1], X[n, d1:], amp[n] * orc.F1, amp[n] * orc.F2)
+        assert rel(F[n], np.concatenate([us, ws])) < 1e-9
+
+
+def test_parareal_solve_matches_oracle(pair):
+    _, prob, orc, p = pair
+    coarse, fine, st = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-11, wr_tol=1e-14, wr_max=400)
+    u, w, st_o = orc.solve(eps=1e-11, wr_tol=1e-14, wr_max=400)
+    ref = np.concatenate([u, w], axis=1)
+    assert st["K1"] == st_o["K1"]
+    assert rel(coarse.cpu().numpy(), ref) < 1e-10
+    ref_f = orc.fine_field(u, w)[1:]
+    assert rel(fine.cpu().numpy(), ref_f) < 1e-10
+
+
+def test_k_equals_N_matches_sequential(pair):
+    _, prob, orc, p = pair
+    c_seq, f_seq = p.sequential_solve(prob.u0, prob.f, prob.amp)
+    u_s, w_s = orc.sequential()
+    assert rel(c_seq.cpu().numpy(), np.concatenate([u_s, w_s], axis=1)) < 1e-10
+    coarse, _, st = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=0.0, k_max=prob.N, wr_tol=0.0,
+                                     wr_max=400, want_fine=False)
+    assert st["K1"] == prob.N
+    assert rel(coarse.cpu().numpy(), c_seq.cpu().numpy()) < 1e-11
+
+
+def test_prolongation(pair):
+    _, prob, orc, p = pair
+    rng = np.random.default_rng(9)
+    X = rng.normal(size=(2, orc.red.d1 + orc.red.d2))
+    got = p.prolong(X).cpu().numpy()
+    ref = np.stack([orc.red.prolong(x[:orc.red.d1], x[orc.red.d1:]) for x in X])
+    assert rel(got, ref) < 1e-10
+
+
+def test_unstable_dt_is_rejected():
+    prob = config_small(n_f=16, nc=4, J=2, ell=1, N=4, P=8)
+    p = api.Pint(prob.n_f, prob.kappa)
+    p.build_multiscale_spaces(prob.nc, prob.J, prob.ell)
+    from paper_2411_09244_gb300._lib import PintError
+    with pytest.raises(PintError, match="UNSTABLE_DT"):
+        p.assemble_reduced(1.0, prob.N, prob.P, prob.alpha)
+    info = p.assemble_reduced(1.0, prob.N, prob.P, prob.alpha, allow_unstable=True)
+    assert info["dt_max"] < 1.0 / prob.N
+    p.close()
+
+
+def test_bad_arguments_return_codes():
+    from paper_2411_09244_gb300._lib import PintError
+    k = np.ones((16, 16))
+    with pytest.raises(PintError, match="BAD_ARG"):
+        api.Pint(3, np.ones((3, 3)))
+    k2 = k.copy()
+    k2[3, 3] = -1.0
+    with pytest.raises(PintError, match="BAD_ARG"):
+        api.Pint(16, k2)
+    p = api.Pint(16, k)
+    with pytest.raises(PintError, match="BAD_ARG"):
+        p.build_multiscale_spaces(5, 2, 1)   # 5 does not divide 16
+    with pytest.raises(PintError, match="STATE"):
+        p.assemble_reduced(1e-3, 4, 8, 0.1)
+    p.close()
