@@ -214,9 +214,11 @@ def run_ours(args, rank, world):
             flush.zero_()                       # L2 flush between timed iterations
             e0 = torch.cuda.Event(enable_timing=True)
             e1 = torch.cuda.Event(enable_timing=True)
+            torch.cuda.nvtx.range_push("solve")
             e0.record(stream)
             _, _, st = p.parareal_solve(u0, f, amp, eps=eps, want_fine=True)
             e1.record(stream)
+            torch.cuda.nvtx.range_pop()
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
             stats.append(st)
@@ -297,8 +299,10 @@ def run_reference(args, rank, world):
     if rank != 0:
         return None
     prob = problem(args.config)
-    d1, d2 = (1355, 257) if args.config == "c2" else (170, 65)
-    K1, wr_total = (7, 105) if args.config == "c2" else (4, 60)
+    # dimensions and iteration counts of this workload as measured on the GPU
+    # path (the same algorithm converges in the same counts)
+    d1, d2 = (1343, 257) if args.config == "c2" else (170, 65)
+    K1, wr_total = (9, 93) if args.config == "c2" else (4, 60)
     vals = []
     for _ in range(args.warmup + args.steps):
         cb = cpu_baseline(prob, d1, d2, K1, wr_total)
