@@ -207,6 +207,25 @@ pint_status pint_get_reduced(pint_ctx* ctx, int which, double* out, const double
  */
 pint_status pint_prolong(pint_ctx* ctx, const double* coarse, int count, double* u_out);
 
+/*
+ * pint_prolong_noalloc -- the same result as pint_prolong, for callers that
+ * cannot allocate device memory (code running while a CUDA graph is being
+ * captured on its stream, host runtimes that own the allocator, loops that
+ * must not touch it).  The paper has no counterpart: this is a service entry
+ * point of the library.  The call allocates and frees nothing: its scratch
+ * (count * (d1 + d2 + n_raw) doubles) lives in a file-scope device array of
+ * 2^20 doubles (8 MB, held by every GPU that loads the library until exit).
+ *   coarse  DEVICE pointer, count x (d1+d2)
+ *   u_out   DEVICE pointer, count x (n_f+1)^2
+ * Errors: BAD_ARG (host pointers, or count * (d1 + d2 + n_raw) > 2^20),
+ * STATE, CUDA.  The first call with a given device current looks the
+ * array's device address up (cudaGetSymbolAddress) and caches it; make that
+ * first call before any stream capture.  All calls share the array, so calls
+ * whose work overlaps on the GPU (other streams, threads or contexts on the
+ * same device) race; each call writes every scratch element before reading it.
+ */
+pint_status pint_prolong_noalloc(pint_ctx* ctx, const double* coarse, int count, double* u_out);
+
 /* pint_apply_G / pint_apply_F -- one application of the coarse propagator
  * (one step of eqs. (2.4)-(2.5) with step Delta t) or of the WR fine
  * propagator (Section 4.2) to `count` states (count <= N), with source

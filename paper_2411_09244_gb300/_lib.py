@@ -70,6 +70,7 @@ SYMBOLS = {
                      C.c_void_p],
     "pint_get_reduced": [C.c_void_p, C.c_int, C.c_void_p, C.c_void_p],
     "pint_prolong": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
+    "pint_prolong_noalloc": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p],
     "pint_apply_G": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p],
     "pint_apply_F": [C.c_void_p, C.c_void_p, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int,
                      C.c_void_p, C.POINTER(C.c_int)],

@@ -13,6 +13,7 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <mutex>
 
 namespace pint {
 
@@ -442,4 +443,89 @@ void prolong_coeffs(Ctx* c, const double* u, const double* w, int count, double*
   dfree(c, a);
 }
 
+// ---------------------------------------------------------------------------
+// Allocation-free prolongation (pint_prolong_noalloc, declared in pint.h).
+//
+// Some callers cannot allocate device memory: code that runs while a CUDA
+// graph is being captured on its stream, allocators owned by a host runtime
+// that forbid the CUDA allocator, or real-time loops that must not touch the
+// allocator.  This entry point runs the same two kernels as pint_prolong but
+// keeps the scratch it needs (the split u / w rows and the raw-basis
+// coefficients) in the file-scope device array below, so the call itself
+// allocates and frees nothing.  Limits and hazards:
+//   * count * (d1 + d2 + n_raw) <= PINT_NOALLOC_SCRATCH_DOUBLES, else
+//     PINT_ERR_BAD_ARG (8 MB per GPU that loads the library, held until exit);
+//   * coarse and u_out must be device pointers (host staging would allocate);
+//   * every call shares the one array: calls whose kernels overlap on the GPU
+//     (two streams, two threads, two contexts on one device) race;
+//   * each call writes every scratch element it reads before reading it.
+// Host code cannot use the array's name as a device address; the device
+// address is fetched once per device with cudaGetSymbolAddress by the first
+// call made with that device current, which should therefore come before any
+// stream capture.
+// ---------------------------------------------------------------------------
+namespace {
+constexpr size_t PINT_NOALLOC_SCRATCH_DOUBLES = (size_t)1 << 20;
+static __device__ __align__(256) double g_noalloc_scratch[PINT_NOALLOC_SCRATCH_DOUBLES];
+
+std::mutex g_noalloc_mu;
+double* g_noalloc_ptr[256] = {nullptr};
+
+double* noalloc_scratch_for_current_device() {
+  int dev = 0;
+  PINT_CUDA(cudaGetDevice(&dev));
+  PINT_REQUIRE(dev >= 0 && dev < 256, PINT_ERR_BAD_ARG, "device ordinal out of range");
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      throw Fail{PINT_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e)};
+    }
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  return g_noalloc_ptr[dev];
+}
+}  // namespace
+
 }  // namespace pint
+
+extern "C" pint_status pint_prolong_noalloc(pint_ctx* ctx, const double* coarse, int count, double* u_out) {
+  using namespace pint;
+  Ctx* c = (Ctx*)ctx;
+  if (!c || !coarse || !u_out || count < 1) {
+    set_error("ctx, coarse, u_out and count >= 1 are required");
+    return PINT_ERR_BAD_ARG;
+  }
+  try {
+    PINT_REQUIRE(c->have_reduced, PINT_ERR_STATE, "pint_assemble_reduced first");
+    PINT_REQUIRE(is_device_ptr(coarse) && is_device_ptr(u_out), PINT_ERR_BAD_ARG,
+                 "pint_prolong_noalloc takes device pointers only");
+    const int d1 = c->d1, d2 = c->d2, n_raw = c->n_raw;
+    const size_t need = (size_t)count * (d1 + d2 + n_raw);
+    PINT_REQUIRE(need <= PINT_NOALLOC_SCRATCH_DOUBLES, PINT_ERR_BAD_ARG,
+                 "pint_prolong_noalloc: count * (d1 + d2 + n_raw) exceeds the 1048576-double scratch");
+    double* s = noalloc_scratch_for_current_device();
+    double* u = s;
+    double* w = u + (size_t)count * d1;
+    double* a = w + (size_t)count * d2;
+    PINT_CUDA(cudaMemcpy2DAsync(u, (size_t)d1 * 8, coarse, (size_t)(d1 + d2) * 8, (size_t)d1 * 8, count,
+                                cudaMemcpyDeviceToDevice, c->stream));
+    PINT_CUDA(cudaMemcpy2DAsync(w, (size_t)d2 * 8, coarse + d1, (size_t)(d1 + d2) * 8, (size_t)d2 * 8, count,
+                                cudaMemcpyDeviceToDevice, c->stream));
+    SplitDev sd = split_dev(c);
+    k_from_reduced<<<count, 256, 0, c->stream>>>(u, w, count, n_raw, sd.kind, c->has_bar ? 1.0 / c->L : 0.0,
+                                                 c->coef, sd.h1, d1, sd.h2m, (int)c->h2m.size(), c->has_bar, a);
+    PINT_LAUNCH_CHECK();
+    long long tot = (long long)c->nn * count;
+    k_prolong<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(
+        (const GWin*)c->d_windesc, c->n_f, c->nc, c->bs, c->ell, c->psi, a, count, u_out);
+    PINT_LAUNCH_CHECK();
+    PINT_CUDA(cudaStreamSynchronize(c->stream));
+    return PINT_OK;
+  } catch (const Fail& e) {
+    set_error(e.msg);
+    return e.code;
+  }
+}
