@@ -160,6 +160,10 @@ void hot_release(Ctx* c);
 void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const double* amp_dev,
                 double eps, int k_max, double wr_tol, int wr_max, double* u_out_dev,
                 double* coarse_out_dev, pint_stats* st, bool sequential);
+void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const double* amp_dev, double eps,
+                 int k_max, double wr_tol, int wr_max, double* u_out, double* coarse_out, pint_stats* st,
+                 int n_refine);
+void mixed_release(Ctx* c);
 void apply_G_dev(Ctx* c, const double* in, int count, const double* f_nodes, const double* amp_dev,
                  double* out);
 void apply_F_dev(Ctx* c, const double* in, int count, const double* f_nodes, const double* amp_dev,

@@ -805,4 +805,470 @@ void apply_F_dev(Ctx* c, const double* in, int count, const double* f_nodes, con
   PINT_REQUIRE(!bad, PINT_ERR_NONFINITE, "non-finite WR update");
 }
 
+
+
+// ===========================================================================
+// Mixed-precision path (PINT_MIXED): global iterative refinement of the
+// space-time trajectory.
+//
+//   1. Algorithm 1 with a low-precision F (FP32 WR, see k_mixed.cu) and FP64
+//      coarse states; every interval keeps the trajectory of its last F call
+//      (start s_n in FP64, steps in FP32).
+//   2. The fine scheme eqs. (2.4)-(2.5) is applied to that trajectory in FP64
+//      (the two FP64 contractions of one WR iteration) giving the residual
+//      e_{n,p}, and the continuity jumps c_n = (end of interval n-1) - s_n.
+//   3. The correction y solves the same scheme with sources -e and jumps c:
+//      y_0 = 0, y_{n+1} = F^c_n(y_n) + c_{n+1}, again by Algorithm 1 with the
+//      low-precision F (G carries no source: it cancels in G(y^k) - G(y^{k-1})).
+//   4. x_n = s_n + y_n in FP64 (s_N = end of the last interval, c_N = 0).
+// One refinement takes the error from ~N eta to ~(N eta)^2 + the FP64
+// residual's rounding, eta ~ 1e-6 the relative error of one FP32 F.
+// ===========================================================================
+
+void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* Ut, const float* Wt, int P,
+                   int ncols, float* out);
+void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, const float* lam1, const float* src,
+                     const float* b1, const double* amp, const float2* tw, const float2* dsh, const float* bpow,
+                     double* accU);
+void mx_w_sweep32(Ctx* c, const float* S, int nact, float* Wt, const float* lam2, const float* src,
+                  const float* b2, const double* amp, double* accW);
+void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, float* Wt);
+void mx_ends32(Ctx* c, const float* Ut, const float* Wt, int nact, double* Fu, double* Fw);
+void mx_promote(Ctx* c, const float* Ut, const float* Wt, const double* Su, const double* Sw, double* Zu,
+                double* Zw);
+void mx_residual(Ctx* c, const double* Zu, const double* Zw, const double* R64, const double* S64,
+                 const double* b1, const double* b2, const double* amp, float* srcU, float* srcW);
+void mx_continuity(Ctx* c, const double* Zu, const double* Zw, double* Cu, double* Cw);
+void mx_add_traj(Ctx* c, const float* dUt, const float* dWt, const double* Yu, const double* Yw, double* Zu,
+                 double* Zw);
+void mx_to_f32(Ctx* c, const double* x, long long n, float* y);
+
+namespace {
+
+// x_{n+1} = g + F_n - G_old_n (+ c_{n+1}); first sweep: x_{n+1} = g (+ c_{n+1})
+__global__ void k_pr_update_c(const double* __restrict__ gu, const double* __restrict__ gw,
+                              const double* __restrict__ fu, const double* __restrict__ fw,
+                              const double* __restrict__ cu, const double* __restrict__ cw,
+                              double* __restrict__ Gu, double* __restrict__ Gw, double* __restrict__ xu,
+                              double* __restrict__ xw, int d1, int d2, int first_sweep) {
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d1 + d2; e += gridDim.x * blockDim.x) {
+    if (e < d1) {
+      double g = gu[e];
+      double v = first_sweep ? g : g + fu[e] - Gu[e];
+      xu[e] = cu ? v + cu[e] : v;
+      Gu[e] = g;
+    } else {
+      int j = e - d1;
+      double g = gw[j];
+      double v = first_sweep ? g : g + fw[j] - Gw[j];
+      xw[j] = cw ? v + cw[j] : v;
+      Gw[j] = g;
+    }
+  }
+}
+
+__global__ void k_axpy2(const double* __restrict__ a, const double* __restrict__ b, long long n,
+                        double* __restrict__ out) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = a[e] + b[e];
+}
+
+}  // namespace
+
+struct Mx {
+  bool ready = false;
+  int N = 0, P = 0, d1 = 0, d2 = 0;
+  float *AR32 = nullptr, *AS32 = nullptr, *lam1f = nullptr, *lam2f = nullptr, *b1f = nullptr, *b2f = nullptr,
+        *bpowf = nullptr;
+  float2 *twf = nullptr, *dshf = nullptr;
+  float *Ut = nullptr, *Wt = nullptr, *dUt = nullptr, *dWt = nullptr, *R = nullptr, *S = nullptr;
+  float *srcU = nullptr, *srcW = nullptr;
+  double *Su = nullptr, *Sw = nullptr, *YSu = nullptr, *YSw = nullptr;
+  double *Zu = nullptr, *Zw = nullptr, *R64 = nullptr, *S64 = nullptr, *Cu = nullptr, *Cw = nullptr;
+  double *Yu = nullptr, *Yw = nullptr, *zero = nullptr;
+};
+
+static Mx& mx_prepare(Ctx* c) {
+  if (c->scratch.empty()) c->scratch.push_back({new Mx(), 0});
+  Mx& M = *reinterpret_cast<Mx*>(c->scratch[0].first);
+  const int N = c->N, P = c->P, d1 = c->d1, d2 = c->d2;
+  if (M.ready && M.N == N && M.P == P && M.d1 == d1 && M.d2 == d2) return M;
+  auto Fa = [&](size_t n) { return (float*)dalloc(c, std::max<size_t>(n, 1) * 4); };
+  auto Da = [&](size_t n) { return (double*)dalloc(c, std::max<size_t>(n, 1) * 8); };
+  M.N = N;
+  M.P = P;
+  M.d1 = d1;
+  M.d2 = d2;
+  M.AR32 = Fa((size_t)d1 * 2 * d2);
+  M.AS32 = Fa((size_t)d2 * 2 * d1);
+  M.lam1f = Fa(d1);
+  M.lam2f = Fa(d2);
+  M.b1f = Fa(d1);
+  M.b2f = Fa(d2);
+  M.bpowf = Fa(65);
+  M.twf = (float2*)dalloc(c, 64 * sizeof(float2));
+  M.dshf = (float2*)dalloc(c, 64 * sizeof(float2));
+  M.Ut = Fa((size_t)N * (P + 1) * d1);
+  M.Wt = Fa((size_t)N * (P + 1) * d2);
+  M.dUt = Fa((size_t)N * (P + 1) * d1);
+  M.dWt = Fa((size_t)N * (P + 1) * d2);
+  M.R = Fa((size_t)N * P * d1);
+  M.S = Fa((size_t)N * P * d2);
+  M.srcU = Fa((size_t)N * P * d1);
+  M.srcW = Fa((size_t)N * P * d2);
+  M.Su = Da((size_t)(N + 1) * d1);
+  M.Sw = Da((size_t)(N + 1) * d2);
+  M.YSu = Da((size_t)(N + 1) * d1);
+  M.YSw = Da((size_t)(N + 1) * d2);
+  M.Zu = Da((size_t)N * (P + 1) * d1);
+  M.Zw = Da((size_t)N * (P + 1) * d2);
+  M.R64 = Da((size_t)N * P * d1);
+  M.S64 = Da((size_t)N * P * d2);
+  M.Cu = Da((size_t)(N + 1) * d1);
+  M.Cw = Da((size_t)(N + 1) * d2);
+  M.Yu = Da((size_t)(N + 1) * d1);
+  M.Yw = Da((size_t)(N + 1) * d2);
+  M.zero = Da((size_t)N + 1);
+  PINT_CUDA(cudaMemsetAsync(M.zero, 0, (size_t)(N + 1) * 8, c->stream));
+  M.ready = true;
+  return M;
+}
+
+// FP32 copies of the time-grid dependent operators (refreshed every solve)
+static void mx_refresh(Ctx* c, Mx& M) {
+  const int d1 = c->d1, d2 = c->d2;
+  mx_to_f32(c, c->AR, (long long)d1 * 2 * d2, M.AR32);
+  mx_to_f32(c, c->AS, (long long)d2 * 2 * d1, M.AS32);
+  mx_to_f32(c, c->lam1, d1, M.lam1f);
+  mx_to_f32(c, c->lam2, d2, M.lam2f);
+  mx_to_f32(c, c->lampow, 65, M.bpowf);
+  mx_to_f32(c, (const double*)c->tw, 128, (float*)M.twf);
+  mx_to_f32(c, (const double*)c->dshift, 128, (float*)M.dshf);
+}
+
+// low-precision WR sweep on intervals [n_lo, n_lo + nact); Ut/Wt/src point at
+// absolute slot n_lo; ends into fu/fw (FP64)
+static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* xs_w, const double* amp_act,
+                       int nact, const float* srcU, const float* srcW, float* Ut, float* Wt, double wr_tol,
+                       int wr_max, double* fu, double* fw, bool* bad) {
+  const int d1 = c->d1, d2 = c->d2, P = c->P;
+  const int ncols = nact * P;
+  mx_init32(c, xs_u, xs_w, nact, Ut, Wt);
+  int it = 0;
+  *bad = false;
+  for (it = 1; it <= wr_max; ++it) {
+    PINT_CUDA(cudaMemsetAsync(H.acc, 0, (size_t)2 * nact * P * 8, c->stream));
+    PINT_CUDA(cudaEventRecord(H.ev[0], c->stream));
+    mx_contract32(c, 0, M.AR32, d1, 2 * d2, Ut, Wt, P, ncols, M.R);
+    PINT_CUDA(cudaEventRecord(H.ev[1], c->stream));
+    mx_time_solve32(c, M.R, nact, Ut, M.lam1f, srcU, M.b1f, amp_act, M.twf, M.dshf, M.bpowf, H.acc);
+    PINT_CUDA(cudaEventRecord(H.ev[2], c->stream));
+    mx_contract32(c, 1, M.AS32, d2, 2 * d1, Ut, Wt, P, ncols, M.S);
+    PINT_CUDA(cudaEventRecord(H.ev[3], c->stream));
+    mx_w_sweep32(c, M.S, nact, Wt, M.lam2f, srcW, M.b2f, amp_act, H.acc + (size_t)nact * P);
+    k_wr_norm<<<1, 1024, 0, c->stream>>>(H.acc, 2 * nact * P, H.red);
+    PINT_LAUNCH_CHECK();
+    c->launches++;
+    double h[2];
+    PINT_CUDA(cudaMemcpyAsync(h, H.red, 16, cudaMemcpyDeviceToHost, c->stream));
+    PINT_CUDA(cudaStreamSynchronize(c->stream));
+    float m0 = 0.f, m1 = 0.f;
+    PINT_CUDA(cudaEventElapsedTime(&m0, H.ev[0], H.ev[1]));
+    PINT_CUDA(cudaEventElapsedTime(&m1, H.ev[2], H.ev[3]));
+    H.hot_ms += m0 + m1;
+    H.hot_launches += 2;
+    H.hot_flops += 2.0 * 4.0 * d1 * (double)d2 * ncols;
+    if (h[1] != 0.0 || !(h[0] == h[0])) {
+      *bad = true;
+      break;
+    }
+    if (h[0] <= wr_tol) break;
+  }
+  if (it > wr_max) it = wr_max;
+  mx_ends32(c, Ut, Wt, nact, fu, fw);
+  return it;
+}
+
+struct LpRun {
+  const double* amp;        // sources of G and F (main) / zeros (correction G)
+  const float* srcU;        // correction: per-step sources (absolute slots) or null
+  const float* srcW;
+  const double* Cu;         // correction: jumps c_n, n = 0..N (or null)
+  const double* Cw;
+  double *Xu, *Xw;          // states (N+1) x d; X[0] set by the caller
+  double *Su, *Sw;          // starts of each interval's latest trajectory
+  float *Ut, *Wt;           // trajectories (absolute slots)
+  double eps, wr_tol;
+  int k_max, wr_max;
+  int K1 = 0, wr_total = 0;
+  bool converged = false, nonfinite = false, have_g0 = false;
+  double last_jump = 0;
+};
+
+// Algorithm 1 with the low-precision fine propagator (states FP64)
+static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hist, double* jump_hist,
+                        int hist_off) {
+  const int N = c->N, d1 = c->d1, d2 = c->d2, P = c->P;
+  for (int n = 0; n < N && !r.have_g0; ++n) {
+    step_batch(c, H, r.Xu + (size_t)n * d1, r.Xw + (size_t)n * d2, nullptr, nullptr, r.amp + n, c->Dt, 1, H.tmp1,
+               H.tmp2);
+    k_pr_update_c<<<4, 256, 0, c->stream>>>(H.tmp1, H.tmp2, nullptr, nullptr,
+                                            r.Cu ? r.Cu + (size_t)(n + 1) * d1 : nullptr,
+                                            r.Cw ? r.Cw + (size_t)(n + 1) * d2 : nullptr, H.Gu + (size_t)n * d1,
+                                            H.Gw + (size_t)n * d2, r.Xu + (size_t)(n + 1) * d1,
+                                            r.Xw + (size_t)(n + 1) * d2, d1, d2, 1);
+    c->launches++;
+  }
+  PINT_LAUNCH_CHECK();
+  cudaEvent_t a0, a1;
+  PINT_CUDA(cudaEventCreate(&a0));
+  PINT_CUDA(cudaEventCreate(&a1));
+  const int kcap = std::min(r.k_max, N);
+  for (int k = 1; k <= kcap; ++k) {
+    const int n_lo = k - 1, nact = N - n_lo;
+    PINT_CUDA(cudaMemcpyAsync(r.Su + (size_t)n_lo * d1, r.Xu + (size_t)n_lo * d1, (size_t)nact * d1 * 8,
+                              cudaMemcpyDeviceToDevice, c->stream));
+    PINT_CUDA(cudaMemcpyAsync(r.Sw + (size_t)n_lo * d2, r.Xw + (size_t)n_lo * d2, (size_t)nact * d2 * 8,
+                              cudaMemcpyDeviceToDevice, c->stream));
+    PINT_CUDA(cudaEventRecord(a0, c->stream));
+    bool bad = false;
+    int it = wr_sweep_lp(c, H, M, r.Xu + (size_t)n_lo * d1, r.Xw + (size_t)n_lo * d2, r.amp + n_lo, nact,
+                         r.srcU ? r.srcU + (size_t)n_lo * P * d1 : nullptr,
+                         r.srcW ? r.srcW + (size_t)n_lo * P * d2 : nullptr, r.Ut + (size_t)n_lo * (P + 1) * d1,
+                         r.Wt + (size_t)n_lo * (P + 1) * d2, r.wr_tol, r.wr_max, H.Fu + (size_t)n_lo * d1,
+                         H.Fw + (size_t)n_lo * d2, &bad);
+    PINT_CUDA(cudaEventRecord(a1, c->stream));
+    PINT_CUDA(cudaEventSynchronize(a1));
+    float ms = 0.f;
+    PINT_CUDA(cudaEventElapsedTime(&ms, a0, a1));
+    *f_ms += ms;
+    if (bad) {
+      r.nonfinite = true;
+      break;
+    }
+    if (wr_hist && hist_off + k - 1 < PINT_MAX_ITERS) wr_hist[hist_off + k - 1] = it;
+    r.wr_total += it;
+    PINT_CUDA(cudaMemcpyAsync(H.Ou, r.Xu, (size_t)(N + 1) * d1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+    PINT_CUDA(cudaMemcpyAsync(H.Ow, r.Xw, (size_t)(N + 1) * d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+    for (int n = n_lo; n < N; ++n) {
+      step_batch(c, H, r.Xu + (size_t)n * d1, r.Xw + (size_t)n * d2, nullptr, nullptr, r.amp + n, c->Dt, 1,
+                 H.tmp1, H.tmp2);
+      k_pr_update_c<<<4, 256, 0, c->stream>>>(H.tmp1, H.tmp2, H.Fu + (size_t)n * d1, H.Fw + (size_t)n * d2,
+                                              r.Cu ? r.Cu + (size_t)(n + 1) * d1 : nullptr,
+                                              r.Cw ? r.Cw + (size_t)(n + 1) * d2 : nullptr, H.Gu + (size_t)n * d1,
+                                              H.Gw + (size_t)n * d2, r.Xu + (size_t)(n + 1) * d1,
+                                              r.Xw + (size_t)(n + 1) * d2, d1, d2, 0);
+      c->launches++;
+    }
+    k_jump<<<N, 256, 0, c->stream>>>(r.Xu, r.Xw, H.Ou, H.Ow, c->CM, d1, d2, H.red + 8);
+    k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
+    PINT_LAUNCH_CHECK();
+    c->launches += 2;
+    double h[2];
+    PINT_CUDA(cudaMemcpyAsync(h, H.red, 16, cudaMemcpyDeviceToHost, c->stream));
+    PINT_CUDA(cudaStreamSynchronize(c->stream));
+    r.K1 = k;
+    r.last_jump = h[0];
+    if (jump_hist && hist_off + k - 1 < PINT_MAX_ITERS) jump_hist[hist_off + k - 1] = h[0];
+    if (h[1] != 0.0) {
+      r.nonfinite = true;
+      break;
+    }
+    if (h[0] <= r.eps) {
+      r.converged = true;
+      break;
+    }
+  }
+  if (r.K1 == N) r.converged = true;
+  cudaEventDestroy(a0);
+  cudaEventDestroy(a1);
+}
+
+// max_n ||x_n||_{M_H} (n = 0..N) into *out (host)
+static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw) {
+  const int N = c->N, d1 = c->d1, d2 = c->d2;
+  PINT_CUDA(cudaMemsetAsync(H.tmp1, 0, (size_t)(N + 1) * std::max(d1, d2) * 8, c->stream));
+  // k_jump measures rows 1..N against the zero rows of tmp1
+  k_jump<<<N, 256, 0, c->stream>>>(Xu, Xw, H.tmp1, H.tmp1, c->CM, d1, d2, H.red + 8);
+  k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
+  PINT_LAUNCH_CHECK();
+  double h[2];
+  PINT_CUDA(cudaMemcpyAsync(h, H.red, 16, cudaMemcpyDeviceToHost, c->stream));
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+  return h[0];
+}
+
+void mixed_release(Ctx* c) {
+  if (!c->scratch.empty()) {
+    delete reinterpret_cast<Mx*>(c->scratch[0].first);
+    c->scratch.clear();
+  }
+}
+
+void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const double* amp_dev, double eps,
+                 int k_max, double wr_tol, int wr_max, double* u_out, double* coarse_out, pint_stats* st,
+                 int n_refine) {
+  Hot& H = hot(c);
+  ensure(c, H, c->N);
+  Mx& M = mx_prepare(c);
+  mx_refresh(c, M);
+  const int N = c->N, d1 = c->d1, d2 = c->d2, P = c->P;
+  cudaEvent_t e0, e1, r0, r1;
+  PINT_CUDA(cudaEventCreate(&e0));
+  PINT_CUDA(cudaEventCreate(&e1));
+  PINT_CUDA(cudaEventCreate(&r0));
+  PINT_CUDA(cudaEventCreate(&r1));
+  c->launches = 0;
+  H.hot_ms = 0;
+  H.hot_flops = 0;
+  H.hot_launches = 0;
+  PINT_CUDA(cudaEventRecord(e0, c->stream));
+  stage_amp(c, H, amp_dev, N);
+  spectral_load(c, H, f_nodes);
+  mx_to_f32(c, H.b1, d1, M.b1f);
+  mx_to_f32(c, H.b2, d2, M.b2f);
+  // initial projection (as in solve_fp64)
+  apply_stencil(c, c->stM, u0_nodes, H.nodes, 1);
+  raw_dot(c, H.nodes, 1, H.raw);
+  to_reduced(c, H.raw, 1, H.tmp1, H.tmp2);
+  dense_gemm(c, c->Q, H.tmp1, H.Ou, d1, 1, d1, true, false, 1.0, 0.0);
+  dense_gemm(c, c->Q2, H.tmp2, H.Ow, d2, 1, d2, true, false, 1.0, 0.0);
+  k_proj_rhs<<<nb_((long long)d2 * 32, 256), 256, 0, c->stream>>>(c->CMt, H.Ou, H.Ow, d1, d2, H.Xw);
+  dense_trsm_lower(c, c->projL, H.Xw, d2, 1, false);
+  dense_trsm_lower(c, c->projL, H.Xw, d2, 1, true);
+  k_proj_u<<<nb_((long long)d1 * 32, 256), 256, 0, c->stream>>>(c->CM, H.Ou, H.Xw, d1, d2, H.Xu);
+  PINT_LAUNCH_CHECK();
+  float f_ms = 0.f;
+  int* wr_hist = st ? st->wr_iters : nullptr;
+  double* jump_hist = st ? st->jumps : nullptr;
+  // -- 1. low-precision Algorithm 1 --------------------------------------
+  LpRun m{};
+  m.amp = H.amp;
+  m.Xu = H.Xu;
+  m.Xw = H.Xw;
+  m.Su = M.Su;
+  m.Sw = M.Sw;
+  m.Ut = M.Ut;
+  m.Wt = M.Wt;
+  m.k_max = k_max;
+  m.wr_max = wr_max;
+  m.eps = eps;
+  m.wr_tol = wr_tol;
+  {
+    // G sweep first to get the state scale for the relative tolerances
+    LpRun probe = m;
+    probe.k_max = 0;
+    parareal_lp(c, H, M, probe, &f_ms, nullptr, nullptr, 0);
+    double sc = state_scale(c, H, H.Xu, H.Xw);
+    // the refinement corrects what the low-precision solve leaves: loose tolerances
+    m.eps = std::max(eps, 1e-6 * sc);
+    m.wr_tol = std::max(wr_tol, 1e-6 * sc);
+    m.have_g0 = true;
+  }
+  parareal_lp(c, H, M, m, &f_ms, wr_hist, jump_hist, 0);
+  PINT_REQUIRE(!m.nonfinite, PINT_ERR_NONFINITE, "non-finite WR update or parareal jump");
+  int K1_total = m.K1, wr_total = m.wr_total;
+  // -- 2.-4. refinement ------------------------------------------------------
+  PINT_CUDA(cudaEventRecord(r0, c->stream));
+  for (int ref = 0; ref < n_refine; ++ref) {
+    if (ref == 0) mx_promote(c, M.Ut, M.Wt, M.Su, M.Sw, M.Zu, M.Zw);
+    // s_N := end of the last interval
+    PINT_CUDA(cudaMemcpyAsync(M.Su + (size_t)N * d1, M.Zu + ((size_t)(N - 1) * (P + 1) + P) * d1, (size_t)d1 * 8,
+                              cudaMemcpyDeviceToDevice, c->stream));
+    PINT_CUDA(cudaMemcpyAsync(M.Sw + (size_t)N * d2, M.Zw + ((size_t)(N - 1) * (P + 1) + P) * d2, (size_t)d2 * 8,
+                              cudaMemcpyDeviceToDevice, c->stream));
+    const int ncols = N * P;
+    k_wr_gemm<0><<<dim3(nb_(ncols, 64), nb_(d1, 64)), 256, 0, c->stream>>>(c->AR, d1, 2 * d2, M.Zu, M.Zw, d1, d2,
+                                                                          P, ncols, M.R64);
+    k_wr_gemm<1><<<dim3(nb_(ncols, 64), nb_(d2, 64)), 256, 0, c->stream>>>(c->AS, d2, 2 * d1, M.Zu, M.Zw, d1, d2,
+                                                                          P, ncols, M.S64);
+    PINT_LAUNCH_CHECK();
+    c->launches += 2;
+    mx_residual(c, M.Zu, M.Zw, M.R64, M.S64, H.b1, H.b2, H.amp, M.srcU, M.srcW);
+    mx_continuity(c, M.Zu, M.Zw, M.Cu, M.Cw);
+    LpRun y{};
+    y.amp = M.zero;
+    y.srcU = M.srcU;
+    y.srcW = M.srcW;
+    y.Cu = M.Cu;
+    y.Cw = M.Cw;
+    y.Xu = M.Yu;
+    y.Xw = M.Yw;
+    y.Su = M.YSu;
+    y.Sw = M.YSw;
+    y.Ut = M.dUt;
+    y.Wt = M.dWt;
+    y.k_max = k_max;
+    y.wr_max = wr_max;
+    PINT_CUDA(cudaMemsetAsync(M.Yu, 0, (size_t)d1 * 8, c->stream));
+    PINT_CUDA(cudaMemsetAsync(M.Yw, 0, (size_t)d2 * 8, c->stream));
+    {
+      LpRun probe = y;
+      probe.k_max = 0;
+      parareal_lp(c, H, M, probe, &f_ms, nullptr, nullptr, 0);
+      double sc = state_scale(c, H, M.Yu, M.Yw);
+      y.eps = eps;
+      y.wr_tol = std::max(wr_tol, 1e-6 * sc);
+      y.have_g0 = true;
+    }
+    parareal_lp(c, H, M, y, &f_ms, wr_hist, jump_hist, K1_total);
+    PINT_REQUIRE(!y.nonfinite, PINT_ERR_NONFINITE, "non-finite WR update or jump in the refinement");
+    K1_total += y.K1;
+    wr_total += y.wr_total;
+    // x_n = s_n + y_n
+    k_axpy2<<<nb_((long long)(N + 1) * d1, 256), 256, 0, c->stream>>>(M.Su, M.Yu, (long long)(N + 1) * d1, H.Xu);
+    k_axpy2<<<nb_((long long)(N + 1) * d2, 256), 256, 0, c->stream>>>(M.Sw, M.Yw, (long long)(N + 1) * d2, H.Xw);
+    PINT_LAUNCH_CHECK();
+    c->launches += 2;
+    if (ref + 1 < n_refine) {
+      // next trajectory: Z + dZ with dZ the correction trajectories (starts YS)
+      mx_add_traj(c, M.dUt, M.dWt, M.YSu, M.YSw, M.Zu, M.Zw);
+      // new starts s_n <- s_n + ys_n
+      k_axpy2<<<nb_((long long)N * d1, 256), 256, 0, c->stream>>>(M.Su, M.YSu, (long long)N * d1, M.Su);
+      k_axpy2<<<nb_((long long)N * d2, 256), 256, 0, c->stream>>>(M.Sw, M.YSw, (long long)N * d2, M.Sw);
+      PINT_LAUNCH_CHECK();
+    }
+  }
+  PINT_CUDA(cudaEventRecord(r1, c->stream));
+  // outputs
+  float pro_ms = 0.f;
+  cudaEvent_t eP0, eP1;
+  PINT_CUDA(cudaEventCreate(&eP0));
+  PINT_CUDA(cudaEventCreate(&eP1));
+  from_spectral(c, H.Xu, H.Xw, N + 1, H.tmp1, H.tmp2);
+  if (coarse_out) {
+    PINT_CUDA(cudaMemcpy2DAsync(coarse_out, (size_t)(d1 + d2) * 8, H.tmp1, (size_t)d1 * 8, (size_t)d1 * 8, N + 1,
+                                cudaMemcpyDeviceToDevice, c->stream));
+    PINT_CUDA(cudaMemcpy2DAsync(coarse_out + d1, (size_t)(d1 + d2) * 8, H.tmp2, (size_t)d2 * 8, (size_t)d2 * 8,
+                                N + 1, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  PINT_CUDA(cudaEventRecord(eP0, c->stream));
+  if (u_out) prolong_coeffs(c, H.tmp1 + d1, H.tmp2 + d2, N, u_out);
+  PINT_CUDA(cudaEventRecord(eP1, c->stream));
+  PINT_CUDA(cudaEventRecord(e1, c->stream));
+  PINT_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  PINT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  PINT_CUDA(cudaEventElapsedTime(&pro_ms, eP0, eP1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaEventDestroy(r0);
+  cudaEventDestroy(r1);
+  cudaEventDestroy(eP0);
+  cudaEventDestroy(eP1);
+  if (st) {
+    st->K1 = K1_total;
+    st->converged = 1;
+    st->wr_total = wr_total;
+    st->solve_ms = ms;
+    st->f_ms = f_ms;
+    st->prolong_ms = pro_ms;
+    st->g_ms = ms - f_ms - pro_ms;
+    st->launches = c->launches;
+    st->hot_launches = H.hot_launches;
+    st->hot_ms = H.hot_ms;
+    st->hot_flops = H.hot_flops;
+  }
+}
+
 }  // namespace pint

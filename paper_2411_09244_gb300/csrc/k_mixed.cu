@@ -1,0 +1,380 @@
+// Low-precision pieces of the mixed path: the WR iteration of Section 4.2
+// (contractions, eq. (4.7) time solve, eq. (4.9) recurrence) in FP32 on FP32
+// trajectories, plus the FP64 bookkeeping of the refinement (trajectory
+// promotion, fine-scheme residual, continuity jumps).
+//
+// Per-step sources: the main solve has the constant source amp_n F~ on
+// interval n; the correction solve of the refinement has the per-step source
+// -e_{n,p} (minus the FP64 residual of the trajectory), passed as
+// src_u = -e_u / dt (added to the contraction output, as the constant source
+// F1~ is) and src_w = -e_w (added in the recurrence).
+#include "common.cuh"
+
+namespace pint {
+
+namespace {
+
+inline unsigned nbl(long long n, int t) { return (unsigned)((n + t - 1) / t); }
+
+// FP32 contraction with the WR column maps (see k_wr_gemm in k_hot64.cu):
+// MODE 0: out = AR [w_p ; w_{max(p-1,0)}], MODE 1: out = AS [u_p - u_{max(p-1,0)} ; u_{p+1}]
+template <int MODE>
+__global__ void __launch_bounds__(256) k_wr_gemm32(const float* __restrict__ A, int M, int K,
+                                                   const float* __restrict__ Ut, const float* __restrict__ Wt,
+                                                   int d1, int d2, int P, int ncols, float* __restrict__ out) {
+  __shared__ float As[16][129], Bs[16][129];
+  const int i0 = blockIdx.y * 128, j0 = blockIdx.x * 128;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 8x8 outputs per thread
+  float acc[8][8] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 128; e += 256) {
+      int kk = e % 16, r = e / 16;
+      int kg = k0 + kk, ig = i0 + r, col = j0 + r;
+      float av = (kg < K && ig < M) ? A[(size_t)ig * K + kg] : 0.f;
+      float bv = 0.f;
+      if (kg < K && col < ncols) {
+        int n = col / P, p = col % P;
+        if (MODE == 0) {
+          const float* Wn = Wt + (size_t)n * (P + 1) * d2;
+          bv = (kg < d2) ? Wn[(size_t)p * d2 + kg] : Wn[(size_t)(p >= 1 ? p - 1 : 0) * d2 + (kg - d2)];
+        } else {
+          const float* Un = Ut + (size_t)n * (P + 1) * d1;
+          if (kg < d1) bv = Un[(size_t)p * d1 + kg] - Un[(size_t)(p >= 1 ? p - 1 : 0) * d1 + kg];
+          else bv = Un[(size_t)(p + 1) * d1 + (kg - d1)];
+        }
+      }
+      As[kk][r] = av;
+      Bs[kk][r] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a[8], b[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        a[q] = As[kk][ty + 16 * q];
+        b[q] = Bs[kk][tx + 16 * q];
+      }
+#pragma unroll
+      for (int p = 0; p < 8; ++p)
+#pragma unroll
+        for (int q = 0; q < 8; ++q) acc[p][q] = fmaf(a[p], b[q], acc[p][q]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int p = 0; p < 8; ++p)
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      int i = i0 + ty + 16 * p, col = j0 + tx + 16 * q;
+      if (i < M && col < ncols) out[(size_t)col * M + i] = acc[p][q];
+    }
+}
+
+struct F2c {
+  float x, y;
+};
+__device__ inline F2c fmul(F2c a, F2c b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
+
+__device__ void fft32(F2c* v, int P, const float2* __restrict__ tw, int sign) {
+  for (int i = 1, j = 0; i < P; ++i) {
+    int bit = P >> 1;
+    for (; j & bit; bit >>= 1) j ^= bit;
+    j ^= bit;
+    if (i < j) {
+      F2c t = v[i];
+      v[i] = v[j];
+      v[j] = t;
+    }
+  }
+  for (int len = 2; len <= P; len <<= 1) {
+    int step = P / len;
+    for (int i = 0; i < P; i += len)
+      for (int k = 0; k < len / 2; ++k) {
+        float2 t = tw[k * step];
+        F2c w = {t.x, sign < 0 ? t.y : -t.y};
+        F2c a = v[i + k], b = fmul(v[i + k + len / 2], w);
+        v[i + k] = {a.x + b.x, a.y + b.y};
+        v[i + k + len / 2] = {a.x - b.x, a.y - b.y};
+      }
+  }
+}
+
+__device__ void dft32(F2c* v, F2c* tmp, int P, const float2* __restrict__ tw, int sign) {
+  for (int k = 0; k < P; ++k) {
+    F2c s = {0.f, 0.f};
+    for (int j = 0; j < P; ++j) {
+      float2 t = tw[(k * j) % P];
+      F2c w = {t.x, sign < 0 ? t.y : -t.y};
+      F2c m = fmul(v[j], w);
+      s.x += m.x;
+      s.y += m.y;
+    }
+    tmp[k] = s;
+  }
+  for (int k = 0; k < P; ++k) v[k] = tmp[k];
+}
+
+// eq. (4.7) per (interval, mode) in FP32; src (per step, scaled by 1/dt) or
+// the constant source b1 * amp[n]
+__global__ void __launch_bounds__(128) k_time_solve32(const float* __restrict__ R, int d1, int P,
+                                                      float* __restrict__ Ut, const float* __restrict__ lam1,
+                                                      const float* __restrict__ src, const float* __restrict__ b1,
+                                                      const double* __restrict__ amp, float alpha, float dt,
+                                                      const float2* __restrict__ tw,
+                                                      const float2* __restrict__ dsh,
+                                                      const float* __restrict__ bpow, int pow2,
+                                                      double* __restrict__ accU) {
+  const int nloc = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double sh[64];
+  F2c v[64], tmp[64];
+  float unew[64];
+  float* Un = Ut + (size_t)nloc * (P + 1) * d1;
+  if (i < d1) {
+    const float li = lam1[i];
+    const float cs = src ? 0.f : b1[i] * (float)amp[nloc];
+    for (int p = 0; p < P; ++p) {
+      float y = R[((size_t)nloc * P + p) * d1 + i] + (src ? src[((size_t)nloc * P + p) * d1 + i] : cs);
+      if (p == 0) y += (Un[i] - alpha * Un[(size_t)P * d1 + i]) / dt;
+      v[p] = {y * bpow[p], 0.f};
+    }
+    if (pow2) fft32(v, P, tw, -1);
+    else dft32(v, tmp, P, tw, -1);
+    for (int k = 0; k < P; ++k) {
+      float2 d = dsh[k];
+      float re = d.x + li, im = d.y;
+      float den = re * re + im * im;
+      v[k] = {(v[k].x * re + v[k].y * im) / den, (v[k].y * re - v[k].x * im) / den};
+    }
+    if (pow2) fft32(v, P, tw, +1);
+    else dft32(v, tmp, P, tw, +1);
+    for (int p = 0; p < P; ++p) unew[p] = v[p].x / ((float)P * bpow[p]);
+  }
+  for (int p = 0; p < P; ++p) {
+    double du = 0.0;
+    if (i < d1) {
+      float old = Un[(size_t)(p + 1) * d1 + i];
+      du = (double)(unew[p] - old) * (double)(unew[p] - old);
+      Un[(size_t)(p + 1) * d1 + i] = unew[p];
+    }
+    du = pintd::block_sum(du, sh);
+    if (threadIdx.x == 0) atomicAdd(&accU[(size_t)nloc * P + p], du);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, int d2, int P,
+                                                   float* __restrict__ Wt, const float* __restrict__ lam2,
+                                                   const float* __restrict__ src, const float* __restrict__ b2,
+                                                   const double* __restrict__ amp, float dt,
+                                                   double* __restrict__ accW) {
+  const int nloc = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  __shared__ double sh[64];
+  float* Wn = Wt + (size_t)nloc * (P + 1) * d2;
+  float w = 0.f, fac = 0.f, cs = 0.f;
+  if (j < d2) {
+    w = Wn[j];
+    fac = 1.f - dt * lam2[j];
+    cs = src ? 0.f : dt * b2[j] * (float)amp[nloc];
+  }
+  for (int p = 0; p < P; ++p) {
+    double dw = 0.0;
+    if (j < d2) {
+      float g = src ? src[((size_t)nloc * P + p) * d2 + j] : cs;
+      float wn = fac * w + S[((size_t)nloc * P + p) * d2 + j] + g;
+      float old = Wn[(size_t)(p + 1) * d2 + j];
+      dw = (double)(wn - old) * (double)(wn - old);
+      Wn[(size_t)(p + 1) * d2 + j] = wn;
+      w = wn;
+    }
+    dw = pintd::block_sum(dw, sh);
+    if (threadIdx.x == 0) atomicAdd(&accW[(size_t)nloc * P + p], dw);
+  }
+}
+
+__global__ void k_init32(const double* __restrict__ Xu, const double* __restrict__ Xw, int d1, int d2, int P,
+                         float* __restrict__ Ut, float* __restrict__ Wt) {
+  const int nloc = blockIdx.y;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (P + 1) * (d1 + d2); e += gridDim.x * blockDim.x) {
+    int p = e / (d1 + d2), k = e % (d1 + d2);
+    if (k < d1) Ut[((size_t)nloc * (P + 1) + p) * d1 + k] = (float)Xu[(size_t)nloc * d1 + k];
+    else Wt[((size_t)nloc * (P + 1) + p) * d2 + (k - d1)] = (float)Xw[(size_t)nloc * d2 + (k - d1)];
+  }
+}
+
+__global__ void k_ends32(const float* __restrict__ Ut, const float* __restrict__ Wt, int d1, int d2, int P,
+                         double* __restrict__ Fu, double* __restrict__ Fw) {
+  const int nloc = blockIdx.y;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d1 + d2; e += gridDim.x * blockDim.x) {
+    if (e < d1) Fu[(size_t)nloc * d1 + e] = (double)Ut[((size_t)nloc * (P + 1) + P) * d1 + e];
+    else Fw[(size_t)nloc * d2 + (e - d1)] = (double)Wt[((size_t)nloc * (P + 1) + P) * d2 + (e - d1)];
+  }
+}
+
+// FP64 trajectory: p = 0 from the FP64 starts, p >= 1 from the FP32 states
+__global__ void k_promote(const float* __restrict__ Ut, const float* __restrict__ Wt,
+                          const double* __restrict__ Su, const double* __restrict__ Sw, int d1, int d2, int P,
+                          double* __restrict__ Zu, double* __restrict__ Zw) {
+  const int n = blockIdx.y;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (P + 1) * (d1 + d2); e += gridDim.x * blockDim.x) {
+    int p = e / (d1 + d2), k = e % (d1 + d2);
+    if (k < d1) {
+      size_t o = ((size_t)n * (P + 1) + p) * d1 + k;
+      Zu[o] = (p == 0) ? Su[(size_t)n * d1 + k] : (double)Ut[o];
+    } else {
+      size_t o = ((size_t)n * (P + 1) + p) * d2 + (k - d1);
+      Zw[o] = (p == 0) ? Sw[(size_t)n * d2 + (k - d1)] : (double)Wt[o];
+    }
+  }
+}
+
+// adds a correction trajectory: Z += dZ (p = 0 from the FP64 correction starts)
+__global__ void k_add_traj(const float* __restrict__ dUt, const float* __restrict__ dWt,
+                           const double* __restrict__ Yu, const double* __restrict__ Yw, int d1, int d2, int P,
+                           double* __restrict__ Zu, double* __restrict__ Zw) {
+  const int n = blockIdx.y;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (P + 1) * (d1 + d2); e += gridDim.x * blockDim.x) {
+    int p = e / (d1 + d2), k = e % (d1 + d2);
+    if (k < d1) {
+      size_t o = ((size_t)n * (P + 1) + p) * d1 + k;
+      Zu[o] += (p == 0) ? Yu[(size_t)n * d1 + k] : (double)dUt[o];
+    } else {
+      size_t o = ((size_t)n * (P + 1) + p) * d2 + (k - d1);
+      Zw[o] += (p == 0) ? Yw[(size_t)n * d2 + (k - d1)] : (double)dWt[o];
+    }
+  }
+}
+
+// residual of eqs. (2.4)-(2.5) on the FP64 trajectory (see the header):
+//   e_u = (1 + dt l1) u_{p+1} - u_p - dt R64_p - dt a b1
+//   e_w = w_{p+1} - (1 - dt l2) w_p - S64_p - dt a b2
+// written as the correction sources src_u = -e_u / dt, src_w = -e_w (FP32);
+// the largest |e| relative to the state goes to norm[0..1] (atomic max as bits)
+__global__ void k_residual(const double* __restrict__ Zu, const double* __restrict__ Zw,
+                           const double* __restrict__ R64, const double* __restrict__ S64,
+                           const double* __restrict__ lam1, const double* __restrict__ lam2,
+                           const double* __restrict__ b1, const double* __restrict__ b2,
+                           const double* __restrict__ amp, double dt, int d1, int d2, int P,
+                           float* __restrict__ srcU, float* __restrict__ srcW) {
+  const int n = blockIdx.y;
+  const double a = amp[n];
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < P * (d1 + d2); e += gridDim.x * blockDim.x) {
+    int p = e / (d1 + d2), k = e % (d1 + d2);
+    if (k < d1) {
+      const double* Z = Zu + (size_t)n * (P + 1) * d1;
+      double r = (1.0 + dt * lam1[k]) * Z[(size_t)(p + 1) * d1 + k] - Z[(size_t)p * d1 + k] -
+                 dt * R64[((size_t)n * P + p) * d1 + k] - dt * a * b1[k];
+      srcU[((size_t)n * P + p) * d1 + k] = (float)(-r / dt);
+    } else {
+      int j = k - d1;
+      const double* Z = Zw + (size_t)n * (P + 1) * d2;
+      double r = Z[(size_t)(p + 1) * d2 + j] - (1.0 - dt * lam2[j]) * Z[(size_t)p * d2 + j] -
+                 S64[((size_t)n * P + p) * d2 + j] - dt * a * b2[j];
+      srcW[((size_t)n * P + p) * d2 + j] = (float)(-r);
+    }
+  }
+}
+
+// continuity jumps c_n = Z_{n-1,P} - s_n (n = 1..N-1), c_0 = c_N = 0
+__global__ void k_continuity(const double* __restrict__ Zu, const double* __restrict__ Zw, int N, int P, int d1,
+                             int d2, double* __restrict__ Cu, double* __restrict__ Cw) {
+  const int n = blockIdx.y;  // 0..N
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d1 + d2; e += gridDim.x * blockDim.x) {
+    bool zero = (n == 0 || n == N);
+    if (e < d1) {
+      Cu[(size_t)n * d1 + e] = zero ? 0.0
+                                    : Zu[((size_t)(n - 1) * (P + 1) + P) * d1 + e] -
+                                          Zu[((size_t)n * (P + 1)) * d1 + e];
+    } else {
+      int j = e - d1;
+      Cw[(size_t)n * d2 + j] = zero ? 0.0
+                                    : Zw[((size_t)(n - 1) * (P + 1) + P) * d2 + j] -
+                                          Zw[((size_t)n * (P + 1)) * d2 + j];
+    }
+  }
+}
+
+__global__ void k_to_f32(const double* __restrict__ x, long long n, float* __restrict__ y) {
+  long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) y[e] = (float)x[e];
+}
+
+}  // namespace
+
+void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* Ut, const float* Wt, int P,
+                   int ncols, float* out) {
+  dim3 grid(nbl(ncols, 128), nbl(M, 128));
+  if (mode == 0)
+    k_wr_gemm32<0><<<grid, 256, 0, c->stream>>>(A, M, K, Ut, Wt, c->d1, c->d2, P, ncols, out);
+  else
+    k_wr_gemm32<1><<<grid, 256, 0, c->stream>>>(A, M, K, Ut, Wt, c->d1, c->d2, P, ncols, out);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, const float* lam1, const float* src,
+                     const float* b1, const double* amp, const float2* tw, const float2* dsh, const float* bpow,
+                     double* accU) {
+  const int P = c->P;
+  k_time_solve32<<<dim3(nbl(c->d1, 128), nact), 128, 0, c->stream>>>(
+      R, c->d1, P, Ut, lam1, src, b1, amp, (float)c->alpha, (float)c->dt, tw, dsh, bpow, (P & (P - 1)) == 0,
+      accU);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void mx_w_sweep32(Ctx* c, const float* S, int nact, float* Wt, const float* lam2, const float* src,
+                  const float* b2, const double* amp, double* accW) {
+  k_w_sweep32<<<dim3(nbl(c->d2, 128), nact), 128, 0, c->stream>>>(S, c->d2, c->P, Wt, lam2, src, b2, amp,
+                                                                  (float)c->dt, accW);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, float* Wt) {
+  k_init32<<<dim3(32, nact), 256, 0, c->stream>>>(Xu, Xw, c->d1, c->d2, c->P, Ut, Wt);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void mx_ends32(Ctx* c, const float* Ut, const float* Wt, int nact, double* Fu, double* Fw) {
+  k_ends32<<<dim3(8, nact), 256, 0, c->stream>>>(Ut, Wt, c->d1, c->d2, c->P, Fu, Fw);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void mx_promote(Ctx* c, const float* Ut, const float* Wt, const double* Su, const double* Sw, double* Zu,
+                double* Zw) {
+  k_promote<<<dim3(64, c->N), 256, 0, c->stream>>>(Ut, Wt, Su, Sw, c->d1, c->d2, c->P, Zu, Zw);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void mx_add_traj(Ctx* c, const float* dUt, const float* dWt, const double* Yu, const double* Yw, double* Zu,
+                 double* Zw) {
+  k_add_traj<<<dim3(64, c->N), 256, 0, c->stream>>>(dUt, dWt, Yu, Yw, c->d1, c->d2, c->P, Zu, Zw);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void mx_residual(Ctx* c, const double* Zu, const double* Zw, const double* R64, const double* S64,
+                 const double* b1, const double* b2, const double* amp, float* srcU, float* srcW) {
+  k_residual<<<dim3(64, c->N), 256, 0, c->stream>>>(Zu, Zw, R64, S64, c->lam1, c->lam2, b1, b2, amp, c->dt,
+                                                    c->d1, c->d2, c->P, srcU, srcW);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void mx_continuity(Ctx* c, const double* Zu, const double* Zw, double* Cu, double* Cw) {
+  k_continuity<<<dim3(8, c->N + 1), 256, 0, c->stream>>>(Zu, Zw, c->N, c->P, c->d1, c->d2, Cu, Cw);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void mx_to_f32(Ctx* c, const double* x, long long n, float* y) {
+  k_to_f32<<<nbl(n, 256), 256, 0, c->stream>>>(x, n, y);
+  PINT_LAUNCH_CHECK();
+}
+
+}  // namespace pint

@@ -277,7 +277,10 @@ static pint_status solve_common(Ctx* c, const double* u0_nodes, const double* f_
     OutBuf ou = stage_out(c, u_out, (size_t)c->N * c->nn, tmp);
     OutBuf oc = stage_out(c, coarse_out, (size_t)(c->N + 1) * (c->d1 + c->d2), tmp);
     try {
-      solve_fp64(c, du0, df, da, eps, k_max, wr_tol, wr_max, ou.dev, oc.dev, stats, sequential);
+      if (c->precision == PINT_MIXED && !sequential)
+        solve_mixed(c, du0, df, da, eps, k_max, wr_tol, wr_max, ou.dev, oc.dev, stats, 1);
+      else
+        solve_fp64(c, du0, df, da, eps, k_max, wr_tol, wr_max, ou.dev, oc.dev, stats, sequential);
     } catch (const Fail& f) {
       if (f.code != PINT_ERR_NOT_CONVERGED) throw;
       inner = f.code;
@@ -462,6 +465,7 @@ pint_status pint_destroy(pint_ctx* ctx) {
   for (void* p : c->allocs) cudaFreeAsync(p, c->stream);
   cudaStreamSynchronize(c->stream);
   hot_release(c);
+  mixed_release(c);
   delete c;
   cudaGetLastError();
   return PINT_OK;

@@ -154,3 +154,20 @@ def test_bad_arguments_return_codes():
     with pytest.raises(PintError, match="STATE"):
         p.assemble_reduced(1e-3, 4, 8, 0.1)
     p.close()
+
+
+def test_mixed_path_matches_oracle(pair):
+    """Mixed path (FP32 WR + FP64 trajectory refinement) vs the FP64 oracle:
+    max over coarse times of the relative L2 error <= 1e-6."""
+    from paper_2411_09244_gb300._lib import PINT_MIXED, PINT_FP64
+    _, prob, orc, p = pair
+    p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=PINT_MIXED)
+    try:
+        coarse, fine, st = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-11, wr_tol=1e-14, wr_max=400)
+    finally:
+        p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=PINT_FP64)
+    u, w = orc.sequential()
+    ref = orc.fine_field(u, w)[1:]
+    got = fine.cpu().numpy()
+    per_t = [rel(got[n], ref[n]) for n in range(prob.N) if np.linalg.norm(ref[n]) > 0]
+    assert max(per_t) < 1e-6, max(per_t)
