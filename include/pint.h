@@ -49,7 +49,13 @@ enum {
   PINT_ERR_TIMEOUT = -9        /* a bounded device wait ran out            */
 };
 
-enum { PINT_FP64 = 0, PINT_MIXED = 1 };
+/* precision of the fine propagator:
+ *   PINT_FP64      every step in FP64
+ *   PINT_MIXED     WR contractions on the tensor cores (TF32 hi/lo split,
+ *                  FP32 accumulation), time solve and recurrence in FP32,
+ *                  FP64 coarse states and FP64 trajectory refinement
+ *   PINT_MIXED_F32 the same with FP32 CUDA-core contractions (comparison) */
+enum { PINT_FP64 = 0, PINT_MIXED = 1, PINT_MIXED_F32 = 2 };
 
 /* flags for pint_assemble_reduced */
 enum { PINT_ALLOW_UNSTABLE = 1 };

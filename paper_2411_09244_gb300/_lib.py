@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(HERE, "libpint.so")
 PINT_OK = 0
 STATUS = {0: "OK", -1: "BAD_ARG", -2: "OOM", -3: "CUDA", -4: "UNSTABLE_DT", -5: "NOT_CONVERGED",
           -6: "NONFINITE", -7: "SINGULAR", -8: "STATE", -9: "TIMEOUT"}
-PINT_FP64, PINT_MIXED = 0, 1
+PINT_FP64, PINT_MIXED, PINT_MIXED_F32 = 0, 1, 2
 PINT_ALLOW_UNSTABLE = 1
 MAX_ITERS = 512
 

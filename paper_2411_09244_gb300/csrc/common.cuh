@@ -104,6 +104,7 @@ struct Ctx {
   double *CM = nullptr, *CA = nullptr;    // Q^T M12 Q2, Q^T A12 Q2 (d1 x d2)
   double *CMt = nullptr, *CAt = nullptr;  // transposes (d2 x d1)
   double* projL = nullptr;                // Cholesky of I - CM^T CM (d2 x d2)
+  double* projInv = nullptr;              // (I - CM^T CM)^-1
   double gamma = 0, lam22 = 0, dt_max = 0;
 
   // time grid

@@ -149,6 +149,46 @@ __global__ void __launch_bounds__(256) k_gemm64(const double* __restrict__ A, co
     }
 }
 
+// 32x32-tile variant (2x2 per thread) for grids that would not fill the GPU
+__global__ void __launch_bounds__(256) k_gemm64_s(const double* __restrict__ A, const double* __restrict__ B,
+                                                  double* __restrict__ C, int m, int n, int k, int ta, int tb,
+                                                  double alpha, double beta) {
+  __shared__ double As[16][33], Bs[16][33];
+  const int i0 = blockIdx.y * 32, j0 = blockIdx.x * 32;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  double acc[2][2] = {};
+  for (int k0 = 0; k0 < k; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * 32; e += 256) {
+      int kk = e / 32, r = e % 32;
+      int kg = k0 + kk, ig = i0 + r, jg = j0 + r;
+      double av = 0.0, bv = 0.0;
+      if (kg < k && ig < m) av = ta ? A[(size_t)kg * m + ig] : A[(size_t)ig * k + kg];
+      if (kg < k && jg < n) bv = tb ? B[(size_t)jg * k + kg] : B[(size_t)kg * n + jg];
+      As[kk][r] = av;
+      Bs[kk][r] = bv;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      double a0 = As[kk][ty * 2], a1 = As[kk][ty * 2 + 1], b0 = Bs[kk][tx * 2], b1 = Bs[kk][tx * 2 + 1];
+      acc[0][0] += a0 * b0;
+      acc[0][1] += a0 * b1;
+      acc[1][0] += a1 * b0;
+      acc[1][1] += a1 * b1;
+    }
+    __syncthreads();
+  }
+  for (int p = 0; p < 2; ++p)
+    for (int q = 0; q < 2; ++q) {
+      int i = i0 + ty * 2 + p, j = j0 + tx * 2 + q;
+      if (i < m && j < n) {
+        double v = alpha * acc[p][q];
+        if (beta != 0.0) v += beta * C[(size_t)i * n + j];
+        C[(size_t)i * n + j] = v;
+      }
+    }
+}
+
 __device__ inline void rot_params(double a, double b, double d, double& c, double& s) {
   if (b == 0.0) {
     c = 1.0;
@@ -293,8 +333,10 @@ void dense_trsm_lower(Ctx* c, const double* L, double* X, int n, int ncols, bool
 
 void dense_gemm(Ctx* c, const double* A, const double* B, double* C, int m, int n, int k, bool ta,
                 bool tb, double alpha, double beta) {
-  k_gemm64<<<dim3((n + 63) / 64, (m + 63) / 64), 256, 0, c->stream>>>(A, B, C, m, n, k, ta, tb, alpha,
-                                                                      beta);
+  if ((long long)((n + 63) / 64) * ((m + 63) / 64) >= 300)
+    k_gemm64<<<dim3((n + 63) / 64, (m + 63) / 64), 256, 0, c->stream>>>(A, B, C, m, n, k, ta, tb, alpha, beta);
+  else
+    k_gemm64_s<<<dim3((n + 31) / 32, (m + 31) / 32), 256, 0, c->stream>>>(A, B, C, m, n, k, ta, tb, alpha, beta);
   PINT_LAUNCH_CHECK();
 }
 

@@ -39,6 +39,7 @@ struct Hot {
   double* raw = nullptr;
   double* nodes = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
+  unsigned* gsync = nullptr;  // grid-barrier counter, generation, error flag
   double hot_ms = 0, hot_flops = 0;
   int hot_launches = 0;
 };
@@ -340,11 +341,14 @@ __global__ void k_pr_update(const double* __restrict__ gu, const double* __restr
   }
 }
 
-// jump of eq. (2.8) per coarse time: ||du||^2 + ||dw||^2 + 2 du^T CM dw
+// jump of eq. (2.8) per coarse time: ||du||^2 + ||dw||^2 + 2 du^T CM dw;
+// CTA (n-1, part) handles rows i = part, part + JS, ... of CM and adds its
+// partial sum to jump2[n-1] (zeroed by the caller); k_max_fin takes sqrt
+constexpr int JS = 8;
 __global__ void k_jump(const double* __restrict__ Xu, const double* __restrict__ Xw,
                        const double* __restrict__ Ou, const double* __restrict__ Ow,
-                       const double* __restrict__ CM, int d1, int d2, double* __restrict__ jump) {
-  const int n = blockIdx.x + 1;
+                       const double* __restrict__ CM, int d1, int d2, double* __restrict__ jump2) {
+  const int n = blockIdx.x + 1, part = blockIdx.y;
   __shared__ double sh[64];
   __shared__ double dw[4096];
   const double* xu = Xu + (size_t)n * d1;
@@ -352,22 +356,29 @@ __global__ void k_jump(const double* __restrict__ Xu, const double* __restrict__
   for (int j = threadIdx.x; j < d2; j += blockDim.x) dw[j] = Xw[(size_t)n * d2 + j] - Ow[(size_t)n * d2 + j];
   __syncthreads();
   double s = 0.0;
-  for (int j = threadIdx.x; j < d2; j += blockDim.x) s += dw[j] * dw[j];
-  for (int i = threadIdx.x; i < d1; i += blockDim.x) {
-    double du = xu[i] - ou[i];
+  if (part == 0)
+    for (int j = threadIdx.x; j < d2; j += blockDim.x) s += dw[j] * dw[j];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int i = part + JS * warp; i < d1; i += JS * nwarp) {
     double t = 0.0;
-    for (int j = 0; j < d2; ++j) t += CM[(size_t)i * d2 + j] * dw[j];
-    s += du * du + 2.0 * du * t;
+    for (int j = lane; j < d2; j += 32) t += CM[(size_t)i * d2 + j] * dw[j];
+    t = pintd::warp_sum(t);
+    if (lane == 0) {
+      const double du = xu[i] - ou[i];
+      s += du * du + 2.0 * du * t;
+    }
   }
   s = pintd::block_sum(s, sh);
-  if (threadIdx.x == 0) jump[n - 1] = sqrt(fmax(s, 0.0));
+  if (threadIdx.x == 0) atomicAdd(&jump2[n - 1], s);
 }
 
+// max over n of sqrt(max(x_n, 0)) (x = squared jumps), flags non-finite values
 __global__ void k_max_fin(const double* __restrict__ x, int n, double* __restrict__ out) {
   __shared__ double sh[64];
   double m = 0.0, bad = 0.0;
   for (int i = threadIdx.x; i < n; i += blockDim.x) {
-    double v = x[i];
+    double v = sqrt(fmax(x[i], 0.0));
+    if (!(x[i] == x[i])) v = x[i];
     if (!(v == v) || v > 1e300) bad = 1.0;
     m = fmax(m, v);
   }
@@ -537,6 +548,157 @@ static void step_batch(Ctx* c, Hot& H, const double* u, const double* w, const d
   c->launches += 2;
 }
 
+// ---------------------------------------------------------------------------
+// The sequential coarse sweep of Algorithm 1 (G step + correction eq. (2.7) at
+// every coarse step) as one persistent cooperative kernel: per coarse step a
+// u-phase (rows of CA w, diagonal implicit solve), a grid barrier, a w-phase
+// (rows of CA^T u' and the update), a grid barrier.  The barrier spins are
+// bounded; on expiry the kernel records an error and returns.
+namespace {
+
+constexpr int GS_THREADS = 512;
+constexpr int GS_SPIN = 1 << 22;
+
+__device__ bool gs_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks, int* err) {
+  __syncthreads();
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
+    s_ok = 1;
+    const unsigned g = *gen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(count, 1u);
+    if (arrived == nblocks - 1) {
+      *count = 0;
+      __threadfence();
+      atomicAdd((unsigned*)gen, 1u);
+    } else {
+      int it = 0;
+      while (*gen == g && it < GS_SPIN) {
+        ++it;
+        __nanosleep(20);
+      }
+      if (it >= GS_SPIN) {
+        atomicExch(err, 1);
+        s_ok = 0;
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return s_ok != 0;
+}
+
+struct GSArgs {
+  const double *CA, *CAt, *lam1, *lam2, *b1, *b2, *amp;
+  const double *Fu, *Fw, *Cu, *Cw;
+  double *Xu, *Xw, *Gu, *Gw, *gu, *gw;
+  int d1, d2, n_lo, n_hi, first;
+  double Dt;
+  unsigned* count;
+  unsigned* gen;
+  int* err;
+};
+
+__global__ void __launch_bounds__(GS_THREADS) k_g_sweep(GSArgs a) {
+  const int lane = threadIdx.x & 31;
+  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int nwarps = (gridDim.x * blockDim.x) >> 5;
+  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
+  const int d1 = a.d1, d2 = a.d2;
+  for (int n = a.n_lo; n < a.n_hi; ++n) {
+    const double* xu = a.Xu + (size_t)n * d1;
+    const double* xw = a.Xw + (size_t)n * d2;
+    const double am = a.amp[n];
+    // u-phase: u' = (u - Dt CA w + Dt a b1) / (1 + Dt lambda1)
+    for (int i = gwarp; i < d1; i += nwarps) {
+      double acc = 0.0;
+      for (int j = lane; j < d2; j += 32) acc += a.CA[(size_t)i * d2 + j] * xw[j];
+      acc = pintd::warp_sum(acc);
+      if (lane == 0) a.gu[i] = (xu[i] - a.Dt * acc + a.Dt * am * a.b1[i]) / (1.0 + a.Dt * a.lam1[i]);
+    }
+    if (!gs_barrier(a.count, a.gen, gridDim.x, a.err)) return;
+    // w-phase: w' = (1 - Dt lambda2) w - Dt CA^T u' + Dt a b2, then eq. (2.7)
+    for (int j = gwarp; j < d2; j += nwarps) {
+      double acc = 0.0;
+      for (int i = lane; i < d1; i += 32) acc += a.CAt[(size_t)j * d1 + i] * a.gu[i];
+      acc = pintd::warp_sum(acc);
+      if (lane == 0) {
+        const double g = (1.0 - a.Dt * a.lam2[j]) * xw[j] - a.Dt * acc + a.Dt * am * a.b2[j];
+        double v = a.first ? g : g + a.Fw[(size_t)n * d2 + j] - a.Gw[(size_t)n * d2 + j];
+        if (a.Cw) v += a.Cw[(size_t)(n + 1) * d2 + j];
+        a.Xw[(size_t)(n + 1) * d2 + j] = v;
+        a.Gw[(size_t)n * d2 + j] = g;
+      }
+    }
+    for (int i = gtid; i < d1; i += gthreads) {
+      const double g = a.gu[i];
+      double v = a.first ? g : g + a.Fu[(size_t)n * d1 + i] - a.Gu[(size_t)n * d1 + i];
+      if (a.Cu) v += a.Cu[(size_t)(n + 1) * d1 + i];
+      a.Xu[(size_t)(n + 1) * d1 + i] = v;
+      a.Gu[(size_t)n * d1 + i] = g;
+    }
+    if (!gs_barrier(a.count, a.gen, gridDim.x, a.err)) return;
+  }
+}
+
+}  // namespace
+
+// one coarse sweep n = n_lo..N-1 (first: x_{n+1} = G(x_n) (+ c_{n+1}))
+static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, const double* Fu, const double* Fw,
+                    const double* Cu, const double* Cw, int n_lo, bool first) {
+  static int blocks_per_sm = -1;
+  static int num_sms = 0;
+  if (blocks_per_sm < 0) {
+    int dev = 0;
+    PINT_CUDA(cudaGetDevice(&dev));
+    PINT_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
+    PINT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_g_sweep, GS_THREADS, 0));
+    PINT_REQUIRE(blocks_per_sm >= 1, PINT_ERR_CUDA, "coarse sweep kernel cannot be resident");
+  }
+  if (!H.gsync) {
+    H.gsync = (unsigned*)dalloc(c, 64);
+    PINT_CUDA(cudaMemsetAsync(H.gsync, 0, 64, c->stream));
+  }
+  GSArgs a;
+  a.CA = c->CA;
+  a.CAt = c->CAt;
+  a.lam1 = c->lam1;
+  a.lam2 = c->lam2;
+  a.b1 = H.b1;
+  a.b2 = H.b2;
+  a.amp = amp;
+  a.Fu = Fu;
+  a.Fw = Fw;
+  a.Cu = Cu;
+  a.Cw = Cw;
+  a.Xu = Xu;
+  a.Xw = Xw;
+  a.Gu = H.Gu;
+  a.Gw = H.Gw;
+  a.gu = H.tmp1;
+  a.gw = H.tmp2;
+  a.d1 = c->d1;
+  a.d2 = c->d2;
+  a.n_lo = n_lo;
+  a.n_hi = c->N;
+  a.first = first ? 1 : 0;
+  a.Dt = c->Dt;
+  a.count = H.gsync;
+  a.gen = H.gsync + 1;
+  a.err = (int*)(H.gsync + 2);
+  void* args[] = {&a};
+  const int blocks = num_sms;  // one block per SM: fewest barrier arrivals
+  PINT_CUDA(cudaLaunchCooperativeKernel((const void*)k_g_sweep, dim3(blocks), dim3(GS_THREADS), args, 0, c->stream));
+  c->launches++;
+}
+
+static void g_sweep_check(Ctx* c, Hot& H) {
+  int e = 0;
+  PINT_CUDA(cudaMemcpyAsync(&e, H.gsync + 2, 4, cudaMemcpyDeviceToHost, c->stream));
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+  PINT_REQUIRE(e == 0, PINT_ERR_TIMEOUT, "coarse sweep: bounded grid barrier expired");
+}
+
 // WR fine propagator on intervals [n_lo, n_lo + nact) whose starts are
 // Xu[n], Xw[n] (relative rows 0..nact-1 of xs_u / xs_w); ends into fu, fw.
 static int wr_sweep(Ctx* c, Hot& H, const double* xs_u, const double* xs_w, const double* amp_act,
@@ -622,9 +784,8 @@ void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const dou
   double* g2 = H.Ow;
   dense_gemm(c, c->Q, H.tmp1, g1, d1, 1, d1, true, false, 1.0, 0.0);
   dense_gemm(c, c->Q2, H.tmp2, g2, d2, 1, d2, true, false, 1.0, 0.0);
-  k_proj_rhs<<<nb_((long long)d2 * 32, 256), 256, 0, c->stream>>>(c->CMt, g1, g2, d1, d2, H.Xw);
-  dense_trsm_lower(c, c->projL, H.Xw, d2, 1, false);
-  dense_trsm_lower(c, c->projL, H.Xw, d2, 1, true);
+  k_proj_rhs<<<nb_((long long)d2 * 32, 256), 256, 0, c->stream>>>(c->CMt, g1, g2, d1, d2, H.tmp2);
+  dense_gemm(c, c->projInv, H.tmp2, H.Xw, d2, 1, d2, false, false, 1.0, 0.0);
   k_proj_u<<<nb_((long long)d1 * 32, 256), 256, 0, c->stream>>>(c->CM, g1, H.Xw, d1, d2, H.Xu);
   PINT_LAUNCH_CHECK();
   c->launches += 7;
@@ -656,15 +817,8 @@ void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const dou
     converged = true;
   } else {
     // k = 0: G sweep (Algorithm 1, step 1)
-    for (int n = 0; n < N; ++n) {
-      step_batch(c, H, H.Xu + (size_t)n * d1, H.Xw + (size_t)n * d2, nullptr, nullptr, H.amp + n, c->Dt, 1,
-                 H.tmp1, H.tmp2);
-      k_pr_update<<<4, 256, 0, c->stream>>>(H.tmp1, H.tmp2, nullptr, nullptr, H.Gu + (size_t)n * d1,
-                                            H.Gw + (size_t)n * d2, H.Xu + (size_t)(n + 1) * d1,
-                                            H.Xw + (size_t)(n + 1) * d2, d1, d2, 1);
-      c->launches++;
-    }
-    PINT_LAUNCH_CHECK();
+    g_sweep(c, H, H.Xu, H.Xw, H.amp, nullptr, nullptr, nullptr, nullptr, 0, true);
+    g_sweep_check(c, H);
     int kcap = std::min(k_max, N);
     for (int k = 1; k <= kcap; ++k) {
       // intervals n < k-1 start from exact states; their F values are unchanged
@@ -687,16 +841,10 @@ void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const dou
       // keep x^{k-1} for the jump, then the sequential correction sweep
       PINT_CUDA(cudaMemcpyAsync(H.Ou, H.Xu, (size_t)(N + 1) * d1 * 8, cudaMemcpyDeviceToDevice, c->stream));
       PINT_CUDA(cudaMemcpyAsync(H.Ow, H.Xw, (size_t)(N + 1) * d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
-      for (int n = n_lo; n < N; ++n) {
-        step_batch(c, H, H.Xu + (size_t)n * d1, H.Xw + (size_t)n * d2, nullptr, nullptr, H.amp + n, c->Dt, 1,
-                   H.tmp1, H.tmp2);
-        k_pr_update<<<4, 256, 0, c->stream>>>(H.tmp1, H.tmp2, H.Fu + (size_t)n * d1, H.Fw + (size_t)n * d2,
-                                              H.Gu + (size_t)n * d1, H.Gw + (size_t)n * d2,
-                                              H.Xu + (size_t)(n + 1) * d1, H.Xw + (size_t)(n + 1) * d2, d1, d2,
-                                              0);
-        c->launches++;
-      }
-      k_jump<<<N, 256, 0, c->stream>>>(H.Xu, H.Xw, H.Ou, H.Ow, c->CM, d1, d2, H.red + 8);
+      g_sweep(c, H, H.Xu, H.Xw, H.amp, H.Fu, H.Fw, nullptr, nullptr, n_lo, false);
+      g_sweep_check(c, H);
+      PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
+    k_jump<<<dim3(N, JS), 256, 0, c->stream>>>(H.Xu, H.Xw, H.Ou, H.Ow, c->CM, d1, d2, H.red + 8);
       k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
       PINT_LAUNCH_CHECK();
       c->launches += 2;
@@ -825,22 +973,25 @@ void apply_F_dev(Ctx* c, const double* in, int count, const double* f_nodes, con
 // residual's rounding, eta ~ 1e-6 the relative error of one FP32 F.
 // ===========================================================================
 
-void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* Ut, const float* Wt, int P,
-                   int ncols, float* out);
-void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, const float* lam1, const float* src,
-                     const float* b1, const double* amp, const float2* tw, const float2* dsh, const float* bpow,
-                     double* accU);
-void mx_w_sweep32(Ctx* c, const float* S, int nact, float* Wt, const float* lam2, const float* src,
+void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* Ut, const float* Wt, int ldu,
+                   int ldw, int P, int ncols, float* out);
+void mx_contract_umma(Ctx* c, int mode, const float* Chi, const float* Clo, int M, int Kp, const float* Ut,
+                      const float* Wt, int ldu, int ldw, int ncols, float* out, int* err);
+void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const float* lam1, const float* src,
+                     const float* b1, const double* amp, const float2* tw, const float2* dsh, const float2* dshbr,
+                     const float* bpow, double* accU);
+void mx_w_sweep32(Ctx* c, const float* S, int nact, float* Wt, int ldw, const float* lam2, const float* src,
                   const float* b2, const double* amp, double* accW);
-void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, float* Wt);
-void mx_ends32(Ctx* c, const float* Ut, const float* Wt, int nact, double* Fu, double* Fw);
-void mx_promote(Ctx* c, const float* Ut, const float* Wt, const double* Su, const double* Sw, double* Zu,
-                double* Zw);
+void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, float* Wt, int ldu, int ldw);
+void mx_ends32(Ctx* c, const float* Ut, const float* Wt, int ldu, int ldw, int nact, double* Fu, double* Fw);
+void mx_promote(Ctx* c, const float* Ut, const float* Wt, int ldu, int ldw, const double* Su, const double* Sw,
+                double* Zu, double* Zw);
+void mx_pad_split(Ctx* c, const double* A, int rows, int dk, int ld, float* a32, float* hi, float* lo);
 void mx_residual(Ctx* c, const double* Zu, const double* Zw, const double* R64, const double* S64,
                  const double* b1, const double* b2, const double* amp, float* srcU, float* srcW);
 void mx_continuity(Ctx* c, const double* Zu, const double* Zw, double* Cu, double* Cw);
-void mx_add_traj(Ctx* c, const float* dUt, const float* dWt, const double* Yu, const double* Yw, double* Zu,
-                 double* Zw);
+void mx_add_traj(Ctx* c, const float* dUt, const float* dWt, int ldu, int ldw, const double* Yu, const double* Yw,
+                 double* Zu, double* Zw);
 void mx_to_f32(Ctx* c, const double* x, long long n, float* y);
 
 namespace {
@@ -877,10 +1028,12 @@ __global__ void k_axpy2(const double* __restrict__ a, const double* __restrict__
 
 struct Mx {
   bool ready = false;
-  int N = 0, P = 0, d1 = 0, d2 = 0;
+  int N = 0, P = 0, d1 = 0, d2 = 0, ldu = 0, ldw = 0;
+  float *Rhi = nullptr, *Rlo = nullptr, *Shi = nullptr, *Slo = nullptr;  // TF32 splits of AR, AS (padded)
+  int* err = nullptr;
   float *AR32 = nullptr, *AS32 = nullptr, *lam1f = nullptr, *lam2f = nullptr, *b1f = nullptr, *b2f = nullptr,
         *bpowf = nullptr;
-  float2 *twf = nullptr, *dshf = nullptr;
+  float2 *twf = nullptr, *dshf = nullptr, *dshbr = nullptr;  // shift table, natural / bit-reversed order
   float *Ut = nullptr, *Wt = nullptr, *dUt = nullptr, *dWt = nullptr, *R = nullptr, *S = nullptr;
   float *srcU = nullptr, *srcW = nullptr;
   double *Su = nullptr, *Sw = nullptr, *YSu = nullptr, *YSw = nullptr;
@@ -899,8 +1052,17 @@ static Mx& mx_prepare(Ctx* c) {
   M.P = P;
   M.d1 = d1;
   M.d2 = d2;
-  M.AR32 = Fa((size_t)d1 * 2 * d2);
-  M.AS32 = Fa((size_t)d2 * 2 * d1);
+  const int ldu = (d1 + 31) / 32 * 32, ldw = (d2 + 31) / 32 * 32;
+  M.ldu = ldu;
+  M.ldw = ldw;
+  M.AR32 = Fa((size_t)d1 * 2 * ldw);
+  M.Rhi = Fa((size_t)d1 * 2 * ldw);
+  M.Rlo = Fa((size_t)d1 * 2 * ldw);
+  M.AS32 = Fa((size_t)d2 * 2 * ldu);
+  M.Shi = Fa((size_t)d2 * 2 * ldu);
+  M.Slo = Fa((size_t)d2 * 2 * ldu);
+  M.err = (int*)dalloc(c, 16);
+  PINT_CUDA(cudaMemsetAsync(M.err, 0, 16, c->stream));
   M.lam1f = Fa(d1);
   M.lam2f = Fa(d2);
   M.b1f = Fa(d1);
@@ -908,10 +1070,16 @@ static Mx& mx_prepare(Ctx* c) {
   M.bpowf = Fa(65);
   M.twf = (float2*)dalloc(c, 64 * sizeof(float2));
   M.dshf = (float2*)dalloc(c, 64 * sizeof(float2));
-  M.Ut = Fa((size_t)N * (P + 1) * d1);
-  M.Wt = Fa((size_t)N * (P + 1) * d2);
-  M.dUt = Fa((size_t)N * (P + 1) * d1);
-  M.dWt = Fa((size_t)N * (P + 1) * d2);
+  M.dshbr = (float2*)dalloc(c, 64 * sizeof(float2));
+  M.Ut = Fa((size_t)N * (P + 1) * ldu);
+  M.Wt = Fa((size_t)N * (P + 1) * ldw);
+  M.dUt = Fa((size_t)N * (P + 1) * ldu);
+  M.dWt = Fa((size_t)N * (P + 1) * ldw);
+  // pad entries of the trajectories stay zero (the contractions read them)
+  PINT_CUDA(cudaMemsetAsync(M.Ut, 0, (size_t)N * (P + 1) * ldu * 4, c->stream));
+  PINT_CUDA(cudaMemsetAsync(M.Wt, 0, (size_t)N * (P + 1) * ldw * 4, c->stream));
+  PINT_CUDA(cudaMemsetAsync(M.dUt, 0, (size_t)N * (P + 1) * ldu * 4, c->stream));
+  PINT_CUDA(cudaMemsetAsync(M.dWt, 0, (size_t)N * (P + 1) * ldw * 4, c->stream));
   M.R = Fa((size_t)N * P * d1);
   M.S = Fa((size_t)N * P * d2);
   M.srcU = Fa((size_t)N * P * d1);
@@ -937,13 +1105,31 @@ static Mx& mx_prepare(Ctx* c) {
 // FP32 copies of the time-grid dependent operators (refreshed every solve)
 static void mx_refresh(Ctx* c, Mx& M) {
   const int d1 = c->d1, d2 = c->d2;
-  mx_to_f32(c, c->AR, (long long)d1 * 2 * d2, M.AR32);
-  mx_to_f32(c, c->AS, (long long)d2 * 2 * d1, M.AS32);
+  mx_pad_split(c, c->AR, d1, d2, M.ldw, M.AR32, M.Rhi, M.Rlo);
+  mx_pad_split(c, c->AS, d2, d1, M.ldu, M.AS32, M.Shi, M.Slo);
   mx_to_f32(c, c->lam1, d1, M.lam1f);
   mx_to_f32(c, c->lam2, d2, M.lam2f);
   mx_to_f32(c, c->lampow, 65, M.bpowf);
   mx_to_f32(c, (const double*)c->tw, 128, (float*)M.twf);
   mx_to_f32(c, (const double*)c->dshift, 128, (float*)M.dshf);
+  // bit-reversed copy for the register-resident time solve (P a power of two)
+  const int P = c->P;
+  if ((P & (P - 1)) == 0) {
+    std::vector<double2> hd(64);
+    PINT_CUDA(cudaMemcpyAsync(hd.data(), c->dshift, 64 * sizeof(double2), cudaMemcpyDeviceToHost, c->stream));
+    PINT_CUDA(cudaStreamSynchronize(c->stream));
+    std::vector<float2> hb(64);
+    int bits = 0;
+    while ((1 << bits) < P) ++bits;
+    for (int q = 0; q < P; ++q) {
+      int r = 0;
+      for (int b = 0; b < bits; ++b)
+        if (q & (1 << b)) r |= 1 << (bits - 1 - b);
+      hb[q] = make_float2((float)hd[r].x, (float)hd[r].y);
+    }
+    PINT_CUDA(cudaMemcpyAsync(M.dshbr, hb.data(), 64 * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
+    PINT_CUDA(cudaStreamSynchronize(c->stream));
+  }
 }
 
 // low-precision WR sweep on intervals [n_lo, n_lo + nact); Ut/Wt/src point at
@@ -953,25 +1139,32 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
                        int wr_max, double* fu, double* fw, bool* bad) {
   const int d1 = c->d1, d2 = c->d2, P = c->P;
   const int ncols = nact * P;
-  mx_init32(c, xs_u, xs_w, nact, Ut, Wt);
+  const int ldu = M.ldu, ldw = M.ldw;
+  const bool tensor = (c->precision == PINT_MIXED);
+  mx_init32(c, xs_u, xs_w, nact, Ut, Wt, ldu, ldw);
   int it = 0;
   *bad = false;
   for (it = 1; it <= wr_max; ++it) {
     PINT_CUDA(cudaMemsetAsync(H.acc, 0, (size_t)2 * nact * P * 8, c->stream));
     PINT_CUDA(cudaEventRecord(H.ev[0], c->stream));
-    mx_contract32(c, 0, M.AR32, d1, 2 * d2, Ut, Wt, P, ncols, M.R);
+    if (tensor) mx_contract_umma(c, 0, M.Rhi, M.Rlo, d1, 2 * ldw, Ut, Wt, ldu, ldw, ncols, M.R, M.err);
+    else mx_contract32(c, 0, M.AR32, d1, 2 * ldw, Ut, Wt, ldu, ldw, P, ncols, M.R);
     PINT_CUDA(cudaEventRecord(H.ev[1], c->stream));
-    mx_time_solve32(c, M.R, nact, Ut, M.lam1f, srcU, M.b1f, amp_act, M.twf, M.dshf, M.bpowf, H.acc);
+    mx_time_solve32(c, M.R, nact, Ut, ldu, M.lam1f, srcU, M.b1f, amp_act, M.twf, M.dshf, M.dshbr, M.bpowf, H.acc);
     PINT_CUDA(cudaEventRecord(H.ev[2], c->stream));
-    mx_contract32(c, 1, M.AS32, d2, 2 * d1, Ut, Wt, P, ncols, M.S);
+    if (tensor) mx_contract_umma(c, 1, M.Shi, M.Slo, d2, 2 * ldu, Ut, Wt, ldu, ldw, ncols, M.S, M.err);
+    else mx_contract32(c, 1, M.AS32, d2, 2 * ldu, Ut, Wt, ldu, ldw, P, ncols, M.S);
     PINT_CUDA(cudaEventRecord(H.ev[3], c->stream));
-    mx_w_sweep32(c, M.S, nact, Wt, M.lam2f, srcW, M.b2f, amp_act, H.acc + (size_t)nact * P);
+    mx_w_sweep32(c, M.S, nact, Wt, ldw, M.lam2f, srcW, M.b2f, amp_act, H.acc + (size_t)nact * P);
     k_wr_norm<<<1, 1024, 0, c->stream>>>(H.acc, 2 * nact * P, H.red);
     PINT_LAUNCH_CHECK();
     c->launches++;
     double h[2];
+    int herr = 0;
     PINT_CUDA(cudaMemcpyAsync(h, H.red, 16, cudaMemcpyDeviceToHost, c->stream));
+    if (tensor) PINT_CUDA(cudaMemcpyAsync(&herr, M.err, 4, cudaMemcpyDeviceToHost, c->stream));
     PINT_CUDA(cudaStreamSynchronize(c->stream));
+    PINT_REQUIRE(herr == 0, PINT_ERR_TIMEOUT, "tensor-core contraction: bounded mbarrier wait expired");
     float m0 = 0.f, m1 = 0.f;
     PINT_CUDA(cudaEventElapsedTime(&m0, H.ev[0], H.ev[1]));
     PINT_CUDA(cudaEventElapsedTime(&m1, H.ev[2], H.ev[3]));
@@ -985,7 +1178,7 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
     if (h[0] <= wr_tol) break;
   }
   if (it > wr_max) it = wr_max;
-  mx_ends32(c, Ut, Wt, nact, fu, fw);
+  mx_ends32(c, Ut, Wt, M.ldu, M.ldw, nact, fu, fw);
   return it;
 }
 
@@ -1009,17 +1202,10 @@ struct LpRun {
 static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hist, double* jump_hist,
                         int hist_off) {
   const int N = c->N, d1 = c->d1, d2 = c->d2, P = c->P;
-  for (int n = 0; n < N && !r.have_g0; ++n) {
-    step_batch(c, H, r.Xu + (size_t)n * d1, r.Xw + (size_t)n * d2, nullptr, nullptr, r.amp + n, c->Dt, 1, H.tmp1,
-               H.tmp2);
-    k_pr_update_c<<<4, 256, 0, c->stream>>>(H.tmp1, H.tmp2, nullptr, nullptr,
-                                            r.Cu ? r.Cu + (size_t)(n + 1) * d1 : nullptr,
-                                            r.Cw ? r.Cw + (size_t)(n + 1) * d2 : nullptr, H.Gu + (size_t)n * d1,
-                                            H.Gw + (size_t)n * d2, r.Xu + (size_t)(n + 1) * d1,
-                                            r.Xw + (size_t)(n + 1) * d2, d1, d2, 1);
-    c->launches++;
+  if (!r.have_g0) {
+    g_sweep(c, H, r.Xu, r.Xw, r.amp, nullptr, nullptr, r.Cu, r.Cw, 0, true);
+    g_sweep_check(c, H);
   }
-  PINT_LAUNCH_CHECK();
   cudaEvent_t a0, a1;
   PINT_CUDA(cudaEventCreate(&a0));
   PINT_CUDA(cudaEventCreate(&a1));
@@ -1034,8 +1220,8 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
     bool bad = false;
     int it = wr_sweep_lp(c, H, M, r.Xu + (size_t)n_lo * d1, r.Xw + (size_t)n_lo * d2, r.amp + n_lo, nact,
                          r.srcU ? r.srcU + (size_t)n_lo * P * d1 : nullptr,
-                         r.srcW ? r.srcW + (size_t)n_lo * P * d2 : nullptr, r.Ut + (size_t)n_lo * (P + 1) * d1,
-                         r.Wt + (size_t)n_lo * (P + 1) * d2, r.wr_tol, r.wr_max, H.Fu + (size_t)n_lo * d1,
+                         r.srcW ? r.srcW + (size_t)n_lo * P * d2 : nullptr, r.Ut + (size_t)n_lo * (P + 1) * M.ldu,
+                         r.Wt + (size_t)n_lo * (P + 1) * M.ldw, r.wr_tol, r.wr_max, H.Fu + (size_t)n_lo * d1,
                          H.Fw + (size_t)n_lo * d2, &bad);
     PINT_CUDA(cudaEventRecord(a1, c->stream));
     PINT_CUDA(cudaEventSynchronize(a1));
@@ -1050,17 +1236,10 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
     r.wr_total += it;
     PINT_CUDA(cudaMemcpyAsync(H.Ou, r.Xu, (size_t)(N + 1) * d1 * 8, cudaMemcpyDeviceToDevice, c->stream));
     PINT_CUDA(cudaMemcpyAsync(H.Ow, r.Xw, (size_t)(N + 1) * d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
-    for (int n = n_lo; n < N; ++n) {
-      step_batch(c, H, r.Xu + (size_t)n * d1, r.Xw + (size_t)n * d2, nullptr, nullptr, r.amp + n, c->Dt, 1,
-                 H.tmp1, H.tmp2);
-      k_pr_update_c<<<4, 256, 0, c->stream>>>(H.tmp1, H.tmp2, H.Fu + (size_t)n * d1, H.Fw + (size_t)n * d2,
-                                              r.Cu ? r.Cu + (size_t)(n + 1) * d1 : nullptr,
-                                              r.Cw ? r.Cw + (size_t)(n + 1) * d2 : nullptr, H.Gu + (size_t)n * d1,
-                                              H.Gw + (size_t)n * d2, r.Xu + (size_t)(n + 1) * d1,
-                                              r.Xw + (size_t)(n + 1) * d2, d1, d2, 0);
-      c->launches++;
-    }
-    k_jump<<<N, 256, 0, c->stream>>>(r.Xu, r.Xw, H.Ou, H.Ow, c->CM, d1, d2, H.red + 8);
+    g_sweep(c, H, r.Xu, r.Xw, r.amp, H.Fu, H.Fw, r.Cu, r.Cw, n_lo, false);
+    g_sweep_check(c, H);
+    PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
+    k_jump<<<dim3(N, JS), 256, 0, c->stream>>>(r.Xu, r.Xw, H.Ou, H.Ow, c->CM, d1, d2, H.red + 8);
     k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
     PINT_LAUNCH_CHECK();
     c->launches += 2;
@@ -1089,7 +1268,8 @@ static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw) {
   const int N = c->N, d1 = c->d1, d2 = c->d2;
   PINT_CUDA(cudaMemsetAsync(H.tmp1, 0, (size_t)(N + 1) * std::max(d1, d2) * 8, c->stream));
   // k_jump measures rows 1..N against the zero rows of tmp1
-  k_jump<<<N, 256, 0, c->stream>>>(Xu, Xw, H.tmp1, H.tmp1, c->CM, d1, d2, H.red + 8);
+  PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
+  k_jump<<<dim3(N, JS), 256, 0, c->stream>>>(Xu, Xw, H.tmp1, H.tmp1, c->CM, d1, d2, H.red + 8);
   k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
   PINT_LAUNCH_CHECK();
   double h[2];
@@ -1133,9 +1313,8 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
   to_reduced(c, H.raw, 1, H.tmp1, H.tmp2);
   dense_gemm(c, c->Q, H.tmp1, H.Ou, d1, 1, d1, true, false, 1.0, 0.0);
   dense_gemm(c, c->Q2, H.tmp2, H.Ow, d2, 1, d2, true, false, 1.0, 0.0);
-  k_proj_rhs<<<nb_((long long)d2 * 32, 256), 256, 0, c->stream>>>(c->CMt, H.Ou, H.Ow, d1, d2, H.Xw);
-  dense_trsm_lower(c, c->projL, H.Xw, d2, 1, false);
-  dense_trsm_lower(c, c->projL, H.Xw, d2, 1, true);
+  k_proj_rhs<<<nb_((long long)d2 * 32, 256), 256, 0, c->stream>>>(c->CMt, H.Ou, H.Ow, d1, d2, H.tmp2);
+  dense_gemm(c, c->projInv, H.tmp2, H.Xw, d2, 1, d2, false, false, 1.0, 0.0);
   k_proj_u<<<nb_((long long)d1 * 32, 256), 256, 0, c->stream>>>(c->CM, H.Ou, H.Xw, d1, d2, H.Xu);
   PINT_LAUNCH_CHECK();
   float f_ms = 0.f;
@@ -1171,7 +1350,7 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
   // -- 2.-4. refinement ------------------------------------------------------
   PINT_CUDA(cudaEventRecord(r0, c->stream));
   for (int ref = 0; ref < n_refine; ++ref) {
-    if (ref == 0) mx_promote(c, M.Ut, M.Wt, M.Su, M.Sw, M.Zu, M.Zw);
+    if (ref == 0) mx_promote(c, M.Ut, M.Wt, M.ldu, M.ldw, M.Su, M.Sw, M.Zu, M.Zw);
     // s_N := end of the last interval
     PINT_CUDA(cudaMemcpyAsync(M.Su + (size_t)N * d1, M.Zu + ((size_t)(N - 1) * (P + 1) + P) * d1, (size_t)d1 * 8,
                               cudaMemcpyDeviceToDevice, c->stream));
@@ -1222,7 +1401,7 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
     c->launches += 2;
     if (ref + 1 < n_refine) {
       // next trajectory: Z + dZ with dZ the correction trajectories (starts YS)
-      mx_add_traj(c, M.dUt, M.dWt, M.YSu, M.YSw, M.Zu, M.Zw);
+      mx_add_traj(c, M.dUt, M.dWt, M.ldu, M.ldw, M.YSu, M.YSw, M.Zu, M.Zw);
       // new starts s_n <- s_n + ys_n
       k_axpy2<<<nb_((long long)N * d1, 256), 256, 0, c->stream>>>(M.Su, M.YSu, (long long)N * d1, M.Su);
       k_axpy2<<<nb_((long long)N * d2, 256), 256, 0, c->stream>>>(M.Sw, M.YSw, (long long)N * d2, M.Sw);

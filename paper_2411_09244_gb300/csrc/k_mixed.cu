@@ -18,10 +18,12 @@ inline unsigned nbl(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
 // FP32 contraction with the WR column maps (see k_wr_gemm in k_hot64.cu):
 // MODE 0: out = AR [w_p ; w_{max(p-1,0)}], MODE 1: out = AS [u_p - u_{max(p-1,0)} ; u_{p+1}]
+// Trajectories use padded strides ldu, ldw (multiples of 32, pad entries 0);
+// the contraction dimension is K = 2 ld with A zero in the pad columns.
 template <int MODE>
 __global__ void __launch_bounds__(256) k_wr_gemm32(const float* __restrict__ A, int M, int K,
                                                    const float* __restrict__ Ut, const float* __restrict__ Wt,
-                                                   int d1, int d2, int P, int ncols, float* __restrict__ out) {
+                                                   int ldu, int ldw, int P, int ncols, float* __restrict__ out) {
   __shared__ float As[16][129], Bs[16][129];
   const int i0 = blockIdx.y * 128, j0 = blockIdx.x * 128;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 8x8 outputs per thread
@@ -35,12 +37,12 @@ __global__ void __launch_bounds__(256) k_wr_gemm32(const float* __restrict__ A, 
       if (kg < K && col < ncols) {
         int n = col / P, p = col % P;
         if (MODE == 0) {
-          const float* Wn = Wt + (size_t)n * (P + 1) * d2;
-          bv = (kg < d2) ? Wn[(size_t)p * d2 + kg] : Wn[(size_t)(p >= 1 ? p - 1 : 0) * d2 + (kg - d2)];
+          const float* Wn = Wt + (size_t)n * (P + 1) * ldw;
+          bv = (kg < ldw) ? Wn[(size_t)p * ldw + kg] : Wn[(size_t)(p >= 1 ? p - 1 : 0) * ldw + (kg - ldw)];
         } else {
-          const float* Un = Ut + (size_t)n * (P + 1) * d1;
-          if (kg < d1) bv = Un[(size_t)p * d1 + kg] - Un[(size_t)(p >= 1 ? p - 1 : 0) * d1 + kg];
-          else bv = Un[(size_t)(p + 1) * d1 + (kg - d1)];
+          const float* Un = Ut + (size_t)n * (P + 1) * ldu;
+          if (kg < ldu) bv = Un[(size_t)p * ldu + kg] - Un[(size_t)(p >= 1 ? p - 1 : 0) * ldu + kg];
+          else bv = Un[(size_t)(p + 1) * ldu + (kg - ldu)];
         }
       }
       As[kk][r] = av;
@@ -117,7 +119,7 @@ __device__ void dft32(F2c* v, F2c* tmp, int P, const float2* __restrict__ tw, in
 
 // eq. (4.7) per (interval, mode) in FP32; src (per step, scaled by 1/dt) or
 // the constant source b1 * amp[n]
-__global__ void __launch_bounds__(128) k_time_solve32(const float* __restrict__ R, int d1, int P,
+__global__ void __launch_bounds__(128) k_time_solve32(const float* __restrict__ R, int d1, int ldu, int P,
                                                       float* __restrict__ Ut, const float* __restrict__ lam1,
                                                       const float* __restrict__ src, const float* __restrict__ b1,
                                                       const double* __restrict__ amp, float alpha, float dt,
@@ -130,13 +132,13 @@ __global__ void __launch_bounds__(128) k_time_solve32(const float* __restrict__ 
   __shared__ double sh[64];
   F2c v[64], tmp[64];
   float unew[64];
-  float* Un = Ut + (size_t)nloc * (P + 1) * d1;
+  float* Un = Ut + (size_t)nloc * (P + 1) * ldu;
   if (i < d1) {
     const float li = lam1[i];
     const float cs = src ? 0.f : b1[i] * (float)amp[nloc];
     for (int p = 0; p < P; ++p) {
       float y = R[((size_t)nloc * P + p) * d1 + i] + (src ? src[((size_t)nloc * P + p) * d1 + i] : cs);
-      if (p == 0) y += (Un[i] - alpha * Un[(size_t)P * d1 + i]) / dt;
+      if (p == 0) y += (Un[i] - alpha * Un[(size_t)P * ldu + i]) / dt;
       v[p] = {y * bpow[p], 0.f};
     }
     if (pow2) fft32(v, P, tw, -1);
@@ -154,24 +156,118 @@ __global__ void __launch_bounds__(128) k_time_solve32(const float* __restrict__ 
   for (int p = 0; p < P; ++p) {
     double du = 0.0;
     if (i < d1) {
-      float old = Un[(size_t)(p + 1) * d1 + i];
+      float old = Un[(size_t)(p + 1) * ldu + i];
       du = (double)(unew[p] - old) * (double)(unew[p] - old);
-      Un[(size_t)(p + 1) * d1 + i] = unew[p];
+      Un[(size_t)(p + 1) * ldu + i] = unew[p];
     }
     du = pintd::block_sum(du, sh);
     if (threadIdx.x == 0) atomicAdd(&accU[(size_t)nloc * P + p], du);
   }
 }
 
-__global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, int d2, int P,
+// Register-resident variant for P = 16, 32, 64: the P values of a series stay
+// in registers.  Forward transform by decimation in frequency (natural order
+// in, bit-reversed out), the pointwise divide with the shift table already
+// permuted to bit-reversed order, inverse by decimation in time (bit-reversed
+// in, natural out); one template instance per stage so every index is a
+// compile-time constant.  Squared updates are reduced per warp.
+template <int P, int LEN>
+__device__ __forceinline__ void dif_stage(float* re, float* im, const float2* __restrict__ tw, float sign) {
+#pragma unroll
+  for (int i = 0; i < P; i += LEN) {
+#pragma unroll
+    for (int k = 0; k < LEN / 2; ++k) {
+      const float2 t = tw[k * (P / LEN)];
+      const float wr = t.x, wi = sign * t.y;
+      const int a = i + k, b = i + k + LEN / 2;
+      const float dr = re[a] - re[b], di = im[a] - im[b];
+      re[a] += re[b];
+      im[a] += im[b];
+      re[b] = dr * wr - di * wi;
+      im[b] = dr * wi + di * wr;
+    }
+  }
+  if constexpr (LEN > 2) dif_stage<P, LEN / 2>(re, im, tw, sign);
+}
+
+template <int P, int LEN>
+__device__ __forceinline__ void dit_stage(float* re, float* im, const float2* __restrict__ tw, float sign) {
+#pragma unroll
+  for (int i = 0; i < P; i += LEN) {
+#pragma unroll
+    for (int k = 0; k < LEN / 2; ++k) {
+      const float2 t = tw[k * (P / LEN)];
+      const float wr = t.x, wi = sign * t.y;
+      const int a = i + k, b = i + k + LEN / 2;
+      const float br = re[b] * wr - im[b] * wi, bi = re[b] * wi + im[b] * wr;
+      re[b] = re[a] - br;
+      im[b] = im[a] - bi;
+      re[a] += br;
+      im[a] += bi;
+    }
+  }
+  if constexpr (LEN < P) dit_stage<P, LEN * 2>(re, im, tw, sign);
+}
+
+template <int P>
+__global__ void __launch_bounds__(128) k_time_solve32_t(const float* __restrict__ R, int d1, int ldu,
+                                                        float* __restrict__ Ut, const float* __restrict__ lam1,
+                                                        const float* __restrict__ src, const float* __restrict__ b1,
+                                                        const double* __restrict__ amp, float alpha, float dt,
+                                                        const float2* __restrict__ tw,
+                                                        const float2* __restrict__ dsh,
+                                                        const float* __restrict__ bpow, double* __restrict__ accU) {
+  const int nloc = blockIdx.y;
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  const int lane = threadIdx.x & 31;
+  float re[P], im[P];
+  float* Un = Ut + (size_t)nloc * (P + 1) * ldu;
+  const bool act = i < d1;
+  if (act) {
+    const float cs = src ? 0.f : b1[i] * (float)amp[nloc];
+    const float first = (Un[i] - alpha * Un[(size_t)P * ldu + i]) / dt;
+#pragma unroll
+    for (int p = 0; p < P; ++p) {
+      float y = R[((size_t)nloc * P + p) * d1 + i] + (src ? src[((size_t)nloc * P + p) * d1 + i] : cs);
+      if (p == 0) y += first;
+      re[p] = y * bpow[p];
+      im[p] = 0.f;
+    }
+    dif_stage<P, P>(re, im, tw, 1.f);                  // forward, output in bit-reversed order
+    const float li = lam1[i];
+#pragma unroll
+    for (int q = 0; q < P; ++q) {                      // dsh_br[q] = d_{bitrev(q)}
+      const float2 d = dsh[q];
+      const float a = d.x + li, b = d.y, den = a * a + b * b;
+      const float qr = (re[q] * a + im[q] * b) / den, qi = (im[q] * a - re[q] * b) / den;
+      re[q] = qr;
+      im[q] = qi;
+    }
+    dit_stage<P, 2>(re, im, tw, -1.f);                 // inverse from bit-reversed input (without 1/P)
+#pragma unroll
+    for (int p = 0; p < P; ++p) re[p] = re[p] / ((float)P * bpow[p]);
+  }
+#pragma unroll
+  for (int p = 0; p < P; ++p) {
+    double du = 0.0;
+    if (act) {
+      const float old = Un[(size_t)(p + 1) * ldu + i];
+      du = (double)(re[p] - old) * (double)(re[p] - old);
+      Un[(size_t)(p + 1) * ldu + i] = re[p];
+    }
+    du = pintd::warp_sum(du);
+    if (lane == 0) atomicAdd(&accU[(size_t)nloc * P + p], du);
+  }
+}
+
+__global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, int d2, int ldw, int P,
                                                    float* __restrict__ Wt, const float* __restrict__ lam2,
                                                    const float* __restrict__ src, const float* __restrict__ b2,
                                                    const double* __restrict__ amp, float dt,
                                                    double* __restrict__ accW) {
   const int nloc = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
-  __shared__ double sh[64];
-  float* Wn = Wt + (size_t)nloc * (P + 1) * d2;
+  float* Wn = Wt + (size_t)nloc * (P + 1) * ldw;
   float w = 0.f, fac = 0.f, cs = 0.f;
   if (j < d2) {
     w = Wn[j];
@@ -183,65 +279,65 @@ __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, 
     if (j < d2) {
       float g = src ? src[((size_t)nloc * P + p) * d2 + j] : cs;
       float wn = fac * w + S[((size_t)nloc * P + p) * d2 + j] + g;
-      float old = Wn[(size_t)(p + 1) * d2 + j];
+      float old = Wn[(size_t)(p + 1) * ldw + j];
       dw = (double)(wn - old) * (double)(wn - old);
-      Wn[(size_t)(p + 1) * d2 + j] = wn;
+      Wn[(size_t)(p + 1) * ldw + j] = wn;
       w = wn;
     }
-    dw = pintd::block_sum(dw, sh);
-    if (threadIdx.x == 0) atomicAdd(&accW[(size_t)nloc * P + p], dw);
+    dw = pintd::warp_sum(dw);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&accW[(size_t)nloc * P + p], dw);
   }
 }
 
-__global__ void k_init32(const double* __restrict__ Xu, const double* __restrict__ Xw, int d1, int d2, int P,
-                         float* __restrict__ Ut, float* __restrict__ Wt) {
+__global__ void k_init32(const double* __restrict__ Xu, const double* __restrict__ Xw, int d1, int d2, int ldu,
+                         int ldw, int P, float* __restrict__ Ut, float* __restrict__ Wt) {
   const int nloc = blockIdx.y;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (P + 1) * (d1 + d2); e += gridDim.x * blockDim.x) {
     int p = e / (d1 + d2), k = e % (d1 + d2);
-    if (k < d1) Ut[((size_t)nloc * (P + 1) + p) * d1 + k] = (float)Xu[(size_t)nloc * d1 + k];
-    else Wt[((size_t)nloc * (P + 1) + p) * d2 + (k - d1)] = (float)Xw[(size_t)nloc * d2 + (k - d1)];
+    if (k < d1) Ut[((size_t)nloc * (P + 1) + p) * ldu + k] = (float)Xu[(size_t)nloc * d1 + k];
+    else Wt[((size_t)nloc * (P + 1) + p) * ldw + (k - d1)] = (float)Xw[(size_t)nloc * d2 + (k - d1)];
   }
 }
 
-__global__ void k_ends32(const float* __restrict__ Ut, const float* __restrict__ Wt, int d1, int d2, int P,
-                         double* __restrict__ Fu, double* __restrict__ Fw) {
+__global__ void k_ends32(const float* __restrict__ Ut, const float* __restrict__ Wt, int d1, int d2, int ldu,
+                         int ldw, int P, double* __restrict__ Fu, double* __restrict__ Fw) {
   const int nloc = blockIdx.y;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d1 + d2; e += gridDim.x * blockDim.x) {
-    if (e < d1) Fu[(size_t)nloc * d1 + e] = (double)Ut[((size_t)nloc * (P + 1) + P) * d1 + e];
-    else Fw[(size_t)nloc * d2 + (e - d1)] = (double)Wt[((size_t)nloc * (P + 1) + P) * d2 + (e - d1)];
+    if (e < d1) Fu[(size_t)nloc * d1 + e] = (double)Ut[((size_t)nloc * (P + 1) + P) * ldu + e];
+    else Fw[(size_t)nloc * d2 + (e - d1)] = (double)Wt[((size_t)nloc * (P + 1) + P) * ldw + (e - d1)];
   }
 }
 
 // FP64 trajectory: p = 0 from the FP64 starts, p >= 1 from the FP32 states
 __global__ void k_promote(const float* __restrict__ Ut, const float* __restrict__ Wt,
-                          const double* __restrict__ Su, const double* __restrict__ Sw, int d1, int d2, int P,
-                          double* __restrict__ Zu, double* __restrict__ Zw) {
+                          const double* __restrict__ Su, const double* __restrict__ Sw, int d1, int d2, int ldu,
+                          int ldw, int P, double* __restrict__ Zu, double* __restrict__ Zw) {
   const int n = blockIdx.y;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (P + 1) * (d1 + d2); e += gridDim.x * blockDim.x) {
     int p = e / (d1 + d2), k = e % (d1 + d2);
     if (k < d1) {
       size_t o = ((size_t)n * (P + 1) + p) * d1 + k;
-      Zu[o] = (p == 0) ? Su[(size_t)n * d1 + k] : (double)Ut[o];
+      Zu[o] = (p == 0) ? Su[(size_t)n * d1 + k] : (double)Ut[((size_t)n * (P + 1) + p) * ldu + k];
     } else {
       size_t o = ((size_t)n * (P + 1) + p) * d2 + (k - d1);
-      Zw[o] = (p == 0) ? Sw[(size_t)n * d2 + (k - d1)] : (double)Wt[o];
+      Zw[o] = (p == 0) ? Sw[(size_t)n * d2 + (k - d1)] : (double)Wt[((size_t)n * (P + 1) + p) * ldw + (k - d1)];
     }
   }
 }
 
 // adds a correction trajectory: Z += dZ (p = 0 from the FP64 correction starts)
 __global__ void k_add_traj(const float* __restrict__ dUt, const float* __restrict__ dWt,
-                           const double* __restrict__ Yu, const double* __restrict__ Yw, int d1, int d2, int P,
-                           double* __restrict__ Zu, double* __restrict__ Zw) {
+                           const double* __restrict__ Yu, const double* __restrict__ Yw, int d1, int d2, int ldu,
+                           int ldw, int P, double* __restrict__ Zu, double* __restrict__ Zw) {
   const int n = blockIdx.y;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (P + 1) * (d1 + d2); e += gridDim.x * blockDim.x) {
     int p = e / (d1 + d2), k = e % (d1 + d2);
     if (k < d1) {
       size_t o = ((size_t)n * (P + 1) + p) * d1 + k;
-      Zu[o] += (p == 0) ? Yu[(size_t)n * d1 + k] : (double)dUt[o];
+      Zu[o] += (p == 0) ? Yu[(size_t)n * d1 + k] : (double)dUt[((size_t)n * (P + 1) + p) * ldu + k];
     } else {
       size_t o = ((size_t)n * (P + 1) + p) * d2 + (k - d1);
-      Zw[o] += (p == 0) ? Yw[(size_t)n * d2 + (k - d1)] : (double)dWt[o];
+      Zw[o] += (p == 0) ? Yw[(size_t)n * d2 + (k - d1)] : (double)dWt[((size_t)n * (P + 1) + p) * ldw + (k - d1)];
     }
   }
 }
@@ -295,6 +391,26 @@ __global__ void k_continuity(const double* __restrict__ Zu, const double* __rest
   }
 }
 
+// A (rows x 2 dk, FP64) -> A32 (rows x 2 ld, FP32), halves at columns 0 and ld,
+// pad columns zero; also the TF32 hi / lo split of every entry
+__global__ void k_pad_split(const double* __restrict__ A, int rows, int dk, int ld, float* __restrict__ a32,
+                            float* __restrict__ hi, float* __restrict__ lo) {
+  long long tot = (long long)rows * 2 * ld;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    int r = (int)(e / (2 * ld)), k = (int)(e % (2 * ld));
+    int seg = k / ld, j = k % ld;
+    float v = (j < dk) ? (float)A[(size_t)r * 2 * dk + seg * dk + j] : 0.f;
+    a32[e] = v;
+    uint32_t h;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
+    float hf = __uint_as_float(h);
+    uint32_t l;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(v - hf));
+    hi[e] = hf;
+    lo[e] = __uint_as_float(l);
+  }
+}
+
 __global__ void k_to_f32(const double* __restrict__ x, long long n, float* __restrict__ y) {
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) y[e] = (float)x[e];
@@ -302,58 +418,69 @@ __global__ void k_to_f32(const double* __restrict__ x, long long n, float* __res
 
 }  // namespace
 
-void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* Ut, const float* Wt, int P,
-                   int ncols, float* out) {
+void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* Ut, const float* Wt, int ldu,
+                   int ldw, int P, int ncols, float* out) {
   dim3 grid(nbl(ncols, 128), nbl(M, 128));
   if (mode == 0)
-    k_wr_gemm32<0><<<grid, 256, 0, c->stream>>>(A, M, K, Ut, Wt, c->d1, c->d2, P, ncols, out);
+    k_wr_gemm32<0><<<grid, 256, 0, c->stream>>>(A, M, K, Ut, Wt, ldu, ldw, P, ncols, out);
   else
-    k_wr_gemm32<1><<<grid, 256, 0, c->stream>>>(A, M, K, Ut, Wt, c->d1, c->d2, P, ncols, out);
+    k_wr_gemm32<1><<<grid, 256, 0, c->stream>>>(A, M, K, Ut, Wt, ldu, ldw, P, ncols, out);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
 
-void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, const float* lam1, const float* src,
-                     const float* b1, const double* amp, const float2* tw, const float2* dsh, const float* bpow,
-                     double* accU) {
+void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const float* lam1, const float* src,
+                     const float* b1, const double* amp, const float2* tw, const float2* dsh, const float2* dshbr,
+                     const float* bpow, double* accU) {
   const int P = c->P;
-  k_time_solve32<<<dim3(nbl(c->d1, 128), nact), 128, 0, c->stream>>>(
-      R, c->d1, P, Ut, lam1, src, b1, amp, (float)c->alpha, (float)c->dt, tw, dsh, bpow, (P & (P - 1)) == 0,
-      accU);
+  const dim3 grid(nbl(c->d1, 128), nact);
+  const float al = (float)c->alpha, dt = (float)c->dt;
+  if (P == 64)
+    k_time_solve32_t<64><<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al, dt, tw, dshbr, bpow,
+                                                       accU);
+  else if (P == 32)
+    k_time_solve32_t<32><<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al, dt, tw, dshbr, bpow,
+                                                       accU);
+  else if (P == 16)
+    k_time_solve32_t<16><<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al, dt, tw, dshbr, bpow,
+                                                       accU);
+  else
+    k_time_solve32<<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, P, Ut, lam1, src, b1, amp, al, dt, tw, dsh, bpow,
+                                                (P & (P - 1)) == 0, accU);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
 
-void mx_w_sweep32(Ctx* c, const float* S, int nact, float* Wt, const float* lam2, const float* src,
+void mx_w_sweep32(Ctx* c, const float* S, int nact, float* Wt, int ldw, const float* lam2, const float* src,
                   const float* b2, const double* amp, double* accW) {
-  k_w_sweep32<<<dim3(nbl(c->d2, 128), nact), 128, 0, c->stream>>>(S, c->d2, c->P, Wt, lam2, src, b2, amp,
+  k_w_sweep32<<<dim3(nbl(c->d2, 128), nact), 128, 0, c->stream>>>(S, c->d2, ldw, c->P, Wt, lam2, src, b2, amp,
                                                                   (float)c->dt, accW);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
 
-void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, float* Wt) {
-  k_init32<<<dim3(32, nact), 256, 0, c->stream>>>(Xu, Xw, c->d1, c->d2, c->P, Ut, Wt);
+void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, float* Wt, int ldu, int ldw) {
+  k_init32<<<dim3(32, nact), 256, 0, c->stream>>>(Xu, Xw, c->d1, c->d2, ldu, ldw, c->P, Ut, Wt);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
 
-void mx_ends32(Ctx* c, const float* Ut, const float* Wt, int nact, double* Fu, double* Fw) {
-  k_ends32<<<dim3(8, nact), 256, 0, c->stream>>>(Ut, Wt, c->d1, c->d2, c->P, Fu, Fw);
+void mx_ends32(Ctx* c, const float* Ut, const float* Wt, int ldu, int ldw, int nact, double* Fu, double* Fw) {
+  k_ends32<<<dim3(8, nact), 256, 0, c->stream>>>(Ut, Wt, c->d1, c->d2, ldu, ldw, c->P, Fu, Fw);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
 
-void mx_promote(Ctx* c, const float* Ut, const float* Wt, const double* Su, const double* Sw, double* Zu,
-                double* Zw) {
-  k_promote<<<dim3(64, c->N), 256, 0, c->stream>>>(Ut, Wt, Su, Sw, c->d1, c->d2, c->P, Zu, Zw);
+void mx_promote(Ctx* c, const float* Ut, const float* Wt, int ldu, int ldw, const double* Su, const double* Sw,
+                double* Zu, double* Zw) {
+  k_promote<<<dim3(64, c->N), 256, 0, c->stream>>>(Ut, Wt, Su, Sw, c->d1, c->d2, ldu, ldw, c->P, Zu, Zw);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
 
-void mx_add_traj(Ctx* c, const float* dUt, const float* dWt, const double* Yu, const double* Yw, double* Zu,
-                 double* Zw) {
-  k_add_traj<<<dim3(64, c->N), 256, 0, c->stream>>>(dUt, dWt, Yu, Yw, c->d1, c->d2, c->P, Zu, Zw);
+void mx_add_traj(Ctx* c, const float* dUt, const float* dWt, int ldu, int ldw, const double* Yu, const double* Yw,
+                 double* Zu, double* Zw) {
+  k_add_traj<<<dim3(64, c->N), 256, 0, c->stream>>>(dUt, dWt, Yu, Yw, c->d1, c->d2, ldu, ldw, c->P, Zu, Zw);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
@@ -370,6 +497,11 @@ void mx_continuity(Ctx* c, const double* Zu, const double* Zw, double* Cu, doubl
   k_continuity<<<dim3(8, c->N + 1), 256, 0, c->stream>>>(Zu, Zw, c->N, c->P, c->d1, c->d2, Cu, Cw);
   PINT_LAUNCH_CHECK();
   c->launches++;
+}
+
+void mx_pad_split(Ctx* c, const double* A, int rows, int dk, int ld, float* a32, float* hi, float* lo) {
+  k_pad_split<<<1024, 256, 0, c->stream>>>(A, rows, dk, ld, a32, hi, lo);
+  PINT_LAUNCH_CHECK();
 }
 
 void mx_to_f32(Ctx* c, const double* x, long long n, float* y) {

@@ -58,6 +58,13 @@ void build_spectral(Ctx* c) {
   c->lam22 = lmax;
   c->dt_max = (1.0 - c->gamma * c->gamma) / lmax;
   dense_cholesky(c, c->projL, d2);
+  // explicit inverse (I - CM^T CM)^-1 for the initial projection
+  if (!c->projInv) c->projInv = A((size_t)d2 * d2);
+  PINT_CUDA(cudaMemsetAsync(G, 0, (size_t)d2 * d2 * 8, c->stream));
+  k_eye_minus<<<(unsigned)(((long long)d2 * d2 + 255) / 256), 256, 0, c->stream>>>(G, d2, c->projInv);
+  PINT_LAUNCH_CHECK();
+  dense_trsm_lower(c, c->projL, c->projInv, d2, d2, false);
+  dense_trsm_lower(c, c->projL, c->projInv, d2, d2, true);
   dfree(c, T);
   dfree(c, G);
   dfree(c, V);

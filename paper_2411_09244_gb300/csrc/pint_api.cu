@@ -220,7 +220,8 @@ pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double 
     PINT_REQUIRE(N >= 1 && N <= 4096, PINT_ERR_BAD_ARG, "N must be in [1, 4096]");
     PINT_REQUIRE(P >= 2 && P <= 64, PINT_ERR_BAD_ARG, "P must be in [2, 64]");
     PINT_REQUIRE(alpha > 0 && alpha < 1, PINT_ERR_BAD_ARG, "alpha must be in (0, 1)");
-    PINT_REQUIRE(precision == PINT_FP64 || precision == PINT_MIXED, PINT_ERR_BAD_ARG, "unknown precision");
+    PINT_REQUIRE(precision == PINT_FP64 || precision == PINT_MIXED || precision == PINT_MIXED_F32,
+                 PINT_ERR_BAD_ARG, "unknown precision");
     cudaEvent_t e0, e1;
     PINT_CUDA(cudaEventCreate(&e0));
     PINT_CUDA(cudaEventCreate(&e1));
@@ -277,7 +278,7 @@ static pint_status solve_common(Ctx* c, const double* u0_nodes, const double* f_
     OutBuf ou = stage_out(c, u_out, (size_t)c->N * c->nn, tmp);
     OutBuf oc = stage_out(c, coarse_out, (size_t)(c->N + 1) * (c->d1 + c->d2), tmp);
     try {
-      if (c->precision == PINT_MIXED && !sequential)
+      if (c->precision != PINT_FP64 && !sequential)
         solve_mixed(c, du0, df, da, eps, k_max, wr_tol, wr_max, ou.dev, oc.dev, stats, 1);
       else
         solve_fp64(c, du0, df, da, eps, k_max, wr_tol, wr_max, ou.dev, oc.dev, stats, sequential);
