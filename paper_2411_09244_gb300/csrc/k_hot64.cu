@@ -322,25 +322,6 @@ __global__ void k_step_w(const double* __restrict__ CMt, const double* __restric
   }
 }
 
-// parareal correction of eq. (2.7) at coarse step n: x_{n+1} = g + F_n - G_old_n
-__global__ void k_pr_update(const double* __restrict__ gu, const double* __restrict__ gw,
-                            const double* __restrict__ fu, const double* __restrict__ fw,
-                            double* __restrict__ Gu, double* __restrict__ Gw, double* __restrict__ xu,
-                            double* __restrict__ xw, int d1, int d2, int first_sweep) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d1 + d2; e += gridDim.x * blockDim.x) {
-    if (e < d1) {
-      double g = gu[e];
-      xu[e] = first_sweep ? g : g + fu[e] - Gu[e];
-      Gu[e] = g;
-    } else {
-      int j = e - d1;
-      double g = gw[j];
-      xw[j] = first_sweep ? g : g + fw[j] - Gw[j];
-      Gw[j] = g;
-    }
-  }
-}
-
 // jump of eq. (2.8) per coarse time: ||du||^2 + ||dw||^2 + 2 du^T CM dw;
 // CTA (n-1, part) handles rows i = part, part + JS, ... of CM and adds its
 // partial sum to jump2[n-1] (zeroed by the caller); k_max_fin takes sqrt
@@ -975,14 +956,16 @@ void apply_F_dev(Ctx* c, const double* in, int count, const double* f_nodes, con
 
 void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* Ut, const float* Wt, int ldu,
                    int ldw, int P, int ncols, float* out);
-void mx_contract_umma(Ctx* c, int mode, const float* Chi, const float* Clo, int M, int Kp, const float* Ut,
-                      const float* Wt, int ldu, int ldw, int ncols, float* out, int* err);
+void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
+                      const float* Blo, int ncols, int nsplit, float* out, int* err);
+int mx_umma_split(int M, int Kp, int ncols, int maxs);
 void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const float* lam1, const float* src,
                      const float* b1, const double* amp, const float2* tw, const float2* dsh, const float2* dshbr,
-                     const float* bpow, double* accU);
-void mx_w_sweep32(Ctx* c, const float* S, int nact, float* Wt, int ldw, const float* lam2, const float* src,
-                  const float* b2, const double* amp, double* accW);
-void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, float* Wt, int ldu, int ldw);
+                     const float* bpow, double* accU, float* B1h, float* B1l);
+void mx_w_sweep32(Ctx* c, const float* S, int nsl, size_t slice, int nact, float* Wt, int ldw, const float* lam2,
+                  const float* src, const float* b2, const double* amp, double* accW, float* B0h, float* B0l);
+void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, float* Wt, int ldu, int ldw,
+               float* B0h, float* B0l);
 void mx_ends32(Ctx* c, const float* Ut, const float* Wt, int ldu, int ldw, int nact, double* Fu, double* Fw);
 void mx_promote(Ctx* c, const float* Ut, const float* Wt, int ldu, int ldw, const double* Su, const double* Sw,
                 double* Zu, double* Zw);
@@ -996,28 +979,6 @@ void mx_to_f32(Ctx* c, const double* x, long long n, float* y);
 
 namespace {
 
-// x_{n+1} = g + F_n - G_old_n (+ c_{n+1}); first sweep: x_{n+1} = g (+ c_{n+1})
-__global__ void k_pr_update_c(const double* __restrict__ gu, const double* __restrict__ gw,
-                              const double* __restrict__ fu, const double* __restrict__ fw,
-                              const double* __restrict__ cu, const double* __restrict__ cw,
-                              double* __restrict__ Gu, double* __restrict__ Gw, double* __restrict__ xu,
-                              double* __restrict__ xw, int d1, int d2, int first_sweep) {
-  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d1 + d2; e += gridDim.x * blockDim.x) {
-    if (e < d1) {
-      double g = gu[e];
-      double v = first_sweep ? g : g + fu[e] - Gu[e];
-      xu[e] = cu ? v + cu[e] : v;
-      Gu[e] = g;
-    } else {
-      int j = e - d1;
-      double g = gw[j];
-      double v = first_sweep ? g : g + fw[j] - Gw[j];
-      xw[j] = cw ? v + cw[j] : v;
-      Gw[j] = g;
-    }
-  }
-}
-
 __global__ void k_axpy2(const double* __restrict__ a, const double* __restrict__ b, long long n,
                         double* __restrict__ out) {
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1026,10 +987,15 @@ __global__ void k_axpy2(const double* __restrict__ a, const double* __restrict__
 
 }  // namespace
 
+constexpr int MX_MAX_SPLIT = 4;
+
 struct Mx {
   bool ready = false;
   int N = 0, P = 0, d1 = 0, d2 = 0, ldu = 0, ldw = 0;
-  float *Rhi = nullptr, *Rlo = nullptr, *Shi = nullptr, *Slo = nullptr;  // TF32 splits of AR, AS (padded)
+  // tensor-core operands (TF32 pairs): couplings [rows][2 ld] and the column
+  // maps of the trajectories [N P][2 ld] (pad entries stay zero)
+  float *Rhi = nullptr, *Rlo = nullptr, *Shi = nullptr, *Slo = nullptr;
+  float *B0h = nullptr, *B0l = nullptr, *B1h = nullptr, *B1l = nullptr;
   int* err = nullptr;
   float *AR32 = nullptr, *AS32 = nullptr, *lam1f = nullptr, *lam2f = nullptr, *b1f = nullptr, *b2f = nullptr,
         *bpowf = nullptr;
@@ -1039,15 +1005,29 @@ struct Mx {
   double *Su = nullptr, *Sw = nullptr, *YSu = nullptr, *YSw = nullptr;
   double *Zu = nullptr, *Zw = nullptr, *R64 = nullptr, *S64 = nullptr, *Cu = nullptr, *Cw = nullptr;
   double *Yu = nullptr, *Yw = nullptr, *zero = nullptr;
+  bool tensor = false;
+  std::vector<void*> bufs;  // every device buffer above
 };
 
 static Mx& mx_prepare(Ctx* c) {
   if (c->scratch.empty()) c->scratch.push_back({new Mx(), 0});
   Mx& M = *reinterpret_cast<Mx*>(c->scratch[0].first);
   const int N = c->N, P = c->P, d1 = c->d1, d2 = c->d2;
-  if (M.ready && M.N == N && M.P == P && M.d1 == d1 && M.d2 == d2) return M;
-  auto Fa = [&](size_t n) { return (float*)dalloc(c, std::max<size_t>(n, 1) * 4); };
-  auto Da = [&](size_t n) { return (double*)dalloc(c, std::max<size_t>(n, 1) * 8); };
+  const bool tensor = (c->precision == PINT_MIXED);
+  if (M.ready && M.N == N && M.P == P && M.d1 == d1 && M.d2 == d2 && M.tensor == tensor) return M;
+  if (M.ready) {  // shapes or precision changed: release the old buffers
+    for (void* b : M.bufs) dfree(c, b);
+    M = Mx();
+  }
+  auto Fa = [&](size_t n) {
+    M.bufs.push_back(dalloc(c, std::max<size_t>(n, 1) * 4));
+    return (float*)M.bufs.back();
+  };
+  auto Da = [&](size_t n) {
+    M.bufs.push_back(dalloc(c, std::max<size_t>(n, 1) * 8));
+    return (double*)M.bufs.back();
+  };
+  M.tensor = tensor;
   M.N = N;
   M.P = P;
   M.d1 = d1;
@@ -1056,21 +1036,32 @@ static Mx& mx_prepare(Ctx* c) {
   M.ldu = ldu;
   M.ldw = ldw;
   M.AR32 = Fa((size_t)d1 * 2 * ldw);
-  M.Rhi = Fa((size_t)d1 * 2 * ldw);
-  M.Rlo = Fa((size_t)d1 * 2 * ldw);
   M.AS32 = Fa((size_t)d2 * 2 * ldu);
-  M.Shi = Fa((size_t)d2 * 2 * ldu);
-  M.Slo = Fa((size_t)d2 * 2 * ldu);
-  M.err = (int*)dalloc(c, 16);
+  if (tensor) {
+    M.Rhi = Fa((size_t)d1 * 2 * ldw);
+    M.Rlo = Fa((size_t)d1 * 2 * ldw);
+    M.Shi = Fa((size_t)d2 * 2 * ldu);
+    M.Slo = Fa((size_t)d2 * 2 * ldu);
+    const size_t n0 = (size_t)N * P * 2 * ldw, n1 = (size_t)N * P * 2 * ldu;
+    M.B0h = Fa(n0);
+    M.B0l = Fa(n0);
+    M.B1h = Fa(n1);
+    M.B1l = Fa(n1);
+    PINT_CUDA(cudaMemsetAsync(M.B0h, 0, n0 * 4, c->stream));
+    PINT_CUDA(cudaMemsetAsync(M.B0l, 0, n0 * 4, c->stream));
+    PINT_CUDA(cudaMemsetAsync(M.B1h, 0, n1 * 4, c->stream));
+    PINT_CUDA(cudaMemsetAsync(M.B1l, 0, n1 * 4, c->stream));
+  }
+  M.err = (int*)Fa(4);
   PINT_CUDA(cudaMemsetAsync(M.err, 0, 16, c->stream));
   M.lam1f = Fa(d1);
   M.lam2f = Fa(d2);
   M.b1f = Fa(d1);
   M.b2f = Fa(d2);
   M.bpowf = Fa(65);
-  M.twf = (float2*)dalloc(c, 64 * sizeof(float2));
-  M.dshf = (float2*)dalloc(c, 64 * sizeof(float2));
-  M.dshbr = (float2*)dalloc(c, 64 * sizeof(float2));
+  M.twf = (float2*)Fa(128);
+  M.dshf = (float2*)Fa(128);
+  M.dshbr = (float2*)Fa(128);
   M.Ut = Fa((size_t)N * (P + 1) * ldu);
   M.Wt = Fa((size_t)N * (P + 1) * ldw);
   M.dUt = Fa((size_t)N * (P + 1) * ldu);
@@ -1081,7 +1072,7 @@ static Mx& mx_prepare(Ctx* c) {
   PINT_CUDA(cudaMemsetAsync(M.dUt, 0, (size_t)N * (P + 1) * ldu * 4, c->stream));
   PINT_CUDA(cudaMemsetAsync(M.dWt, 0, (size_t)N * (P + 1) * ldw * 4, c->stream));
   M.R = Fa((size_t)N * P * d1);
-  M.S = Fa((size_t)N * P * d2);
+  M.S = Fa((size_t)MX_MAX_SPLIT * N * P * d2);  // K-sliced partial sums of the second contraction
   M.srcU = Fa((size_t)N * P * d1);
   M.srcW = Fa((size_t)N * P * d2);
   M.Su = Da((size_t)(N + 1) * d1);
@@ -1141,21 +1132,25 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
   const int ncols = nact * P;
   const int ldu = M.ldu, ldw = M.ldw;
   const bool tensor = (c->precision == PINT_MIXED);
-  mx_init32(c, xs_u, xs_w, nact, Ut, Wt, ldu, ldw);
+  const int nsl = tensor ? mx_umma_split(d2, 2 * ldu, ncols, MX_MAX_SPLIT) : 1;
+  // column maps of the active window start at column 0 of B0 / B1
+  mx_init32(c, xs_u, xs_w, nact, Ut, Wt, ldu, ldw, M.B0h, M.B0l);
   int it = 0;
   *bad = false;
   for (it = 1; it <= wr_max; ++it) {
     PINT_CUDA(cudaMemsetAsync(H.acc, 0, (size_t)2 * nact * P * 8, c->stream));
     PINT_CUDA(cudaEventRecord(H.ev[0], c->stream));
-    if (tensor) mx_contract_umma(c, 0, M.Rhi, M.Rlo, d1, 2 * ldw, Ut, Wt, ldu, ldw, ncols, M.R, M.err);
+    if (tensor) mx_contract_umma(c, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, M.R, M.err);
     else mx_contract32(c, 0, M.AR32, d1, 2 * ldw, Ut, Wt, ldu, ldw, P, ncols, M.R);
     PINT_CUDA(cudaEventRecord(H.ev[1], c->stream));
-    mx_time_solve32(c, M.R, nact, Ut, ldu, M.lam1f, srcU, M.b1f, amp_act, M.twf, M.dshf, M.dshbr, M.bpowf, H.acc);
+    mx_time_solve32(c, M.R, nact, Ut, ldu, M.lam1f, srcU, M.b1f, amp_act, M.twf, M.dshf, M.dshbr, M.bpowf, H.acc,
+                    M.B1h, M.B1l);
     PINT_CUDA(cudaEventRecord(H.ev[2], c->stream));
-    if (tensor) mx_contract_umma(c, 1, M.Shi, M.Slo, d2, 2 * ldu, Ut, Wt, ldu, ldw, ncols, M.S, M.err);
+    if (tensor) mx_contract_umma(c, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, nsl, M.S, M.err);
     else mx_contract32(c, 1, M.AS32, d2, 2 * ldu, Ut, Wt, ldu, ldw, P, ncols, M.S);
     PINT_CUDA(cudaEventRecord(H.ev[3], c->stream));
-    mx_w_sweep32(c, M.S, nact, Wt, ldw, M.lam2f, srcW, M.b2f, amp_act, H.acc + (size_t)nact * P);
+    mx_w_sweep32(c, M.S, tensor ? nsl : 1, (size_t)ncols * d2, nact, Wt, ldw, M.lam2f, srcW, M.b2f, amp_act,
+                 H.acc + (size_t)nact * P, M.B0h, M.B0l);
     k_wr_norm<<<1, 1024, 0, c->stream>>>(H.acc, 2 * nact * P, H.red);
     PINT_LAUNCH_CHECK();
     c->launches++;

@@ -16,6 +16,16 @@ namespace {
 
 inline unsigned nbl(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 
+// x as a TF32 pair: hi = tf32(x), lo = tf32(x - hi) (round to nearest, ties away)
+__device__ __forceinline__ void put_split(float* __restrict__ hi, float* __restrict__ lo, size_t o, float x) {
+  uint32_t h, l;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
+  const float hf = __uint_as_float(h);
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(x - hf));
+  hi[o] = hf;
+  lo[o] = __uint_as_float(l);
+}
+
 // FP32 contraction with the WR column maps (see k_wr_gemm in k_hot64.cu):
 // MODE 0: out = AR [w_p ; w_{max(p-1,0)}], MODE 1: out = AS [u_p - u_{max(p-1,0)} ; u_{p+1}]
 // Trajectories use padded strides ldu, ldw (multiples of 32, pad entries 0);
@@ -126,7 +136,8 @@ __global__ void __launch_bounds__(128) k_time_solve32(const float* __restrict__ 
                                                       const float2* __restrict__ tw,
                                                       const float2* __restrict__ dsh,
                                                       const float* __restrict__ bpow, int pow2,
-                                                      double* __restrict__ accU) {
+                                                      double* __restrict__ accU, float* __restrict__ B1h,
+                                                      float* __restrict__ B1l) {
   const int nloc = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   __shared__ double sh[64];
@@ -152,6 +163,15 @@ __global__ void __launch_bounds__(128) k_time_solve32(const float* __restrict__ 
     if (pow2) fft32(v, P, tw, +1);
     else dft32(v, tmp, P, tw, +1);
     for (int p = 0; p < P; ++p) unew[p] = v[p].x / ((float)P * bpow[p]);
+    if (B1h) {  // second-contraction column map [u_p - u_{p-1} ; u_{p+1}]
+      const float u0 = Un[i];
+      for (int p = 0; p < P; ++p) {
+        const size_t o = ((size_t)nloc * P + p) * 2 * ldu + i;
+        const float dp = (p == 0) ? 0.f : unew[p - 1] - (p == 1 ? u0 : unew[p - 2]);
+        put_split(B1h, B1l, o, dp);
+        put_split(B1h, B1l, o + ldu, unew[p]);
+      }
+    }
   }
   for (int p = 0; p < P; ++p) {
     double du = 0.0;
@@ -216,16 +236,19 @@ __global__ void __launch_bounds__(128) k_time_solve32_t(const float* __restrict_
                                                         const double* __restrict__ amp, float alpha, float dt,
                                                         const float2* __restrict__ tw,
                                                         const float2* __restrict__ dsh,
-                                                        const float* __restrict__ bpow, double* __restrict__ accU) {
+                                                        const float* __restrict__ bpow, double* __restrict__ accU,
+                                                        float* __restrict__ B1h, float* __restrict__ B1l) {
   const int nloc = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
   float re[P], im[P];
   float* Un = Ut + (size_t)nloc * (P + 1) * ldu;
   const bool act = i < d1;
+  float u0 = 0.f;
   if (act) {
     const float cs = src ? 0.f : b1[i] * (float)amp[nloc];
-    const float first = (Un[i] - alpha * Un[(size_t)P * ldu + i]) / dt;
+    u0 = Un[i];
+    const float first = (u0 - alpha * Un[(size_t)P * ldu + i]) / dt;
 #pragma unroll
     for (int p = 0; p < P; ++p) {
       float y = R[((size_t)nloc * P + p) * d1 + i] + (src ? src[((size_t)nloc * P + p) * d1 + i] : cs);
@@ -246,6 +269,15 @@ __global__ void __launch_bounds__(128) k_time_solve32_t(const float* __restrict_
     dit_stage<P, 2>(re, im, tw, -1.f);                 // inverse from bit-reversed input (without 1/P)
 #pragma unroll
     for (int p = 0; p < P; ++p) re[p] = re[p] / ((float)P * bpow[p]);
+    if (B1h) {  // second-contraction column map [u_p - u_{p-1} ; u_{p+1}]
+#pragma unroll
+      for (int p = 0; p < P; ++p) {
+        const size_t o = ((size_t)nloc * P + p) * 2 * ldu + i;
+        const float dp = (p == 0) ? 0.f : re[p - 1] - (p == 1 ? u0 : re[p - 2]);
+        put_split(B1h, B1l, o, dp);
+        put_split(B1h, B1l, o + ldu, re[p]);
+      }
+    }
   }
 #pragma unroll
   for (int p = 0; p < P; ++p) {
@@ -263,8 +295,9 @@ __global__ void __launch_bounds__(128) k_time_solve32_t(const float* __restrict_
 __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, int d2, int ldw, int P,
                                                    float* __restrict__ Wt, const float* __restrict__ lam2,
                                                    const float* __restrict__ src, const float* __restrict__ b2,
-                                                   const double* __restrict__ amp, float dt,
-                                                   double* __restrict__ accW) {
+                                                   const double* __restrict__ amp, float dt, int nsl,
+                                                   size_t slice, double* __restrict__ accW,
+                                                   float* __restrict__ B0h, float* __restrict__ B0l) {
   const int nloc = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   float* Wn = Wt + (size_t)nloc * (P + 1) * ldw;
@@ -278,10 +311,17 @@ __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, 
     double dw = 0.0;
     if (j < d2) {
       float g = src ? src[((size_t)nloc * P + p) * d2 + j] : cs;
-      float wn = fac * w + S[((size_t)nloc * P + p) * d2 + j] + g;
+      float sv = 0.f;
+      for (int z = 0; z < nsl; ++z) sv += S[(size_t)z * slice + ((size_t)nloc * P + p) * d2 + j];
+      float wn = fac * w + sv + g;
       float old = Wn[(size_t)(p + 1) * ldw + j];
       dw = (double)(wn - old) * (double)(wn - old);
       Wn[(size_t)(p + 1) * ldw + j] = wn;
+      if (B0h && p + 1 < P) {  // first-contraction column map of step p + 1: [w_{p+1} ; w_p]
+        const size_t o = ((size_t)nloc * P + p + 1) * 2 * ldw + j;
+        put_split(B0h, B0l, o, wn);
+        put_split(B0h, B0l, o + ldw, w);
+      }
       w = wn;
     }
     dw = pintd::warp_sum(dw);
@@ -289,13 +329,26 @@ __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, 
   }
 }
 
+// constant initial trajectories; with B0h, also the first-contraction column
+// map [w_p ; w_{p-1}] = [x_w ; x_w] of every step
 __global__ void k_init32(const double* __restrict__ Xu, const double* __restrict__ Xw, int d1, int d2, int ldu,
-                         int ldw, int P, float* __restrict__ Ut, float* __restrict__ Wt) {
+                         int ldw, int P, float* __restrict__ Ut, float* __restrict__ Wt, float* __restrict__ B0h,
+                         float* __restrict__ B0l) {
   const int nloc = blockIdx.y;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < (P + 1) * (d1 + d2); e += gridDim.x * blockDim.x) {
     int p = e / (d1 + d2), k = e % (d1 + d2);
-    if (k < d1) Ut[((size_t)nloc * (P + 1) + p) * ldu + k] = (float)Xu[(size_t)nloc * d1 + k];
-    else Wt[((size_t)nloc * (P + 1) + p) * ldw + (k - d1)] = (float)Xw[(size_t)nloc * d2 + (k - d1)];
+    if (k < d1) {
+      Ut[((size_t)nloc * (P + 1) + p) * ldu + k] = (float)Xu[(size_t)nloc * d1 + k];
+    } else {
+      const int j = k - d1;
+      const float x = (float)Xw[(size_t)nloc * d2 + j];
+      Wt[((size_t)nloc * (P + 1) + p) * ldw + j] = x;
+      if (B0h && p < P) {
+        const size_t o = ((size_t)nloc * P + p) * 2 * ldw + j;
+        put_split(B0h, B0l, o, x);
+        put_split(B0h, B0l, o + ldw, x);
+      }
+    }
   }
 }
 
@@ -392,22 +445,16 @@ __global__ void k_continuity(const double* __restrict__ Zu, const double* __rest
 }
 
 // A (rows x 2 dk, FP64) -> A32 (rows x 2 ld, FP32), halves at columns 0 and ld,
-// pad columns zero; also the TF32 hi / lo split of every entry
+// pad columns zero; with hi, also the TF32 pair of every entry
 __global__ void k_pad_split(const double* __restrict__ A, int rows, int dk, int ld, float* __restrict__ a32,
                             float* __restrict__ hi, float* __restrict__ lo) {
   long long tot = (long long)rows * 2 * ld;
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
     int r = (int)(e / (2 * ld)), k = (int)(e % (2 * ld));
     int seg = k / ld, j = k % ld;
-    float v = (j < dk) ? (float)A[(size_t)r * 2 * dk + seg * dk + j] : 0.f;
+    const float v = (j < dk) ? (float)A[(size_t)r * 2 * dk + seg * dk + j] : 0.f;
     a32[e] = v;
-    uint32_t h;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(v));
-    float hf = __uint_as_float(h);
-    uint32_t l;
-    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(l) : "f"(v - hf));
-    hi[e] = hf;
-    lo[e] = __uint_as_float(l);
+    if (hi) put_split(hi, lo, (size_t)e, v);
   }
 }
 
@@ -431,36 +478,38 @@ void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* 
 
 void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const float* lam1, const float* src,
                      const float* b1, const double* amp, const float2* tw, const float2* dsh, const float2* dshbr,
-                     const float* bpow, double* accU) {
+                     const float* bpow, double* accU, float* B1h, float* B1l) {
   const int P = c->P;
   const dim3 grid(nbl(c->d1, 128), nact);
   const float al = (float)c->alpha, dt = (float)c->dt;
   if (P == 64)
     k_time_solve32_t<64><<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al, dt, tw, dshbr, bpow,
-                                                       accU);
+                                                       accU, B1h, B1l);
   else if (P == 32)
     k_time_solve32_t<32><<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al, dt, tw, dshbr, bpow,
-                                                       accU);
+                                                       accU, B1h, B1l);
   else if (P == 16)
     k_time_solve32_t<16><<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al, dt, tw, dshbr, bpow,
-                                                       accU);
+                                                       accU, B1h, B1l);
   else
     k_time_solve32<<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, P, Ut, lam1, src, b1, amp, al, dt, tw, dsh, bpow,
-                                                (P & (P - 1)) == 0, accU);
+                                                (P & (P - 1)) == 0, accU, B1h, B1l);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
 
-void mx_w_sweep32(Ctx* c, const float* S, int nact, float* Wt, int ldw, const float* lam2, const float* src,
-                  const float* b2, const double* amp, double* accW) {
+// S holds nsl K-slices of the contraction, slice floats apart (summed here)
+void mx_w_sweep32(Ctx* c, const float* S, int nsl, size_t slice, int nact, float* Wt, int ldw, const float* lam2,
+                  const float* src, const float* b2, const double* amp, double* accW, float* B0h, float* B0l) {
   k_w_sweep32<<<dim3(nbl(c->d2, 128), nact), 128, 0, c->stream>>>(S, c->d2, ldw, c->P, Wt, lam2, src, b2, amp,
-                                                                  (float)c->dt, accW);
+                                                                  (float)c->dt, nsl, slice, accW, B0h, B0l);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
 
-void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, float* Wt, int ldu, int ldw) {
-  k_init32<<<dim3(32, nact), 256, 0, c->stream>>>(Xu, Xw, c->d1, c->d2, ldu, ldw, c->P, Ut, Wt);
+void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, float* Wt, int ldu, int ldw,
+               float* B0h, float* B0l) {
+  k_init32<<<dim3(32, nact), 256, 0, c->stream>>>(Xu, Xw, c->d1, c->d2, ldu, ldw, c->P, Ut, Wt, B0h, B0l);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }

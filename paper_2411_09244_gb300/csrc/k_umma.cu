@@ -1,45 +1,58 @@
 // WR contractions on the 5th-generation tensor cores (tcgen05, kind::tf32).
 //
-// The two contractions of one WR iteration (Section 4.2; a2 and a6 of the
-// hot path) are out[col][i] = sum_k T(k, col) C(i, k), where col = (interval,
-// step) runs over the N P trajectory columns, i over the modes of the output
-// space and C is the coupling operator ([-(CA + CM/dt) | CM/dt] or
-// [-CM^T | -dt CA^T], rows padded to K = 2 ld).  T(k, col) is gathered from the
-// FP32 trajectories with the step shifts of eqs. (4.8)-(4.9):
-//   MODE 0: T = [w_p ; w_{max(p-1,0)}]      MODE 1: T = [u_p - u_{max(p-1,0)} ; u_{p+1}]
+// The two contractions of one WR iteration (Section 4.2, eqs. (4.8)-(4.9))
+// are out[col][i] = sum_k C(i, k) B(col, k): i runs over the modes of the
+// output space, col = (interval, step) over the trajectory columns, C is the
+// coupling operator ([-(CA + CM/dt) | CM/dt] or [-CM^T | -dt CA^T], both K
+// halves padded to ld with zeros) and B(col, :) the column map of the
+// trajectories (written by the producing kernels of the iteration):
+//   first contraction:  B = [w_p ; w_{max(p-1,0)}]
+//   second contraction: B = [u_p - u_{max(p-1,0)} ; u_{p+1}].
+// FP32 accuracy from TF32 operands: every operand is stored as a hi/lo pair
+// (hi = tf32(x), lo = tf32(x - hi)) and each K step issues three MMAs
+// (hi hi + hi lo + lo hi); the dropped lo lo term is below FP32 rounding.
 //
-// One CTA computes a 128-column x BN-mode tile: MMA M = 128 trajectory
-// columns (A operand, built in shared memory by all threads), N = BN modes (B
-// operand = coupling rows), accumulator in TMEM (128 lanes x BN FP32
-// columns), so that each thread's TMEM row is a contiguous run of output
-// modes.  FP32 accuracy from TF32 operands: x = hi + lo with hi = tf32(x),
-// lo = tf32(x - hi), three MMAs per K step (hi hi + hi lo + lo hi).
-// Shared memory holds two K-blocks of 32 in the canonical K-major layout
-// without swizzle: 8-row x 16-byte core matrices, the 8 K-chunks of a row
-// group contiguous (leading byte offset 128 B), row groups 1024 B apart
-// (stride byte offset).  One thread issues the MMAs and commits them to the
-// stage's mbarrier; waits are bounded and set an error flag on expiry.
+// One CTA computes a 128-mode x 128-column tile of one K slice: MMA M = 128
+// (A = coupling rows), N = 128 (B = trajectory columns), FP32 accumulator in
+// TMEM with lane = mode, so the epilogue's stores are coalesced along modes.
+// Warp 0 (one lane) streams 32-wide K stages with TMA (128-byte swizzle) into
+// a ring of STAGES buffers; warp 1 allocates TMEM and one lane issues the
+// MMAs; all four warps drain the accumulator.  "full" barriers complete on the
+// TMA transaction count, "empty" barriers on tcgen05.commit.  Every wait is
+// bounded: on expiry the kernel records an error flag, waits (bounded) for the
+// copies it has in flight, frees its TMEM and returns.
 #include "common.cuh"
+
+#include <cuda.h>
+#include <cudaTypedefs.h>
 
 namespace pint {
 
 namespace {
 
-constexpr int UM = 128;   // MMA M (trajectory columns per CTA)
-constexpr int KB = 32;    // K elements per stage
-constexpr int THREADS = 256;
-constexpr int WAIT_LIMIT = 1 << 20;
+constexpr int TM = 128;  // modes per tile (MMA M)
+constexpr int TN = 128;  // trajectory columns per tile (MMA N)
+constexpr int KB = 32;   // K elements per stage = one 128-byte swizzle row
+constexpr int STAGES = 3;
+constexpr int THREADS = 128;
+constexpr int WAIT_LIMIT = 1 << 22;
+constexpr int OPB = TM * KB * 4;      // bytes of one operand tile (16 KB)
+constexpr int STAGE_BYTES = 4 * OPB;  // A hi, A lo, B hi, B lo
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + slack for 1024-byte alignment
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-__device__ __forceinline__ uint64_t umma_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
+// 1024 bytes apart (stride byte offset), descriptor version 1
+__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo & 0x3FFFFu) >> 4) << 16;
-  d |= (uint64_t)((sbo & 0x3FFFFu) >> 4) << 32;
-  d |= (uint64_t)1 << 46;  // descriptor version; base offset 0, no swizzle
+  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;            // version
+  d |= (uint64_t)2 << 61;            // layout: 128-byte swizzle
   return d;
 }
 
@@ -52,11 +65,17 @@ __device__ __forceinline__ void mma_tf32(uint32_t dt, uint64_t a, uint64_t b, ui
   asm volatile(
       "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
       "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}\n" ::"r"(dt),
-      "l"(a), "l"(b), "r"(idesc), "r"(acc));
+      "l"(a), "l"(b), "r"(idesc), "r"(acc)
+      : "memory");
 }
 
 __device__ __forceinline__ void mma_commit(uint64_t* bar) {
   asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_u32(bar))
+               : "memory");
+}
+
+__device__ __forceinline__ void bar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
                : "memory");
 }
 
@@ -74,194 +93,211 @@ __device__ __forceinline__ bool bar_wait(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-__device__ __forceinline__ float tf32_rna(float x) {
-  uint32_t h;
-  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(h) : "f"(x));
-  return __uint_as_float(h);
+__device__ __forceinline__ void tma_load_2d(void* dst, const CUtensorMap* map, uint64_t* bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], "
+      "[%4];" ::"r"(smem_u32(dst)),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(smem_u32(bar))
+      : "memory");
 }
 
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, float* v) {
-  uint32_t r[16];
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
+  uint32_t r[32];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+      "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
+        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
+        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-// byte offset of (row, k) in the canonical no-swizzle K-major tile (KB = 32)
-__device__ __forceinline__ uint32_t tile_off(int row, int chunk) {
-  return (uint32_t)((row >> 3) * 1024 + chunk * 128 + (row & 7) * 16);
-}
-
-template <int MODE, int BN>
-__global__ void __launch_bounds__(THREADS) k_wr_umma(const float* __restrict__ Chi, const float* __restrict__ Clo,
-                                                     int M, int Kp, const float* __restrict__ Ut,
-                                                     const float* __restrict__ Wt, int ldu, int ldw, int P,
-                                                     int ncols, float* __restrict__ out, int* __restrict__ err) {
-  constexpr int A_BYTES = UM * KB * 4;   // 16 KB
-  constexpr int B_BYTES = BN * KB * 4;
-  constexpr int STAGE = 2 * A_BYTES + 2 * B_BYTES;
-  constexpr int TCOLS = (BN <= 32) ? 32 : (BN <= 64) ? 64 : (BN <= 128) ? 128 : 256;
-  constexpr uint32_t IDESC = idesc_tf32(UM, BN);
-  extern __shared__ __align__(1024) uint8_t smem[];
-  __shared__ __align__(8) uint64_t bars[2];
+// out + z * ncols * M: the K slice [z kspan, (z + 1) kspan) of the product
+__global__ void __launch_bounds__(THREADS, 1)
+    k_wr_umma(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
+              const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, int M, int ncols,
+              int kspan, float* __restrict__ out, int* __restrict__ err) {
+  constexpr uint32_t IDESC = idesc_tf32(TM, TN);
+  extern __shared__ uint8_t smem_raw[];
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
   __shared__ uint32_t s_tmem;
   __shared__ int s_fail;
+  // the 128-byte swizzle pattern repeats every 1024 bytes: align the ring to it
+  uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
 
-  const int col0 = blockIdx.x * UM;
-  const int row0 = blockIdx.y * BN;
+  const int col0 = blockIdx.x * TN;
+  const int row0 = blockIdx.y * TM;
+  const int kbeg = blockIdx.z * kspan;
+  const int nkb = kspan / KB;
   const int tid = threadIdx.x, warp = tid >> 5;
   if (tid == 0) {
     s_fail = 0;
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[0])));
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&bars[1])));
+    for (int s = 0; s < STAGES; ++s) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 0) {
+  if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                 "r"(TCOLS));
+                 "r"(TN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
-  const int nkb = Kp / KB;
-  const int ld = (MODE == 0) ? ldw : ldu;
 
-  int last = -1;  // index of the last committed K-block (uniform)
-  for (int kb = 0; kb < nkb; ++kb) {
-    const int s = kb & 1;
-    uint8_t* base = smem + s * STAGE;
-    if (kb >= 2) {
-      // the MMAs of K-block kb-2 read this stage: the issuing thread waits for
-      // their commit, the barrier publishes the outcome to every thread
-      if (tid == 0 && !bar_wait(&bars[s], (uint32_t)(((kb - 2) >> 1) & 1))) s_fail = 1;
-      __syncthreads();
-      if (s_fail) break;
-    }
-    const int k0 = kb * KB;
-    const int seg = k0 / ld, j0 = k0 - seg * ld;
-    // A: trajectory columns, float4 per (column, 4-k chunk)
-    for (int idx = tid; idx < UM * 8; idx += THREADS) {
-      const int rlow = idx & 7, chunk = (idx >> 3) & 7, rg = idx >> 6;
-      const int r = rg * 8 + rlow;
-      const int col = col0 + r;
-      float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-      if (col < ncols) {
-        const int n = col / P, p = col - n * P;
-        if (MODE == 0) {
-          const int q = (seg == 0) ? p : (p >= 1 ? p - 1 : 0);
-          v = *reinterpret_cast<const float4*>(Wt + ((size_t)n * (P + 1) + q) * ldw + j0 + 4 * chunk);
-        } else if (seg == 0) {
-          float4 a = *reinterpret_cast<const float4*>(Ut + ((size_t)n * (P + 1) + p) * ldu + j0 + 4 * chunk);
-          float4 b = *reinterpret_cast<const float4*>(Ut + ((size_t)n * (P + 1) + (p >= 1 ? p - 1 : 0)) * ldu +
-                                                      j0 + 4 * chunk);
-          v = make_float4(a.x - b.x, a.y - b.y, a.z - b.z, a.w - b.w);
-        } else {
-          v = *reinterpret_cast<const float4*>(Ut + ((size_t)n * (P + 1) + p + 1) * ldu + j0 + 4 * chunk);
-        }
+  if (tid == 0) {
+    // ---------------- TMA producer ----------------
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES, use = kb / STAGES;
+      if (use >= 1 && !bar_wait(&empty[s], (uint32_t)((use - 1) & 1))) {
+        s_fail = 1;
+        break;
       }
-      float4 h = make_float4(tf32_rna(v.x), tf32_rna(v.y), tf32_rna(v.z), tf32_rna(v.w));
-      float4 l = make_float4(tf32_rna(v.x - h.x), tf32_rna(v.y - h.y), tf32_rna(v.z - h.z), tf32_rna(v.w - h.w));
-      const uint32_t o = tile_off(r, chunk);
-      *reinterpret_cast<float4*>(base + o) = h;
-      *reinterpret_cast<float4*>(base + A_BYTES + o) = l;
+      uint8_t* base = smem + s * STAGE_BYTES;
+      const int k0 = kbeg + kb * KB;
+      bar_expect_tx(&full[s], STAGE_BYTES);
+      tma_load_2d(base, &mAh, &full[s], k0, row0);
+      tma_load_2d(base + OPB, &mAl, &full[s], k0, row0);
+      tma_load_2d(base + 2 * OPB, &mBh, &full[s], k0, col0);
+      tma_load_2d(base + 3 * OPB, &mBl, &full[s], k0, col0);
+      issued = kb + 1;
     }
-    // B: coupling rows (already split), float4 per (row, chunk)
-    for (int idx = tid; idx < BN * 8; idx += THREADS) {
-      const int rlow = idx & 7, chunk = (idx >> 3) & 7, rg = idx >> 6;
-      const int r = rg * 8 + rlow;
-      const int row = row0 + r;
-      float4 h = make_float4(0.f, 0.f, 0.f, 0.f), l = h;
-      if (row < M) {
-        h = *reinterpret_cast<const float4*>(Chi + (size_t)row * Kp + k0 + 4 * chunk);
-        l = *reinterpret_cast<const float4*>(Clo + (size_t)row * Kp + k0 + 4 * chunk);
+    // copies still in flight must land before the CTA's shared memory goes
+    for (int s = 0; s < STAGES && s < issued; ++s) {
+      const int last_use = (issued - 1 - s) / STAGES;
+      if (!bar_wait(&full[s], (uint32_t)(last_use & 1))) s_fail = 1;
+    }
+  } else if (tid == 32) {
+    // ---------------- MMA issuer ----------------
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES, use = kb / STAGES;
+      if (!bar_wait(&full[s], (uint32_t)(use & 1))) {
+        s_fail = 1;
+        break;
       }
-      const uint32_t o = tile_off(r, chunk);
-      *reinterpret_cast<float4*>(base + 2 * A_BYTES + o) = h;
-      *reinterpret_cast<float4*>(base + 2 * A_BYTES + B_BYTES + o) = l;
-    }
-    // make the generic-proxy stores visible to the tensor cores
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a_hi = smem_u32(base), a_lo = a_hi + A_BYTES;
-      const uint32_t b_hi = a_hi + 2 * A_BYTES, b_lo = b_hi + B_BYTES;
+      const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
 #pragma unroll
       for (int kk = 0; kk < KB / 8; ++kk) {
-        const uint32_t ko = kk * 256;  // two 16-byte chunks per K = 8 step
-        const uint64_t dah = umma_desc(a_hi + ko, 128, 1024), dal = umma_desc(a_lo + ko, 128, 1024);
-        const uint64_t dbh = umma_desc(b_hi + ko, 128, 1024), dbl = umma_desc(b_lo + ko, 128, 1024);
+        const uint32_t ko = kk * 32;  // K = 8 TF32 = 32 bytes along the swizzle row
+        const uint64_t dah = desc_sw128(base + ko), dal = desc_sw128(base + OPB + ko);
+        const uint64_t dbh = desc_sw128(base + 2 * OPB + ko), dbl = desc_sw128(base + 3 * OPB + ko);
         mma_tf32(tmem, dah, dbh, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
         mma_tf32(tmem, dah, dbl, IDESC, 1u);
         mma_tf32(tmem, dal, dbh, IDESC, 1u);
       }
-      mma_commit(&bars[s]);
+      mma_commit(&empty[s]);
     }
-    last = kb;
+    mma_commit(&done);  // arrives once every MMA issued above has completed
   }
-  // the last commit covers every earlier MMA of the issuing thread
-  if (tid == 0 && last >= 0 && !bar_wait(&bars[last & 1], (uint32_t)((last >> 1) & 1))) s_fail = 1;
+  __syncwarp();
+  // ---------------- epilogue: all four warps ----------------
+  if (!bar_wait(&done, 0u)) s_fail = 1;
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  // epilogue: warp w reads TMEM lanes 32 (w % 4) ..; warps w and w + 4 split the columns
-  if (!s_fail) {
-    const int lane_base = 32 * (warp & 3);
-    const int r = lane_base + (tid & 31);
-    const int col = col0 + r;
-    const int half = (BN / 16 + 1) / 2;  // 16-column chunks per warp half
-    const int c_begin = (warp < 4) ? 0 : half;
-    const int c_end = (warp < 4) ? half : BN / 16;
-    for (int cc = c_begin; cc < c_end; ++cc) {
-      float v[16];
-      tmem_ld16(tmem + ((uint32_t)lane_base << 16) + (uint32_t)(cc * 16), v);
-      if (col < ncols) {
-        float* o = out + (size_t)col * M + row0 + cc * 16;
+  if (!s_fail && nkb > 0) {
+    const int i = row0 + 32 * warp + (tid & 31);  // output mode of this thread (TMEM lane)
+    float* o = out + (size_t)blockIdx.z * ncols * M;
+    for (int cc = 0; cc < TN; cc += 32) {
+      float v[32];
+      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cc, v);
+      if (i < M) {
 #pragma unroll
-        for (int q = 0; q < 16; ++q)
-          if (row0 + cc * 16 + q < M) o[q] = v[q];
+        for (int q = 0; q < 32; ++q) {
+          const int col = col0 + cc + q;
+          if (col < ncols) o[(size_t)col * M + i] = v[q];
+        }
       }
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TCOLS));
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
   if (tid == 0 && s_fail) atomicExch(err, 1);
 }
 
-template <int MODE, int BN>
-void launch(Ctx* c, const float* Chi, const float* Clo, int M, int Kp, const float* Ut, const float* Wt, int ldu,
-            int ldw, int ncols, float* out, int* err) {
-  constexpr int STAGE = 2 * UM * KB * 4 + 2 * BN * KB * 4;
-  constexpr int SMEM = 2 * STAGE;
-  static bool attr = false;
-  if (!attr) {
-    PINT_CUDA(cudaFuncSetAttribute(k_wr_umma<MODE, BN>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM));
-    attr = true;
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    PINT_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    PINT_REQUIRE(p && q == cudaDriverEntryPointSuccess, PINT_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
   }
-  dim3 grid((ncols + UM - 1) / UM, (M + BN - 1) / BN);
-  k_wr_umma<MODE, BN><<<grid, THREADS, SMEM, c->stream>>>(Chi, Clo, M, Kp, Ut, Wt, ldu, ldw, c->P, ncols, out,
-                                                          err);
-  PINT_LAUNCH_CHECK();
-  c->launches++;
+  return fn;
+}
+
+// row-major [rows][Kp] FP32 matrix, boxes of 128 rows x 32 K with the
+// 128-byte swizzle; rows past the end read as zero
+CUtensorMap make_map(const float* base, int rows, int Kp) {
+  CUtensorMap m;
+  const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)Kp * 4};
+  const cuuint32_t box[2] = {(cuuint32_t)KB, 128u};
+  const cuuint32_t estr[2] = {1u, 1u};
+  PINT_REQUIRE(((uintptr_t)base & 15) == 0 && Kp % KB == 0, PINT_ERR_BAD_ARG, "contraction operand misaligned");
+  const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides,
+                                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                 CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  PINT_REQUIRE(r == CUDA_SUCCESS, PINT_ERR_CUDA, "cuTensorMapEncodeTiled failed");
+  return m;
 }
 
 }  // namespace
 
-// MODE 0: M = d1 modes, Kp = 2 ldw; MODE 1: M = d2, Kp = 2 ldu.  Mode tile
-// widths keep the grid near a multiple of the 152 SMs for N P = 4096 columns.
-void mx_contract_umma(Ctx* c, int mode, const float* Chi, const float* Clo, int M, int Kp, const float* Ut,
-                      const float* Wt, int ldu, int ldw, int ncols, float* out, int* err) {
-  if (mode == 0)
-    launch<0, 224>(c, Chi, Clo, M, Kp, Ut, Wt, ldu, ldw, ncols, out, err);
-  else
-    launch<1, 48>(c, Chi, Clo, M, Kp, Ut, Wt, ldu, ldw, ncols, out, err);
+// K split that best fills the SMs (one CTA per SM: the stage ring takes most
+// of the shared memory): minimises waves(tiles * s) / s over s <= maxs.
+int mx_umma_split(int M, int Kp, int ncols, int maxs) {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  const long long tiles = (long long)((ncols + TN - 1) / TN) * ((M + TM - 1) / TM);
+  int best = 1;
+  double best_t = 1e300;
+  for (int s = 1; s <= maxs; ++s) {
+    if (Kp % (KB * s)) continue;
+    const double t = (double)((tiles * s + sms - 1) / sms) / s;
+    if (t < best_t * 0.999) {
+      best_t = t;
+      best = s;
+    }
+  }
+  return best;
+}
+
+// out[z][col][i] = sum over the z-th K slice of A(i, k) B(col, k); A = Ahi + Alo
+// ([M][Kp]), B = Bhi + Blo ([ncols][Kp]), TF32 pairs in FP32 containers, both
+// 16-byte aligned with Kp a multiple of 32 nsplit.
+void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
+                      const float* Blo, int ncols, int nsplit, float* out, int* err) {
+  static bool attr = false;
+  if (!attr) {
+    PINT_CUDA(cudaFuncSetAttribute(k_wr_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr = true;
+  }
+  PINT_REQUIRE(nsplit >= 1 && Kp % (KB * nsplit) == 0, PINT_ERR_BAD_ARG,
+               "contraction K not divisible by the split");
+  if (ncols <= 0 || M <= 0) return;
+  const CUtensorMap ah = make_map(Ahi, M, Kp), al = make_map(Alo, M, Kp);
+  const CUtensorMap bh = make_map(Bhi, ncols, Kp), bl = make_map(Blo, ncols, Kp);
+  dim3 grid((ncols + TN - 1) / TN, (M + TM - 1) / TM, nsplit);
+  k_wr_umma<<<grid, THREADS, SMEM_BYTES, c->stream>>>(ah, al, bh, bl, M, ncols, Kp / nsplit, out, err);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
 }
 
 }  // namespace pint
