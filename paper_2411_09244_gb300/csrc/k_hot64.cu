@@ -580,7 +580,11 @@ struct GSArgs {
   int* err;
 };
 
+constexpr int GS_SPLIT = 8;                          // warps per w-phase row
+constexpr int GS_ROWS = GS_THREADS / 32 / GS_SPLIT;   // w-phase rows per block and pass
+
 __global__ void __launch_bounds__(GS_THREADS) k_g_sweep(GSArgs a) {
+  __shared__ double s_part[GS_THREADS / 32];
   const int lane = threadIdx.x & 31;
   const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -598,18 +602,28 @@ __global__ void __launch_bounds__(GS_THREADS) k_g_sweep(GSArgs a) {
       if (lane == 0) a.gu[i] = (xu[i] - a.Dt * acc + a.Dt * am * a.b1[i]) / (1.0 + a.Dt * a.lam1[i]);
     }
     if (!gs_barrier(a.count, a.gen, gridDim.x, a.err)) return;
-    // w-phase: w' = (1 - Dt lambda2) w - Dt CA^T u' + Dt a b2, then eq. (2.7)
-    for (int j = gwarp; j < d2; j += nwarps) {
+    // w-phase: w' = (1 - Dt lambda2) w - Dt CA^T u' + Dt a b2, then eq. (2.7);
+    // each row's length-d1 dot product is split over GS_SPLIT warps of a block
+    for (int j0 = blockIdx.x * GS_ROWS; j0 < d2; j0 += gridDim.x * GS_ROWS) {
+      const int wib = threadIdx.x >> 5, slot = wib / GS_SPLIT, piece = wib % GS_SPLIT;
+      const int j = j0 + slot;
       double acc = 0.0;
-      for (int i = lane; i < d1; i += 32) acc += a.CAt[(size_t)j * d1 + i] * a.gu[i];
+      if (j < d2)
+        for (int i = piece * 32 + lane; i < d1; i += GS_SPLIT * 32) acc += a.CAt[(size_t)j * d1 + i] * a.gu[i];
       acc = pintd::warp_sum(acc);
-      if (lane == 0) {
-        const double g = (1.0 - a.Dt * a.lam2[j]) * xw[j] - a.Dt * acc + a.Dt * am * a.b2[j];
-        double v = a.first ? g : g + a.Fw[(size_t)n * d2 + j] - a.Gw[(size_t)n * d2 + j];
-        if (a.Cw) v += a.Cw[(size_t)(n + 1) * d2 + j];
-        a.Xw[(size_t)(n + 1) * d2 + j] = v;
-        a.Gw[(size_t)n * d2 + j] = g;
+      if (lane == 0) s_part[wib] = acc;
+      __syncthreads();
+      if (threadIdx.x < GS_ROWS && j0 + (int)threadIdx.x < d2) {
+        const int jj = j0 + threadIdx.x;
+        double dot = 0.0;
+        for (int q = 0; q < GS_SPLIT; ++q) dot += s_part[threadIdx.x * GS_SPLIT + q];
+        const double g = (1.0 - a.Dt * a.lam2[jj]) * xw[jj] - a.Dt * dot + a.Dt * am * a.b2[jj];
+        double v = a.first ? g : g + a.Fw[(size_t)n * d2 + jj] - a.Gw[(size_t)n * d2 + jj];
+        if (a.Cw) v += a.Cw[(size_t)(n + 1) * d2 + jj];
+        a.Xw[(size_t)(n + 1) * d2 + jj] = v;
+        a.Gw[(size_t)n * d2 + jj] = g;
       }
+      __syncthreads();
     }
     for (int i = gtid; i < d1; i += gthreads) {
       const double g = a.gu[i];

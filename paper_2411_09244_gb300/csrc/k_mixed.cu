@@ -26,6 +26,37 @@ __device__ __forceinline__ void put_split(float* __restrict__ hi, float* __restr
   lo[o] = __uint_as_float(l);
 }
 
+// Sum v[0..P) over the 32 lanes of a warp and add the P totals to acc[0..P):
+// recursive halving leaves each lane the totals of a contiguous slice of
+// max(P / 32, 1) entries (P a power of two), so one atomic instruction per
+// slice entry covers the warp.
+template <int P>
+__device__ __forceinline__ void warp_sum_scatter(float* v, double* __restrict__ acc) {
+  const int lane = threadIdx.x & 31;
+  int off = 0;
+  int mask = 16;
+#pragma unroll
+  for (int C = P; C > 1 && mask >= 1; C >>= 1, mask >>= 1) {
+    const int half = C / 2;
+    const bool upper = (lane & mask) != 0;
+#pragma unroll
+    for (int k = 0; k < half; ++k) {
+      const float send = upper ? v[k] : v[k + half];
+      const float keep = upper ? v[k + half] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+    }
+    if (upper) off += half;
+  }
+  // P < 32: lanes differing in the remaining low bits hold the same entries
+  for (; mask >= 1; mask >>= 1) v[0] += __shfl_xor_sync(0xffffffffu, v[0], mask);
+  constexpr int KEEP = (P >= 32) ? P / 32 : 1;
+  const int low = (P >= 32) ? 0 : (lane & (32 / P - 1));
+  if (low == 0) {
+#pragma unroll
+    for (int k = 0; k < KEEP; ++k) atomicAdd(&acc[off + k], (double)v[k]);
+  }
+}
+
 // FP32 contraction with the WR column maps (see k_wr_gemm in k_hot64.cu):
 // MODE 0: out = AR [w_p ; w_{max(p-1,0)}], MODE 1: out = AS [u_p - u_{max(p-1,0)} ; u_{p+1}]
 // Trajectories use padded strides ldu, ldw (multiples of 32, pad entries 0);
@@ -269,6 +300,11 @@ __global__ void __launch_bounds__(128) k_time_solve32_t(const float* __restrict_
     dit_stage<P, 2>(re, im, tw, -1.f);                 // inverse from bit-reversed input (without 1/P)
 #pragma unroll
     for (int p = 0; p < P; ++p) re[p] = re[p] / ((float)P * bpow[p]);
+    // previous iterate: every load issued before any store
+#pragma unroll
+    for (int p = 0; p < P; ++p) im[p] = Un[(size_t)(p + 1) * ldu + i];
+#pragma unroll
+    for (int p = 0; p < P; ++p) Un[(size_t)(p + 1) * ldu + i] = re[p];
     if (B1h) {  // second-contraction column map [u_p - u_{p-1} ; u_{p+1}]
 #pragma unroll
       for (int p = 0; p < P; ++p) {
@@ -278,18 +314,17 @@ __global__ void __launch_bounds__(128) k_time_solve32_t(const float* __restrict_
         put_split(B1h, B1l, o + ldu, re[p]);
       }
     }
-  }
 #pragma unroll
-  for (int p = 0; p < P; ++p) {
-    double du = 0.0;
-    if (act) {
-      const float old = Un[(size_t)(p + 1) * ldu + i];
-      du = (double)(re[p] - old) * (double)(re[p] - old);
-      Un[(size_t)(p + 1) * ldu + i] = re[p];
+    for (int p = 0; p < P; ++p) {
+      const float d = re[p] - im[p];
+      im[p] = d * d;
     }
-    du = pintd::warp_sum(du);
-    if (lane == 0) atomicAdd(&accU[(size_t)nloc * P + p], du);
+  } else {
+#pragma unroll
+    for (int p = 0; p < P; ++p) im[p] = 0.f;
   }
+  (void)lane;
+  warp_sum_scatter<P>(im, accU + (size_t)nloc * P);
 }
 
 __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, int d2, int ldw, int P,
@@ -327,6 +362,60 @@ __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, 
     dw = pintd::warp_sum(dw);
     if ((threadIdx.x & 31) == 0) atomicAdd(&accW[(size_t)nloc * P + p], dw);
   }
+}
+
+// Register variant for P = 16, 32, 64: the contraction inputs and previous
+// states of 16 steps at a time are loaded before the recurrence consumes them.
+constexpr int MAX_SLICES = 4;
+template <int P>
+__global__ void __launch_bounds__(32) k_w_sweep32_t(const float* __restrict__ S, int d2, int ldw,
+                                                    float* __restrict__ Wt, const float* __restrict__ lam2,
+                                                    const float* __restrict__ src, const float* __restrict__ b2,
+                                                    const double* __restrict__ amp, float dt, int nsl,
+                                                    size_t slice, double* __restrict__ accW,
+                                                    float* __restrict__ B0h, float* __restrict__ B0l) {
+  constexpr int CH = 16;
+  const int nloc = blockIdx.y;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  float* Wn = Wt + (size_t)nloc * (P + 1) * ldw;
+  float dd[P];
+  if (j < d2) {
+    const float fac = 1.f - dt * lam2[j];
+    const float cs = src ? 0.f : dt * b2[j] * (float)amp[nloc];
+    float w = Wn[j];
+#pragma unroll
+    for (int c0 = 0; c0 < P; c0 += CH) {
+      float sv[CH], ov[CH];
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const size_t o = ((size_t)nloc * P + c0 + q) * d2 + j;
+        float a = src ? src[o] : cs;
+#pragma unroll
+        for (int z = 0; z < MAX_SLICES; ++z)
+          if (z < nsl) a += S[(size_t)z * slice + o];
+        sv[q] = a;
+        ov[q] = Wn[(size_t)(c0 + q + 1) * ldw + j];
+      }
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const int p = c0 + q;
+        const float wn = fac * w + sv[q];
+        Wn[(size_t)(p + 1) * ldw + j] = wn;
+        if (B0h && p + 1 < P) {  // first-contraction column map of step p + 1: [w_{p+1} ; w_p]
+          const size_t o = ((size_t)nloc * P + p + 1) * 2 * ldw + j;
+          put_split(B0h, B0l, o, wn);
+          put_split(B0h, B0l, o + ldw, w);
+        }
+        const float d = wn - ov[q];
+        dd[p] = d * d;
+        w = wn;
+      }
+    }
+  } else {
+#pragma unroll
+    for (int p = 0; p < P; ++p) dd[p] = 0.f;
+  }
+  warp_sum_scatter<P>(dd, accW + (size_t)nloc * P);
 }
 
 // constant initial trajectories; with B0h, also the first-contraction column
@@ -501,8 +590,19 @@ void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const
 // S holds nsl K-slices of the contraction, slice floats apart (summed here)
 void mx_w_sweep32(Ctx* c, const float* S, int nsl, size_t slice, int nact, float* Wt, int ldw, const float* lam2,
                   const float* src, const float* b2, const double* amp, double* accW, float* B0h, float* B0l) {
-  k_w_sweep32<<<dim3(nbl(c->d2, 128), nact), 128, 0, c->stream>>>(S, c->d2, ldw, c->P, Wt, lam2, src, b2, amp,
-                                                                  (float)c->dt, nsl, slice, accW, B0h, B0l);
+  PINT_REQUIRE(nsl >= 1 && nsl <= MAX_SLICES, PINT_ERR_BAD_ARG, "too many contraction slices");
+  const int P = c->P, d2 = c->d2;
+  const float dt = (float)c->dt;
+  const dim3 g32(nbl(d2, 32), nact);
+  if (P == 64)
+    k_w_sweep32_t<64><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l);
+  else if (P == 32)
+    k_w_sweep32_t<32><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l);
+  else if (P == 16)
+    k_w_sweep32_t<16><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l);
+  else
+    k_w_sweep32<<<dim3(nbl(d2, 128), nact), 128, 0, c->stream>>>(S, d2, ldw, P, Wt, lam2, src, b2, amp, dt, nsl,
+                                                                 slice, accW, B0h, B0l);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
