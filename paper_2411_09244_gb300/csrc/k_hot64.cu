@@ -51,18 +51,21 @@ inline unsigned nb_(long long n, int t) { return (unsigned)((n + t - 1) / t); }
 // ---------------------------------------------------------------------------
 // FP64 tiled GEMM with the WR column maps.  MODE 0: R (rows d1, K = 2 d2),
 // MODE 1: S (rows d2, K = 2 d1).  Column col -> interval n = n_lo + col / P,
-// step p = col % P.  Output out[(n - n_lo)][p][row] (row fastest).
-template <int MODE>
+// step p = col % P.  Output out[(n - n_lo)][p][row] (row fastest).  T x T
+// tiles, (T/16)^2 outputs per thread: the FP64 pipe, not shared memory,
+// bounds this kernel, so T is chosen for an even spread over the SMs.
+template <int MODE, int T>
 __global__ void __launch_bounds__(256) k_wr_gemm(const double* __restrict__ A, int M, int K,
                                                  const double* __restrict__ Ut,
                                                  const double* __restrict__ Wt, int d1, int d2, int P,
                                                  int ncols, double* __restrict__ out) {
-  __shared__ double As[16][65], Bs[16][65];
-  const int i0 = blockIdx.y * 64, j0 = blockIdx.x * 64;
+  constexpr int R = T / 16;
+  __shared__ double As[16][T + 1], Bs[16][T + 1];
+  const int i0 = blockIdx.y * T, j0 = blockIdx.x * T;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  double acc[4][4] = {};
+  double acc[R][R] = {};
   for (int k0 = 0; k0 < K; k0 += 16) {
-    for (int e = threadIdx.x; e < 16 * 64; e += 256) {
+    for (int e = threadIdx.x; e < 16 * T; e += 256) {
       int kk = e % 16, r = e / 16;  // k fastest for coalesced column reads
       int kg = k0 + kk;
       int ig = i0 + r, col = j0 + r;
@@ -87,24 +90,62 @@ __global__ void __launch_bounds__(256) k_wr_gemm(const double* __restrict__ A, i
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      double a[4], b[4];
+      double a[R], b[R];
 #pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        a[q] = As[kk][ty * 4 + q];
-        b[q] = Bs[kk][tx * 4 + q];
+      for (int q = 0; q < R; ++q) {
+        a[q] = As[kk][ty * R + q];
+        b[q] = Bs[kk][tx * R + q];
       }
 #pragma unroll
-      for (int p = 0; p < 4; ++p)
+      for (int p = 0; p < R; ++p)
 #pragma unroll
-        for (int q = 0; q < 4; ++q) acc[p][q] += a[p] * b[q];
+        for (int q = 0; q < R; ++q) acc[p][q] += a[p] * b[q];
     }
     __syncthreads();
   }
-  for (int p = 0; p < 4; ++p)
-    for (int q = 0; q < 4; ++q) {
-      int i = i0 + ty * 4 + p, col = j0 + tx * 4 + q;
+  for (int p = 0; p < R; ++p)
+    for (int q = 0; q < R; ++q) {
+      int i = i0 + ty * R + p, col = j0 + tx * R + q;
       if (i < M && col < ncols) out[(size_t)col * M + i] = acc[p][q];
     }
+}
+
+int sm_count() {
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 1;
+  }
+  return sms;
+}
+
+// useful work per SM-slot for tile T: (M ncols / T^2 tiles spread over the
+// SMs, the busiest SM setting the time) x the fraction of each tile in range
+double tile_eff(int M, int ncols, int T) {
+  const long long tm = nb_(M, T), tn = nb_(ncols, T), tiles = tm * tn;
+  const int sms = sm_count();
+  const double waves = (double)((tiles + sms - 1) / sms);
+  return ((double)tiles / sms / waves) * ((double)M * ncols / ((double)tiles * T * T));
+}
+
+// out = A [column map] for MODE 0 / 1 on the stream
+template <int MODE>
+void wr_gemm64(Ctx* c, const double* A, int M, int K, const double* Ut, const double* Wt, int ncols,
+               double* out) {
+  const int d1 = c->d1, d2 = c->d2, P = c->P;
+  const double e64 = tile_eff(M, ncols, 64), e32 = tile_eff(M, ncols, 32), e16 = tile_eff(M, ncols, 16);
+  if (e64 >= e32 && e64 >= e16)
+    k_wr_gemm<MODE, 64><<<dim3(nb_(ncols, 64), nb_(M, 64)), 256, 0, c->stream>>>(A, M, K, Ut, Wt, d1, d2, P,
+                                                                                ncols, out);
+  else if (e32 >= e16)
+    k_wr_gemm<MODE, 32><<<dim3(nb_(ncols, 32), nb_(M, 32)), 256, 0, c->stream>>>(A, M, K, Ut, Wt, d1, d2, P,
+                                                                                ncols, out);
+  else
+    k_wr_gemm<MODE, 16><<<dim3(nb_(ncols, 16), nb_(M, 16)), 256, 0, c->stream>>>(A, M, K, Ut, Wt, d1, d2, P,
+                                                                                ncols, out);
+  PINT_LAUNCH_CHECK();
 }
 
 struct C2 {
@@ -709,15 +750,13 @@ static int wr_sweep(Ctx* c, Hot& H, const double* xs_u, const double* xs_w, cons
   for (it = 1; it <= wr_max; ++it) {
     PINT_CUDA(cudaMemsetAsync(H.acc, 0, (size_t)2 * nact * P * 8, c->stream));
     PINT_CUDA(cudaEventRecord(H.ev[0], c->stream));
-    k_wr_gemm<0><<<dim3(nb_(ncols, 64), nb_(d1, 64)), 256, 0, c->stream>>>(c->AR, d1, 2 * d2, H.Ut, H.Wt,
-                                                                          d1, d2, P, ncols, H.R);
+    wr_gemm64<0>(c, c->AR, d1, 2 * d2, H.Ut, H.Wt, ncols, H.R);
     PINT_CUDA(cudaEventRecord(H.ev[1], c->stream));
     k_time_solve<<<dim3(nb_(d1, 128), nact), 128, 0, c->stream>>>(
         H.R, d1, P, nact, 0, H.Ut, c->lam1, H.b1, amp_act, c->alpha, c->dt, c->tw, c->dshift, c->lampow,
         pow2, H.acc);
     PINT_CUDA(cudaEventRecord(H.ev[2], c->stream));
-    k_wr_gemm<1><<<dim3(nb_(ncols, 64), nb_(d2, 64)), 256, 0, c->stream>>>(c->AS, d2, 2 * d1, H.Ut, H.Wt,
-                                                                          d1, d2, P, ncols, H.S);
+    wr_gemm64<1>(c, c->AS, d2, 2 * d1, H.Ut, H.Wt, ncols, H.S);
     PINT_CUDA(cudaEventRecord(H.ev[3], c->stream));
     k_w_sweep<<<dim3(nb_(d2, 128), nact), 128, 0, c->stream>>>(H.S, d2, P, 0, H.Wt, c->lam2, H.b2,
                                                               amp_act, c->dt, H.acc + (size_t)nact * P);
@@ -1366,11 +1405,8 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
     PINT_CUDA(cudaMemcpyAsync(M.Sw + (size_t)N * d2, M.Zw + ((size_t)(N - 1) * (P + 1) + P) * d2, (size_t)d2 * 8,
                               cudaMemcpyDeviceToDevice, c->stream));
     const int ncols = N * P;
-    k_wr_gemm<0><<<dim3(nb_(ncols, 64), nb_(d1, 64)), 256, 0, c->stream>>>(c->AR, d1, 2 * d2, M.Zu, M.Zw, d1, d2,
-                                                                          P, ncols, M.R64);
-    k_wr_gemm<1><<<dim3(nb_(ncols, 64), nb_(d2, 64)), 256, 0, c->stream>>>(c->AS, d2, 2 * d1, M.Zu, M.Zw, d1, d2,
-                                                                          P, ncols, M.S64);
-    PINT_LAUNCH_CHECK();
+    wr_gemm64<0>(c, c->AR, d1, 2 * d2, M.Zu, M.Zw, ncols, M.R64);
+    wr_gemm64<1>(c, c->AS, d2, 2 * d1, M.Zu, M.Zw, ncols, M.S64);
     c->launches += 2;
     mx_residual(c, M.Zu, M.Zw, M.R64, M.S64, H.b1, H.b2, H.amp, M.srcU, M.srcW);
     mx_continuity(c, M.Zu, M.Zw, M.Cu, M.Cw);

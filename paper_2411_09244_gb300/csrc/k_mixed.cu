@@ -364,6 +364,215 @@ __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Four-step variant for P = R^2 (R = 4, 8): R lanes share one series.  With
+// p = g + R m and k = a + R b (g, a the lane in the group; m, b registers),
+//   Y[a + R b] = sum_g w_R^{g b} w_P^{g a} sum_m w_R^{m a} y[g + R m],
+// so each lane runs an R-point DFT over its registers, applies its twiddles
+// w_P^{g a}, the group transposes its R x R block through shuffles, and a
+// second R-point DFT leaves lane a holding Y[a + R b].  The inverse is the
+// same procedure with conjugate roots and returns lane g holding y[g + R m].
+// The right-hand sides and results pass through a shared-memory tile so that
+// every global access is coalesced along the modes.
+
+// cos / sin of 2 pi k / 8
+__host__ __device__ constexpr float cos8(int k) {
+  return k == 0 ? 1.f : k == 1 ? 0.70710678118654752f : k == 2 ? 0.f : k == 3 ? -0.70710678118654752f
+       : k == 4 ? -1.f : k == 5 ? -0.70710678118654752f : k == 6 ? 0.f : 0.70710678118654752f;
+}
+__host__ __device__ constexpr float sin8(int k) { return cos8((k + 6) & 7); }
+__host__ __device__ constexpr int bitrev(int k, int bits) {
+  int r = 0;
+  for (int b = 0; b < bits; ++b)
+    if (k & (1 << b)) r |= 1 << (bits - 1 - b);
+  return r;
+}
+
+// radix-2 decimation-in-frequency stages of an R-point DFT with roots
+// e^{SGN 2 pi i / R} (R <= 8): natural order in, bit-reversed order out
+template <int R, int LEN, int SGN>
+__device__ __forceinline__ void small_dif(float* re, float* im) {
+#pragma unroll
+  for (int i0 = 0; i0 < R; i0 += LEN) {
+#pragma unroll
+    for (int k = 0; k < LEN / 2; ++k) {
+      const int ti = k * (8 / LEN);
+      const float wr = cos8(ti), wi = SGN * sin8(ti);
+      const int a = i0 + k, b = a + LEN / 2;
+      const float dr = re[a] - re[b], di = im[a] - im[b];
+      re[a] += re[b];
+      im[a] += im[b];
+      re[b] = dr * wr - di * wi;
+      im[b] = dr * wi + di * wr;
+    }
+  }
+  if constexpr (LEN > 2) small_dif<R, LEN / 2, SGN>(re, im);
+}
+
+// out[f] = sum_n x[n] e^{SGN 2 pi i n f / R}, in place, natural order
+template <int R, int SGN>
+__device__ __forceinline__ void small_dft(float* re, float* im) {
+  constexpr int BITS = R == 2 ? 1 : R == 4 ? 2 : 3;
+  small_dif<R, R, SGN>(re, im);
+  float tr[R], ti[R];
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    tr[k] = re[bitrev(k, BITS)];
+    ti[k] = im[bitrev(k, BITS)];
+  }
+#pragma unroll
+  for (int k = 0; k < R; ++k) {
+    re[k] = tr[k];
+    im[k] = ti[k];
+  }
+}
+
+// a[t] <- a[(t - g) mod R] for the lane's own g, as log2(R) selected rotations
+template <int R>
+__device__ __forceinline__ void rotate_right(float* a, int g) {
+#pragma unroll
+  for (int b = 1; b < R; b <<= 1) {
+    const bool on = (g & b) != 0;
+    float t2[R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) t2[t] = a[(t - b + R) % R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) a[t] = on ? t2[t] : a[t];
+  }
+}
+
+// lane g of an R-lane group (first lane `base`) holds X_g[0..R); afterwards
+// it holds X_0[g] .. X_{R-1}[g].  Round t reads lane (g + t) mod R, which
+// sends X_{g+t}[g] once its registers are reversed and rotated by its g.
+template <int R>
+__device__ __forceinline__ void group_transpose(float* v, int g, int base) {
+  float a[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) a[t] = v[(R - t) % R];
+  rotate_right<R>(a, g);
+#pragma unroll
+  for (int t = 0; t < R; ++t) a[t] = __shfl_sync(0xffffffffu, a[t], base + ((g + t) & (R - 1)));
+  rotate_right<R>(a, g);
+#pragma unroll
+  for (int t = 0; t < R; ++t) v[t] = a[t];
+}
+
+template <int R>
+__global__ void __launch_bounds__(256) k_time_solve32_sq(const float* __restrict__ Rc, int d1, int ldu,
+                                                         float* __restrict__ Ut, const float* __restrict__ lam1,
+                                                         const float* __restrict__ src,
+                                                         const float* __restrict__ b1,
+                                                         const double* __restrict__ amp, float alpha, float dt,
+                                                         const float2* __restrict__ tw,
+                                                         const float2* __restrict__ dsh,
+                                                         const float* __restrict__ bpow, double* __restrict__ accU,
+                                                         float* __restrict__ B1h, float* __restrict__ B1l) {
+  constexpr int P = R * R;       // steps per interval
+  constexpr int NS = 256 / R;    // series (modes) per block
+  constexpr int LD = NS + 1;     // tile row stride
+  constexpr int PER = P * NS / 256;
+  __shared__ float sT[P * LD];
+  __shared__ float su0[NS];
+  const int nloc = blockIdx.y, i0 = blockIdx.x * NS;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  float* Un = Ut + (size_t)nloc * (P + 1) * ldu;
+  const float an = (float)amp[nloc];
+  // right-hand sides of eq. (4.7) scaled by beta^p, tile [p][mode]
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int e = tid + 256 * r, p = e / NS, s = e % NS, i = i0 + s;
+    float y = 0.f;
+    if (i < d1) {
+      const size_t o = ((size_t)nloc * P + p) * d1 + i;
+      y = Rc[o] + (src ? src[o] : b1[i] * an);
+      if (p == 0) {
+        const float u0 = Un[i];
+        su0[s] = u0;
+        y += (u0 - alpha * Un[(size_t)P * ldu + i]) / dt;
+      }
+      y *= bpow[p];
+    }
+    sT[p * LD + s] = y;
+  }
+  __syncthreads();
+  // one series per R-lane group; series s = warp + 8 j keeps the tile reads
+  // free of bank conflicts for R = 8
+  const int g = lane % R, j = lane / R, s = warp + 8 * j, base = lane - g;
+  const int i = i0 + s;
+  const float li = (i < d1) ? lam1[i] : 0.f;
+  float re[R], im[R], twr[R], twi[R];
+#pragma unroll
+  for (int m = 0; m < R; ++m) {
+    re[m] = sT[(g + R * m) * LD + s];
+    im[m] = 0.f;
+  }
+#pragma unroll
+  for (int a = 0; a < R; ++a) {
+    const float2 t = tw[(g * a) % P];  // e^{-2 pi i g a / P}
+    twr[a] = t.x;
+    twi[a] = t.y;
+  }
+  small_dft<R, -1>(re, im);
+#pragma unroll
+  for (int a = 0; a < R; ++a) {
+    const float xr = re[a] * twr[a] - im[a] * twi[a], xi = re[a] * twi[a] + im[a] * twr[a];
+    re[a] = xr;
+    im[a] = xi;
+  }
+  group_transpose<R>(re, g, base);
+  group_transpose<R>(im, g, base);
+  small_dft<R, -1>(re, im);  // lane g: Y[g + R b]
+#pragma unroll
+  for (int b = 0; b < R; ++b) {
+    const float2 d = dsh[g + R * b];
+    const float a = d.x + li, c = d.y, inv = 1.f / (a * a + c * c);
+    const float qr = (re[b] * a + im[b] * c) * inv, qi = (im[b] * a - re[b] * c) * inv;
+    re[b] = qr;
+    im[b] = qi;
+  }
+  small_dft<R, 1>(re, im);
+#pragma unroll
+  for (int a = 0; a < R; ++a) {
+    const float xr = re[a] * twr[a] + im[a] * twi[a], xi = im[a] * twr[a] - re[a] * twi[a];
+    re[a] = xr;
+    im[a] = xi;
+  }
+  group_transpose<R>(re, g, base);
+  group_transpose<R>(im, g, base);
+  small_dft<R, 1>(re, im);  // lane g: P y[g + R m]
+  __syncthreads();          // every read of the right-hand sides is done
+#pragma unroll
+  for (int m = 0; m < R; ++m) sT[(g + R * m) * LD + s] = re[m] / ((float)P * bpow[g + R * m]);
+  __syncthreads();
+  // new states u_{p+1} (tile row p), previous iterate loaded before any store
+  float oldv[PER];
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int e = tid + 256 * r, p = e / NS, ii = i0 + e % NS;
+    oldv[r] = (ii < d1) ? Un[(size_t)(p + 1) * ldu + ii] : 0.f;
+  }
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int e = tid + 256 * r, p = e / NS, ss = e % NS, ii = i0 + ss;
+    float dd = 0.f;
+    if (ii < d1) {
+      const float uq = sT[p * LD + ss];
+      Un[(size_t)(p + 1) * ldu + ii] = uq;
+      if (B1h) {  // second-contraction column map [u_p - u_{p-1} ; u_{p+1}]
+        const size_t o = ((size_t)nloc * P + p) * 2 * ldu + ii;
+        const float dp = (p == 0) ? 0.f : sT[(p - 1) * LD + ss] - (p == 1 ? su0[ss] : sT[(p - 2) * LD + ss]);
+        put_split(B1h, B1l, o, dp);
+        put_split(B1h, B1l, o + ldu, uq);
+      }
+      const float dv = uq - oldv[r];
+      dd = dv * dv;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, off);
+    if (lane == 0) atomicAdd(&accU[(size_t)nloc * P + p], (double)dd);  // a warp covers one row segment
+  }
+}
+
 // Register variant for P = 16, 32, 64: the contraction inputs and previous
 // states of 16 steps at a time are loaded before the recurrence consumes them.
 constexpr int MAX_SLICES = 4;
@@ -572,14 +781,14 @@ void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const
   const dim3 grid(nbl(c->d1, 128), nact);
   const float al = (float)c->alpha, dt = (float)c->dt;
   if (P == 64)
-    k_time_solve32_t<64><<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al, dt, tw, dshbr, bpow,
-                                                       accU, B1h, B1l);
+    k_time_solve32_sq<8><<<dim3(nbl(c->d1, 32), nact), 256, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al,
+                                                                           dt, tw, dsh, bpow, accU, B1h, B1l);
   else if (P == 32)
     k_time_solve32_t<32><<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al, dt, tw, dshbr, bpow,
                                                        accU, B1h, B1l);
   else if (P == 16)
-    k_time_solve32_t<16><<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al, dt, tw, dshbr, bpow,
-                                                       accU, B1h, B1l);
+    k_time_solve32_sq<4><<<dim3(nbl(c->d1, 64), nact), 256, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al,
+                                                                           dt, tw, dsh, bpow, accU, B1h, B1l);
   else
     k_time_solve32<<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, P, Ut, lam1, src, b1, amp, al, dt, tw, dsh, bpow,
                                                 (P & (P - 1)) == 0, accU, B1h, B1l);
