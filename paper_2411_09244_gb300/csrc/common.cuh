@@ -170,6 +170,18 @@ void apply_G_dev(Ctx* c, const double* in, int count, const double* f_nodes, con
 void apply_F_dev(Ctx* c, const double* in, int count, const double* f_nodes, const double* amp_dev,
                  double wr_tol, int wr_max, double* out, int* iters);
 
+// FP32 coarse sweep on one thread-block cluster (k_gcluster.cu)
+struct GcArgs {
+  const float* CA;  // [d1][d2] FP32 coupling
+  const double *lam1, *lam2, *b1, *b2, *amp;
+  const double *Fu, *Fw, *Cu, *Cw;  // F ends, jumps (may be null)
+  double *Xu, *Xw, *Gu, *Gw;        // states (in/out), G outputs (in/out)
+  int d1, d2, n_lo, n_hi, first;
+  double Dt;
+};
+int gc_cluster_size(int d1, int d2);
+void g_sweep_cluster(Ctx* c, const GcArgs& a, int CL);
+
 }  // namespace pint
 
 // ------------------------------------------------------ device helpers --

@@ -1,0 +1,298 @@
+// Coarse sweep of the mixed path on one thread-block cluster.
+//
+// One sweep of Algorithm 1's sequential correction runs N coarse steps of the
+// splitting scheme, eqs. (2.4)-(2.5) with the coarse step Dt, in spectral
+// coordinates:
+//   u' = (u - Dt CA w + Dt a_n b1) / (1 + Dt Lambda1)
+//   w' = (1 - Dt Lambda2) w - Dt CA^T u' + Dt a_n b2
+// and applies the update of eq. (2.7), x_{n+1} = G(x_n) + F_n - G_old_n
+// (+ c_{n+1} in a correction solve).  The low-precision path only needs G to
+// contract the parareal error (its fixed point is that of F), so the two
+// coupling products run in FP32 while states and updates stay FP64.
+//
+// The FP32 coupling CA stays resident in the distributed shared memory of a
+// cluster of CL CTAs (rows split evenly).  Per step: each CTA forms u' for its
+// rows (warp per row), the partial products CA^T u' over its rows for every
+// column, then after a cluster barrier each CTA reduces its slice of columns
+// over the CL partials (DSMEM loads in a fixed order, so the sweep is
+// deterministic), forms w' for that slice and writes it into every CTA's copy
+// of w; a second cluster barrier closes the step.  Both barriers are the
+// hardware cluster barrier: no software spin-waits.
+#include "common.cuh"
+
+namespace pint {
+
+namespace {
+
+constexpr int GC_THREADS = 1024;
+constexpr int GC_MAX_RT = 8;  // rows per warp and CTA (rows per CTA <= 256)
+
+struct GcLayout {
+  int rpc, spc, ng;
+  size_t f_CA, f_xw, f_part, f_gu, f_gtmp, f_sbuf, n_f;  // float offsets
+  size_t d_xu, d_xw, d_ia, d_cb, d_fw, d_cw, n_d;        // double offsets (after the floats)
+  size_t bytes;
+};
+
+__host__ __device__ inline GcLayout gc_layout(int d1, int d2, int CL) {
+  GcLayout L{};
+  L.rpc = (d1 + CL - 1) / CL;
+  L.spc = (d2 + CL - 1) / CL;
+  L.ng = d2 >= GC_THREADS ? 1 : (GC_THREADS / d2 > 8 ? 8 : GC_THREADS / d2);
+  size_t o = 0;
+  L.f_CA = o;
+  o += (size_t)L.rpc * d2;
+  L.f_xw = o;
+  o += d2;
+  L.f_part = o;
+  o += d2;
+  L.f_gu = o;
+  o += L.rpc;
+  L.f_gtmp = o;
+  o += (size_t)L.ng * d2;
+  L.f_sbuf = o;
+  o += L.spc;
+  L.n_f = (o + 1) & ~(size_t)1;  // doubles start 8-byte aligned
+  size_t q = 0;
+  L.d_xu = q;
+  q += L.rpc;
+  L.d_ia = q;
+  q += L.rpc;
+  L.d_cb = q;
+  q += L.rpc;
+  L.d_xw = q;
+  q += L.spc;
+  L.d_fw = q;
+  q += L.spc;
+  L.d_cw = q;
+  q += L.spc;
+  L.n_d = q;
+  L.bytes = L.n_f * 4 + L.n_d * 8;
+  return L;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ uint32_t cl_rank() {
+  uint32_t r;
+  asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+  return r;
+}
+__device__ __forceinline__ void cl_sync() {
+  asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t dsmem_addr(const void* p, uint32_t rank) {
+  uint32_t r;
+  asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_u32(p)), "r"(rank));
+  return r;
+}
+__device__ __forceinline__ float ld_dsmem(uint32_t a) {
+  float v;
+  asm volatile("ld.shared::cluster.f32 %0, [%1];" : "=f"(v) : "r"(a) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_dsmem(uint32_t a, float v) {
+  asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
+}
+
+template <int CL>
+__global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  const int d1 = a.d1, d2 = a.d2;
+  const GcLayout L = gc_layout(d1, d2, CL);
+  float* fs = reinterpret_cast<float*>(gsm);
+  double* ds = reinterpret_cast<double*>(gsm + L.n_f * 4);
+  float *sCA = fs + L.f_CA, *xw32 = fs + L.f_xw, *part = fs + L.f_part, *gu32 = fs + L.f_gu,
+        *gtmp = fs + L.f_gtmp, *sbuf = fs + L.f_sbuf;
+  double *xud = ds + L.d_xu, *ia = ds + L.d_ia, *cb = ds + L.d_cb, *xwd = ds + L.d_xw, *fw = ds + L.d_fw,
+         *cw = ds + L.d_cw;
+  const int rank = (int)cl_rank();
+  const int r0 = rank * L.rpc, nr = max(0, min(d1, r0 + L.rpc) - r0);
+  const int j0 = rank * L.spc, ns = max(0, min(d2, j0 + L.spc) - j0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const double Dt = a.Dt;
+  const size_t n0 = (size_t)a.n_lo;
+  for (size_t e = tid; e < (size_t)nr * d2; e += GC_THREADS) sCA[e] = a.CA[(size_t)r0 * d2 + e];
+  for (int j = tid; j < d2; j += GC_THREADS) xw32[j] = (float)a.Xw[n0 * d2 + j];
+  for (int q = tid; q < nr; q += GC_THREADS) {
+    const int i = r0 + q;
+    xud[q] = a.Xu[n0 * d1 + i];
+    ia[q] = 1.0 / (1.0 + Dt * a.lam1[i]);
+    cb[q] = Dt * a.b1[i] * ia[q];
+  }
+  for (int q = tid; q < ns; q += GC_THREADS) {
+    const int j = j0 + q;
+    xwd[q] = a.Xw[n0 * d2 + j];
+    fw[q] = 1.0 - Dt * a.lam2[j];
+    cw[q] = Dt * a.b2[j];
+  }
+  __syncthreads();
+  cl_sync();  // every CTA of the cluster is resident before any DSMEM access
+  const int rt = nr > warp ? (nr - warp + 31) / 32 : 0;  // rows of this warp: q = warp + 32 t
+  for (int n = a.n_lo; n < a.n_hi; ++n) {
+    const double am = a.amp[n];
+    // values of this step that do not depend on the sweep, fetched up front
+    double pf = 0.0, pg = 0.0, pc = 0.0;
+    if (lane < rt) {
+      const int i = r0 + warp + 32 * lane;
+      if (!a.first) {
+        pf = a.Fu[(size_t)n * d1 + i];
+        pg = a.Gu[(size_t)n * d1 + i];
+      }
+      if (a.Cu) pc = a.Cu[(size_t)(n + 1) * d1 + i];
+    }
+    double wf = 0.0, wg = 0.0, wc = 0.0;
+    if (tid < ns) {
+      const int j = j0 + tid;
+      if (!a.first) {
+        wf = a.Fw[(size_t)n * d2 + j];
+        wg = a.Gw[(size_t)n * d2 + j];
+      }
+      if (a.Cw) wc = a.Cw[(size_t)(n + 1) * d2 + j];
+    }
+    // u-phase: one warp per row; lane t keeps row t's product
+    float mine = 0.f;
+#pragma unroll
+    for (int t = 0; t < GC_MAX_RT; ++t) {
+      if (t < rt) {
+        const int q = warp + 32 * t;
+        const float* row = sCA + (size_t)q * d2;
+        float acc = 0.f;
+        for (int j = lane; j < d2; j += 32) acc = fmaf(row[j], xw32[j], acc);
+        acc = pintd::warp_sumf(acc);
+        if (lane == t) mine = acc;
+      }
+    }
+    if (lane < rt) {
+      const int q = warp + 32 * lane, i = r0 + q;
+      const double g = xud[q] * ia[q] - Dt * ia[q] * (double)mine + am * cb[q];
+      double v = a.first ? g : g + pf - pg;
+      v += pc;
+      a.Xu[(size_t)(n + 1) * d1 + i] = v;
+      a.Gu[(size_t)n * d1 + i] = g;
+      xud[q] = v;
+      gu32[q] = (float)g;
+    }
+    __syncthreads();
+    // partial products CA^T u' over this CTA's rows, L.ng row groups per column
+    {
+      const int grp = tid / d2, j = tid - grp * d2;
+      if (grp < L.ng) {
+        for (int jj = j; jj < d2; jj += GC_THREADS) {  // d2 > GC_THREADS: one group loops over columns
+          float acc = 0.f;
+          for (int q = grp; q < nr; q += L.ng) acc = fmaf(sCA[(size_t)q * d2 + jj], gu32[q], acc);
+          gtmp[(size_t)grp * d2 + jj] = acc;
+        }
+      }
+    }
+    __syncthreads();
+    for (int j = tid; j < d2; j += GC_THREADS) {
+      float s = 0.f;
+      for (int g = 0; g < L.ng; ++g) s += gtmp[(size_t)g * d2 + j];
+      part[j] = s;
+    }
+    cl_sync();  // partials of every CTA visible
+    if (tid < ns) {
+      const int j = j0 + tid;
+      float s = 0.f;
+#pragma unroll
+      for (int r = 0; r < CL; ++r) s += ld_dsmem(dsmem_addr(&part[j], (uint32_t)r));
+      const double g = fw[tid] * xwd[tid] - Dt * (double)s + am * cw[tid];
+      double v = a.first ? g : g + wf - wg;
+      v += wc;
+      a.Xw[(size_t)(n + 1) * d2 + j] = v;
+      a.Gw[(size_t)n * d2 + j] = g;
+      xwd[tid] = v;
+      sbuf[tid] = (float)v;
+    }
+    __syncthreads();
+    for (int e = tid; e < ns * CL; e += GC_THREADS) {
+      const int q = e % ns, r = e / ns;
+      st_dsmem(dsmem_addr(&xw32[j0 + q], (uint32_t)r), sbuf[q]);
+    }
+    cl_sync();  // new w in every CTA; partial buffers free again
+  }
+}
+
+template <int CL>
+bool gc_feasible(size_t bytes) {
+  static int ok = -1;
+  if (ok < 0) {
+    ok = 0;
+    if (cudaFuncSetAttribute(k_g_sweep_cl<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    if (CL > 8 && cudaFuncSetAttribute(k_g_sweep_cl<CL>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+                      cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(CL);
+    cfg.blockDim = dim3(GC_THREADS);
+    cfg.dynamicSmemBytes = 200 * 1024;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_g_sweep_cl<CL>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    ok = nclusters >= 1 ? 1 : 0;
+  }
+  return ok == 1 && bytes <= 200 * 1024;
+}
+
+template <int CL>
+void gc_launch(Ctx* c, const GcArgs& a) {
+  const GcLayout L = gc_layout(a.d1, a.d2, CL);
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(CL);
+  cfg.blockDim = dim3(GC_THREADS);
+  cfg.dynamicSmemBytes = L.bytes;
+  cfg.stream = c->stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  PINT_CUDA(cudaLaunchKernelEx(&cfg, k_g_sweep_cl<CL>, a));
+  c->launches++;
+}
+
+}  // namespace
+
+// Cluster size for the FP32 coarse sweep (16 or 8), or 0 when the coupling
+// does not fit in the cluster's shared memory (the caller then uses the
+// grid-wide FP64 sweep).
+int gc_cluster_size(int d1, int d2) {
+  for (int CL : {16, 8}) {
+    const GcLayout L = gc_layout(d1, d2, CL);
+    if (L.rpc > 32 * GC_MAX_RT) continue;
+    if (CL == 16 && gc_feasible<16>(L.bytes)) return 16;
+    if (CL == 8 && gc_feasible<8>(L.bytes)) return 8;
+  }
+  return 0;
+}
+
+void g_sweep_cluster(Ctx* c, const GcArgs& a, int CL) {
+  if (a.n_lo >= a.n_hi) return;
+  if (CL == 16)
+    gc_launch<16>(c, a);
+  else if (CL == 8)
+    gc_launch<8>(c, a);
+  else
+    PINT_REQUIRE(false, PINT_ERR_BAD_ARG, "unsupported cluster size");
+}
+
+}  // namespace pint

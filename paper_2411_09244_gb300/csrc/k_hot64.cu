@@ -1030,6 +1030,7 @@ void mx_add_traj(Ctx* c, const float* dUt, const float* dWt, int ldu, int ldw, c
                  double* Zu, double* Zw);
 void mx_to_f32(Ctx* c, const double* x, long long n, float* y);
 
+
 namespace {
 
 __global__ void k_axpy2(const double* __restrict__ a, const double* __restrict__ b, long long n,
@@ -1058,6 +1059,8 @@ struct Mx {
   double *Su = nullptr, *Sw = nullptr, *YSu = nullptr, *YSw = nullptr;
   double *Zu = nullptr, *Zw = nullptr, *R64 = nullptr, *S64 = nullptr, *Cu = nullptr, *Cw = nullptr;
   double *Yu = nullptr, *Yw = nullptr, *zero = nullptr;
+  float* CA32 = nullptr;  // FP32 coupling of the cluster coarse sweep
+  int gcl = 0;            // its cluster size (0: grid-wide FP64 sweep)
   bool tensor = false;
   std::vector<void*> bufs;  // every device buffer above
 };
@@ -1090,6 +1093,8 @@ static Mx& mx_prepare(Ctx* c) {
   M.ldw = ldw;
   M.AR32 = Fa((size_t)d1 * 2 * ldw);
   M.AS32 = Fa((size_t)d2 * 2 * ldu);
+  M.gcl = gc_cluster_size(d1, d2);
+  if (M.gcl) M.CA32 = Fa((size_t)d1 * d2);
   if (tensor) {
     M.Rhi = Fa((size_t)d1 * 2 * ldw);
     M.Rlo = Fa((size_t)d1 * 2 * ldw);
@@ -1151,6 +1156,7 @@ static void mx_refresh(Ctx* c, Mx& M) {
   const int d1 = c->d1, d2 = c->d2;
   mx_pad_split(c, c->AR, d1, d2, M.ldw, M.AR32, M.Rhi, M.Rlo);
   mx_pad_split(c, c->AS, d2, d1, M.ldu, M.AS32, M.Shi, M.Slo);
+  if (M.CA32) mx_to_f32(c, c->CA, (long long)d1 * d2, M.CA32);
   mx_to_f32(c, c->lam1, d1, M.lam1f);
   mx_to_f32(c, c->lam2, d2, M.lam2f);
   mx_to_f32(c, c->lampow, 65, M.bpowf);
@@ -1246,13 +1252,45 @@ struct LpRun {
   double last_jump = 0;
 };
 
+// coarse sweep of the low-precision path: FP32 couplings on one cluster when
+// they fit in its shared memory, else the grid-wide FP64 sweep
+static void g_sweep_lp(Ctx* c, Hot& H, Mx& M, double* Xu, double* Xw, const double* amp, const double* Fu,
+                       const double* Fw, const double* Cu, const double* Cw, int n_lo, bool first) {
+  if (!M.gcl) {
+    g_sweep(c, H, Xu, Xw, amp, Fu, Fw, Cu, Cw, n_lo, first);
+    g_sweep_check(c, H);
+    return;
+  }
+  GcArgs a;
+  a.CA = M.CA32;
+  a.lam1 = c->lam1;
+  a.lam2 = c->lam2;
+  a.b1 = H.b1;
+  a.b2 = H.b2;
+  a.amp = amp;
+  a.Fu = Fu;
+  a.Fw = Fw;
+  a.Cu = Cu;
+  a.Cw = Cw;
+  a.Xu = Xu;
+  a.Xw = Xw;
+  a.Gu = H.Gu;
+  a.Gw = H.Gw;
+  a.d1 = c->d1;
+  a.d2 = c->d2;
+  a.n_lo = n_lo;
+  a.n_hi = c->N;
+  a.first = first ? 1 : 0;
+  a.Dt = c->Dt;
+  g_sweep_cluster(c, a, M.gcl);
+}
+
 // Algorithm 1 with the low-precision fine propagator (states FP64)
 static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hist, double* jump_hist,
                         int hist_off) {
   const int N = c->N, d1 = c->d1, d2 = c->d2, P = c->P;
   if (!r.have_g0) {
-    g_sweep(c, H, r.Xu, r.Xw, r.amp, nullptr, nullptr, r.Cu, r.Cw, 0, true);
-    g_sweep_check(c, H);
+    g_sweep_lp(c, H, M, r.Xu, r.Xw, r.amp, nullptr, nullptr, r.Cu, r.Cw, 0, true);
   }
   cudaEvent_t a0, a1;
   PINT_CUDA(cudaEventCreate(&a0));
@@ -1284,8 +1322,7 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
     r.wr_total += it;
     PINT_CUDA(cudaMemcpyAsync(H.Ou, r.Xu, (size_t)(N + 1) * d1 * 8, cudaMemcpyDeviceToDevice, c->stream));
     PINT_CUDA(cudaMemcpyAsync(H.Ow, r.Xw, (size_t)(N + 1) * d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
-    g_sweep(c, H, r.Xu, r.Xw, r.amp, H.Fu, H.Fw, r.Cu, r.Cw, n_lo, false);
-    g_sweep_check(c, H);
+    g_sweep_lp(c, H, M, r.Xu, r.Xw, r.amp, H.Fu, H.Fw, r.Cu, r.Cw, n_lo, false);
     PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
     k_jump<<<dim3(N, JS), 256, 0, c->stream>>>(r.Xu, r.Xw, H.Ou, H.Ow, c->CM, d1, d2, H.red + 8);
     k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
