@@ -20,22 +20,29 @@
 // hardware cluster barrier: no software spin-waits.
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace pint {
 
 namespace {
 
 constexpr int GC_THREADS = 1024;
 constexpr int GC_MAX_RT = 8;  // rows per warp and CTA (rows per CTA <= 256)
+constexpr size_t GC_SMEM = 200 * 1024;  // dynamic shared memory budget per CTA
 
+// nb: coarse steps whose outputs are staged in shared memory before they are
+// written out (no global stores inside a chunk, so the release side of the
+// cluster barriers has only shared-memory traffic to order)
 struct GcLayout {
-  int rpc, spc, ng;
-  size_t f_CA, f_xw, f_part, f_gu, f_gtmp, f_sbuf, n_f;  // float offsets
-  size_t d_xu, d_xw, d_ia, d_cb, d_fw, d_cw, n_d;        // double offsets (after the floats)
+  int rpc, spc, ng, nb;
+  size_t f_CA, f_xw, f_part, f_gu, f_acc, f_gtmp, f_sbuf, n_f;        // float offsets
+  size_t d_xu, d_xw, d_ia, d_cb, d_fw, d_cw, d_su, d_sg, d_sw, d_sh, n_d;  // double offsets (after the floats)
   size_t bytes;
 };
 
-__host__ __device__ inline GcLayout gc_layout(int d1, int d2, int CL) {
+__host__ __device__ inline GcLayout gc_layout(int d1, int d2, int CL, int nb) {
   GcLayout L{};
+  L.nb = nb;
   L.rpc = (d1 + CL - 1) / CL;
   L.spc = (d2 + CL - 1) / CL;
   L.ng = d2 >= GC_THREADS ? 1 : (GC_THREADS / d2 > 8 ? 8 : GC_THREADS / d2);
@@ -47,6 +54,8 @@ __host__ __device__ inline GcLayout gc_layout(int d1, int d2, int CL) {
   L.f_part = o;
   o += d2;
   L.f_gu = o;
+  o += L.rpc;
+  L.f_acc = o;
   o += L.rpc;
   L.f_gtmp = o;
   o += (size_t)L.ng * d2;
@@ -66,6 +75,14 @@ __host__ __device__ inline GcLayout gc_layout(int d1, int d2, int CL) {
   q += L.spc;
   L.d_cw = q;
   q += L.spc;
+  L.d_su = q;  // staged X_u rows, nb x rpc
+  q += (size_t)nb * L.rpc;
+  L.d_sg = q;  // staged G_u rows
+  q += (size_t)nb * L.rpc;
+  L.d_sw = q;  // staged X_w slice, nb x spc
+  q += (size_t)nb * L.spc;
+  L.d_sh = q;  // staged G_w slice
+  q += (size_t)nb * L.spc;
   L.n_d = q;
   L.bytes = L.n_f * 4 + L.n_d * 8;
   return L;
@@ -97,16 +114,16 @@ __device__ __forceinline__ void st_dsmem(uint32_t a, float v) {
 }
 
 template <int CL>
-__global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a) {
+__global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a, int nb) {
   extern __shared__ __align__(16) unsigned char gsm[];
   const int d1 = a.d1, d2 = a.d2;
-  const GcLayout L = gc_layout(d1, d2, CL);
+  const GcLayout L = gc_layout(d1, d2, CL, nb);
   float* fs = reinterpret_cast<float*>(gsm);
   double* ds = reinterpret_cast<double*>(gsm + L.n_f * 4);
-  float *sCA = fs + L.f_CA, *xw32 = fs + L.f_xw, *part = fs + L.f_part, *gu32 = fs + L.f_gu,
+  float *sCA = fs + L.f_CA, *xw32 = fs + L.f_xw, *part = fs + L.f_part, *gu32 = fs + L.f_gu, *accs = fs + L.f_acc,
         *gtmp = fs + L.f_gtmp, *sbuf = fs + L.f_sbuf;
   double *xud = ds + L.d_xu, *ia = ds + L.d_ia, *cb = ds + L.d_cb, *xwd = ds + L.d_xw, *fw = ds + L.d_fw,
-         *cw = ds + L.d_cw;
+         *cw = ds + L.d_cw, *stXu = ds + L.d_su, *stGu = ds + L.d_sg, *stXw = ds + L.d_sw, *stGw = ds + L.d_sh;
   const int rank = (int)cl_rank();
   const int r0 = rank * L.rpc, nr = max(0, min(d1, r0 + L.rpc) - r0);
   const int j0 = rank * L.spc, ns = max(0, min(d2, j0 + L.spc) - j0);
@@ -129,13 +146,16 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a) {
   }
   __syncthreads();
   cl_sync();  // every CTA of the cluster is resident before any DSMEM access
-  const int rt = nr > warp ? (nr - warp + 31) / 32 : 0;  // rows of this warp: q = warp + 32 t
+  const int rt = nr > warp ? (nr - warp + 31) / 32 : 0;  // matvec rows of this warp: q = warp + 32 t
+  int nbase = a.n_lo;
   for (int n = a.n_lo; n < a.n_hi; ++n) {
+    const int sl = n - nbase;  // staging slot of this step
     const double am = a.amp[n];
-    // values of this step that do not depend on the sweep, fetched up front
+    // inputs of this step that do not depend on the sweep, fetched up front by
+    // the threads that use them (row q = tid, column slice entry tid)
     double pf = 0.0, pg = 0.0, pc = 0.0;
-    if (lane < rt) {
-      const int i = r0 + warp + 32 * lane;
+    if (tid < nr) {
+      const int i = r0 + tid;
       if (!a.first) {
         pf = a.Fu[(size_t)n * d1 + i];
         pg = a.Gu[(size_t)n * d1 + i];
@@ -151,8 +171,7 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a) {
       }
       if (a.Cw) wc = a.Cw[(size_t)(n + 1) * d2 + j];
     }
-    // u-phase: one warp per row; lane t keeps row t's product
-    float mine = 0.f;
+    // u-phase products CA w: one warp per row
 #pragma unroll
     for (int t = 0; t < GC_MAX_RT; ++t) {
       if (t < rt) {
@@ -161,16 +180,18 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a) {
         float acc = 0.f;
         for (int j = lane; j < d2; j += 32) acc = fmaf(row[j], xw32[j], acc);
         acc = pintd::warp_sumf(acc);
-        if (lane == t) mine = acc;
+        if (lane == 0) accs[q] = acc;
       }
     }
-    if (lane < rt) {
-      const int q = warp + 32 * lane, i = r0 + q;
-      const double g = xud[q] * ia[q] - Dt * ia[q] * (double)mine + am * cb[q];
+    __syncthreads();
+    // FP64 updates packed into the first warps (the FP64 pipe is narrow)
+    if (tid < nr) {
+      const int q = tid;
+      const double g = xud[q] * ia[q] - Dt * ia[q] * (double)accs[q] + am * cb[q];
       double v = a.first ? g : g + pf - pg;
       v += pc;
-      a.Xu[(size_t)(n + 1) * d1 + i] = v;
-      a.Gu[(size_t)n * d1 + i] = g;
+      stXu[(size_t)sl * L.rpc + q] = v;
+      stGu[(size_t)sl * L.rpc + q] = g;
       xud[q] = v;
       gu32[q] = (float)g;
     }
@@ -201,8 +222,8 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a) {
       const double g = fw[tid] * xwd[tid] - Dt * (double)s + am * cw[tid];
       double v = a.first ? g : g + wf - wg;
       v += wc;
-      a.Xw[(size_t)(n + 1) * d2 + j] = v;
-      a.Gw[(size_t)n * d2 + j] = g;
+      stXw[(size_t)sl * L.spc + tid] = v;
+      stGw[(size_t)sl * L.spc + tid] = g;
       xwd[tid] = v;
       sbuf[tid] = (float)v;
     }
@@ -212,6 +233,21 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a) {
       st_dsmem(dsmem_addr(&xw32[j0 + q], (uint32_t)r), sbuf[q]);
     }
     cl_sync();  // new w in every CTA; partial buffers free again
+    if (sl + 1 == nb || n + 1 == a.n_hi) {  // write the staged chunk out
+      const int cnt = sl + 1;
+      for (int e = tid; e < cnt * nr; e += GC_THREADS) {
+        const int st = e / nr, q = e - st * nr;
+        a.Xu[(size_t)(nbase + st + 1) * d1 + r0 + q] = stXu[(size_t)st * L.rpc + q];
+        a.Gu[(size_t)(nbase + st) * d1 + r0 + q] = stGu[(size_t)st * L.rpc + q];
+      }
+      for (int e = tid; e < cnt * ns; e += GC_THREADS) {
+        const int st = e / ns, q = e - st * ns;
+        a.Xw[(size_t)(nbase + st + 1) * d2 + j0 + q] = stXw[(size_t)st * L.spc + q];
+        a.Gw[(size_t)(nbase + st) * d2 + j0 + q] = stGw[(size_t)st * L.spc + q];
+      }
+      __syncthreads();
+      nbase = n + 1;
+    }
   }
 }
 
@@ -238,7 +274,7 @@ bool gc_feasible(size_t bytes) {
     at[0].val.clusterDim.z = 1;
     cfg.gridDim = dim3(CL);
     cfg.blockDim = dim3(GC_THREADS);
-    cfg.dynamicSmemBytes = 200 * 1024;
+    cfg.dynamicSmemBytes = GC_SMEM;
     cfg.attrs = at;
     cfg.numAttrs = 1;
     int nclusters = 0;
@@ -248,12 +284,22 @@ bool gc_feasible(size_t bytes) {
     }
     ok = nclusters >= 1 ? 1 : 0;
   }
-  return ok == 1 && bytes <= 200 * 1024;
+  return ok == 1 && bytes <= GC_SMEM;
+}
+
+// staging depth: as many coarse steps as fit next to the resident coupling
+int gc_chunk(int d1, int d2, int CL, int steps) {
+  const GcLayout L1 = gc_layout(d1, d2, CL, 1), L0 = gc_layout(d1, d2, CL, 0);
+  const size_t per = L1.bytes - L0.bytes;
+  if (L1.bytes > GC_SMEM) return 0;
+  return (int)std::min<size_t>((size_t)std::max(steps, 1), 1 + (GC_SMEM - L1.bytes) / per);
 }
 
 template <int CL>
 void gc_launch(Ctx* c, const GcArgs& a) {
-  const GcLayout L = gc_layout(a.d1, a.d2, CL);
+  const int nb = gc_chunk(a.d1, a.d2, CL, a.n_hi - a.n_lo);
+  PINT_REQUIRE(nb >= 1, PINT_ERR_BAD_ARG, "coarse sweep does not fit the cluster");
+  const GcLayout L = gc_layout(a.d1, a.d2, CL, nb);
   cudaLaunchConfig_t cfg{};
   cudaLaunchAttribute at[1];
   at[0].id = cudaLaunchAttributeClusterDimension;
@@ -266,7 +312,7 @@ void gc_launch(Ctx* c, const GcArgs& a) {
   cfg.stream = c->stream;
   cfg.attrs = at;
   cfg.numAttrs = 1;
-  PINT_CUDA(cudaLaunchKernelEx(&cfg, k_g_sweep_cl<CL>, a));
+  PINT_CUDA(cudaLaunchKernelEx(&cfg, k_g_sweep_cl<CL>, a, nb));
   c->launches++;
 }
 
@@ -277,7 +323,7 @@ void gc_launch(Ctx* c, const GcArgs& a) {
 // grid-wide FP64 sweep).
 int gc_cluster_size(int d1, int d2) {
   for (int CL : {16, 8}) {
-    const GcLayout L = gc_layout(d1, d2, CL);
+    const GcLayout L = gc_layout(d1, d2, CL, 1);
     if (L.rpc > 32 * GC_MAX_RT) continue;
     if (CL == 16 && gc_feasible<16>(L.bytes)) return 16;
     if (CL == 8 && gc_feasible<8>(L.bytes)) return 8;

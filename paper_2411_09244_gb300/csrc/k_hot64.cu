@@ -275,12 +275,13 @@ __global__ void __launch_bounds__(128) k_w_sweep(const double* __restrict__ S, i
   }
 }
 
-__global__ void k_wr_norm(const double* __restrict__ acc, int cnt, double* __restrict__ out) {
+template <typename T>
+__global__ void k_wr_norm(const T* __restrict__ acc, int cnt, double* __restrict__ out) {
   __shared__ double sh[64];
   double m = 0.0;
   bool bad = false;
   for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-    double v = acc[e];
+    double v = (double)acc[e];
     if (!(v == v) || v > 1e300) bad = true;
     m = fmax(m, v);
   }
@@ -367,31 +368,42 @@ __global__ void k_step_w(const double* __restrict__ CMt, const double* __restric
 // CTA (n-1, part) handles rows i = part, part + JS, ... of CM and adds its
 // partial sum to jump2[n-1] (zeroed by the caller); k_max_fin takes sqrt
 constexpr int JS = 8;
+// T: arithmetic type of the coupling product (FP32 in the low-precision
+// path, where the jumps only steer the stopping test)
+template <typename T>
 __global__ void k_jump(const double* __restrict__ Xu, const double* __restrict__ Xw,
                        const double* __restrict__ Ou, const double* __restrict__ Ow,
-                       const double* __restrict__ CM, int d1, int d2, double* __restrict__ jump2) {
+                       const T* __restrict__ CM, int d1, int d2, double* __restrict__ jump2) {
   const int n = blockIdx.x + 1, part = blockIdx.y;
   __shared__ double sh[64];
-  __shared__ double dw[4096];
+  __shared__ T dw[4096];
   const double* xu = Xu + (size_t)n * d1;
   const double* ou = Ou + (size_t)n * d1;
-  for (int j = threadIdx.x; j < d2; j += blockDim.x) dw[j] = Xw[(size_t)n * d2 + j] - Ow[(size_t)n * d2 + j];
+  for (int j = threadIdx.x; j < d2; j += blockDim.x) dw[j] = (T)(Xw[(size_t)n * d2 + j] - Ow[(size_t)n * d2 + j]);
   __syncthreads();
-  double s = 0.0;
+  T s = 0;
   if (part == 0)
     for (int j = threadIdx.x; j < d2; j += blockDim.x) s += dw[j] * dw[j];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int i = part + JS * warp; i < d1; i += JS * nwarp) {
-    double t = 0.0;
-    for (int j = lane; j < d2; j += 32) t += CM[(size_t)i * d2 + j] * dw[j];
-    t = pintd::warp_sum(t);
-    if (lane == 0) {
-      const double du = xu[i] - ou[i];
-      s += du * du + 2.0 * du * t;
+  for (int i0 = part + JS * 32 * warp; i0 < d1; i0 += JS * 32 * nwarp) {
+    // 32 rows per warp pass; lane r keeps row i0 + JS r's product
+    T mine = 0;
+    for (int r = 0; r < 32; ++r) {
+      const int i = i0 + JS * r;
+      if (i >= d1) break;
+      T t = 0;
+      for (int j = lane; j < d2; j += 32) t += CM[(size_t)i * d2 + j] * dw[j];
+      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
+      if (lane == r) mine = t;
+    }
+    const int i = i0 + JS * lane;
+    if (i < d1) {
+      const T du = (T)(xu[i] - ou[i]);
+      s += du * du + 2 * du * mine;
     }
   }
-  s = pintd::block_sum(s, sh);
-  if (threadIdx.x == 0) atomicAdd(&jump2[n - 1], s);
+  const double sd = pintd::block_sum((double)s, sh);
+  if (threadIdx.x == 0) atomicAdd(&jump2[n - 1], sd);
 }
 
 // max over n of sqrt(max(x_n, 0)) (x = squared jumps), flags non-finite values
@@ -760,7 +772,7 @@ static int wr_sweep(Ctx* c, Hot& H, const double* xs_u, const double* xs_w, cons
     PINT_CUDA(cudaEventRecord(H.ev[3], c->stream));
     k_w_sweep<<<dim3(nb_(d2, 128), nact), 128, 0, c->stream>>>(H.S, d2, P, 0, H.Wt, c->lam2, H.b2,
                                                               amp_act, c->dt, H.acc + (size_t)nact * P);
-    k_wr_norm<<<1, 1024, 0, c->stream>>>(H.acc, 2 * nact * P, H.red);
+    k_wr_norm<double><<<1, 1024, 0, c->stream>>>(H.acc, 2 * nact * P, H.red);
     PINT_LAUNCH_CHECK();
     c->launches += 5;
     double h[2];
@@ -878,7 +890,7 @@ void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const dou
       g_sweep(c, H, H.Xu, H.Xw, H.amp, H.Fu, H.Fw, nullptr, nullptr, n_lo, false);
       g_sweep_check(c, H);
       PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
-    k_jump<<<dim3(N, JS), 256, 0, c->stream>>>(H.Xu, H.Xw, H.Ou, H.Ow, c->CM, d1, d2, H.red + 8);
+    k_jump<double><<<dim3(N, JS), 256, 0, c->stream>>>(H.Xu, H.Xw, H.Ou, H.Ow, c->CM, d1, d2, H.red + 8);
       k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
       PINT_LAUNCH_CHECK();
       c->launches += 2;
@@ -1014,9 +1026,9 @@ void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp,
 int mx_umma_split(int M, int Kp, int ncols, int maxs);
 void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const float* lam1, const float* src,
                      const float* b1, const double* amp, const float2* tw, const float2* dsh, const float2* dshbr,
-                     const float* bpow, double* accU, float* B1h, float* B1l);
+                     const float* bpow, float* accU, float* B1h, float* B1l);
 void mx_w_sweep32(Ctx* c, const float* S, int nsl, size_t slice, int nact, float* Wt, int ldw, const float* lam2,
-                  const float* src, const float* b2, const double* amp, double* accW, float* B0h, float* B0l);
+                  const float* src, const float* b2, const double* amp, float* accW, float* B0h, float* B0l);
 void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, float* Wt, int ldu, int ldw,
                float* B0h, float* B0l);
 void mx_ends32(Ctx* c, const float* Ut, const float* Wt, int ldu, int ldw, int nact, double* Fu, double* Fw);
@@ -1026,6 +1038,7 @@ void mx_pad_split(Ctx* c, const double* A, int rows, int dk, int ld, float* a32,
 void mx_residual(Ctx* c, const double* Zu, const double* Zw, const double* R64, const double* S64,
                  const double* b1, const double* b2, const double* amp, float* srcU, float* srcW);
 void mx_continuity(Ctx* c, const double* Zu, const double* Zw, double* Cu, double* Cw);
+void mx_ar_diff(Ctx* c, int ld, float* a32, float* hi, float* lo);
 void mx_add_traj(Ctx* c, const float* dUt, const float* dWt, int ldu, int ldw, const double* Yu, const double* Yw,
                  double* Zu, double* Zw);
 void mx_to_f32(Ctx* c, const double* x, long long n, float* y);
@@ -1060,6 +1073,7 @@ struct Mx {
   double *Zu = nullptr, *Zw = nullptr, *R64 = nullptr, *S64 = nullptr, *Cu = nullptr, *Cw = nullptr;
   double *Yu = nullptr, *Yw = nullptr, *zero = nullptr;
   float* CA32 = nullptr;  // FP32 coupling of the cluster coarse sweep
+  float* CM32 = nullptr;  // FP32 coupling of the jump norms
   int gcl = 0;            // its cluster size (0: grid-wide FP64 sweep)
   bool tensor = false;
   std::vector<void*> bufs;  // every device buffer above
@@ -1095,6 +1109,7 @@ static Mx& mx_prepare(Ctx* c) {
   M.AS32 = Fa((size_t)d2 * 2 * ldu);
   M.gcl = gc_cluster_size(d1, d2);
   if (M.gcl) M.CA32 = Fa((size_t)d1 * d2);
+  M.CM32 = Fa((size_t)d1 * d2);
   if (tensor) {
     M.Rhi = Fa((size_t)d1 * 2 * ldw);
     M.Rlo = Fa((size_t)d1 * 2 * ldw);
@@ -1154,9 +1169,10 @@ static Mx& mx_prepare(Ctx* c) {
 // FP32 copies of the time-grid dependent operators (refreshed every solve)
 static void mx_refresh(Ctx* c, Mx& M) {
   const int d1 = c->d1, d2 = c->d2;
-  mx_pad_split(c, c->AR, d1, d2, M.ldw, M.AR32, M.Rhi, M.Rlo);
+  mx_ar_diff(c, M.ldw, M.AR32, M.Rhi, M.Rlo);  // [-CA | -CM/dt] against [w_p ; w_p - w_{p-1}]
   mx_pad_split(c, c->AS, d2, d1, M.ldu, M.AS32, M.Shi, M.Slo);
   if (M.CA32) mx_to_f32(c, c->CA, (long long)d1 * d2, M.CA32);
+  mx_to_f32(c, c->CM, (long long)d1 * d2, M.CM32);
   mx_to_f32(c, c->lam1, d1, M.lam1f);
   mx_to_f32(c, c->lam2, d2, M.lam2f);
   mx_to_f32(c, c->lampow, 65, M.bpowf);
@@ -1192,25 +1208,26 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
   const int ldu = M.ldu, ldw = M.ldw;
   const bool tensor = (c->precision == PINT_MIXED);
   const int nsl = tensor ? mx_umma_split(d2, 2 * ldu, ncols, MX_MAX_SPLIT) : 1;
+  float* acc32 = reinterpret_cast<float*>(H.acc);  // FP32 squared updates (2 nact P)
   // column maps of the active window start at column 0 of B0 / B1
   mx_init32(c, xs_u, xs_w, nact, Ut, Wt, ldu, ldw, M.B0h, M.B0l);
   int it = 0;
   *bad = false;
   for (it = 1; it <= wr_max; ++it) {
-    PINT_CUDA(cudaMemsetAsync(H.acc, 0, (size_t)2 * nact * P * 8, c->stream));
+    PINT_CUDA(cudaMemsetAsync(acc32, 0, (size_t)2 * nact * P * 4, c->stream));
     PINT_CUDA(cudaEventRecord(H.ev[0], c->stream));
     if (tensor) mx_contract_umma(c, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, M.R, M.err);
     else mx_contract32(c, 0, M.AR32, d1, 2 * ldw, Ut, Wt, ldu, ldw, P, ncols, M.R);
     PINT_CUDA(cudaEventRecord(H.ev[1], c->stream));
-    mx_time_solve32(c, M.R, nact, Ut, ldu, M.lam1f, srcU, M.b1f, amp_act, M.twf, M.dshf, M.dshbr, M.bpowf, H.acc,
+    mx_time_solve32(c, M.R, nact, Ut, ldu, M.lam1f, srcU, M.b1f, amp_act, M.twf, M.dshf, M.dshbr, M.bpowf, acc32,
                     M.B1h, M.B1l);
     PINT_CUDA(cudaEventRecord(H.ev[2], c->stream));
     if (tensor) mx_contract_umma(c, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, nsl, M.S, M.err);
     else mx_contract32(c, 1, M.AS32, d2, 2 * ldu, Ut, Wt, ldu, ldw, P, ncols, M.S);
     PINT_CUDA(cudaEventRecord(H.ev[3], c->stream));
     mx_w_sweep32(c, M.S, tensor ? nsl : 1, (size_t)ncols * d2, nact, Wt, ldw, M.lam2f, srcW, M.b2f, amp_act,
-                 H.acc + (size_t)nact * P, M.B0h, M.B0l);
-    k_wr_norm<<<1, 1024, 0, c->stream>>>(H.acc, 2 * nact * P, H.red);
+                 acc32 + (size_t)nact * P, M.B0h, M.B0l);
+    k_wr_norm<float><<<1, 1024, 0, c->stream>>>(acc32, 2 * nact * P, H.red);
     PINT_LAUNCH_CHECK();
     c->launches++;
     double h[2];
@@ -1324,7 +1341,10 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
     PINT_CUDA(cudaMemcpyAsync(H.Ow, r.Xw, (size_t)(N + 1) * d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
     g_sweep_lp(c, H, M, r.Xu, r.Xw, r.amp, H.Fu, H.Fw, r.Cu, r.Cw, n_lo, false);
     PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
-    k_jump<<<dim3(N, JS), 256, 0, c->stream>>>(r.Xu, r.Xw, H.Ou, H.Ow, c->CM, d1, d2, H.red + 8);
+    if (M.CM32)
+      k_jump<float><<<dim3(N, JS), 256, 0, c->stream>>>(r.Xu, r.Xw, H.Ou, H.Ow, M.CM32, d1, d2, H.red + 8);
+    else
+      k_jump<double><<<dim3(N, JS), 256, 0, c->stream>>>(r.Xu, r.Xw, H.Ou, H.Ow, c->CM, d1, d2, H.red + 8);
     k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
     PINT_LAUNCH_CHECK();
     c->launches += 2;
@@ -1354,7 +1374,7 @@ static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw) {
   PINT_CUDA(cudaMemsetAsync(H.tmp1, 0, (size_t)(N + 1) * std::max(d1, d2) * 8, c->stream));
   // k_jump measures rows 1..N against the zero rows of tmp1
   PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
-  k_jump<<<dim3(N, JS), 256, 0, c->stream>>>(Xu, Xw, H.tmp1, H.tmp1, c->CM, d1, d2, H.red + 8);
+  k_jump<double><<<dim3(N, JS), 256, 0, c->stream>>>(Xu, Xw, H.tmp1, H.tmp1, c->CM, d1, d2, H.red + 8);
   k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
   PINT_LAUNCH_CHECK();
   double h[2];
@@ -1442,6 +1462,9 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
     PINT_CUDA(cudaMemcpyAsync(M.Sw + (size_t)N * d2, M.Zw + ((size_t)(N - 1) * (P + 1) + P) * d2, (size_t)d2 * 8,
                               cudaMemcpyDeviceToDevice, c->stream));
     const int ncols = N * P;
+    // The residual's terms are O(|x|) and cancel down to the rounding of the
+    // FP32 trajectory, so its contractions need FP64 accumulation: products
+    // accumulated in FP32 would err by as much as the residual itself.
     wr_gemm64<0>(c, c->AR, d1, 2 * d2, M.Zu, M.Zw, ncols, M.R64);
     wr_gemm64<1>(c, c->AS, d2, 2 * d1, M.Zu, M.Zw, ncols, M.S64);
     c->launches += 2;

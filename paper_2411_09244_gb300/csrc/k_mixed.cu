@@ -26,12 +26,14 @@ __device__ __forceinline__ void put_split(float* __restrict__ hi, float* __restr
   lo[o] = __uint_as_float(l);
 }
 
+// Squared WR updates are accumulated in FP32: they only steer the stopping
+// test, and FP64 conversions cost time on this part's narrow FP64 pipe.
 // Sum v[0..P) over the 32 lanes of a warp and add the P totals to acc[0..P):
 // recursive halving leaves each lane the totals of a contiguous slice of
 // max(P / 32, 1) entries (P a power of two), so one atomic instruction per
 // slice entry covers the warp.
 template <int P>
-__device__ __forceinline__ void warp_sum_scatter(float* v, double* __restrict__ acc) {
+__device__ __forceinline__ void warp_sum_scatter(float* v, float* __restrict__ acc) {
   const int lane = threadIdx.x & 31;
   int off = 0;
   int mask = 16;
@@ -53,12 +55,14 @@ __device__ __forceinline__ void warp_sum_scatter(float* v, double* __restrict__ 
   const int low = (P >= 32) ? 0 : (lane & (32 / P - 1));
   if (low == 0) {
 #pragma unroll
-    for (int k = 0; k < KEEP; ++k) atomicAdd(&acc[off + k], (double)v[k]);
+    for (int k = 0; k < KEEP; ++k) atomicAdd(&acc[off + k], v[k]);
   }
 }
 
-// FP32 contraction with the WR column maps (see k_wr_gemm in k_hot64.cu):
-// MODE 0: out = AR [w_p ; w_{max(p-1,0)}], MODE 1: out = AS [u_p - u_{max(p-1,0)} ; u_{p+1}]
+// FP32 contraction with the WR column maps in difference form:
+// MODE 0: out = AR' [w_p ; w_p - w_{max(p-1,0)}] with AR' = [-CA | -CM/dt]
+//         (= AR [w_p ; w_{p-1}] of k_wr_gemm without the CM/dt cancellation),
+// MODE 1: out = AS [u_p - u_{max(p-1,0)} ; u_{p+1}]
 // Trajectories use padded strides ldu, ldw (multiples of 32, pad entries 0);
 // the contraction dimension is K = 2 ld with A zero in the pad columns.
 template <int MODE>
@@ -79,7 +83,8 @@ __global__ void __launch_bounds__(256) k_wr_gemm32(const float* __restrict__ A, 
         int n = col / P, p = col % P;
         if (MODE == 0) {
           const float* Wn = Wt + (size_t)n * (P + 1) * ldw;
-          bv = (kg < ldw) ? Wn[(size_t)p * ldw + kg] : Wn[(size_t)(p >= 1 ? p - 1 : 0) * ldw + (kg - ldw)];
+          bv = (kg < ldw) ? Wn[(size_t)p * ldw + kg]
+                          : Wn[(size_t)p * ldw + (kg - ldw)] - Wn[(size_t)(p >= 1 ? p - 1 : 0) * ldw + (kg - ldw)];
         } else {
           const float* Un = Ut + (size_t)n * (P + 1) * ldu;
           if (kg < ldu) bv = Un[(size_t)p * ldu + kg] - Un[(size_t)(p >= 1 ? p - 1 : 0) * ldu + kg];
@@ -167,7 +172,7 @@ __global__ void __launch_bounds__(128) k_time_solve32(const float* __restrict__ 
                                                       const float2* __restrict__ tw,
                                                       const float2* __restrict__ dsh,
                                                       const float* __restrict__ bpow, int pow2,
-                                                      double* __restrict__ accU, float* __restrict__ B1h,
+                                                      float* __restrict__ accU, float* __restrict__ B1h,
                                                       float* __restrict__ B1l) {
   const int nloc = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -212,7 +217,7 @@ __global__ void __launch_bounds__(128) k_time_solve32(const float* __restrict__ 
       Un[(size_t)(p + 1) * ldu + i] = unew[p];
     }
     du = pintd::block_sum(du, sh);
-    if (threadIdx.x == 0) atomicAdd(&accU[(size_t)nloc * P + p], du);
+    if (threadIdx.x == 0) atomicAdd(&accU[(size_t)nloc * P + p], (float)du);
   }
 }
 
@@ -267,7 +272,7 @@ __global__ void __launch_bounds__(128) k_time_solve32_t(const float* __restrict_
                                                         const double* __restrict__ amp, float alpha, float dt,
                                                         const float2* __restrict__ tw,
                                                         const float2* __restrict__ dsh,
-                                                        const float* __restrict__ bpow, double* __restrict__ accU,
+                                                        const float* __restrict__ bpow, float* __restrict__ accU,
                                                         float* __restrict__ B1h, float* __restrict__ B1l) {
   const int nloc = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
@@ -331,7 +336,7 @@ __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, 
                                                    float* __restrict__ Wt, const float* __restrict__ lam2,
                                                    const float* __restrict__ src, const float* __restrict__ b2,
                                                    const double* __restrict__ amp, float dt, int nsl,
-                                                   size_t slice, double* __restrict__ accW,
+                                                   size_t slice, float* __restrict__ accW,
                                                    float* __restrict__ B0h, float* __restrict__ B0l) {
   const int nloc = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -352,15 +357,15 @@ __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, 
       float old = Wn[(size_t)(p + 1) * ldw + j];
       dw = (double)(wn - old) * (double)(wn - old);
       Wn[(size_t)(p + 1) * ldw + j] = wn;
-      if (B0h && p + 1 < P) {  // first-contraction column map of step p + 1: [w_{p+1} ; w_p]
+      if (B0h && p + 1 < P) {  // first-contraction column map of step p + 1: [w_{p+1} ; w_{p+1} - w_p]
         const size_t o = ((size_t)nloc * P + p + 1) * 2 * ldw + j;
         put_split(B0h, B0l, o, wn);
-        put_split(B0h, B0l, o + ldw, w);
+        put_split(B0h, B0l, o + ldw, wn - w);
       }
       w = wn;
     }
     dw = pintd::warp_sum(dw);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&accW[(size_t)nloc * P + p], dw);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&accW[(size_t)nloc * P + p], (float)dw);
   }
 }
 
@@ -465,7 +470,7 @@ __global__ void __launch_bounds__(256) k_time_solve32_sq(const float* __restrict
                                                          const double* __restrict__ amp, float alpha, float dt,
                                                          const float2* __restrict__ tw,
                                                          const float2* __restrict__ dsh,
-                                                         const float* __restrict__ bpow, double* __restrict__ accU,
+                                                         const float* __restrict__ bpow, float* __restrict__ accU,
                                                          float* __restrict__ B1h, float* __restrict__ B1l) {
   constexpr int P = R * R;       // steps per interval
   constexpr int NS = 256 / R;    // series (modes) per block
@@ -569,7 +574,7 @@ __global__ void __launch_bounds__(256) k_time_solve32_sq(const float* __restrict
     }
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, off);
-    if (lane == 0) atomicAdd(&accU[(size_t)nloc * P + p], (double)dd);  // a warp covers one row segment
+    if (lane == 0) atomicAdd(&accU[(size_t)nloc * P + p], dd);  // a warp covers one row segment
   }
 }
 
@@ -581,7 +586,7 @@ __global__ void __launch_bounds__(32) k_w_sweep32_t(const float* __restrict__ S,
                                                     float* __restrict__ Wt, const float* __restrict__ lam2,
                                                     const float* __restrict__ src, const float* __restrict__ b2,
                                                     const double* __restrict__ amp, float dt, int nsl,
-                                                    size_t slice, double* __restrict__ accW,
+                                                    size_t slice, float* __restrict__ accW,
                                                     float* __restrict__ B0h, float* __restrict__ B0l) {
   constexpr int CH = 16;
   const int nloc = blockIdx.y;
@@ -610,10 +615,10 @@ __global__ void __launch_bounds__(32) k_w_sweep32_t(const float* __restrict__ S,
         const int p = c0 + q;
         const float wn = fac * w + sv[q];
         Wn[(size_t)(p + 1) * ldw + j] = wn;
-        if (B0h && p + 1 < P) {  // first-contraction column map of step p + 1: [w_{p+1} ; w_p]
+        if (B0h && p + 1 < P) {  // first-contraction column map of step p + 1: [w_{p+1} ; w_{p+1} - w_p]
           const size_t o = ((size_t)nloc * P + p + 1) * 2 * ldw + j;
           put_split(B0h, B0l, o, wn);
-          put_split(B0h, B0l, o + ldw, w);
+          put_split(B0h, B0l, o + ldw, wn - w);
         }
         const float d = wn - ov[q];
         dd[p] = d * d;
@@ -628,7 +633,7 @@ __global__ void __launch_bounds__(32) k_w_sweep32_t(const float* __restrict__ S,
 }
 
 // constant initial trajectories; with B0h, also the first-contraction column
-// map [w_p ; w_{p-1}] = [x_w ; x_w] of every step
+// map [w_p ; w_p - w_{p-1}] = [x_w ; 0] of every step
 __global__ void k_init32(const double* __restrict__ Xu, const double* __restrict__ Xw, int d1, int d2, int ldu,
                          int ldw, int P, float* __restrict__ Ut, float* __restrict__ Wt, float* __restrict__ B0h,
                          float* __restrict__ B0l) {
@@ -641,10 +646,10 @@ __global__ void k_init32(const double* __restrict__ Xu, const double* __restrict
       const int j = k - d1;
       const float x = (float)Xw[(size_t)nloc * d2 + j];
       Wt[((size_t)nloc * (P + 1) + p) * ldw + j] = x;
-      if (B0h && p < P) {
+      if (B0h && p < P) {  // constant trajectory: [x_w ; 0]
         const size_t o = ((size_t)nloc * P + p) * 2 * ldw + j;
         put_split(B0h, B0l, o, x);
-        put_split(B0h, B0l, o + ldw, x);
+        put_split(B0h, B0l, o + ldw, 0.f);
       }
     }
   }
@@ -694,10 +699,9 @@ __global__ void k_add_traj(const float* __restrict__ dUt, const float* __restric
 }
 
 // residual of eqs. (2.4)-(2.5) on the FP64 trajectory (see the header):
-//   e_u = (1 + dt l1) u_{p+1} - u_p - dt R64_p - dt a b1
-//   e_w = w_{p+1} - (1 - dt l2) w_p - S64_p - dt a b2
-// written as the correction sources src_u = -e_u / dt, src_w = -e_w (FP32);
-// the largest |e| relative to the state goes to norm[0..1] (atomic max as bits)
+//   e_u = (1 + dt l1) u_{p+1} - u_p - dt R_p - dt a b1
+//   e_w = w_{p+1} - (1 - dt l2) w_p - S_p - dt a b2
+// written as the correction sources src_u = -e_u / dt, src_w = -e_w (FP32)
 __global__ void k_residual(const double* __restrict__ Zu, const double* __restrict__ Zw,
                            const double* __restrict__ R64, const double* __restrict__ S64,
                            const double* __restrict__ lam1, const double* __restrict__ lam2,
@@ -756,6 +760,21 @@ __global__ void k_pad_split(const double* __restrict__ A, int rows, int dk, int 
   }
 }
 
+// AR' = [-CA | -CM/dt] (d1 x 2 d2, FP64 couplings) -> FP32 rows of 2 ld with
+// both halves padded; with hi, also the TF32 pairs
+__global__ void k_ar_diff(const double* __restrict__ CA, const double* __restrict__ CM, double dt, int d1, int d2,
+                          int ld, float* __restrict__ a32, float* __restrict__ hi, float* __restrict__ lo) {
+  long long tot = (long long)d1 * 2 * ld;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < tot; e += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(e / (2 * ld)), k = (int)(e % (2 * ld));
+    const int seg = k / ld, j = k % ld;
+    float v = 0.f;
+    if (j < d2) v = seg == 0 ? (float)(-CA[(size_t)r * d2 + j]) : (float)(-CM[(size_t)r * d2 + j] / dt);
+    a32[e] = v;
+    if (hi) put_split(hi, lo, (size_t)e, v);
+  }
+}
+
 __global__ void k_to_f32(const double* __restrict__ x, long long n, float* __restrict__ y) {
   long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (e < n) y[e] = (float)x[e];
@@ -776,7 +795,7 @@ void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* 
 
 void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const float* lam1, const float* src,
                      const float* b1, const double* amp, const float2* tw, const float2* dsh, const float2* dshbr,
-                     const float* bpow, double* accU, float* B1h, float* B1l) {
+                     const float* bpow, float* accU, float* B1h, float* B1l) {
   const int P = c->P;
   const dim3 grid(nbl(c->d1, 128), nact);
   const float al = (float)c->alpha, dt = (float)c->dt;
@@ -798,7 +817,7 @@ void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const
 
 // S holds nsl K-slices of the contraction, slice floats apart (summed here)
 void mx_w_sweep32(Ctx* c, const float* S, int nsl, size_t slice, int nact, float* Wt, int ldw, const float* lam2,
-                  const float* src, const float* b2, const double* amp, double* accW, float* B0h, float* B0l) {
+                  const float* src, const float* b2, const double* amp, float* accW, float* B0h, float* B0l) {
   PINT_REQUIRE(nsl >= 1 && nsl <= MAX_SLICES, PINT_ERR_BAD_ARG, "too many contraction slices");
   const int P = c->P, d2 = c->d2;
   const float dt = (float)c->dt;
@@ -849,6 +868,11 @@ void mx_residual(Ctx* c, const double* Zu, const double* Zw, const double* R64, 
                                                     c->d1, c->d2, c->P, srcU, srcW);
   PINT_LAUNCH_CHECK();
   c->launches++;
+}
+
+void mx_ar_diff(Ctx* c, int ld, float* a32, float* hi, float* lo) {
+  k_ar_diff<<<1024, 256, 0, c->stream>>>(c->CA, c->CM, c->dt, c->d1, c->d2, ld, a32, hi, lo);
+  PINT_LAUNCH_CHECK();
 }
 
 void mx_continuity(Ctx* c, const double* Zu, const double* Zw, double* Cu, double* Cw) {
