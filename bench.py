@@ -132,6 +132,23 @@ def load_peaks():
 # float64, 4096^3, best of 10); MEASURED_PEAKS.json carries no FP64 figure.
 FP64_MEASURED_TFLOPS = 1.096
 
+# DRAM bytes (read + write) per launch of the tensor-core contraction on this
+# workload, averaged over its two launches, from the ncu capture summarised in
+# profiles/k_wr_umma_c2_mixed.md; only valid for the kernel source it was taken on.
+UMMA_TRAFFIC = {"sha1": "b2ad359729746bd1b09cd3377111a4023eb07edd",
+                "bytes": (23.915264e6 + 0.014080e6 + 89.975808e6 + 3.693568e6) / 2}
+
+
+def umma_traffic():
+    import hashlib
+    path = os.path.join(ROOT, "paper_2411_09244_gb300", "csrc", "k_umma.cu")
+    try:
+        with open(path, "rb") as fh:
+            h = hashlib.sha1(fh.read()).hexdigest()
+    except OSError:
+        return None
+    return UMMA_TRAFFIC["bytes"] if h == UMMA_TRAFFIC["sha1"] else None
+
 
 def problem(name):
     from paper_2411_09244_gb300 import inputs
@@ -273,11 +290,15 @@ def run_ours(args, rank, world):
     elif args.precision == "mixed":
         # TF32 dense peak = measured sustained BF16 x nominal TF32/BF16 ratio (1.1 / 2.25)
         pk = peaks.get("bf16_tflops_sustained", peaks.get("bf16_tflops")) * (1.1 / 2.25)
+        tr = umma_traffic() if args.config == "c2" else None
         roof = {"bound": "tensor", "kernel": "k_wr_umma (tcgen05 kind::tf32 WR contractions)",
                 "achieved": achieved, "peak": pk, "unit": "TFLOP/s",
-                "frac": (achieved / pk) if achieved else None, "traffic": None,
+                "frac": (achieved / pk) if achieved else None, "traffic": tr,
+                "traffic_unit": "bytes per launch (ncu dram read+write, profiles/k_wr_umma_c2_mixed.md)",
                 "peak_source": f"{src} bf16 sustained x 1.1/2.25 (TF32)",
-                "note": "achieved counts the algorithmic 2 M N K once; the hi/lo split issues 3 MMAs per K step"}
+                "mma_frac": (3 * achieved / pk) if achieved else None,
+                "note": "achieved counts the algorithmic 2 M N K once; the hi/lo split issues 3 MMAs per "
+                        "K step, so the tensor pipe runs mma_frac of its peak"}
     else:
         pk = 69.7
         roof = {"bound": "alu", "kernel": "k_wr_gemm32 (FP32 CUDA-core WR contractions)", "achieved": achieved,
