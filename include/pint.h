@@ -178,15 +178,23 @@ pint_status pint_sequential_solve(pint_ctx* ctx, const double* u0_nodes, const d
  * pint_adjoint -- gradient of the observation misfit
  * J = 1/2 sum_{n=1..N} sum_o (u_H^n(x_o) - d_{o,n})^2 with respect to u0
  * and the amplitudes, through the transposed parareal sweeps (the forward
- * map of Algorithm 1 at its limit is linear in (u0, amp)).
- *   obs_nodes   ptr (int32), n_obs node ids
+ * map of Algorithm 1 at its limit is affine in (u0, amp); the paper does
+ * not treat differentiation).  Runs the forward solve (the context's
+ * precision), keeps the coarse states as checkpoints, then parareal
+ * backwards in time with the transposed fine scheme on all intervals at once
+ * and the transposed coarse step (FP64 on the FP64 path, FP32 transposed
+ * sweeps on the low-precision paths).
+ *   obs_nodes   ptr (int32, host or device), n_obs node ids in [0, (n_f+1)^2)
  *   data        ptr, N x n_obs observations d_{o,n}
  *   u0_nodes, f_shape, amp   as in pint_parareal_solve
- *   eps, k_max, wr_tol, wr_max  controls of the forward and adjoint sweeps
+ *   eps, k_max, wr_tol, wr_max  controls of the forward solve; the backward
+ *               sweep stops when the summed change of the adjoint states is
+ *               below 1e-14 (FP64) or 1e-7 (FP32) of their largest norm, or
+ *               at k = N, where it is exact
  *   misfit      host double*, receives J (may be NULL)
  *   grad_u0     ptr or NULL, (n_f+1)^2
  *   grad_amp    ptr or NULL, N
- * Errors: as pint_parareal_solve.
+ * Errors: as pint_parareal_solve; BAD_ARG for an observation id out of range.
  */
 pint_status pint_adjoint(pint_ctx* ctx, const int* obs_nodes, int n_obs, const double* data,
                          const double* u0_nodes, const double* f_shape, const double* amp,

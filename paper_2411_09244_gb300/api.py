@@ -158,6 +158,44 @@ class Pint:
         return out, it.value
 
 
+    def adjoint(self, obs_nodes, data, u0_nodes, f_shape, amp=None, eps=1e-10, k_max=None, wr_tol=None,
+                wr_max=200):
+        """pint_adjoint: (J, dJ/du0 [(n_f+1)^2], dJ/damp [N]) of the misfit
+        J = 1/2 sum_{n=1..N} sum_o (u_H^n(x_o) - data[n-1, o])^2."""
+        obs = torch.as_tensor(np.asarray(obs_nodes), dtype=torch.int32).contiguous()
+        d = _f64(data, self.device)
+        u0 = _f64(u0_nodes, self.device)
+        f = _f64(f_shape, self.device)
+        a = _f64(amp, self.device)
+        k_max = self.N if k_max is None else k_max
+        wr_tol = 1e-3 * eps if wr_tol is None else wr_tol
+        J = C.c_double(0.0)
+        g_u0 = torch.empty(self.nn, dtype=torch.float64, device=self.device)
+        g_amp = torch.empty(self.N, dtype=torch.float64, device=self.device)
+        L.check(self.lib.pint_adjoint(self.h, L.ptr(obs), int(obs.numel()), L.ptr(d), L.ptr(u0), L.ptr(f),
+                                      L.ptr(a), eps, k_max, wr_tol, wr_max, C.byref(J), L.ptr(g_u0),
+                                      L.ptr(g_amp)))
+        return J.value, g_u0, g_amp
+
+
+class ObservationMisfit(torch.autograd.Function):
+    """J(u0, amp) = 1/2 sum_{n,o} (u_H^n(x_o) - d_{o,n})^2 through the limit of
+    Algorithm 1; backward runs the adjoint (backward) parareal sweep of
+    pint_adjoint.  Usage: J = ObservationMisfit.apply(u0, amp, pint, obs, data, f_shape, opts)."""
+
+    @staticmethod
+    def forward(ctx, u0, amp, pint, obs_nodes, data, f_shape, opts=None):
+        opts = dict(opts or {})
+        J, g_u0, g_amp = pint.adjoint(obs_nodes, data, u0.detach(), f_shape, amp.detach(), **opts)
+        ctx.save_for_backward(g_u0.to(u0.device, u0.dtype), g_amp.to(amp.device, amp.dtype))
+        return torch.tensor(J, dtype=u0.dtype, device=u0.device)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        g_u0, g_amp = ctx.saved_tensors
+        return grad_out * g_u0, grad_out * g_amp, None, None, None, None, None
+
+
 def from_problem(prob, device="cuda", precision=L.PINT_FP64, T=None):
     """Build a Pint for a seeded Problem (inputs module) through all setup stages."""
     p = Pint(prob.n_f, prob.kappa, device=device)

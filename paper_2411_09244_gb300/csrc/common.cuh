@@ -121,6 +121,7 @@ struct Ctx {
 
   // mixed-path state lives in mixed.cu
   void* mixed = nullptr;
+  void* adj = nullptr;  // adjoint buffers (k_adjoint.cu)
 
   // scratch for solves (grown on demand)
   std::vector<std::pair<void*, size_t>> scratch;
@@ -169,6 +170,15 @@ void apply_G_dev(Ctx* c, const double* in, int count, const double* f_nodes, con
                  double* out);
 void apply_F_dev(Ctx* c, const double* in, int count, const double* f_nodes, const double* amp_dev,
                  double wr_tol, int wr_max, double* out, int* iters);
+
+// adjoint of the converged parareal map (k_adjoint.cu); obs and data on the device
+void adjoint_solve(Ctx* c, const int* obs, int n_obs, const double* data, const double* u0_nodes,
+                   const double* f_nodes, const double* amp_dev, double eps, int k_max, double wr_tol, int wr_max,
+                   double* misfit_host, double* grad_u0, double* grad_amp);
+void adjoint_release(Ctx* c);
+// forward-state access for the adjoint (k_hot64.cu)
+void hot_states(Ctx* c, double** Xu, double** Xw);
+void unit_response(Ctx* c, double* su, double* sw);
 
 // FP32 coarse sweep on one thread-block cluster (k_gcluster.cu)
 struct GcArgs {

@@ -953,6 +953,34 @@ void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const dou
   PINT_REQUIRE(converged, PINT_ERR_NOT_CONVERGED, "parareal stopped at k_max above eps");
 }
 
+// spectral coarse states of the last solve, (N+1) rows each
+void hot_states(Ctx* c, double** Xu, double** Xw) {
+  Hot& H = hot(c);
+  *Xu = H.Xu;
+  *Xw = H.Xw;
+}
+
+// s~ = F*(0; unit source) in spectral coordinates: P fine steps from a zero
+// state (lags restarted) with the spectral loads of the last solve, FP64
+void unit_response(Ctx* c, double* su, double* sw) {
+  Hot& H = hot(c);
+  const int d1 = c->d1, d2 = c->d2;
+  double *u = H.Fu, *w = H.Fw, *ul = H.Gu, *wl = H.Gw, *uo = H.tmp1, *wo = H.tmp2;
+  PINT_CUDA(cudaMemsetAsync(u, 0, d1 * 8, c->stream));
+  PINT_CUDA(cudaMemsetAsync(w, 0, d2 * 8, c->stream));
+  PINT_CUDA(cudaMemsetAsync(ul, 0, d1 * 8, c->stream));
+  PINT_CUDA(cudaMemsetAsync(wl, 0, d2 * 8, c->stream));
+  for (int p = 0; p < c->P; ++p) {
+    step_batch(c, H, u, w, ul, wl, nullptr, c->dt, 1, uo, wo);
+    std::swap(ul, u);  // lag <- current (old lag buffer is recycled below)
+    std::swap(wl, w);
+    std::swap(u, uo);  // current <- new
+    std::swap(w, wo);
+  }
+  PINT_CUDA(cudaMemcpyAsync(su, u, d1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(sw, w, d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+}
+
 void apply_G_dev(Ctx* c, const double* in, int count, const double* f_nodes, const double* amp_dev,
                  double* out) {
   Hot& H = hot(c);

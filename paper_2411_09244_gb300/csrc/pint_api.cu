@@ -309,25 +309,41 @@ pint_status pint_adjoint(pint_ctx* ctx, const int* obs_nodes, int n_obs, const d
                          const double* u0_nodes, const double* f_shape, const double* amp, double eps,
                          int k_max, double wr_tol, int wr_max, double* misfit, double* grad_u0,
                          double* grad_amp) {
-  (void)obs_nodes;
-  (void)n_obs;
-  (void)data;
-  (void)u0_nodes;
-  (void)f_shape;
-  (void)amp;
-  (void)eps;
-  (void)k_max;
-  (void)wr_tol;
-  (void)wr_max;
-  (void)misfit;
-  (void)grad_u0;
-  (void)grad_amp;
-  if (!ctx) {
+  Ctx* c = (Ctx*)ctx;
+  if (!c) {
     set_error("ctx is NULL");
     return PINT_ERR_BAD_ARG;
   }
-  set_error("pint_adjoint: not available in this build");
-  return PINT_ERR_STATE;
+  return guarded(c, [&](std::vector<void*>& tmp) {
+    PINT_REQUIRE(c->have_time, PINT_ERR_STATE, "pint_assemble_reduced first");
+    PINT_REQUIRE(obs_nodes && n_obs >= 1 && data && u0_nodes && f_shape, PINT_ERR_BAD_ARG,
+                 "obs_nodes, n_obs >= 1, data, u0_nodes and f_shape are required");
+    PINT_REQUIRE(eps >= 0 && wr_tol >= 0 && k_max >= 1 && wr_max >= 1, PINT_ERR_BAD_ARG,
+                 "eps, wr_tol >= 0 and k_max, wr_max >= 1");
+    // observation node ids: checked on the host, used on the device
+    std::vector<int> h_obs(n_obs);
+    const bool obs_dev = is_device_ptr(obs_nodes);
+    if (obs_dev)
+      PINT_CUDA(cudaMemcpyAsync(h_obs.data(), obs_nodes, (size_t)n_obs * 4, cudaMemcpyDeviceToHost, c->stream));
+    else
+      std::memcpy(h_obs.data(), obs_nodes, (size_t)n_obs * 4);
+    PINT_CUDA(cudaStreamSynchronize(c->stream));
+    for (int o = 0; o < n_obs; ++o)
+      PINT_REQUIRE(h_obs[o] >= 0 && h_obs[o] < c->nn, PINT_ERR_BAD_ARG, "observation node id out of range");
+    int* d_obs = (int*)dalloc(c, (size_t)n_obs * 4);
+    tmp.push_back(d_obs);
+    PINT_CUDA(cudaMemcpyAsync(d_obs, h_obs.data(), (size_t)n_obs * 4, cudaMemcpyHostToDevice, c->stream));
+    const double* dd = stage_in(c, data, (size_t)c->N * n_obs, tmp);
+    const double* du0 = stage_in(c, u0_nodes, c->nn, tmp);
+    const double* df = stage_in(c, f_shape, c->nn, tmp);
+    const double* da = stage_in(c, amp, c->N, tmp);
+    OutBuf og = stage_out(c, grad_u0, c->nn, tmp);
+    OutBuf oa = stage_out(c, grad_amp, c->N, tmp);
+    adjoint_solve(c, d_obs, n_obs, dd, du0, df, da, eps, k_max, wr_tol, wr_max, misfit, og.dev, oa.dev);
+    finish_out(c, og);
+    finish_out(c, oa);
+    PINT_CUDA(cudaStreamSynchronize(c->stream));
+  });
 }
 
 pint_status pint_get_reduced(pint_ctx* ctx, int which, double* out, const double* aux) {
@@ -467,6 +483,7 @@ pint_status pint_destroy(pint_ctx* ctx) {
   cudaStreamSynchronize(c->stream);
   hot_release(c);
   mixed_release(c);
+  adjoint_release(c);
   delete c;
   cudaGetLastError();
   return PINT_OK;
