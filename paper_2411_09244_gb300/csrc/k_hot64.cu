@@ -1067,6 +1067,9 @@ void mx_residual(Ctx* c, const double* Zu, const double* Zw, const double* R64, 
                  const double* b1, const double* b2, const double* amp, float* srcU, float* srcW);
 void mx_continuity(Ctx* c, const double* Zu, const double* Zw, double* Cu, double* Cw);
 void mx_ar_diff(Ctx* c, int ld, float* a32, float* hi, float* lo);
+void mx_split_df(Ctx* c, const double* x, long long n, float* h, float* l);
+void mx_wr_gemm_df(Ctx* c, int mode, const float* Ah, const float* Al, int M, int K, const float* Uh,
+                   const float* Ul, const float* Wh, const float* Wl, int ncols, double* out);
 void mx_add_traj(Ctx* c, const float* dUt, const float* dWt, int ldu, int ldw, const double* Yu, const double* Yw,
                  double* Zu, double* Zw);
 void mx_to_f32(Ctx* c, const double* x, long long n, float* y);
@@ -1102,6 +1105,9 @@ struct Mx {
   double *Yu = nullptr, *Yw = nullptr, *zero = nullptr;
   float* CA32 = nullptr;  // FP32 coupling of the cluster coarse sweep
   float* CM32 = nullptr;  // FP32 coupling of the jump norms
+  // double-float pairs of AR, AS and of the FP64 trajectory (refinement residual)
+  float *ARh = nullptr, *ARl = nullptr, *ASh = nullptr, *ASl = nullptr;
+  float *Zuh = nullptr, *Zul = nullptr, *Zwh = nullptr, *Zwl = nullptr;
   int gcl = 0;            // its cluster size (0: grid-wide FP64 sweep)
   bool tensor = false;
   std::vector<void*> bufs;  // every device buffer above
@@ -1184,6 +1190,14 @@ static Mx& mx_prepare(Ctx* c) {
   M.Zw = Da((size_t)N * (P + 1) * d2);
   M.R64 = Da((size_t)N * P * d1);
   M.S64 = Da((size_t)N * P * d2);
+  M.ARh = Fa((size_t)d1 * 2 * d2);
+  M.ARl = Fa((size_t)d1 * 2 * d2);
+  M.ASh = Fa((size_t)d2 * 2 * d1);
+  M.ASl = Fa((size_t)d2 * 2 * d1);
+  M.Zuh = Fa((size_t)N * (P + 1) * d1);
+  M.Zul = Fa((size_t)N * (P + 1) * d1);
+  M.Zwh = Fa((size_t)N * (P + 1) * d2);
+  M.Zwl = Fa((size_t)N * (P + 1) * d2);
   M.Cu = Da((size_t)(N + 1) * d1);
   M.Cw = Da((size_t)(N + 1) * d2);
   M.Yu = Da((size_t)(N + 1) * d1);
@@ -1201,6 +1215,8 @@ static void mx_refresh(Ctx* c, Mx& M) {
   mx_pad_split(c, c->AS, d2, d1, M.ldu, M.AS32, M.Shi, M.Slo);
   if (M.CA32) mx_to_f32(c, c->CA, (long long)d1 * d2, M.CA32);
   mx_to_f32(c, c->CM, (long long)d1 * d2, M.CM32);
+  mx_split_df(c, c->AR, (long long)d1 * 2 * d2, M.ARh, M.ARl);
+  mx_split_df(c, c->AS, (long long)d2 * 2 * d1, M.ASh, M.ASl);
   mx_to_f32(c, c->lam1, d1, M.lam1f);
   mx_to_f32(c, c->lam2, d2, M.lam2f);
   mx_to_f32(c, c->lampow, 65, M.bpowf);
@@ -1491,11 +1507,13 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
                               cudaMemcpyDeviceToDevice, c->stream));
     const int ncols = N * P;
     // The residual's terms are O(|x|) and cancel down to the rounding of the
-    // FP32 trajectory, so its contractions need FP64 accumulation: products
-    // accumulated in FP32 would err by as much as the residual itself.
-    wr_gemm64<0>(c, c->AR, d1, 2 * d2, M.Zu, M.Zw, ncols, M.R64);
-    wr_gemm64<1>(c, c->AS, d2, 2 * d1, M.Zu, M.Zw, ncols, M.S64);
-    c->launches += 2;
+    // FP32 trajectory, so its contractions need more than FP32 accumulation
+    // (products accumulated in FP32 would err by as much as the residual);
+    // double-float arithmetic on the FP32 pipe gives ~48 bits.
+    mx_split_df(c, M.Zu, (long long)N * (P + 1) * d1, M.Zuh, M.Zul);
+    mx_split_df(c, M.Zw, (long long)N * (P + 1) * d2, M.Zwh, M.Zwl);
+    mx_wr_gemm_df(c, 0, M.ARh, M.ARl, d1, 2 * d2, M.Zuh, M.Zul, M.Zwh, M.Zwl, ncols, M.R64);
+    mx_wr_gemm_df(c, 1, M.ASh, M.ASl, d2, 2 * d1, M.Zuh, M.Zul, M.Zwh, M.Zwl, ncols, M.S64);
     mx_residual(c, M.Zu, M.Zw, M.R64, M.S64, H.b1, H.b2, H.amp, M.srcU, M.srcW);
     mx_continuity(c, M.Zu, M.Zw, M.Cu, M.Cw);
     LpRun y{};

@@ -10,6 +10,8 @@
 // F1~ is) and src_w = -e_w (added in the recurrence).
 #include "common.cuh"
 
+#include <algorithm>
+
 namespace pint {
 
 namespace {
@@ -366,6 +368,121 @@ __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, 
     }
     dw = pintd::warp_sum(dw);
     if ((threadIdx.x & 31) == 0) atomicAdd(&accW[(size_t)nloc * P + p], (float)dw);
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Refinement residual contractions in double-float arithmetic.
+//
+// The residual's terms are O(|x|) and cancel down to the rounding of the FP32
+// trajectory, so its products need more than FP32 accumulation but not the
+// full FP64 format: ~34 correct bits suffice.  GB300's FP64 pipe is narrow
+// (~1.1 TFLOP/s), its FP32 pipe tens of times wider, so the products run as
+// double-float arithmetic (a value is the unevaluated pair hi + lo of two
+// FP32 numbers, ~48 bits): each product's high part is formed exactly by the
+// FMA form of Dekker's product (p = ah bh, e = fma(ah, bh, -p)), the cross
+// terms ah bl + al bh join the error term, and the running sum is kept as a
+// pair, Knuth's TwoSum on the high parts and the errors summed in FP32.
+// Same column maps as k_wr_gemm (FP64 path), operands pre-split into pairs.
+__device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float s = sh + p;
+  const float bb = s - sh;
+  const float err = (sh - (s - bb)) + (p - bb);
+  sh = s;
+  sl += err + e;
+}
+
+// (ah + al) - (bh + bl) as a renormalised pair
+__device__ __forceinline__ void df_sub(float ah, float al, float bh, float bl, float& h, float& l) {
+  const float s = ah - bh;
+  const float bb = s - ah;
+  float e = (ah - (s - bb)) + (-bh - bb);
+  e += al - bl;
+  h = s + e;
+  l = e - (h - s);
+}
+
+template <int MODE, int T>
+__global__ void __launch_bounds__(256) k_wr_gemm_df(const float* __restrict__ Ah, const float* __restrict__ Al,
+                                                    int M, int K, const float* __restrict__ Uh,
+                                                    const float* __restrict__ Ul, const float* __restrict__ Wh,
+                                                    const float* __restrict__ Wl, int d1, int d2, int P, int ncols,
+                                                    double* __restrict__ out) {
+  constexpr int R = T / 16;
+  __shared__ float Ash[16][T + 1], Asl[16][T + 1], Bsh[16][T + 1], Bsl[16][T + 1];
+  const int i0 = blockIdx.y * T, j0 = blockIdx.x * T;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float sh[R][R] = {}, sl[R][R] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * T; e += 256) {
+      const int kk = e % 16, r = e / 16;
+      const int kg = k0 + kk, ig = i0 + r, col = j0 + r;
+      float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
+      if (kg < K && ig < M) {
+        ah = Ah[(size_t)ig * K + kg];
+        al = Al[(size_t)ig * K + kg];
+      }
+      if (kg < K && col < ncols) {
+        const int n = col / P, p = col % P;
+        if (MODE == 0) {  // [w_p ; w_{max(p-1,0)}]
+          const size_t base = (size_t)n * (P + 1) * d2;
+          const size_t o = (kg < d2) ? base + (size_t)p * d2 + kg
+                                     : base + (size_t)(p >= 1 ? p - 1 : 0) * d2 + (kg - d2);
+          bh = Wh[o];
+          bl = Wl[o];
+        } else {  // [u_p - u_{max(p-1,0)} ; u_{p+1}]
+          const size_t base = (size_t)n * (P + 1) * d1;
+          if (kg < d1) {
+            const size_t o1 = base + (size_t)p * d1 + kg, o0 = base + (size_t)(p >= 1 ? p - 1 : 0) * d1 + kg;
+            df_sub(Uh[o1], Ul[o1], Uh[o0], Ul[o0], bh, bl);
+          } else {
+            const size_t o = base + (size_t)(p + 1) * d1 + (kg - d1);
+            bh = Uh[o];
+            bl = Ul[o];
+          }
+        }
+      }
+      Ash[kk][r] = ah;
+      Asl[kk][r] = al;
+      Bsh[kk][r] = bh;
+      Bsl[kk][r] = bl;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a_h[R], a_l[R], b_h[R], b_l[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        a_h[q] = Ash[kk][ty * R + q];
+        a_l[q] = Asl[kk][ty * R + q];
+        b_h[q] = Bsh[kk][tx * R + q];
+        b_l[q] = Bsl[kk][tx * R + q];
+      }
+#pragma unroll
+      for (int p = 0; p < R; ++p)
+#pragma unroll
+        for (int q = 0; q < R; ++q) df_fma(a_h[p], a_l[p], b_h[q], b_l[q], sh[p][q], sl[p][q]);
+    }
+    __syncthreads();
+  }
+  for (int p = 0; p < R; ++p)
+    for (int q = 0; q < R; ++q) {
+      const int i = i0 + ty * R + p, col = j0 + tx * R + q;
+      if (i < M && col < ncols) out[(size_t)col * M + i] = (double)sh[p][q] + (double)sl[p][q];
+    }
+}
+
+// x -> (h, l) with h = fl32(x), l = fl32(x - h)
+__global__ void k_split_df(const double* __restrict__ x, long long n, float* __restrict__ h, float* __restrict__ l) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double v = x[e];
+    const float hv = (float)v;
+    h[e] = hv;
+    l[e] = (float)(v - (double)hv);
   }
 }
 
@@ -884,6 +1001,44 @@ void mx_continuity(Ctx* c, const double* Zu, const double* Zw, double* Cu, doubl
 void mx_pad_split(Ctx* c, const double* A, int rows, int dk, int ld, float* a32, float* hi, float* lo) {
   k_pad_split<<<1024, 256, 0, c->stream>>>(A, rows, dk, ld, a32, hi, lo);
   PINT_LAUNCH_CHECK();
+}
+
+void mx_split_df(Ctx* c, const double* x, long long n, float* h, float* l) {
+  k_split_df<<<std::min<long long>(nbl(n, 256), 4096), 256, 0, c->stream>>>(x, n, h, l);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+}
+
+// out = A [column map of the double-float trajectory] (MODE 0: A = AR, rows d1,
+// K = 2 d2; MODE 1: A = AS, rows d2, K = 2 d1), all N P columns; T x T tiles
+// chosen for an even spread over the SMs
+void mx_wr_gemm_df(Ctx* c, int mode, const float* Ah, const float* Al, int M, int K, const float* Uh,
+                   const float* Ul, const float* Wh, const float* Wl, int ncols, double* out) {
+  int sms = 0, dev = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  sms = std::max(sms, 1);
+  auto eff = [&](int T) {
+    const long long t = (long long)nbl(M, T) * nbl(ncols, T);
+    const double waves = (double)((t + 3 * sms - 1) / (3 * sms));  // ~3 resident CTAs per SM
+    return ((double)t / (3 * sms) / waves) * ((double)M * ncols / ((double)t * T * T));
+  };
+  const int T = eff(64) >= eff(32) ? 64 : 32;
+  const dim3 grid(nbl(ncols, T), nbl(M, T));
+  const int d1 = c->d1, d2 = c->d2, P = c->P;
+  if (mode == 0) {
+    if (T == 64)
+      k_wr_gemm_df<0, 64><<<grid, 256, 0, c->stream>>>(Ah, Al, M, K, Uh, Ul, Wh, Wl, d1, d2, P, ncols, out);
+    else
+      k_wr_gemm_df<0, 32><<<grid, 256, 0, c->stream>>>(Ah, Al, M, K, Uh, Ul, Wh, Wl, d1, d2, P, ncols, out);
+  } else {
+    if (T == 64)
+      k_wr_gemm_df<1, 64><<<grid, 256, 0, c->stream>>>(Ah, Al, M, K, Uh, Ul, Wh, Wl, d1, d2, P, ncols, out);
+    else
+      k_wr_gemm_df<1, 32><<<grid, 256, 0, c->stream>>>(Ah, Al, M, K, Uh, Ul, Wh, Wl, d1, d2, P, ncols, out);
+  }
+  PINT_LAUNCH_CHECK();
+  c->launches++;
 }
 
 void mx_to_f32(Ctx* c, const double* x, long long n, float* y) {
