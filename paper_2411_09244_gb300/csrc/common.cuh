@@ -145,6 +145,10 @@ void apply_stencil(Ctx* c, const double* st, const double* x, double* y, int cou
 void raw_dot(Ctx* c, const double* vec_nodes, int count, double* out_raw);  // k_galerkin.cu
 void to_reduced(Ctx* c, const double* raw, int count, double* v1, double* v2);  // k_galerkin.cu
 void prolong_coeffs(Ctx* c, const double* u, const double* w, int count, double* out_nodes);
+// the same in double-float arithmetic, with the bases as FP32 pairs (psih, psil)
+void prolong_coeffs_df(Ctx* c, const double* u, const double* w, int count, double* out_nodes, const float* psih,
+                       const float* psil);
+void split_bases(Ctx* c, float* psih, float* psil);
 
 // dense FP64 helpers (k_dense.cu); all matrices row-major on the device
 void dense_cholesky(Ctx* c, double* A, int n);              // lower L in place (upper zeroed)
@@ -205,6 +209,32 @@ __device__ __forceinline__ double warp_max(double v) {
   for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
   return v;
 }
+// Double-float arithmetic (a value is the unevaluated pair hi + lo of two
+// FP32 numbers, ~48 bits).  df_fma adds (ah + al)(bh + bl) to the running
+// pair (sh, sl): the product's high part is exact by the FMA form of Dekker's
+// product (p = ah bh, e = fma(ah, bh, -p)), the cross terms join the error
+// term, Knuth's TwoSum adds p to sh, and the errors are summed in sl.
+__device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, float& sh, float& sl) {
+  const float p = ah * bh;
+  float e = fmaf(ah, bh, -p);
+  e = fmaf(ah, bl, e);
+  e = fmaf(al, bh, e);
+  const float s = sh + p;
+  const float bb = s - sh;
+  const float err = (sh - (s - bb)) + (p - bb);
+  sh = s;
+  sl += err + e;
+}
+// (ah + al) - (bh + bl) as a renormalised pair (TwoSum, then Fast2Sum)
+__device__ __forceinline__ void df_sub(float ah, float al, float bh, float bl, float& h, float& l) {
+  const float s = ah - bh;
+  const float bb = s - ah;
+  float e = (ah - (s - bb)) + (-bh - bb);
+  e += al - bl;
+  h = s + e;
+  l = e - (h - s);
+}
+
 __device__ __forceinline__ float warp_sumf(float v) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;

@@ -331,8 +331,75 @@ void dense_trsm_lower(Ctx* c, const double* L, double* X, int n, int ncols, bool
   PINT_LAUNCH_CHECK();
 }
 
+namespace {
+// y[i] = alpha sum_k A[i][k] x[k] + beta y[i] (A rows contiguous): warp per row
+__global__ void k_gemv_rows(const double* __restrict__ A, const double* __restrict__ x, double* __restrict__ y,
+                            int m, int k, double alpha, double beta) {
+  const int i = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (i >= m) return;
+  double s = 0.0;
+  for (int q = lane; q < k; q += 32) s += A[(size_t)i * k + q] * x[q];
+  s = pintd::warp_sum(s);
+  if (lane == 0) y[i] = alpha * s + (beta != 0.0 ? beta * y[i] : 0.0);
+}
+// partial[z][j] = sum over the z-th K chunk of x[q] B[q][j] (B rows contiguous)
+__global__ void k_gemv_cols(const double* __restrict__ B, const double* __restrict__ x, int k, int n, int kchunk,
+                            double* __restrict__ partial) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x, z = blockIdx.y;
+  if (j >= n) return;
+  const int q0 = z * kchunk, q1 = min(k, q0 + kchunk);
+  double s = 0.0;
+  for (int q = q0; q < q1; ++q) s += x[q] * B[(size_t)q * n + j];
+  partial[(size_t)z * n + j] = s;
+}
+__global__ void k_gemv_cols_fin(const double* __restrict__ partial, int nz, int n, double alpha, double beta,
+                                double* __restrict__ y) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  double s = 0.0;
+  for (int z = 0; z < nz; ++z) s += partial[(size_t)z * n + j];
+  y[j] = alpha * s + (beta != 0.0 ? beta * y[j] : 0.0);
+}
+
+// matrix-vector product: y (len) = alpha op(M) x + beta y with M stored row-major
+// as (rows x cols); rows-form when op(M) is M itself (y has `rows` entries)
+void gemv(Ctx* c, const double* M, const double* x, double* y, int rows, int cols, bool by_rows, double alpha,
+          double beta) {
+  if (by_rows) {
+    k_gemv_rows<<<nblk((long long)rows * 32, 256), 256, 0, c->stream>>>(M, x, y, rows, cols, alpha, beta);
+    PINT_LAUNCH_CHECK();
+    return;
+  }
+  // y[j] = sum_q x[q] M[q][j], j < cols: split the q range so the grid covers the SMs
+  const int bx = (cols + 127) / 128;
+  int nz = std::max(1, std::min(rows / 32, (2 * 152 + bx - 1) / bx));
+  const int kchunk = (rows + nz - 1) / nz;
+  nz = (rows + kchunk - 1) / kchunk;
+  double* part = (double*)dalloc(c, (size_t)nz * cols * 8);
+  k_gemv_cols<<<dim3(bx, nz), 128, 0, c->stream>>>(M, x, rows, cols, kchunk, part);
+  k_gemv_cols_fin<<<bx, 128, 0, c->stream>>>(part, nz, cols, alpha, beta, y);
+  PINT_LAUNCH_CHECK();
+  dfree(c, part);
+}
+}  // namespace
+
 void dense_gemm(Ctx* c, const double* A, const double* B, double* C, int m, int n, int k, bool ta,
                 bool tb, double alpha, double beta) {
+  // matrix-vector shapes: a warp per output row, or a K-split column sweep
+  if (n == 1) {  // C (m) = op(A) (m x k) b
+    if (!ta)
+      gemv(c, A, B, C, m, k, true, alpha, beta);  // A is m x k
+    else
+      gemv(c, A, B, C, k, m, false, alpha, beta);  // A is k x m
+    return;
+  }
+  if (m == 1) {  // C (n) = a (k) op(B) (k x n)
+    if (!tb)
+      gemv(c, B, A, C, k, n, false, alpha, beta);  // B is k x n
+    else
+      gemv(c, B, A, C, n, k, true, alpha, beta);  // B is n x k
+    return;
+  }
   if ((long long)((n + 63) / 64) * ((m + 63) / 64) >= 300)
     k_gemm64<<<dim3((n + 63) / 64, (m + 63) / 64), 256, 0, c->stream>>>(A, B, C, m, n, k, ta, tb, alpha, beta);
   else

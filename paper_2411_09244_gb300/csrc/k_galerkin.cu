@@ -273,6 +273,52 @@ __global__ void k_prolong(const GWin* __restrict__ gw, int n_f, int nc, int bs, 
   out[t] = acc;
 }
 
+// k_prolong in double-float arithmetic: thread per node, VB states per thread
+// (the coefficient pairs of the VB states are contiguous), bases as FP32 pairs
+template <int VB>
+__global__ void k_prolong_df(const GWin* __restrict__ gw, int n_f, int nc, int bs, int ell,
+                             const float* __restrict__ psih, const float* __restrict__ psil,
+                             const float* __restrict__ ah, const float* __restrict__ al, int count,
+                             double* __restrict__ out) {
+  const int nn1 = n_f + 1, nn = nn1 * nn1;
+  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  const int v0 = blockIdx.y * VB;
+  if (node >= nn) return;
+  const int gx = node % nn1, gy = node / nn1;
+  const int cx = min(gx / bs, nc - 1), cy = min(gy / bs, nc - 1);
+  float sh[VB], sl[VB];
+#pragma unroll
+  for (int v = 0; v < VB; ++v) sh[v] = sl[v] = 0.f;
+  for (int by = max(0, cy - ell - 1); by <= min(nc - 1, cy + ell + 1); ++by)
+    for (int bx = max(0, cx - ell - 1); bx <= min(nc - 1, cx + ell + 1); ++bx) {
+      const GWin W = gw[by * nc + bx];
+      const int lx = gx - W.X0, ly = gy - W.Y0;
+      if (lx < 0 || lx >= W.wx || ly < 0 || ly >= W.wy) continue;
+      const int l = ly * W.wx + lx;
+      for (int q = 0; q < W.kt; ++q) {
+        const size_t pi = W.psi_off + (size_t)q * W.nw + l;
+        const float ph = psih[pi], pl = psil[pi];
+        const size_t ai = (size_t)(W.raw0 + q) * count + v0;
+#pragma unroll
+        for (int v = 0; v < VB; ++v)
+          if (v0 + v < count) pintd::df_fma(ah[ai + v], al[ai + v], ph, pl, sh[v], sl[v]);
+      }
+    }
+#pragma unroll
+  for (int v = 0; v < VB; ++v)
+    if (v0 + v < count) out[(size_t)(v0 + v) * nn + node] = (double)sh[v] + (double)sl[v];
+}
+
+__global__ void k_split_pairs(const double* __restrict__ x, long long n, float* __restrict__ h,
+                              float* __restrict__ l) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double v = x[e];
+    const float hv = (float)v;
+    h[e] = hv;
+    l[e] = (float)(v - (double)hv);
+  }
+}
+
 }  // namespace
 
 static GWin* make_gwin(Ctx* c) {
@@ -441,6 +487,34 @@ void prolong_coeffs(Ctx* c, const double* u, const double* w, int count, double*
   PINT_LAUNCH_CHECK();
   c->launches += 2;
   dfree(c, a);
+}
+
+void prolong_coeffs_df(Ctx* c, const double* u, const double* w, int count, double* out_nodes, const float* psih,
+                       const float* psil) {
+  SplitDev sd = split_dev(c);
+  const size_t na = (size_t)c->n_raw * count;
+  double* a = (double*)dalloc(c, na * 8);
+  float* ap = (float*)dalloc(c, na * 8);
+  k_from_reduced<<<count, 256, 0, c->stream>>>(u, w, count, c->n_raw, sd.kind, c->has_bar ? 1.0 / c->L : 0.0,
+                                               c->coef, sd.h1, c->d1, sd.h2m, (int)c->h2m.size(), c->has_bar, a);
+  PINT_LAUNCH_CHECK();
+  k_split_pairs<<<(unsigned)std::min<size_t>((na + 255) / 256, 4096), 256, 0, c->stream>>>(a, (long long)na, ap,
+                                                                                        ap + na);
+  PINT_LAUNCH_CHECK();
+  constexpr int VB = 16;
+  const dim3 grid((unsigned)((c->nn + 127) / 128), (unsigned)((count + VB - 1) / VB));
+  k_prolong_df<VB><<<grid, 128, 0, c->stream>>>((const GWin*)c->d_windesc, c->n_f, c->nc, c->bs, c->ell, psih, psil,
+                                                ap, ap + na, count, out_nodes);
+  PINT_LAUNCH_CHECK();
+  c->launches += 3;
+  dfree(c, a);
+  dfree(c, ap);
+}
+
+// FP64 bases -> FP32 pairs (for prolong_coeffs_df)
+void split_bases(Ctx* c, float* psih, float* psil) {
+  k_split_pairs<<<4096, 256, 0, c->stream>>>(c->psi, c->psi_total, psih, psil);
+  PINT_LAUNCH_CHECK();
 }
 
 // ---------------------------------------------------------------------------

@@ -1108,6 +1108,9 @@ struct Mx {
   // double-float pairs of AR, AS and of the FP64 trajectory (refinement residual)
   float *ARh = nullptr, *ARl = nullptr, *ASh = nullptr, *ASl = nullptr;
   float *Zuh = nullptr, *Zul = nullptr, *Zwh = nullptr, *Zwl = nullptr;
+  // the multiscale bases as FP32 pairs (double-float prolongation of the outputs)
+  float *psih = nullptr, *psil = nullptr;
+  const double* psi_src = nullptr;
   int gcl = 0;            // its cluster size (0: grid-wide FP64 sweep)
   bool tensor = false;
   std::vector<void*> bufs;  // every device buffer above
@@ -1211,6 +1214,16 @@ static Mx& mx_prepare(Ctx* c) {
 // FP32 copies of the time-grid dependent operators (refreshed every solve)
 static void mx_refresh(Ctx* c, Mx& M) {
   const int d1 = c->d1, d2 = c->d2;
+  if (M.psi_src != c->psi) {  // bases rebuilt (or first solve): split them again
+    if (!M.psih) {
+      M.bufs.push_back(dalloc(c, (size_t)c->psi_total * 4));
+      M.psih = (float*)M.bufs.back();
+      M.bufs.push_back(dalloc(c, (size_t)c->psi_total * 4));
+      M.psil = (float*)M.bufs.back();
+    }
+    split_bases(c, M.psih, M.psil);
+    M.psi_src = c->psi;
+  }
   mx_ar_diff(c, M.ldw, M.AR32, M.Rhi, M.Rlo);  // [-CA | -CM/dt] against [w_p ; w_p - w_{p-1}]
   mx_pad_split(c, c->AS, d2, d1, M.ldu, M.AS32, M.Shi, M.Slo);
   if (M.CA32) mx_to_f32(c, c->CA, (long long)d1 * d2, M.CA32);
@@ -1573,7 +1586,7 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
                                 N + 1, cudaMemcpyDeviceToDevice, c->stream));
   }
   PINT_CUDA(cudaEventRecord(eP0, c->stream));
-  if (u_out) prolong_coeffs(c, H.tmp1 + d1, H.tmp2 + d2, N, u_out);
+  if (u_out) prolong_coeffs_df(c, H.tmp1 + d1, H.tmp2 + d2, N, u_out, M.psih, M.psil);
   PINT_CUDA(cudaEventRecord(eP1, c->stream));
   PINT_CUDA(cudaEventRecord(e1, c->stream));
   PINT_CUDA(cudaEventSynchronize(e1));

@@ -384,28 +384,6 @@ __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, 
 // terms ah bl + al bh join the error term, and the running sum is kept as a
 // pair, Knuth's TwoSum on the high parts and the errors summed in FP32.
 // Same column maps as k_wr_gemm (FP64 path), operands pre-split into pairs.
-__device__ __forceinline__ void df_fma(float ah, float al, float bh, float bl, float& sh, float& sl) {
-  const float p = ah * bh;
-  float e = fmaf(ah, bh, -p);
-  e = fmaf(ah, bl, e);
-  e = fmaf(al, bh, e);
-  const float s = sh + p;
-  const float bb = s - sh;
-  const float err = (sh - (s - bb)) + (p - bb);
-  sh = s;
-  sl += err + e;
-}
-
-// (ah + al) - (bh + bl) as a renormalised pair
-__device__ __forceinline__ void df_sub(float ah, float al, float bh, float bl, float& h, float& l) {
-  const float s = ah - bh;
-  const float bb = s - ah;
-  float e = (ah - (s - bb)) + (-bh - bb);
-  e += al - bl;
-  h = s + e;
-  l = e - (h - s);
-}
-
 template <int MODE, int T>
 __global__ void __launch_bounds__(256) k_wr_gemm_df(const float* __restrict__ Ah, const float* __restrict__ Al,
                                                     int M, int K, const float* __restrict__ Uh,
@@ -438,7 +416,7 @@ __global__ void __launch_bounds__(256) k_wr_gemm_df(const float* __restrict__ Ah
           const size_t base = (size_t)n * (P + 1) * d1;
           if (kg < d1) {
             const size_t o1 = base + (size_t)p * d1 + kg, o0 = base + (size_t)(p >= 1 ? p - 1 : 0) * d1 + kg;
-            df_sub(Uh[o1], Ul[o1], Uh[o0], Ul[o0], bh, bl);
+            pintd::df_sub(Uh[o1], Ul[o1], Uh[o0], Ul[o0], bh, bl);
           } else {
             const size_t o = base + (size_t)(p + 1) * d1 + (kg - d1);
             bh = Uh[o];
@@ -465,7 +443,7 @@ __global__ void __launch_bounds__(256) k_wr_gemm_df(const float* __restrict__ Ah
 #pragma unroll
       for (int p = 0; p < R; ++p)
 #pragma unroll
-        for (int q = 0; q < R; ++q) df_fma(a_h[p], a_l[p], b_h[q], b_l[q], sh[p][q], sl[p][q]);
+        for (int q = 0; q < R; ++q) pintd::df_fma(a_h[p], a_l[p], b_h[q], b_l[q], sh[p][q], sl[p][q]);
     }
     __syncthreads();
   }
