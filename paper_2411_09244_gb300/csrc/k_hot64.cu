@@ -18,6 +18,8 @@
 // with w~_{-1} = w~_0 and u~_{-1} = u~_0 (lags restart at the interval start).
 #include "common.cuh"
 
+#include <cstring>
+
 #include <algorithm>
 #include <cmath>
 
@@ -290,6 +292,30 @@ __global__ void k_wr_norm(const T* __restrict__ acc, int cnt, double* __restrict
   if (threadIdx.x == 0) {
     out[0] = sqrt(m);
     out[1] = b;
+  }
+}
+
+// WR stopping test of the low-precision sweep without a host round trip:
+// unless *gate is set, out = (sqrt(max acc), non-finite flag) and *gate is
+// set once the update is below tol (or non-finite), which turns the remaining
+// launches of later iterations into no-ops
+__global__ void k_wr_norm_gate(const float* __restrict__ acc, int cnt, double tol, int* __restrict__ gate,
+                               double* __restrict__ out) {
+  if (*gate) return;
+  __shared__ double sh[64];
+  double m = 0.0;
+  bool bad = false;
+  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
+    const double v = (double)acc[e];
+    if (!(v == v) || v > 1e300) bad = true;
+    m = fmax(m, v);
+  }
+  m = pintd::block_max(m, sh);
+  const double b = pintd::block_max(bad ? 1.0 : 0.0, sh);
+  if (threadIdx.x == 0) {
+    out[0] = sqrt(m);
+    out[1] = b;
+    if (b != 0.0 || sqrt(m) <= tol) *gate = 1;
   }
 }
 
@@ -1048,15 +1074,16 @@ void apply_F_dev(Ctx* c, const double* in, int count, const double* f_nodes, con
 // ===========================================================================
 
 void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* Ut, const float* Wt, int ldu,
-                   int ldw, int P, int ncols, float* out);
+                   int ldw, int P, int ncols, float* out, const int* gate);
 void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
-                      const float* Blo, int ncols, int nsplit, float* out, int* err);
+                      const float* Blo, int ncols, int nsplit, float* out, int* err, const int* gate);
 int mx_umma_split(int M, int Kp, int ncols, int maxs);
 void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const float* lam1, const float* src,
                      const float* b1, const double* amp, const float2* tw, const float2* dsh, const float2* dshbr,
-                     const float* bpow, float* accU, float* B1h, float* B1l);
+                     const float* bpow, float* accU, float* B1h, float* B1l, const int* gate);
 void mx_w_sweep32(Ctx* c, const float* S, int nsl, size_t slice, int nact, float* Wt, int ldw, const float* lam2,
-                  const float* src, const float* b2, const double* amp, float* accW, float* B0h, float* B0l);
+                  const float* src, const float* b2, const double* amp, float* accW, float* B0h, float* B0l,
+                  const int* gate);
 void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, float* Wt, int ldu, int ldw,
                float* B0h, float* B0l);
 void mx_ends32(Ctx* c, const float* Ut, const float* Wt, int ldu, int ldw, int nact, double* Fu, double* Fw);
@@ -1103,6 +1130,10 @@ struct Mx {
   double *Su = nullptr, *Sw = nullptr, *YSu = nullptr, *YSw = nullptr;
   double *Zu = nullptr, *Zw = nullptr, *R64 = nullptr, *S64 = nullptr, *Cu = nullptr, *Cw = nullptr;
   double *Yu = nullptr, *Yw = nullptr, *zero = nullptr;
+  int* gate = nullptr;      // device: WR sweep converged (later launches are no-ops)
+  double* nrm = nullptr;   // device: (norm, bad) per WR iteration
+  double* hnrm = nullptr;  // pinned host copy of nrm
+  cudaEvent_t iev[2][5] = {};  // per in-flight iteration: contraction brackets + norm ready
   float* CA32 = nullptr;  // FP32 coupling of the cluster coarse sweep
   float* CM32 = nullptr;  // FP32 coupling of the jump norms
   // double-float pairs of AR, AS and of the FP64 trajectory (refinement residual)
@@ -1122,9 +1153,14 @@ static Mx& mx_prepare(Ctx* c) {
   const int N = c->N, P = c->P, d1 = c->d1, d2 = c->d2;
   const bool tensor = (c->precision == PINT_MIXED);
   if (M.ready && M.N == N && M.P == P && M.d1 == d1 && M.d2 == d2 && M.tensor == tensor) return M;
-  if (M.ready) {  // shapes or precision changed: release the old buffers
+  if (M.ready) {  // shapes or precision changed: release the old buffers (keep host-side resources)
     for (void* b : M.bufs) dfree(c, b);
+    double* hn = M.hnrm;
+    cudaEvent_t ev[2][5];
+    std::memcpy(ev, M.iev, sizeof(ev));
     M = Mx();
+    M.hnrm = hn;
+    std::memcpy(M.iev, ev, sizeof(ev));
   }
   auto Fa = [&](size_t n) {
     M.bufs.push_back(dalloc(c, std::max<size_t>(n, 1) * 4));
@@ -1163,6 +1199,12 @@ static Mx& mx_prepare(Ctx* c) {
     PINT_CUDA(cudaMemsetAsync(M.B1l, 0, n1 * 4, c->stream));
   }
   M.err = (int*)Fa(4);
+  M.gate = (int*)Fa(4);
+  M.nrm = Da(2 * PINT_MAX_ITERS + 2);
+  if (!M.hnrm) PINT_CUDA(cudaMallocHost(&M.hnrm, (2 * PINT_MAX_ITERS + 2) * sizeof(double)));
+  for (auto& row : M.iev)
+    for (auto& e : row)
+      if (!e) PINT_CUDA(cudaEventCreate(&e));
   PINT_CUDA(cudaMemsetAsync(M.err, 0, 16, c->stream));
   M.lam1f = Fa(d1);
   M.lam2f = Fa(d2);
@@ -1266,47 +1308,62 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
   const bool tensor = (c->precision == PINT_MIXED);
   const int nsl = tensor ? mx_umma_split(d2, 2 * ldu, ncols, MX_MAX_SPLIT) : 1;
   float* acc32 = reinterpret_cast<float*>(H.acc);  // FP32 squared updates (2 nact P)
+  wr_max = std::min(wr_max, PINT_MAX_ITERS);
   // column maps of the active window start at column 0 of B0 / B1
   mx_init32(c, xs_u, xs_w, nact, Ut, Wt, ldu, ldw, M.B0h, M.B0l);
-  int it = 0;
-  *bad = false;
-  for (it = 1; it <= wr_max; ++it) {
+  PINT_CUDA(cudaMemsetAsync(M.gate, 0, 4, c->stream));
+  // One WR iteration; every launch is a no-op once the stopping test of an
+  // earlier iteration has set the gate, so the host can queue iteration
+  // it + 1 before it reads the norm of iteration it (no idle GPU between them).
+  auto enqueue = [&](int it) {
+    cudaEvent_t* ev = M.iev[it & 1];
     PINT_CUDA(cudaMemsetAsync(acc32, 0, (size_t)2 * nact * P * 4, c->stream));
-    PINT_CUDA(cudaEventRecord(H.ev[0], c->stream));
-    if (tensor) mx_contract_umma(c, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, M.R, M.err);
-    else mx_contract32(c, 0, M.AR32, d1, 2 * ldw, Ut, Wt, ldu, ldw, P, ncols, M.R);
-    PINT_CUDA(cudaEventRecord(H.ev[1], c->stream));
+    PINT_CUDA(cudaEventRecord(ev[0], c->stream));
+    if (tensor) mx_contract_umma(c, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, M.R, M.err, M.gate);
+    else mx_contract32(c, 0, M.AR32, d1, 2 * ldw, Ut, Wt, ldu, ldw, P, ncols, M.R, M.gate);
+    PINT_CUDA(cudaEventRecord(ev[1], c->stream));
     mx_time_solve32(c, M.R, nact, Ut, ldu, M.lam1f, srcU, M.b1f, amp_act, M.twf, M.dshf, M.dshbr, M.bpowf, acc32,
-                    M.B1h, M.B1l);
-    PINT_CUDA(cudaEventRecord(H.ev[2], c->stream));
-    if (tensor) mx_contract_umma(c, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, nsl, M.S, M.err);
-    else mx_contract32(c, 1, M.AS32, d2, 2 * ldu, Ut, Wt, ldu, ldw, P, ncols, M.S);
-    PINT_CUDA(cudaEventRecord(H.ev[3], c->stream));
+                    M.B1h, M.B1l, M.gate);
+    PINT_CUDA(cudaEventRecord(ev[2], c->stream));
+    if (tensor) mx_contract_umma(c, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, nsl, M.S, M.err, M.gate);
+    else mx_contract32(c, 1, M.AS32, d2, 2 * ldu, Ut, Wt, ldu, ldw, P, ncols, M.S, M.gate);
+    PINT_CUDA(cudaEventRecord(ev[3], c->stream));
     mx_w_sweep32(c, M.S, tensor ? nsl : 1, (size_t)ncols * d2, nact, Wt, ldw, M.lam2f, srcW, M.b2f, amp_act,
-                 acc32 + (size_t)nact * P, M.B0h, M.B0l);
-    k_wr_norm<float><<<1, 1024, 0, c->stream>>>(acc32, 2 * nact * P, H.red);
+                 acc32 + (size_t)nact * P, M.B0h, M.B0l, M.gate);
+    k_wr_norm_gate<<<1, 1024, 0, c->stream>>>(acc32, 2 * nact * P, wr_tol, M.gate, M.nrm + 2 * it);
     PINT_LAUNCH_CHECK();
     c->launches++;
-    double h[2];
-    int herr = 0;
-    PINT_CUDA(cudaMemcpyAsync(h, H.red, 16, cudaMemcpyDeviceToHost, c->stream));
-    if (tensor) PINT_CUDA(cudaMemcpyAsync(&herr, M.err, 4, cudaMemcpyDeviceToHost, c->stream));
-    PINT_CUDA(cudaStreamSynchronize(c->stream));
-    PINT_REQUIRE(herr == 0, PINT_ERR_TIMEOUT, "tensor-core contraction: bounded mbarrier wait expired");
+    PINT_CUDA(cudaMemcpyAsync(M.hnrm + 2 * it, M.nrm + 2 * it, 16, cudaMemcpyDeviceToHost, c->stream));
+    PINT_CUDA(cudaEventRecord(ev[4], c->stream));
+  };
+  int it = 0;
+  *bad = false;
+  enqueue(1);
+  for (it = 1; it <= wr_max; ++it) {
+    if (it < wr_max) enqueue(it + 1);  // look-ahead: gated no-op if iteration it converges
+    cudaEvent_t* ev = M.iev[it & 1];
+    PINT_CUDA(cudaEventSynchronize(ev[4]));
     float m0 = 0.f, m1 = 0.f;
-    PINT_CUDA(cudaEventElapsedTime(&m0, H.ev[0], H.ev[1]));
-    PINT_CUDA(cudaEventElapsedTime(&m1, H.ev[2], H.ev[3]));
+    PINT_CUDA(cudaEventElapsedTime(&m0, ev[0], ev[1]));
+    PINT_CUDA(cudaEventElapsedTime(&m1, ev[2], ev[3]));
     H.hot_ms += m0 + m1;
     H.hot_launches += 2;
     H.hot_flops += 2.0 * 4.0 * d1 * (double)d2 * ncols;
-    if (h[1] != 0.0 || !(h[0] == h[0])) {
+    const double nrm = M.hnrm[2 * it], flag = M.hnrm[2 * it + 1];
+    if (flag != 0.0 || !(nrm == nrm)) {
       *bad = true;
       break;
     }
-    if (h[0] <= wr_tol) break;
+    if (nrm <= wr_tol) break;
   }
   if (it > wr_max) it = wr_max;
   mx_ends32(c, Ut, Wt, M.ldu, M.ldw, nact, fu, fw);
+  if (tensor) {
+    int herr = 0;
+    PINT_CUDA(cudaMemcpyAsync(&herr, M.err, 4, cudaMemcpyDeviceToHost, c->stream));
+    PINT_CUDA(cudaStreamSynchronize(c->stream));
+    PINT_REQUIRE(herr == 0, PINT_ERR_TIMEOUT, "tensor-core contraction: bounded mbarrier wait expired");
+  }
   return it;
 }
 
@@ -1442,7 +1499,12 @@ static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw) {
 
 void mixed_release(Ctx* c) {
   if (!c->scratch.empty()) {
-    delete reinterpret_cast<Mx*>(c->scratch[0].first);
+    Mx* M = reinterpret_cast<Mx*>(c->scratch[0].first);
+    if (M->hnrm) cudaFreeHost(M->hnrm);
+    for (auto& row : M->iev)
+      for (auto& e : row)
+        if (e) cudaEventDestroy(e);
+    delete M;
     c->scratch.clear();
   }
 }

@@ -70,7 +70,9 @@ __device__ __forceinline__ void warp_sum_scatter(float* v, float* __restrict__ a
 template <int MODE>
 __global__ void __launch_bounds__(256) k_wr_gemm32(const float* __restrict__ A, int M, int K,
                                                    const float* __restrict__ Ut, const float* __restrict__ Wt,
-                                                   int ldu, int ldw, int P, int ncols, float* __restrict__ out) {
+                                                   int ldu, int ldw, int P, int ncols, float* __restrict__ out,
+                                                   const int* __restrict__ gate) {
+  if (gate && *gate) return;
   __shared__ float As[16][129], Bs[16][129];
   const int i0 = blockIdx.y * 128, j0 = blockIdx.x * 128;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;  // 8x8 outputs per thread
@@ -175,7 +177,8 @@ __global__ void __launch_bounds__(128) k_time_solve32(const float* __restrict__ 
                                                       const float2* __restrict__ dsh,
                                                       const float* __restrict__ bpow, int pow2,
                                                       float* __restrict__ accU, float* __restrict__ B1h,
-                                                      float* __restrict__ B1l) {
+                                                      float* __restrict__ B1l, const int* __restrict__ gate) {
+  if (gate && *gate) return;
   const int nloc = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   __shared__ double sh[64];
@@ -275,7 +278,8 @@ __global__ void __launch_bounds__(128) k_time_solve32_t(const float* __restrict_
                                                         const float2* __restrict__ tw,
                                                         const float2* __restrict__ dsh,
                                                         const float* __restrict__ bpow, float* __restrict__ accU,
-                                                        float* __restrict__ B1h, float* __restrict__ B1l) {
+                                                        float* __restrict__ B1h, float* __restrict__ B1l, const int* __restrict__ gate) {
+  if (gate && *gate) return;
   const int nloc = blockIdx.y;
   const int i = blockIdx.x * blockDim.x + threadIdx.x;
   const int lane = threadIdx.x & 31;
@@ -339,7 +343,8 @@ __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, 
                                                    const float* __restrict__ src, const float* __restrict__ b2,
                                                    const double* __restrict__ amp, float dt, int nsl,
                                                    size_t slice, float* __restrict__ accW,
-                                                   float* __restrict__ B0h, float* __restrict__ B0l) {
+                                                   float* __restrict__ B0h, float* __restrict__ B0l, const int* __restrict__ gate) {
+  if (gate && *gate) return;
   const int nloc = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   float* Wn = Wt + (size_t)nloc * (P + 1) * ldw;
@@ -566,7 +571,8 @@ __global__ void __launch_bounds__(256) k_time_solve32_sq(const float* __restrict
                                                          const float2* __restrict__ tw,
                                                          const float2* __restrict__ dsh,
                                                          const float* __restrict__ bpow, float* __restrict__ accU,
-                                                         float* __restrict__ B1h, float* __restrict__ B1l) {
+                                                         float* __restrict__ B1h, float* __restrict__ B1l, const int* __restrict__ gate) {
+  if (gate && *gate) return;
   constexpr int P = R * R;       // steps per interval
   constexpr int NS = 256 / R;    // series (modes) per block
   constexpr int LD = NS + 1;     // tile row stride
@@ -682,7 +688,8 @@ __global__ void __launch_bounds__(32) k_w_sweep32_t(const float* __restrict__ S,
                                                     const float* __restrict__ src, const float* __restrict__ b2,
                                                     const double* __restrict__ amp, float dt, int nsl,
                                                     size_t slice, float* __restrict__ accW,
-                                                    float* __restrict__ B0h, float* __restrict__ B0l) {
+                                                    float* __restrict__ B0h, float* __restrict__ B0l, const int* __restrict__ gate) {
+  if (gate && *gate) return;
   constexpr int CH = 16;
   const int nloc = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -878,54 +885,55 @@ __global__ void k_to_f32(const double* __restrict__ x, long long n, float* __res
 }  // namespace
 
 void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* Ut, const float* Wt, int ldu,
-                   int ldw, int P, int ncols, float* out) {
+                   int ldw, int P, int ncols, float* out, const int* gate) {
   dim3 grid(nbl(ncols, 128), nbl(M, 128));
   if (mode == 0)
-    k_wr_gemm32<0><<<grid, 256, 0, c->stream>>>(A, M, K, Ut, Wt, ldu, ldw, P, ncols, out);
+    k_wr_gemm32<0><<<grid, 256, 0, c->stream>>>(A, M, K, Ut, Wt, ldu, ldw, P, ncols, out, gate);
   else
-    k_wr_gemm32<1><<<grid, 256, 0, c->stream>>>(A, M, K, Ut, Wt, ldu, ldw, P, ncols, out);
+    k_wr_gemm32<1><<<grid, 256, 0, c->stream>>>(A, M, K, Ut, Wt, ldu, ldw, P, ncols, out, gate);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
 
 void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const float* lam1, const float* src,
                      const float* b1, const double* amp, const float2* tw, const float2* dsh, const float2* dshbr,
-                     const float* bpow, float* accU, float* B1h, float* B1l) {
+                     const float* bpow, float* accU, float* B1h, float* B1l, const int* gate) {
   const int P = c->P;
   const dim3 grid(nbl(c->d1, 128), nact);
   const float al = (float)c->alpha, dt = (float)c->dt;
   if (P == 64)
     k_time_solve32_sq<8><<<dim3(nbl(c->d1, 32), nact), 256, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al,
-                                                                           dt, tw, dsh, bpow, accU, B1h, B1l);
+                                                                           dt, tw, dsh, bpow, accU, B1h, B1l, gate);
   else if (P == 32)
     k_time_solve32_t<32><<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al, dt, tw, dshbr, bpow,
-                                                       accU, B1h, B1l);
+                                                       accU, B1h, B1l, gate);
   else if (P == 16)
     k_time_solve32_sq<4><<<dim3(nbl(c->d1, 64), nact), 256, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al,
-                                                                           dt, tw, dsh, bpow, accU, B1h, B1l);
+                                                                           dt, tw, dsh, bpow, accU, B1h, B1l, gate);
   else
     k_time_solve32<<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, P, Ut, lam1, src, b1, amp, al, dt, tw, dsh, bpow,
-                                                (P & (P - 1)) == 0, accU, B1h, B1l);
+                                                (P & (P - 1)) == 0, accU, B1h, B1l, gate);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
 
 // S holds nsl K-slices of the contraction, slice floats apart (summed here)
 void mx_w_sweep32(Ctx* c, const float* S, int nsl, size_t slice, int nact, float* Wt, int ldw, const float* lam2,
-                  const float* src, const float* b2, const double* amp, float* accW, float* B0h, float* B0l) {
+                  const float* src, const float* b2, const double* amp, float* accW, float* B0h, float* B0l,
+                  const int* gate) {
   PINT_REQUIRE(nsl >= 1 && nsl <= MAX_SLICES, PINT_ERR_BAD_ARG, "too many contraction slices");
   const int P = c->P, d2 = c->d2;
   const float dt = (float)c->dt;
   const dim3 g32(nbl(d2, 32), nact);
   if (P == 64)
-    k_w_sweep32_t<64><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l);
+    k_w_sweep32_t<64><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l, gate);
   else if (P == 32)
-    k_w_sweep32_t<32><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l);
+    k_w_sweep32_t<32><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l, gate);
   else if (P == 16)
-    k_w_sweep32_t<16><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l);
+    k_w_sweep32_t<16><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l, gate);
   else
     k_w_sweep32<<<dim3(nbl(d2, 128), nact), 128, 0, c->stream>>>(S, d2, ldw, P, Wt, lam2, src, b2, amp, dt, nsl,
-                                                                 slice, accW, B0h, B0l);
+                                                                 slice, accW, B0h, B0l, gate);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }

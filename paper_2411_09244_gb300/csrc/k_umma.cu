@@ -3,10 +3,10 @@
 // The two contractions of one WR iteration (Section 4.2, eqs. (4.8)-(4.9))
 // are out[col][i] = sum_k C(i, k) B(col, k): i runs over the modes of the
 // output space, col = (interval, step) over the trajectory columns, C is the
-// coupling operator ([-(CA + CM/dt) | CM/dt] or [-CM^T | -dt CA^T], both K
-// halves padded to ld with zeros) and B(col, :) the column map of the
+// coupling operator in difference form ([-CA | -CM/dt] or [-CM^T | -dt CA^T],
+// both K halves padded to ld with zeros) and B(col, :) the column map of the
 // trajectories (written by the producing kernels of the iteration):
-//   first contraction:  B = [w_p ; w_{max(p-1,0)}]
+//   first contraction:  B = [w_p ; w_p - w_{max(p-1,0)}]
 //   second contraction: B = [u_p - u_{max(p-1,0)} ; u_{p+1}].
 // FP32 accuracy from TF32 operands: every operand is stored as a hi/lo pair
 // (hi = tf32(x), lo = tf32(x - hi)) and each K step issues three MMAs
@@ -120,8 +120,9 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
 __global__ void __launch_bounds__(THREADS, 1)
     k_wr_umma(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, int M, int ncols,
-              int kspan, float* __restrict__ out, int* __restrict__ err) {
+              int kspan, float* __restrict__ out, int* __restrict__ err, const int* __restrict__ gate) {
   constexpr uint32_t IDESC = idesc_tf32(TM, TN);
+  if (gate && *gate) return;  // the WR sweep has already converged: no-op launch
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
   __shared__ uint32_t s_tmem;
@@ -281,9 +282,10 @@ int mx_umma_split(int M, int Kp, int ncols, int maxs) {
 
 // out[z][col][i] = sum over the z-th K slice of A(i, k) B(col, k); A = Ahi + Alo
 // ([M][Kp]), B = Bhi + Blo ([ncols][Kp]), TF32 pairs in FP32 containers, both
-// 16-byte aligned with Kp a multiple of 32 nsplit.
+// 16-byte aligned with Kp a multiple of 32 nsplit.  gate (device, may be
+// null): the launch does nothing when *gate != 0.
 void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
-                      const float* Blo, int ncols, int nsplit, float* out, int* err) {
+                      const float* Blo, int ncols, int nsplit, float* out, int* err, const int* gate) {
   static bool attr = false;
   if (!attr) {
     PINT_CUDA(cudaFuncSetAttribute(k_wr_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
@@ -295,7 +297,7 @@ void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp,
   const CUtensorMap ah = make_map(Ahi, M, Kp), al = make_map(Alo, M, Kp);
   const CUtensorMap bh = make_map(Bhi, ncols, Kp), bl = make_map(Blo, ncols, Kp);
   dim3 grid((ncols + TN - 1) / TN, (M + TM - 1) / TM, nsplit);
-  k_wr_umma<<<grid, THREADS, SMEM_BYTES, c->stream>>>(ah, al, bh, bl, M, ncols, Kp / nsplit, out, err);
+  k_wr_umma<<<grid, THREADS, SMEM_BYTES, c->stream>>>(ah, al, bh, bl, M, ncols, Kp / nsplit, out, err, gate);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
