@@ -12,16 +12,21 @@
 // (hi = tf32(x), lo = tf32(x - hi)) and each K step issues three MMAs
 // (hi hi + hi lo + lo hi); the dropped lo lo term is below FP32 rounding.
 //
-// One CTA computes a 128-mode x 128-column tile of one K slice: MMA M = 128
-// (A = coupling rows), N = 128 (B = trajectory columns), FP32 accumulator in
-// TMEM with lane = mode, so the epilogue's stores are coalesced along modes.
-// Warp 0 (one lane) streams 32-wide K stages with TMA (128-byte swizzle) into
-// a ring of STAGES buffers; warp 1 allocates TMEM and one lane issues the
-// MMAs; all four warps drain the accumulator.  "full" barriers complete on the
-// TMA transaction count, "empty" barriers on tcgen05.commit.  Every wait is
-// bounded: on expiry the kernel records an error flag, waits (bounded) for the
-// copies it has in flight, frees its TMEM and returns.
+// Persistent kernel, one CTA per SM: tiles of 128 modes x 128 columns of one
+// K slice (MMA M = 128 with A = coupling rows, N = 128 with B = trajectory
+// columns) are dealt out round-robin.  Warp 0 (one lane) streams 32-wide K
+// stages with TMA (128-byte swizzle) into a ring of STAGES buffers across tile
+// boundaries; warp 1 allocates TMEM and one lane issues the MMAs into one of
+// two accumulators (2 x 128 TMEM columns, lane = mode); warps 2-5 drain the
+// other accumulator to global memory meanwhile (stores coalesced along the
+// modes).  mbarriers: "full"/"empty" for the ring (TMA transaction count /
+// tcgen05.commit), "tfull"/"tempty" for the accumulators (tcgen05.commit /
+// 128 epilogue arrivals).  Every wait is bounded: on expiry the kernel records
+// an error flag, stops issuing, waits (bounded) for the copies and MMAs it has
+// in flight, frees its TMEM and returns.
 #include "common.cuh"
+
+#include <algorithm>
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -34,7 +39,9 @@ constexpr int TM = 128;  // modes per tile (MMA M)
 constexpr int TN = 128;  // trajectory columns per tile (MMA N)
 constexpr int KB = 32;   // K elements per stage = one 128-byte swizzle row
 constexpr int STAGES = 3;
-constexpr int THREADS = 128;
+constexpr int THREADS = 192;     // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
+constexpr int EPI_THREADS = 128;
+constexpr int NACC = 2;          // TMEM accumulators
 constexpr int WAIT_LIMIT = 1 << 22;
 constexpr int OPB = TM * KB * 4;      // bytes of one operand tile (16 KB)
 constexpr int STAGE_BYTES = 4 * OPB;  // A hi, A lo, B hi, B lo
@@ -116,37 +123,55 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float* v) {
   for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
 }
 
+__device__ __forceinline__ void bar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// tile tg -> (K slice z, row tile, column tile); column tiles fastest, so CTAs
+// working at the same time share the coupling rows in L2
+struct Tile {
+  int z, row0, col0;
+};
+__device__ __forceinline__ Tile decode(int tg, int n_ct, int n_rt) {
+  const int per = n_ct * n_rt, rem = tg % per;
+  return {tg / per, (rem / n_ct) * TM, (rem % n_ct) * TN};
+}
+
 // out + z * ncols * M: the K slice [z kspan, (z + 1) kspan) of the product
 __global__ void __launch_bounds__(THREADS, 1)
     k_wr_umma(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, int M, int ncols,
-              int kspan, float* __restrict__ out, int* __restrict__ err, const int* __restrict__ gate) {
+              int kspan, int nsplit, float* __restrict__ out, int* __restrict__ err, const int* __restrict__ gate) {
   constexpr uint32_t IDESC = idesc_tf32(TM, TN);
   if (gate && *gate) return;  // the WR sweep has already converged: no-op launch
   extern __shared__ uint8_t smem_raw[];
-  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], done;
+  __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[NACC], tempty[NACC], done;
   __shared__ uint32_t s_tmem;
-  __shared__ int s_fail;
+  __shared__ volatile int s_fail;
   // the 128-byte swizzle pattern repeats every 1024 bytes: align the ring to it
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
 
-  const int col0 = blockIdx.x * TN;
-  const int row0 = blockIdx.y * TM;
-  const int kbeg = blockIdx.z * kspan;
+  const int n_ct = (ncols + TN - 1) / TN, n_rt = (M + TM - 1) / TM;
+  const int n_tiles = n_ct * n_rt * nsplit;
+  const int my_tiles = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int nkb = kspan / KB;
-  const int tid = threadIdx.x, warp = tid >> 5;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
     s_fail = 0;
     for (int s = 0; s < STAGES; ++s) {
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&full[s])));
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&empty[s])));
     }
+    for (int a = 0; a < NACC; ++a) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&tfull[a])));
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&tempty[a])), "r"(EPI_THREADS));
+    }
     asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&done)));
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                 "r"(TN));
+                 "r"(NACC * TN));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -154,75 +179,113 @@ __global__ void __launch_bounds__(THREADS, 1)
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
 
-  if (tid == 0) {
-    // ---------------- TMA producer ----------------
-    int issued = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES, use = kb / STAGES;
-      if (use >= 1 && !bar_wait(&empty[s], (uint32_t)((use - 1) & 1))) {
-        s_fail = 1;
-        break;
-      }
-      uint8_t* base = smem + s * STAGE_BYTES;
-      const int k0 = kbeg + kb * KB;
-      bar_expect_tx(&full[s], STAGE_BYTES);
-      tma_load_2d(base, &mAh, &full[s], k0, row0);
-      tma_load_2d(base + OPB, &mAl, &full[s], k0, row0);
-      tma_load_2d(base + 2 * OPB, &mBh, &full[s], k0, col0);
-      tma_load_2d(base + 3 * OPB, &mBl, &full[s], k0, col0);
-      issued = kb + 1;
-    }
-    // copies still in flight must land before the CTA's shared memory goes
-    for (int s = 0; s < STAGES && s < issued; ++s) {
-      const int last_use = (issued - 1 - s) / STAGES;
-      if (!bar_wait(&full[s], (uint32_t)(last_use & 1))) s_fail = 1;
-    }
-  } else if (tid == 32) {
-    // ---------------- MMA issuer ----------------
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES, use = kb / STAGES;
-      if (!bar_wait(&full[s], (uint32_t)(use & 1))) {
-        s_fail = 1;
-        break;
-      }
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
-#pragma unroll
-      for (int kk = 0; kk < KB / 8; ++kk) {
-        const uint32_t ko = kk * 32;  // K = 8 TF32 = 32 bytes along the swizzle row
-        const uint64_t dah = desc_sw128(base + ko), dal = desc_sw128(base + OPB + ko);
-        const uint64_t dbh = desc_sw128(base + 2 * OPB + ko), dbl = desc_sw128(base + 3 * OPB + ko);
-        mma_tf32(tmem, dah, dbh, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
-        mma_tf32(tmem, dah, dbl, IDESC, 1u);
-        mma_tf32(tmem, dal, dbh, IDESC, 1u);
-      }
-      mma_commit(&empty[s]);
-    }
-    mma_commit(&done);  // arrives once every MMA issued above has completed
-  }
-  __syncwarp();
-  // ---------------- epilogue: all four warps ----------------
-  if (!bar_wait(&done, 0u)) s_fail = 1;
-  __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (!s_fail && nkb > 0) {
-    const int i = row0 + 32 * warp + (tid & 31);  // output mode of this thread (TMEM lane)
-    float* o = out + (size_t)blockIdx.z * ncols * M;
-    for (int cc = 0; cc < TN; cc += 32) {
-      float v[32];
-      tmem_ld32(tmem + ((uint32_t)(32 * warp) << 16) + (uint32_t)cc, v);
-      if (i < M) {
-#pragma unroll
-        for (int q = 0; q < 32; ++q) {
-          const int col = col0 + cc + q;
-          if (col < ncols) o[(size_t)col * M + i] = v[q];
+  if (warp == 0) {
+    if (lane == 0) {
+      // ---------------- TMA producer (continuous ring across tiles) ----------------
+      int g = 0;
+      bool stop = false;
+      for (int j = 0; j < my_tiles && !stop; ++j) {
+        const Tile T = decode((int)blockIdx.x + j * (int)gridDim.x, n_ct, n_rt);
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = g % STAGES, use = g / STAGES;
+          if (s_fail || (use >= 1 && !bar_wait(&empty[s], (uint32_t)((use - 1) & 1)))) {
+            s_fail = 1;
+            stop = true;
+            break;
+          }
+          uint8_t* base = smem + s * STAGE_BYTES;
+          const int k0 = T.z * kspan + kb * KB;
+          bar_expect_tx(&full[s], STAGE_BYTES);
+          tma_load_2d(base, &mAh, &full[s], k0, T.row0);
+          tma_load_2d(base + OPB, &mAl, &full[s], k0, T.row0);
+          tma_load_2d(base + 2 * OPB, &mBh, &full[s], k0, T.col0);
+          tma_load_2d(base + 3 * OPB, &mBl, &full[s], k0, T.col0);
         }
       }
+      // copies still in flight must land before the CTA's shared memory goes
+      for (int s = 0; s < STAGES && s < g; ++s) {
+        const int last_use = (g - 1 - s) / STAGES;
+        if (!bar_wait(&full[s], (uint32_t)(last_use & 1))) s_fail = 1;
+      }
+    }
+  } else if (warp == 1) {
+    if (lane == 0) {
+      // ---------------- MMA issuer ----------------
+      int g = 0;
+      bool stop = false;
+      for (int j = 0; j < my_tiles && !stop; ++j) {
+        const int acc = j & 1, u = j >> 1;
+        if (s_fail || (u >= 1 && !bar_wait(&tempty[acc], (uint32_t)((u - 1) & 1)))) {
+          s_fail = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t d = tmem + (uint32_t)(acc * TN);
+        for (int kb = 0; kb < nkb; ++kb, ++g) {
+          const int s = g % STAGES, use = g / STAGES;
+          if (!bar_wait(&full[s], (uint32_t)(use & 1))) {
+            s_fail = 1;
+            stop = true;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t base = smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+          for (int kk = 0; kk < KB / 8; ++kk) {
+            const uint32_t ko = kk * 32;  // K = 8 TF32 = 32 bytes along the swizzle row
+            const uint64_t dah = desc_sw128(base + ko), dal = desc_sw128(base + OPB + ko);
+            const uint64_t dbh = desc_sw128(base + 2 * OPB + ko), dbl = desc_sw128(base + 3 * OPB + ko);
+            mma_tf32(d, dah, dbh, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
+            mma_tf32(d, dah, dbl, IDESC, 1u);
+            mma_tf32(d, dal, dbh, IDESC, 1u);
+          }
+          mma_commit(&empty[s]);
+        }
+        if (!stop) mma_commit(&tfull[acc]);
+      }
+      mma_commit(&done);  // arrives once every MMA issued above has completed
+    }
+  } else {
+    // ---------------- epilogue (warps 2-5, TMEM lane quadrant warp % 4) ----------------
+    const int qd = warp & 3;
+    for (int j = 0; j < my_tiles; ++j) {
+      const int acc = j & 1, u = j >> 1;
+      // one lane waits and the warp follows its verdict, so the warp stays
+      // converged for the .sync.aligned TMEM loads
+      int bad = 0;
+      if (lane == 0) bad = (s_fail || !bar_wait(&tfull[acc], (uint32_t)(u & 1))) ? 1 : 0;
+      bad = __shfl_sync(0xffffffffu, bad, 0);
+      if (bad) {
+        s_fail = 1;
+        break;
+      }
+      bar_wait(&tfull[acc], (uint32_t)(u & 1));  // completed: returns at once; acquire for every lane
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const Tile T = decode((int)blockIdx.x + j * (int)gridDim.x, n_ct, n_rt);
+      const int i = T.row0 + 32 * qd + lane;  // output mode of this thread (TMEM lane)
+      float* o = out + (size_t)T.z * ncols * M;
+      for (int cc = 0; cc < TN; cc += 32) {
+        float v[32];
+        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(acc * TN + cc), v);
+        if (i < M) {
+#pragma unroll
+          for (int q = 0; q < 32; ++q) {
+            const int col = T.col0 + cc + q;
+            if (col < ncols) o[(size_t)col * M + i] = v[q];
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      bar_arrive(&tempty[acc]);
     }
   }
+  __syncwarp();
+  // every MMA has completed before the accumulators are freed
+  if (!bar_wait(&done, 0u)) s_fail = 1;
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TN));
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NACC * TN));
   if (tid == 0 && s_fail) atomicExch(err, 1);
 }
 
@@ -296,8 +359,16 @@ void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp,
   if (ncols <= 0 || M <= 0) return;
   const CUtensorMap ah = make_map(Ahi, M, Kp), al = make_map(Alo, M, Kp);
   const CUtensorMap bh = make_map(Bhi, ncols, Kp), bl = make_map(Blo, ncols, Kp);
-  dim3 grid((ncols + TN - 1) / TN, (M + TM - 1) / TM, nsplit);
-  k_wr_umma<<<grid, THREADS, SMEM_BYTES, c->stream>>>(ah, al, bh, bl, M, ncols, Kp / nsplit, out, err, gate);
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    PINT_CUDA(cudaGetDevice(&dev));
+    PINT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  }
+  const int tiles = ((ncols + TN - 1) / TN) * ((M + TM - 1) / TM) * nsplit;
+  const int grid = std::min(tiles, std::max(sms, 1));  // persistent: one CTA per SM at most
+  k_wr_umma<<<grid, THREADS, SMEM_BYTES, c->stream>>>(ah, al, bh, bl, M, ncols, Kp / nsplit, nsplit, out, err,
+                                                      gate);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
