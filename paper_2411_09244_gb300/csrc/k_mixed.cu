@@ -562,8 +562,15 @@ __device__ __forceinline__ void group_transpose(float* v, int g, int base) {
   for (int t = 0; t < R; ++t) v[t] = a[t];
 }
 
+__device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"((uint32_t)__cvta_generic_to_shared(sdst)),
+               "l"(gsrc)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
+
 template <int R>
-__global__ void __launch_bounds__(256) k_time_solve32_sq(const float* __restrict__ Rc, int d1, int ldu,
+__global__ void __launch_bounds__(256, 4) k_time_solve32_sq(const float* __restrict__ Rc, int d1, int ldu,
                                                          float* __restrict__ Ut, const float* __restrict__ lam1,
                                                          const float* __restrict__ src,
                                                          const float* __restrict__ b1,
@@ -577,25 +584,37 @@ __global__ void __launch_bounds__(256) k_time_solve32_sq(const float* __restrict
   constexpr int NS = 256 / R;    // series (modes) per block
   constexpr int LD = NS + 1;     // tile row stride
   constexpr int PER = P * NS / 256;
-  __shared__ float sT[P * LD];
+  __shared__ float sT[P * LD];   // right-hand sides, then the new states
+  __shared__ float sO[P * LD];   // previous iterate u_{p+1}
   __shared__ float su0[NS];
   const int nloc = blockIdx.y, i0 = blockIdx.x * NS;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float* Un = Ut + (size_t)nloc * (P + 1) * ldu;
   const float an = (float)amp[nloc];
+  // every global read of the block is issued at once as asynchronous copies
+  // into shared memory (the contraction output and the previous iterate)
+#pragma unroll
+  for (int r = 0; r < PER; ++r) {
+    const int e = tid + 256 * r, p = e / NS, s = e % NS, i = i0 + s;
+    if (i < d1) {
+      cp_async4(&sT[p * LD + s], Rc + ((size_t)nloc * P + p) * d1 + i);
+      cp_async4(&sO[p * LD + s], Un + (size_t)(p + 1) * ldu + i);
+    } else {
+      sT[p * LD + s] = 0.f;
+      sO[p * LD + s] = 0.f;
+    }
+  }
+  if (tid < NS) su0[tid] = (i0 + tid < d1) ? Un[i0 + tid] : 0.f;
+  cp_async_wait_all();
+  __syncthreads();
   // right-hand sides of eq. (4.7) scaled by beta^p, tile [p][mode]
 #pragma unroll
   for (int r = 0; r < PER; ++r) {
     const int e = tid + 256 * r, p = e / NS, s = e % NS, i = i0 + s;
     float y = 0.f;
     if (i < d1) {
-      const size_t o = ((size_t)nloc * P + p) * d1 + i;
-      y = Rc[o] + (src ? src[o] : b1[i] * an);
-      if (p == 0) {
-        const float u0 = Un[i];
-        su0[s] = u0;
-        y += (u0 - alpha * Un[(size_t)P * ldu + i]) / dt;
-      }
+      y = sT[p * LD + s] + (src ? src[((size_t)nloc * P + p) * d1 + i] : b1[i] * an);
+      if (p == 0) y += (su0[s] - alpha * sO[(P - 1) * LD + s]) / dt;  // u_P of the previous iterate
       y *= bpow[p];
     }
     sT[p * LD + s] = y;
@@ -650,13 +669,7 @@ __global__ void __launch_bounds__(256) k_time_solve32_sq(const float* __restrict
 #pragma unroll
   for (int m = 0; m < R; ++m) sT[(g + R * m) * LD + s] = re[m] / ((float)P * bpow[g + R * m]);
   __syncthreads();
-  // new states u_{p+1} (tile row p), previous iterate loaded before any store
-  float oldv[PER];
-#pragma unroll
-  for (int r = 0; r < PER; ++r) {
-    const int e = tid + 256 * r, p = e / NS, ii = i0 + e % NS;
-    oldv[r] = (ii < d1) ? Un[(size_t)(p + 1) * ldu + ii] : 0.f;
-  }
+  // new states u_{p+1} (tile row p); the previous iterate is in sO
 #pragma unroll
   for (int r = 0; r < PER; ++r) {
     const int e = tid + 256 * r, p = e / NS, ss = e % NS, ii = i0 + ss;
@@ -670,7 +683,7 @@ __global__ void __launch_bounds__(256) k_time_solve32_sq(const float* __restrict
         put_split(B1h, B1l, o, dp);
         put_split(B1h, B1l, o + ldu, uq);
       }
-      const float dv = uq - oldv[r];
+      const float dv = uq - sO[p * LD + ss];
       dd = dv * dv;
     }
 #pragma unroll
