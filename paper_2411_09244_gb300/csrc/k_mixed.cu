@@ -706,15 +706,17 @@ __global__ void __launch_bounds__(32) k_w_sweep32_t(const float* __restrict__ S,
   constexpr int CH = 16;
   const int nloc = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = j < d2;
   float* Wn = Wt + (size_t)nloc * (P + 1) * ldw;
-  float dd[P];
-  if (j < d2) {
-    const float fac = 1.f - dt * lam2[j];
-    const float cs = src ? 0.f : dt * b2[j] * (float)amp[nloc];
-    float w = Wn[j];
-#pragma unroll
-    for (int c0 = 0; c0 < P; c0 += CH) {
-      float sv[CH], ov[CH];
+  const float fac = act ? 1.f - dt * lam2[j] : 0.f;
+  const float cs = (act && !src) ? dt * b2[j] * (float)amp[nloc] : 0.f;
+  float w = act ? Wn[j] : 0.f;
+  // chunks of CH steps, kept rolled (a fully unrolled sweep overflows the
+  // instruction cache); the squared updates of a chunk are reduced at its end
+#pragma unroll 1
+  for (int c0 = 0; c0 < P; c0 += CH) {
+    float sv[CH], ov[CH], dd[CH];
+    if (act) {
 #pragma unroll
       for (int q = 0; q < CH; ++q) {
         const size_t o = ((size_t)nloc * P + c0 + q) * d2 + j;
@@ -736,15 +738,15 @@ __global__ void __launch_bounds__(32) k_w_sweep32_t(const float* __restrict__ S,
           put_split(B0h, B0l, o + ldw, wn - w);
         }
         const float d = wn - ov[q];
-        dd[p] = d * d;
+        dd[q] = d * d;
         w = wn;
       }
-    }
-  } else {
+    } else {
 #pragma unroll
-    for (int p = 0; p < P; ++p) dd[p] = 0.f;
+      for (int q = 0; q < CH; ++q) dd[q] = 0.f;
+    }
+    warp_sum_scatter<CH>(dd, accW + (size_t)nloc * P + c0);
   }
-  warp_sum_scatter<P>(dd, accW + (size_t)nloc * P);
 }
 
 // constant initial trajectories; with B0h, also the first-contraction column
