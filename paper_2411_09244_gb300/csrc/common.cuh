@@ -188,8 +188,9 @@ void unit_response(Ctx* c, double* su, double* sw);
 struct GcArgs {
   const float* CA;  // [d1][d2] FP32 coupling
   const double *lam1, *lam2, *b1, *b2, *amp;
-  const double *Fu, *Fw, *Cu, *Cw;  // F ends, jumps (may be null)
-  double *Xu, *Xw, *Gu, *Gw;        // states (in/out), G outputs (in/out)
+  const float *Fu, *Fw, *Cu, *Cw;  // F ends, jumps (may be null), FP32
+  double *Xu, *Xw;                 // states (in/out), FP64
+  float *Gu, *Gw;                  // G outputs of the previous sweep (in/out), FP32
   int d1, d2, n_lo, n_hi, first;
   double Dt;
 };

@@ -7,8 +7,10 @@
 //   w' = (1 - Dt Lambda2) w - Dt CA^T u' + Dt a_n b2
 // and applies the update of eq. (2.7), x_{n+1} = G(x_n) + F_n - G_old_n
 // (+ c_{n+1} in a correction solve).  The low-precision path only needs G to
-// contract the parareal error (its fixed point is that of F), so the two
-// coupling products run in FP32 while states and updates stay FP64.
+// contract the parareal error (its fixed point is that of F, and the FP64
+// refinement measures what the low-precision solve leaves), so the whole step
+// runs in FP32: products, updates, and the F ends, old G values and jumps it
+// reads (FP32 copies).  Only the states X are written back in FP64.
 //
 // The FP32 coupling CA stays resident in the distributed shared memory of a
 // cluster of CL CTAs (rows split evenly).  Per step: each CTA forms u' for its
@@ -35,8 +37,7 @@ constexpr size_t GC_SMEM = 200 * 1024;  // dynamic shared memory budget per CTA
 // cluster barriers has only shared-memory traffic to order)
 struct GcLayout {
   int rpc, spc, ng, nb;
-  size_t f_CA, f_xw, f_part, f_gu, f_acc, f_gtmp, f_sbuf, n_f;        // float offsets
-  size_t d_xu, d_xw, d_ia, d_cb, d_fw, d_cw, d_su, d_sg, d_sw, d_sh, n_d;  // double offsets (after the floats)
+  size_t CA, xw, part, gu, acc, gtmp, sbuf, xu, ia, cb, wo, fw, cw, su, sg, sw, sh, n;  // float offsets
   size_t bytes;
 };
 
@@ -47,44 +48,30 @@ __host__ __device__ inline GcLayout gc_layout(int d1, int d2, int CL, int nb) {
   L.spc = (d2 + CL - 1) / CL;
   L.ng = d2 >= GC_THREADS ? 1 : (GC_THREADS / d2 > 8 ? 8 : GC_THREADS / d2);
   size_t o = 0;
-  L.f_CA = o;
-  o += (size_t)L.rpc * d2;
-  L.f_xw = o;
-  o += d2;
-  L.f_part = o;
-  o += d2;
-  L.f_gu = o;
-  o += L.rpc;
-  L.f_acc = o;
-  o += L.rpc;
-  L.f_gtmp = o;
-  o += (size_t)L.ng * d2;
-  L.f_sbuf = o;
-  o += L.spc;
-  L.n_f = (o + 1) & ~(size_t)1;  // doubles start 8-byte aligned
-  size_t q = 0;
-  L.d_xu = q;
-  q += L.rpc;
-  L.d_ia = q;
-  q += L.rpc;
-  L.d_cb = q;
-  q += L.rpc;
-  L.d_xw = q;
-  q += L.spc;
-  L.d_fw = q;
-  q += L.spc;
-  L.d_cw = q;
-  q += L.spc;
-  L.d_su = q;  // staged X_u rows, nb x rpc
-  q += (size_t)nb * L.rpc;
-  L.d_sg = q;  // staged G_u rows
-  q += (size_t)nb * L.rpc;
-  L.d_sw = q;  // staged X_w slice, nb x spc
-  q += (size_t)nb * L.spc;
-  L.d_sh = q;  // staged G_w slice
-  q += (size_t)nb * L.spc;
-  L.n_d = q;
-  L.bytes = L.n_f * 4 + L.n_d * 8;
+  auto take = [&](size_t n) {
+    const size_t at = o;
+    o += n;
+    return at;
+  };
+  L.CA = take((size_t)L.rpc * d2);
+  L.xw = take(d2);       // the whole w (FP32), replicated
+  L.part = take(d2);     // this CTA's partial products
+  L.gu = take(L.rpc);    // u' rows
+  L.acc = take(L.rpc);   // CA w rows
+  L.gtmp = take((size_t)L.ng * d2);
+  L.sbuf = take(L.spc);  // new w of the own slice, for the broadcast
+  L.xu = take(L.rpc);    // own states u
+  L.ia = take(L.rpc);    // 1 / (1 + Dt lambda1)
+  L.cb = take(L.rpc);    // Dt b1 / (1 + Dt lambda1)
+  L.wo = take(L.spc);    // own slice of w
+  L.fw = take(L.spc);    // 1 - Dt lambda2
+  L.cw = take(L.spc);    // Dt b2
+  L.su = take((size_t)nb * L.rpc);  // staged X_u, G_u rows and X_w, G_w slices
+  L.sg = take((size_t)nb * L.rpc);
+  L.sw = take((size_t)nb * L.spc);
+  L.sh = take((size_t)nb * L.spc);
+  L.n = o;
+  L.bytes = o * 4;
   return L;
 }
 
@@ -119,30 +106,29 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a, int nb) 
   const int d1 = a.d1, d2 = a.d2;
   const GcLayout L = gc_layout(d1, d2, CL, nb);
   float* fs = reinterpret_cast<float*>(gsm);
-  double* ds = reinterpret_cast<double*>(gsm + L.n_f * 4);
-  float *sCA = fs + L.f_CA, *xw32 = fs + L.f_xw, *part = fs + L.f_part, *gu32 = fs + L.f_gu, *accs = fs + L.f_acc,
-        *gtmp = fs + L.f_gtmp, *sbuf = fs + L.f_sbuf;
-  double *xud = ds + L.d_xu, *ia = ds + L.d_ia, *cb = ds + L.d_cb, *xwd = ds + L.d_xw, *fw = ds + L.d_fw,
-         *cw = ds + L.d_cw, *stXu = ds + L.d_su, *stGu = ds + L.d_sg, *stXw = ds + L.d_sw, *stGw = ds + L.d_sh;
+  float *sCA = fs + L.CA, *xw32 = fs + L.xw, *part = fs + L.part, *gu32 = fs + L.gu, *accs = fs + L.acc,
+        *gtmp = fs + L.gtmp, *sbuf = fs + L.sbuf, *xu = fs + L.xu, *ia = fs + L.ia, *cb = fs + L.cb,
+        *wo = fs + L.wo, *fw = fs + L.fw, *cw = fs + L.cw, *stXu = fs + L.su, *stGu = fs + L.sg, *stXw = fs + L.sw,
+        *stGw = fs + L.sh;
   const int rank = (int)cl_rank();
   const int r0 = rank * L.rpc, nr = max(0, min(d1, r0 + L.rpc) - r0);
   const int j0 = rank * L.spc, ns = max(0, min(d2, j0 + L.spc) - j0);
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const double Dt = a.Dt;
+  const float Dt = (float)a.Dt;
   const size_t n0 = (size_t)a.n_lo;
   for (size_t e = tid; e < (size_t)nr * d2; e += GC_THREADS) sCA[e] = a.CA[(size_t)r0 * d2 + e];
   for (int j = tid; j < d2; j += GC_THREADS) xw32[j] = (float)a.Xw[n0 * d2 + j];
   for (int q = tid; q < nr; q += GC_THREADS) {
     const int i = r0 + q;
-    xud[q] = a.Xu[n0 * d1 + i];
-    ia[q] = 1.0 / (1.0 + Dt * a.lam1[i]);
-    cb[q] = Dt * a.b1[i] * ia[q];
+    xu[q] = (float)a.Xu[n0 * d1 + i];
+    ia[q] = (float)(1.0 / (1.0 + a.Dt * a.lam1[i]));
+    cb[q] = (float)(a.Dt * a.b1[i] / (1.0 + a.Dt * a.lam1[i]));
   }
   for (int q = tid; q < ns; q += GC_THREADS) {
     const int j = j0 + q;
-    xwd[q] = a.Xw[n0 * d2 + j];
-    fw[q] = 1.0 - Dt * a.lam2[j];
-    cw[q] = Dt * a.b2[j];
+    wo[q] = (float)a.Xw[n0 * d2 + j];
+    fw[q] = (float)(1.0 - a.Dt * a.lam2[j]);
+    cw[q] = (float)(a.Dt * a.b2[j]);
   }
   __syncthreads();
   cl_sync();  // every CTA of the cluster is resident before any DSMEM access
@@ -150,10 +136,10 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a, int nb) 
   int nbase = a.n_lo;
   for (int n = a.n_lo; n < a.n_hi; ++n) {
     const int sl = n - nbase;  // staging slot of this step
-    const double am = a.amp[n];
+    const float am = (float)a.amp[n];
     // inputs of this step that do not depend on the sweep, fetched up front by
     // the threads that use them (row q = tid, column slice entry tid)
-    double pf = 0.0, pg = 0.0, pc = 0.0;
+    float pf = 0.f, pg = 0.f, pc = 0.f;
     if (tid < nr) {
       const int i = r0 + tid;
       if (!a.first) {
@@ -162,7 +148,7 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a, int nb) 
       }
       if (a.Cu) pc = a.Cu[(size_t)(n + 1) * d1 + i];
     }
-    double wf = 0.0, wg = 0.0, wc = 0.0;
+    float wf = 0.f, wg = 0.f, wc = 0.f;
     if (tid < ns) {
       const int j = j0 + tid;
       if (!a.first) {
@@ -184,16 +170,14 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a, int nb) 
       }
     }
     __syncthreads();
-    // FP64 updates packed into the first warps (the FP64 pipe is narrow)
     if (tid < nr) {
       const int q = tid;
-      const double g = xud[q] * ia[q] - Dt * ia[q] * (double)accs[q] + am * cb[q];
-      double v = a.first ? g : g + pf - pg;
-      v += pc;
+      const float g = xu[q] * ia[q] - Dt * ia[q] * accs[q] + am * cb[q];
+      const float v = (a.first ? g : g + pf - pg) + pc;
       stXu[(size_t)sl * L.rpc + q] = v;
       stGu[(size_t)sl * L.rpc + q] = g;
-      xud[q] = v;
-      gu32[q] = (float)g;
+      xu[q] = v;
+      gu32[q] = g;
     }
     __syncthreads();
     // partial products CA^T u' over this CTA's rows, L.ng row groups per column
@@ -219,13 +203,12 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a, int nb) 
       float s = 0.f;
 #pragma unroll
       for (int r = 0; r < CL; ++r) s += ld_dsmem(dsmem_addr(&part[j], (uint32_t)r));
-      const double g = fw[tid] * xwd[tid] - Dt * (double)s + am * cw[tid];
-      double v = a.first ? g : g + wf - wg;
-      v += wc;
+      const float g = fw[tid] * wo[tid] - Dt * s + am * cw[tid];
+      const float v = (a.first ? g : g + wf - wg) + wc;
       stXw[(size_t)sl * L.spc + tid] = v;
       stGw[(size_t)sl * L.spc + tid] = g;
-      xwd[tid] = v;
-      sbuf[tid] = (float)v;
+      wo[tid] = v;
+      sbuf[tid] = v;
     }
     __syncthreads();
     for (int e = tid; e < ns * CL; e += GC_THREADS) {
@@ -233,16 +216,16 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a, int nb) 
       st_dsmem(dsmem_addr(&xw32[j0 + q], (uint32_t)r), sbuf[q]);
     }
     cl_sync();  // new w in every CTA; partial buffers free again
-    if (sl + 1 == nb || n + 1 == a.n_hi) {  // write the staged chunk out
+    if (sl + 1 == nb || n + 1 == a.n_hi) {  // write the staged chunk out (states in FP64)
       const int cnt = sl + 1;
       for (int e = tid; e < cnt * nr; e += GC_THREADS) {
         const int st = e / nr, q = e - st * nr;
-        a.Xu[(size_t)(nbase + st + 1) * d1 + r0 + q] = stXu[(size_t)st * L.rpc + q];
+        a.Xu[(size_t)(nbase + st + 1) * d1 + r0 + q] = (double)stXu[(size_t)st * L.rpc + q];
         a.Gu[(size_t)(nbase + st) * d1 + r0 + q] = stGu[(size_t)st * L.rpc + q];
       }
       for (int e = tid; e < cnt * ns; e += GC_THREADS) {
         const int st = e / ns, q = e - st * ns;
-        a.Xw[(size_t)(nbase + st + 1) * d2 + j0 + q] = stXw[(size_t)st * L.spc + q];
+        a.Xw[(size_t)(nbase + st + 1) * d2 + j0 + q] = (double)stXw[(size_t)st * L.spc + q];
         a.Gw[(size_t)(nbase + st) * d2 + j0 + q] = stGw[(size_t)st * L.spc + q];
       }
       __syncthreads();

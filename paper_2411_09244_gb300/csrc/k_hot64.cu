@@ -1086,7 +1086,8 @@ void mx_w_sweep32(Ctx* c, const float* S, int nsl, size_t slice, int nact, float
                   const int* gate);
 void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, float* Wt, int ldu, int ldw,
                float* B0h, float* B0l);
-void mx_ends32(Ctx* c, const float* Ut, const float* Wt, int ldu, int ldw, int nact, double* Fu, double* Fw);
+void mx_ends32(Ctx* c, const float* Ut, const float* Wt, int ldu, int ldw, int nact, double* Fu, double* Fw,
+               float* Fu32, float* Fw32);
 void mx_promote(Ctx* c, const float* Ut, const float* Wt, int ldu, int ldw, const double* Su, const double* Sw,
                 double* Zu, double* Zw);
 void mx_pad_split(Ctx* c, const double* A, int rows, int dk, int ld, float* a32, float* hi, float* lo);
@@ -1136,6 +1137,8 @@ struct Mx {
   cudaEvent_t iev[2][5] = {};  // per in-flight iteration: contraction brackets + norm ready
   float* CA32 = nullptr;  // FP32 coupling of the cluster coarse sweep
   float* CM32 = nullptr;  // FP32 coupling of the jump norms
+  // FP32 copies for the cluster coarse sweep: F ends, old G values, jumps
+  float *Fu32 = nullptr, *Fw32 = nullptr, *Gu32 = nullptr, *Gw32 = nullptr, *Cu32 = nullptr, *Cw32 = nullptr;
   // double-float pairs of AR, AS and of the FP64 trajectory (refinement residual)
   float *ARh = nullptr, *ARl = nullptr, *ASh = nullptr, *ASl = nullptr;
   float *Zuh = nullptr, *Zul = nullptr, *Zwh = nullptr, *Zwl = nullptr;
@@ -1181,7 +1184,15 @@ static Mx& mx_prepare(Ctx* c) {
   M.AR32 = Fa((size_t)d1 * 2 * ldw);
   M.AS32 = Fa((size_t)d2 * 2 * ldu);
   M.gcl = gc_cluster_size(d1, d2);
-  if (M.gcl) M.CA32 = Fa((size_t)d1 * d2);
+  if (M.gcl) {
+    M.CA32 = Fa((size_t)d1 * d2);
+    M.Fu32 = Fa((size_t)N * d1);
+    M.Fw32 = Fa((size_t)N * d2);
+    M.Gu32 = Fa((size_t)N * d1);
+    M.Gw32 = Fa((size_t)N * d2);
+    M.Cu32 = Fa((size_t)(N + 1) * d1);
+    M.Cw32 = Fa((size_t)(N + 1) * d2);
+  }
   M.CM32 = Fa((size_t)d1 * d2);
   if (tensor) {
     M.Rhi = Fa((size_t)d1 * 2 * ldw);
@@ -1301,7 +1312,7 @@ static void mx_refresh(Ctx* c, Mx& M) {
 // absolute slot n_lo; ends into fu/fw (FP64)
 static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* xs_w, const double* amp_act,
                        int nact, const float* srcU, const float* srcW, float* Ut, float* Wt, double wr_tol,
-                       int wr_max, double* fu, double* fw, bool* bad) {
+                       int wr_max, double* fu, double* fw, float* fu32, float* fw32, bool* bad) {
   const int d1 = c->d1, d2 = c->d2, P = c->P;
   const int ncols = nact * P;
   const int ldu = M.ldu, ldw = M.ldw;
@@ -1357,7 +1368,7 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
     if (nrm <= wr_tol) break;
   }
   if (it > wr_max) it = wr_max;
-  mx_ends32(c, Ut, Wt, M.ldu, M.ldw, nact, fu, fw);
+  mx_ends32(c, Ut, Wt, M.ldu, M.ldw, nact, fu, fw, fu32, fw32);
   if (tensor) {
     int herr = 0;
     PINT_CUDA(cudaMemcpyAsync(&herr, M.err, 4, cudaMemcpyDeviceToHost, c->stream));
@@ -1399,14 +1410,14 @@ static void g_sweep_lp(Ctx* c, Hot& H, Mx& M, double* Xu, double* Xw, const doub
   a.b1 = H.b1;
   a.b2 = H.b2;
   a.amp = amp;
-  a.Fu = Fu;
-  a.Fw = Fw;
-  a.Cu = Cu;
-  a.Cw = Cw;
+  a.Fu = Fu ? M.Fu32 : nullptr;  // FP32 twins of the FP64 arrays the grid sweep reads
+  a.Fw = Fw ? M.Fw32 : nullptr;
+  a.Cu = Cu ? M.Cu32 : nullptr;
+  a.Cw = Cw ? M.Cw32 : nullptr;
   a.Xu = Xu;
   a.Xw = Xw;
-  a.Gu = H.Gu;
-  a.Gw = H.Gw;
+  a.Gu = M.Gu32;
+  a.Gw = M.Gw32;
   a.d1 = c->d1;
   a.d2 = c->d2;
   a.n_lo = n_lo;
@@ -1439,7 +1450,8 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
                          r.srcU ? r.srcU + (size_t)n_lo * P * d1 : nullptr,
                          r.srcW ? r.srcW + (size_t)n_lo * P * d2 : nullptr, r.Ut + (size_t)n_lo * (P + 1) * M.ldu,
                          r.Wt + (size_t)n_lo * (P + 1) * M.ldw, r.wr_tol, r.wr_max, H.Fu + (size_t)n_lo * d1,
-                         H.Fw + (size_t)n_lo * d2, &bad);
+                         H.Fw + (size_t)n_lo * d2, M.Fu32 ? M.Fu32 + (size_t)n_lo * d1 : nullptr,
+                         M.Fw32 ? M.Fw32 + (size_t)n_lo * d2 : nullptr, &bad);
     PINT_CUDA(cudaEventRecord(a1, c->stream));
     PINT_CUDA(cudaEventSynchronize(a1));
     float ms = 0.f;
@@ -1591,6 +1603,10 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
     mx_wr_gemm_df(c, 1, M.ASh, M.ASl, d2, 2 * d1, M.Zuh, M.Zul, M.Zwh, M.Zwl, ncols, M.S64);
     mx_residual(c, M.Zu, M.Zw, M.R64, M.S64, H.b1, H.b2, H.amp, M.srcU, M.srcW);
     mx_continuity(c, M.Zu, M.Zw, M.Cu, M.Cw);
+    if (M.Cu32) {
+      mx_to_f32(c, M.Cu, (long long)(N + 1) * d1, M.Cu32);
+      mx_to_f32(c, M.Cw, (long long)(N + 1) * d2, M.Cw32);
+    }
     LpRun y{};
     y.amp = M.zero;
     y.srcU = M.srcU;

@@ -772,12 +772,21 @@ __global__ void k_init32(const double* __restrict__ Xu, const double* __restrict
   }
 }
 
+// interval ends u_P, w_P in FP64 and, when Fu32 is given, in FP32
 __global__ void k_ends32(const float* __restrict__ Ut, const float* __restrict__ Wt, int d1, int d2, int ldu,
-                         int ldw, int P, double* __restrict__ Fu, double* __restrict__ Fw) {
+                         int ldw, int P, double* __restrict__ Fu, double* __restrict__ Fw, float* __restrict__ Fu32,
+                         float* __restrict__ Fw32) {
   const int nloc = blockIdx.y;
   for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < d1 + d2; e += gridDim.x * blockDim.x) {
-    if (e < d1) Fu[(size_t)nloc * d1 + e] = (double)Ut[((size_t)nloc * (P + 1) + P) * ldu + e];
-    else Fw[(size_t)nloc * d2 + (e - d1)] = (double)Wt[((size_t)nloc * (P + 1) + P) * ldw + (e - d1)];
+    if (e < d1) {
+      const float v = Ut[((size_t)nloc * (P + 1) + P) * ldu + e];
+      Fu[(size_t)nloc * d1 + e] = (double)v;
+      if (Fu32) Fu32[(size_t)nloc * d1 + e] = v;
+    } else {
+      const float v = Wt[((size_t)nloc * (P + 1) + P) * ldw + (e - d1)];
+      Fw[(size_t)nloc * d2 + (e - d1)] = (double)v;
+      if (Fw32) Fw32[(size_t)nloc * d2 + (e - d1)] = v;
+    }
   }
 }
 
@@ -960,8 +969,9 @@ void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, 
   c->launches++;
 }
 
-void mx_ends32(Ctx* c, const float* Ut, const float* Wt, int ldu, int ldw, int nact, double* Fu, double* Fw) {
-  k_ends32<<<dim3(8, nact), 256, 0, c->stream>>>(Ut, Wt, c->d1, c->d2, ldu, ldw, c->P, Fu, Fw);
+void mx_ends32(Ctx* c, const float* Ut, const float* Wt, int ldu, int ldw, int nact, double* Fu, double* Fw,
+               float* Fu32, float* Fw32) {
+  k_ends32<<<dim3(8, nact), 256, 0, c->stream>>>(Ut, Wt, c->d1, c->d2, ldu, ldw, c->P, Fu, Fw, Fu32, Fw32);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
