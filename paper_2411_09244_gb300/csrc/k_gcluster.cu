@@ -133,13 +133,13 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a, int nb) 
   __syncthreads();
   cl_sync();  // every CTA of the cluster is resident before any DSMEM access
   const int rt = nr > warp ? (nr - warp + 31) / 32 : 0;  // matvec rows of this warp: q = warp + 32 t
-  int nbase = a.n_lo;
-  for (int n = a.n_lo; n < a.n_hi; ++n) {
-    const int sl = n - nbase;  // staging slot of this step
-    const float am = (float)a.amp[n];
-    // inputs of this step that do not depend on the sweep, fetched up front by
-    // the threads that use them (row q = tid, column slice entry tid)
-    float pf = 0.f, pg = 0.f, pc = 0.f;
+  // inputs of a step that do not depend on the sweep (F end, old G, jump, for
+  // row q = tid and slice entry tid) are fetched one step ahead
+  auto fetch = [&](int n, float& pf, float& pg, float& pc, float& wf, float& wg, float& wc, float& am) {
+    pf = pg = pc = wf = wg = wc = 0.f;
+    am = 0.f;
+    if (n >= a.n_hi) return;
+    am = (float)a.amp[n];
     if (tid < nr) {
       const int i = r0 + tid;
       if (!a.first) {
@@ -148,7 +148,6 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a, int nb) 
       }
       if (a.Cu) pc = a.Cu[(size_t)(n + 1) * d1 + i];
     }
-    float wf = 0.f, wg = 0.f, wc = 0.f;
     if (tid < ns) {
       const int j = j0 + tid;
       if (!a.first) {
@@ -157,6 +156,16 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a, int nb) 
       }
       if (a.Cw) wc = a.Cw[(size_t)(n + 1) * d2 + j];
     }
+  };
+  float npf, npg, npc, nwf, nwg, nwc, nam;
+  fetch(a.n_lo, npf, npg, npc, nwf, nwg, nwc, nam);
+  int nbase = a.n_lo;
+  for (int n = a.n_lo; n < a.n_hi; ++n) {
+    const int sl = n - nbase;  // staging slot of this step
+    const float pf = npf, pg = npg, pc = npc, wf = nwf, wg = nwg, wc = nwc, am = nam;
+    // G_old of step n + 1 is read here, before this sweep rewrites it: this
+    // step writes G_old of step n only (staged), so the read sees the old value
+    fetch(n + 1, npf, npg, npc, nwf, nwg, nwc, nam);
     // u-phase products CA w: one warp per row
 #pragma unroll
     for (int t = 0; t < GC_MAX_RT; ++t) {
