@@ -38,7 +38,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c5"])
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "mixed_f32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
@@ -152,7 +152,7 @@ def umma_traffic():
 
 def problem(name):
     from paper_2411_09244_gb300 import inputs
-    return {"c1": inputs.config_c1, "c2": inputs.config_c2}[name]()
+    return {"c1": inputs.config_c1, "c2": inputs.config_c2, "c5": inputs.config_c5}[name]()
 
 
 def cpu_baseline(prob, d1, d2, K1, wr_total, budget_s=25.0):
