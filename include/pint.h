@@ -207,7 +207,10 @@ pint_status pint_adjoint(pint_ctx* ctx, const int* obs_nodes, int n_obs, const d
  *          6 load F1 and F2 of f_shape (d1 then d2; pass f_shape in aux),
  *          7 the raw-basis Gram matrices G_M (n_raw^2),
  *          8 per raw basis: kind (0 matrix, 1 fracture, 2 enrichment) and
- *            owner block, as doubles (2*n_raw)
+ *            owner block, as doubles (2*n_raw),
+ *          9 wall time of the setup stages in ms (6 doubles: block
+ *            eigenproblems, oversampled basis solves, Galerkin products,
+ *            reduced matrices, spectral bases, time-grid operators)
  *   out    ptr, large enough for the quantity
  *   aux    ptr or NULL, extra input for which = 6
  */

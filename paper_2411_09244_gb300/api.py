@@ -123,10 +123,11 @@ class Pint:
         return coarse, fine
 
     def get_reduced(self, which: str, aux=None):
-        names = {"M11": 0, "A11": 1, "M22": 2, "A22": 3, "M12": 4, "A12": 5, "load": 6, "GM": 7, "kinds": 8}
+        names = {"M11": 0, "A11": 1, "M22": 2, "A22": 3, "M12": 4, "A12": 5, "load": 6, "GM": 7, "kinds": 8,
+                 "setup_ms": 9}
         d1, d2, nr = self.info["d1"], self.info["d2"], self.info["n_raw"]
         shapes = {"M11": (d1, d1), "A11": (d1, d1), "M22": (d2, d2), "A22": (d2, d2), "M12": (d1, d2),
-                  "A12": (d1, d2), "load": (d1 + d2,), "GM": (nr, nr), "kinds": (nr, 2)}
+                  "A12": (d1, d2), "load": (d1 + d2,), "GM": (nr, nr), "kinds": (nr, 2), "setup_ms": (6,)}
         out = torch.empty(shapes[which], dtype=torch.float64, device=self.device)
         x = _f64(aux, self.device)
         L.check(self.lib.pint_get_reduced(self.h, names[which], L.ptr(out), L.ptr(x)))

@@ -122,6 +122,9 @@ struct Ctx {
   // mixed-path state lives in mixed.cu
   void* mixed = nullptr;
   void* adj = nullptr;  // adjoint buffers (k_adjoint.cu)
+  // wall time of the setup stages, ms: blocks, windows, Galerkin, reduced,
+  // spectral, time-grid operators
+  double stage_ms[6] = {0, 0, 0, 0, 0, 0};
 
   // scratch for solves (grown on demand)
   std::vector<std::pair<void*, size_t>> scratch;

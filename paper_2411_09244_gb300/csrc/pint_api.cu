@@ -5,6 +5,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <chrono>
 #include <cstring>
 
 namespace pint {
@@ -109,6 +110,16 @@ static pint_status guarded(Ctx* c, F&& f) {
   }
 }
 
+// wall time of one setup stage (synchronised), accumulated into c->stage_ms[k]
+template <typename F>
+static void timed_stage(Ctx* c, int k, F&& f) {
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+  const auto t0 = std::chrono::steady_clock::now();
+  f();
+  PINT_CUDA(cudaStreamSynchronize(c->stream));
+  c->stage_ms[k] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+}
+
 static void fill_info(Ctx* c, pint_space_info* info, double ms) {
   if (!info) return;
   info->n_f = c->n_f;
@@ -193,8 +204,8 @@ pint_status pint_build_multiscale_spaces(pint_ctx* ctx, int nc, int J, int ell, 
     c->bs = c->n_f / nc;
     c->nb = (c->bs + 1) * (c->bs + 1);
     c->n_blocks = nc * nc;
-    build_blocks(c);
-    build_windows(c);
+    timed_stage(c, 0, [&] { build_blocks(c); });
+    timed_stage(c, 1, [&] { build_windows(c); });
     c->have_spaces = true;
     PINT_CUDA(cudaEventRecord(e1, c->stream));
     PINT_CUDA(cudaEventSynchronize(e1));
@@ -227,10 +238,10 @@ pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double 
     PINT_CUDA(cudaEventCreate(&e1));
     PINT_CUDA(cudaEventRecord(e0, c->stream));
     if (!c->have_reduced) {
-      build_galerkin(c);
-      build_reduced(c);
+      timed_stage(c, 2, [&] { build_galerkin(c); });
+      timed_stage(c, 3, [&] { build_reduced(c); });
       PINT_REQUIRE(c->d2 <= 4096, PINT_ERR_BAD_ARG, "dim V_H2 above 4096 (nc <= 63)");
-      build_spectral(c);
+      timed_stage(c, 4, [&] { build_spectral(c); });
       c->have_reduced = true;
     }
     c->T = T;
@@ -240,7 +251,7 @@ pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double 
     c->precision = precision;
     c->Dt = T / N;
     c->dt = c->Dt / P;
-    hot_prepare(c);
+    timed_stage(c, 5, [&] { hot_prepare(c); });
     c->have_time = true;
     PINT_CUDA(cudaEventRecord(e1, c->stream));
     PINT_CUDA(cudaEventSynchronize(e1));
@@ -380,6 +391,14 @@ pint_status pint_get_reduced(pint_ctx* ctx, int which, double* out, const double
         src = v;
         n = (size_t)(d1 + d2);
         break;
+      }
+      case 9: {  // setup stage wall times, ms (6 doubles)
+        if (is_device_ptr(out))
+          PINT_CUDA(cudaMemcpyAsync(out, c->stage_ms, sizeof(c->stage_ms), cudaMemcpyHostToDevice, c->stream));
+        else
+          std::memcpy(out, c->stage_ms, sizeof(c->stage_ms));
+        PINT_CUDA(cudaStreamSynchronize(c->stream));
+        return;
       }
       case 8: {
         std::vector<double> h(2 * (size_t)c->n_raw);
