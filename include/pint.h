@@ -58,7 +58,7 @@ enum {
 enum { PINT_FP64 = 0, PINT_MIXED = 1, PINT_MIXED_F32 = 2 };
 
 /* flags for pint_assemble_reduced */
-enum { PINT_ALLOW_UNSTABLE = 1 };
+enum { PINT_ALLOW_UNSTABLE = 1, PINT_FINE_SEQUENTIAL = 2 };
 
 typedef struct {
   int n_f, nc, J, ell;
@@ -130,7 +130,12 @@ pint_status pint_build_multiscale_spaces(pint_ctx* ctx, int nc, int J, int ell,
  *   T, N, P, alpha   time grid and WR parameter (0 < alpha < 1, P <= 64)
  *   precision        PINT_FP64 or PINT_MIXED
  *   flags            PINT_ALLOW_UNSTABLE: do not reject a Delta t above
- *                    dt_max (Section 3.2 condition)
+ *                    dt_max (Section 3.2 condition);
+ *                    PINT_FINE_SEQUENTIAL: on the FP64 path, the fine
+ *                    propagator of Algorithm 1 is the fine scheme stepped
+ *                    P times on all active intervals at once instead of the
+ *                    WR all-at-once solve (same fixed point; a comparison
+ *                    mode without the paper's counterpart)
  *   info             optional, receives gamma, lambda_max22, dt_max
  * Errors: BAD_ARG, STATE, UNSTABLE_DT (Delta t > dt_max without the flag;
  * info is still filled), SINGULAR, OOM, CUDA.

@@ -20,6 +20,7 @@ STATUS = {0: "OK", -1: "BAD_ARG", -2: "OOM", -3: "CUDA", -4: "UNSTABLE_DT", -5: 
           -6: "NONFINITE", -7: "SINGULAR", -8: "STATE", -9: "TIMEOUT"}
 PINT_FP64, PINT_MIXED, PINT_MIXED_F32 = 0, 1, 2
 PINT_ALLOW_UNSTABLE = 1
+PINT_FINE_SEQUENTIAL = 2
 MAX_ITERS = 512
 
 

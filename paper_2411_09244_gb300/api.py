@@ -71,10 +71,11 @@ class Pint:
         return self.info
 
     def assemble_reduced(self, T: float | None, N: int, P: int, alpha: float, precision: int = L.PINT_FP64,
-                         allow_unstable: bool = False) -> dict:
-        """T = None picks the stable final time from gamma and lambda_max."""
+                         allow_unstable: bool = False, fine_sequential: bool = False) -> dict:
+        """T = None picks the stable final time from gamma and lambda_max.
+        fine_sequential: PINT_FINE_SEQUENTIAL (FP64 path comparison mode)."""
         info = L.SpaceInfo()
-        flags = L.PINT_ALLOW_UNSTABLE if allow_unstable else 0
+        flags = (L.PINT_ALLOW_UNSTABLE if allow_unstable else 0) | (L.PINT_FINE_SEQUENTIAL if fine_sequential else 0)
         if T is None:
             # first pass with a tiny T to obtain gamma and lambda_max
             L.check(self.lib.pint_assemble_reduced(self.h, 1e-30, N, P, alpha, precision, flags,

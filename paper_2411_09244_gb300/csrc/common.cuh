@@ -110,6 +110,7 @@ struct Ctx {
   // time grid
   int N = 0, P = 0, precision = PINT_FP64;
   double T = 0, Dt = 0, dt = 0, alpha = 0;
+  bool fine_seq = false;  // PINT_FINE_SEQUENTIAL
   bool have_time = false;
 
   // hot-path operators (FP64): [-G1 | G2] and [-CM^T | -dt CA^T]

@@ -823,6 +823,33 @@ static int wr_sweep(Ctx* c, Hot& H, const double* xs_u, const double* xs_w, cons
   return it;
 }
 
+// The fine scheme stepped P times on intervals [n_lo, n_lo + nact) at once
+// (lags restarted at the interval starts), columns batched over intervals:
+// F* itself, the fixed point the WR iteration converges to, without the WR
+// iterations (PINT_FINE_SEQUENTIAL).  Work per sweep equals that of one WR
+// iteration; the price is P dependent launches of N-column products.
+static void seq_sweep(Ctx* c, Hot& H, const double* xs_u, const double* xs_w, const double* amp_act, int nact,
+                      double* fu, double* fw) {
+  const int d1 = c->d1, d2 = c->d2;
+  const size_t s1 = (size_t)nact * d1, s2 = (size_t)nact * d2;
+  // three state buffers per space inside the (unused) WR trajectory storage
+  double *u = H.Ut, *ul = H.Ut + s1, *uo = H.Ut + 2 * s1;
+  double *w = H.Wt, *wl = H.Wt + s2, *wo = H.Wt + 2 * s2;
+  PINT_CUDA(cudaMemcpyAsync(u, xs_u, s1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(w, xs_w, s2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(ul, xs_u, s1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(wl, xs_w, s2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+  for (int p = 0; p < c->P; ++p) {
+    step_batch(c, H, u, w, ul, wl, amp_act, c->dt, nact, uo, wo);
+    std::swap(ul, u);  // lag <- current; the old lag buffer is recycled
+    std::swap(wl, w);
+    std::swap(u, uo);  // current <- new
+    std::swap(w, wo);
+  }
+  PINT_CUDA(cudaMemcpyAsync(fu, u, s1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(fw, w, s2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+}
+
 static void stage_amp(Ctx* c, Hot& H, const double* amp_dev, int count) {
   if (amp_dev)
     PINT_CUDA(cudaMemcpyAsync(H.amp, amp_dev, (size_t)count * 8, cudaMemcpyDeviceToDevice, c->stream));
@@ -897,8 +924,13 @@ void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const dou
       const int n_lo = k - 1, nact = N - n_lo;
       PINT_CUDA(cudaEventRecord(eF0, c->stream));
       bool bad = false;
-      int it = wr_sweep(c, H, H.Xu + (size_t)n_lo * d1, H.Xw + (size_t)n_lo * d2, H.amp + n_lo, nact, wr_tol,
-                        wr_max, H.Fu + (size_t)n_lo * d1, H.Fw + (size_t)n_lo * d2, &bad);
+      int it = 0;
+      if (c->fine_seq)
+        seq_sweep(c, H, H.Xu + (size_t)n_lo * d1, H.Xw + (size_t)n_lo * d2, H.amp + n_lo, nact,
+                  H.Fu + (size_t)n_lo * d1, H.Fw + (size_t)n_lo * d2);
+      else
+        it = wr_sweep(c, H, H.Xu + (size_t)n_lo * d1, H.Xw + (size_t)n_lo * d2, H.amp + n_lo, nact, wr_tol,
+                      wr_max, H.Fu + (size_t)n_lo * d1, H.Fw + (size_t)n_lo * d2, &bad);
       PINT_CUDA(cudaEventRecord(eF1, c->stream));
       PINT_CUDA(cudaEventSynchronize(eF1));
       float ms = 0.f;

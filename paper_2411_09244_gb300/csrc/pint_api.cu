@@ -249,6 +249,7 @@ pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double 
     c->P = P;
     c->alpha = alpha;
     c->precision = precision;
+    c->fine_seq = (flags & PINT_FINE_SEQUENTIAL) != 0;
     c->Dt = T / N;
     c->dt = c->Dt / P;
     timed_stage(c, 5, [&] { hot_prepare(c); });

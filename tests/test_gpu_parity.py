@@ -171,3 +171,22 @@ def test_mixed_path_matches_oracle(pair):
     got = fine.cpu().numpy()
     per_t = [rel(got[n], ref[n]) for n in range(prob.N) if np.linalg.norm(ref[n]) > 0]
     assert max(per_t) < 1e-6, max(per_t)
+
+
+def test_sequential_batched_fine_propagator(pair):
+    """PINT_FINE_SEQUENTIAL: Algorithm 1 with F* stepped on all intervals at
+    once reaches the same fixed point as the WR fine propagator (and k = N
+    reproduces the sequential fine scheme)."""
+    name, prob, orc, p = pair
+    q = api.Pint(prob.n_f, prob.kappa)
+    try:
+        q.build_multiscale_spaces(prob.nc, prob.J, prob.ell)
+        q.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, fine_sequential=True)
+        cs, fs, st = q.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-13, k_max=prob.N)
+        cq, fq = q.sequential_solve(prob.u0, prob.f, prob.amp)
+    finally:
+        q.close()
+    assert rel(cs.cpu().numpy(), cq.cpu().numpy()) < 1e-10
+    u, w = orc.sequential()
+    ref = orc.fine_field(u, w)[1:]
+    assert rel(fs.cpu().numpy(), ref) < 1e-10
