@@ -1108,8 +1108,8 @@ void apply_F_dev(Ctx* c, const double* in, int count, const double* f_nodes, con
 void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* Ut, const float* Wt, int ldu,
                    int ldw, int P, int ncols, float* out, const int* gate);
 void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
-                      const float* Blo, int ncols, int nsplit, float* out, int* err, const int* gate);
-int mx_umma_split(int M, int Kp, int ncols, int maxs);
+                      const float* Blo, int ncols, int nsplit, int tn, float* out, int* err, const int* gate);
+void umma_plan(int M, int Kp, int ncols, int maxs, int* tn, int* s);
 void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const float* lam1, const float* src,
                      const float* b1, const double* amp, const float2* tw, const float2* dsh, const float2* dshbr,
                      const float* bpow, float* accU, float* B1h, float* B1l, const int* gate);
@@ -1349,7 +1349,13 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
   const int ncols = nact * P;
   const int ldu = M.ldu, ldw = M.ldw;
   const bool tensor = (c->precision == PINT_MIXED);
-  const int nsl = tensor ? mx_umma_split(d2, 2 * ldu, ncols, MX_MAX_SPLIT) : 1;
+  // tile widths and K splits of the two contractions (the time solve reads one
+  // slice of the first; the W recurrence sums the slices of the second)
+  int tn0 = 128, tn1 = 128, nsl = 1, one = 1;
+  if (tensor) {
+    umma_plan(d1, 2 * ldw, ncols, 1, &tn0, &one);
+    umma_plan(d2, 2 * ldu, ncols, MX_MAX_SPLIT, &tn1, &nsl);
+  }
   float* acc32 = reinterpret_cast<float*>(H.acc);  // FP32 squared updates (2 nact P)
   wr_max = std::min(wr_max, PINT_MAX_ITERS);
   // column maps of the active window start at column 0 of B0 / B1
@@ -1362,13 +1368,14 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
     cudaEvent_t* ev = M.iev[it & 1];
     PINT_CUDA(cudaMemsetAsync(acc32, 0, (size_t)2 * nact * P * 4, c->stream));
     PINT_CUDA(cudaEventRecord(ev[0], c->stream));
-    if (tensor) mx_contract_umma(c, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, M.R, M.err, M.gate);
+    if (tensor) mx_contract_umma(c, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, tn0, M.R, M.err, M.gate);
     else mx_contract32(c, 0, M.AR32, d1, 2 * ldw, Ut, Wt, ldu, ldw, P, ncols, M.R, M.gate);
     PINT_CUDA(cudaEventRecord(ev[1], c->stream));
     mx_time_solve32(c, M.R, nact, Ut, ldu, M.lam1f, srcU, M.b1f, amp_act, M.twf, M.dshf, M.dshbr, M.bpowf, acc32,
                     M.B1h, M.B1l, M.gate);
     PINT_CUDA(cudaEventRecord(ev[2], c->stream));
-    if (tensor) mx_contract_umma(c, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, nsl, M.S, M.err, M.gate);
+    if (tensor)
+      mx_contract_umma(c, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, nsl, tn1, M.S, M.err, M.gate);
     else mx_contract32(c, 1, M.AS32, d2, 2 * ldu, Ut, Wt, ldu, ldw, P, ncols, M.S, M.gate);
     PINT_CUDA(cudaEventRecord(ev[3], c->stream));
     mx_w_sweep32(c, M.S, tensor ? nsl : 1, (size_t)ncols * d2, nact, Wt, ldw, M.lam2f, srcW, M.b2f, amp_act,

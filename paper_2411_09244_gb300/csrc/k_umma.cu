@@ -12,12 +12,13 @@
 // (hi = tf32(x), lo = tf32(x - hi)) and each K step issues three MMAs
 // (hi hi + hi lo + lo hi); the dropped lo lo term is below FP32 rounding.
 //
-// Persistent kernel, one CTA per SM: tiles of 128 modes x 128 columns of one
-// K slice (MMA M = 128 with A = coupling rows, N = 128 with B = trajectory
-// columns) are dealt out round-robin.  Warp 0 (one lane) streams 32-wide K
-// stages with TMA (128-byte swizzle) into a ring of STAGES buffers across tile
+// Persistent kernel, one CTA per SM: tiles of 128 modes x tn columns of one
+// K slice (MMA M = 128 with A = coupling rows, N = tn in 128..256 with B =
+// trajectory columns; tn and the K split chosen per shape by umma_plan) are
+// dealt out round-robin.  Warp 0 (one lane) streams 16-wide K stages with TMA
+// (64-byte swizzle) into a ring of STAGES buffers across tile
 // boundaries; warp 1 allocates TMEM and one lane issues the MMAs into one of
-// two accumulators (2 x 128 TMEM columns, lane = mode); warps 2-5 drain the
+// two accumulators (2 x 256 TMEM columns, lane = mode); warps 2-5 drain the
 // other accumulator to global memory meanwhile (stores coalesced along the
 // modes).  mbarriers: "full"/"empty" for the ring (TMA transaction count /
 // tcgen05.commit), "tfull"/"tempty" for the accumulators (tcgen05.commit /
@@ -35,31 +36,32 @@ namespace pint {
 
 namespace {
 
-constexpr int TM = 128;  // modes per tile (MMA M)
-constexpr int TN = 128;  // trajectory columns per tile (MMA N)
-constexpr int KB = 32;   // K elements per stage = one 128-byte swizzle row
-constexpr int STAGES = 3;
+constexpr int TM = 128;    // modes per tile (MMA M)
+constexpr int TNMAX = 256; // trajectory columns per tile (MMA N, chosen per shape: 128..256)
+constexpr int KB = 16;     // K elements per stage = one 64-byte swizzle row
+constexpr int STAGES = 4;
 constexpr int THREADS = 192;     // warp 0 TMA, warp 1 MMA, warps 2-5 epilogue
 constexpr int EPI_THREADS = 128;
 constexpr int NACC = 2;          // TMEM accumulators
 constexpr int WAIT_LIMIT = 1 << 22;
-constexpr int OPB = TM * KB * 4;      // bytes of one operand tile (16 KB)
-constexpr int STAGE_BYTES = 4 * OPB;  // A hi, A lo, B hi, B lo
+constexpr int OPA = TM * KB * 4;                     // one A operand tile (8 KB)
+constexpr int OPBM = TNMAX * KB * 4;                 // room for one B operand tile (16 KB)
+constexpr int STAGE_BYTES = 2 * OPA + 2 * OPBM;      // A hi, A lo, B hi, B lo
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024;  // + slack for 1024-byte alignment
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return (uint32_t)__cvta_generic_to_shared(p);
 }
 
-// shared-memory matrix descriptor: K-major, 128-byte swizzle, 8-row groups
-// 1024 bytes apart (stride byte offset), descriptor version 1
-__device__ __forceinline__ uint64_t desc_sw128(uint32_t saddr) {
+// shared-memory matrix descriptor: K-major, 64-byte swizzle (rows of 16 TF32),
+// 8-row groups 512 bytes apart (stride byte offset), descriptor version 1
+__device__ __forceinline__ uint64_t desc_sw64(uint32_t saddr) {
   uint64_t d = 0;
   d |= (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)1 << 16;            // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;  // stride byte offset
-  d |= (uint64_t)1 << 46;            // version
-  d |= (uint64_t)2 << 61;            // layout: 128-byte swizzle
+  d |= (uint64_t)1 << 16;           // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(512 >> 4) << 32;  // stride byte offset
+  d |= (uint64_t)1 << 46;           // version
+  d |= (uint64_t)4 << 61;           // layout: 64-byte swizzle
   return d;
 }
 
@@ -132,17 +134,18 @@ __device__ __forceinline__ void bar_arrive(uint64_t* bar) {
 struct Tile {
   int z, row0, col0;
 };
-__device__ __forceinline__ Tile decode(int tg, int n_ct, int n_rt) {
+__device__ __forceinline__ Tile decode(int tg, int n_ct, int n_rt, int tn) {
   const int per = n_ct * n_rt, rem = tg % per;
-  return {tg / per, (rem / n_ct) * TM, (rem % n_ct) * TN};
+  return {tg / per, (rem / n_ct) * TM, (rem % n_ct) * tn};
 }
 
 // out + z * ncols * M: the K slice [z kspan, (z + 1) kspan) of the product
 __global__ void __launch_bounds__(THREADS, 1)
     k_wr_umma(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, int M, int ncols,
-              int kspan, int nsplit, float* __restrict__ out, int* __restrict__ err, const int* __restrict__ gate) {
-  constexpr uint32_t IDESC = idesc_tf32(TM, TN);
+              int kspan, int nsplit, int tn, float* __restrict__ out, int* __restrict__ err,
+              const int* __restrict__ gate) {
+  const uint32_t IDESC = idesc_tf32(TM, tn);
   if (gate && *gate) return;  // the WR sweep has already converged: no-op launch
   extern __shared__ uint8_t smem_raw[];
   __shared__ __align__(8) uint64_t full[STAGES], empty[STAGES], tfull[NACC], tempty[NACC], done;
@@ -151,7 +154,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   // the 128-byte swizzle pattern repeats every 1024 bytes: align the ring to it
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
 
-  const int n_ct = (ncols + TN - 1) / TN, n_rt = (M + TM - 1) / TM;
+  const int n_ct = (ncols + tn - 1) / tn, n_rt = (M + TM - 1) / TM;
+  const uint32_t stage_tx = 2 * OPA + 2 * tn * KB * 4;  // bytes the four copies of a stage land
   const int n_tiles = n_ct * n_rt * nsplit;
   const int my_tiles = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int nkb = kspan / KB;
@@ -171,7 +175,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   }
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                 "r"(NACC * TN));
+                 "r"(NACC * TNMAX));
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -185,7 +189,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       int g = 0;
       bool stop = false;
       for (int j = 0; j < my_tiles && !stop; ++j) {
-        const Tile T = decode((int)blockIdx.x + j * (int)gridDim.x, n_ct, n_rt);
+        const Tile T = decode((int)blockIdx.x + j * (int)gridDim.x, n_ct, n_rt, tn);
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = g % STAGES, use = g / STAGES;
           if (s_fail || (use >= 1 && !bar_wait(&empty[s], (uint32_t)((use - 1) & 1)))) {
@@ -195,11 +199,11 @@ __global__ void __launch_bounds__(THREADS, 1)
           }
           uint8_t* base = smem + s * STAGE_BYTES;
           const int k0 = T.z * kspan + kb * KB;
-          bar_expect_tx(&full[s], STAGE_BYTES);
+          bar_expect_tx(&full[s], stage_tx);
           tma_load_2d(base, &mAh, &full[s], k0, T.row0);
-          tma_load_2d(base + OPB, &mAl, &full[s], k0, T.row0);
-          tma_load_2d(base + 2 * OPB, &mBh, &full[s], k0, T.col0);
-          tma_load_2d(base + 3 * OPB, &mBl, &full[s], k0, T.col0);
+          tma_load_2d(base + OPA, &mAl, &full[s], k0, T.row0);
+          tma_load_2d(base + 2 * OPA, &mBh, &full[s], k0, T.col0);
+          tma_load_2d(base + 2 * OPA + OPBM, &mBl, &full[s], k0, T.col0);
         }
       }
       // copies still in flight must land before the CTA's shared memory goes
@@ -220,7 +224,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t d = tmem + (uint32_t)(acc * TN);
+        const uint32_t d = tmem + (uint32_t)(acc * TNMAX);
         for (int kb = 0; kb < nkb; ++kb, ++g) {
           const int s = g % STAGES, use = g / STAGES;
           if (!bar_wait(&full[s], (uint32_t)(use & 1))) {
@@ -233,8 +237,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
           for (int kk = 0; kk < KB / 8; ++kk) {
             const uint32_t ko = kk * 32;  // K = 8 TF32 = 32 bytes along the swizzle row
-            const uint64_t dah = desc_sw128(base + ko), dal = desc_sw128(base + OPB + ko);
-            const uint64_t dbh = desc_sw128(base + 2 * OPB + ko), dbl = desc_sw128(base + 3 * OPB + ko);
+            const uint64_t dah = desc_sw64(base + ko), dal = desc_sw64(base + OPA + ko);
+            const uint64_t dbh = desc_sw64(base + 2 * OPA + ko), dbl = desc_sw64(base + 2 * OPA + OPBM + ko);
             mma_tf32(d, dah, dbh, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
             mma_tf32(d, dah, dbl, IDESC, 1u);
             mma_tf32(d, dal, dbh, IDESC, 1u);
@@ -261,12 +265,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       }
       bar_wait(&tfull[acc], (uint32_t)(u & 1));  // completed: returns at once; acquire for every lane
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const Tile T = decode((int)blockIdx.x + j * (int)gridDim.x, n_ct, n_rt);
+      const Tile T = decode((int)blockIdx.x + j * (int)gridDim.x, n_ct, n_rt, tn);
       const int i = T.row0 + 32 * qd + lane;  // output mode of this thread (TMEM lane)
       float* o = out + (size_t)T.z * ncols * M;
-      for (int cc = 0; cc < TN; cc += 32) {
+      for (int cc = 0; cc < tn; cc += 32) {
         float v[32];
-        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(acc * TN + cc), v);
+        tmem_ld32(tmem + ((uint32_t)(32 * qd) << 16) + (uint32_t)(acc * TNMAX + cc), v);
         if (i < M) {
 #pragma unroll
           for (int q = 0; q < 32; ++q) {
@@ -285,7 +289,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NACC * TN));
+  if (warp == 1) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(NACC * TNMAX));
   if (tid == 0 && s_fail) atomicExch(err, 1);
 }
 
@@ -301,17 +305,17 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-// row-major [rows][Kp] FP32 matrix, boxes of 128 rows x 32 K with the
-// 128-byte swizzle; rows past the end read as zero
-CUtensorMap make_map(const float* base, int rows, int Kp) {
+// row-major [rows][Kp] FP32 matrix, boxes of box_rows rows x 16 K with the
+// 64-byte swizzle; rows past the end read as zero
+CUtensorMap make_map(const float* base, int rows, int Kp, int box_rows) {
   CUtensorMap m;
   const cuuint64_t dims[2] = {(cuuint64_t)Kp, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)Kp * 4};
-  const cuuint32_t box[2] = {(cuuint32_t)KB, 128u};
+  const cuuint32_t box[2] = {(cuuint32_t)KB, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1u, 1u};
   PINT_REQUIRE(((uintptr_t)base & 15) == 0 && Kp % KB == 0, PINT_ERR_BAD_ARG, "contraction operand misaligned");
   const CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides,
-                                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                                 box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
                                  CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   PINT_REQUIRE(r == CUDA_SUCCESS, PINT_ERR_CUDA, "cuTensorMapEncodeTiled failed");
   return m;
@@ -319,9 +323,7 @@ CUtensorMap make_map(const float* base, int rows, int Kp) {
 
 }  // namespace
 
-// K split that best fills the SMs (one CTA per SM: the stage ring takes most
-// of the shared memory): minimises waves(tiles * s) / s over s <= maxs.
-int mx_umma_split(int M, int Kp, int ncols, int maxs) {
+int umma_sms() {
   static int sms = 0;
   if (!sms) {
     int dev = 0;
@@ -329,18 +331,31 @@ int mx_umma_split(int M, int Kp, int ncols, int maxs) {
     cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (sms <= 0) sms = 1;
   }
-  const long long tiles = (long long)((ncols + TN - 1) / TN) * ((M + TM - 1) / TM);
-  int best = 1;
-  double best_t = 1e300;
-  for (int s = 1; s <= maxs; ++s) {
-    if (Kp % (KB * s)) continue;
-    const double t = (double)((tiles * s + sms - 1) / sms) / s;
-    if (t < best_t * 0.999) {
-      best_t = t;
-      best = s;
+  return sms;
+}
+
+// Tile width and K split for one contraction shape, picked by a cost model of
+// the persistent launch: every CTA runs its tiles back to back, so the time is
+// set by the busiest SM, ceil(tiles / SMs) tiles of (tn / s) column-K work each,
+// plus the operand bytes each tile streams through L2 (1 / tn + 1 / 128 per
+// output).  nsplit = 1 when the consumer cannot sum K slices.
+void umma_plan(int M, int Kp, int ncols, int maxs, int* tn_out, int* s_out) {
+  const int sms = umma_sms();
+  double best = 1e300;
+  *tn_out = 128;
+  *s_out = 1;
+  for (int tn = 128; tn <= TNMAX; tn += 32)
+    for (int s = 1; s <= maxs; ++s) {
+      if (Kp % (KB * s)) continue;
+      const long long tiles = (long long)((ncols + tn - 1) / tn) * ((M + TM - 1) / TM) * s;
+      const double rounds = (double)((tiles + sms - 1) / sms);
+      const double cost = rounds * (double)tn / s * (1.0 + 0.5 * (128.0 / tn + 1.0));
+      if (cost < best * 0.999) {
+        best = cost;
+        *tn_out = tn;
+        *s_out = s;
+      }
     }
-  }
-  return best;
 }
 
 // out[z][col][i] = sum over the z-th K slice of A(i, k) B(col, k); A = Ahi + Alo
@@ -348,7 +363,7 @@ int mx_umma_split(int M, int Kp, int ncols, int maxs) {
 // 16-byte aligned with Kp a multiple of 32 nsplit.  gate (device, may be
 // null): the launch does nothing when *gate != 0.
 void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
-                      const float* Blo, int ncols, int nsplit, float* out, int* err, const int* gate) {
+                      const float* Blo, int ncols, int nsplit, int tn, float* out, int* err, const int* gate) {
   static bool attr = false;
   if (!attr) {
     PINT_CUDA(cudaFuncSetAttribute(k_wr_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
@@ -356,18 +371,13 @@ void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp,
   }
   PINT_REQUIRE(nsplit >= 1 && Kp % (KB * nsplit) == 0, PINT_ERR_BAD_ARG,
                "contraction K not divisible by the split");
+  PINT_REQUIRE(tn >= 32 && tn <= TNMAX && tn % 32 == 0, PINT_ERR_BAD_ARG, "contraction tile width");
   if (ncols <= 0 || M <= 0) return;
-  const CUtensorMap ah = make_map(Ahi, M, Kp), al = make_map(Alo, M, Kp);
-  const CUtensorMap bh = make_map(Bhi, ncols, Kp), bl = make_map(Blo, ncols, Kp);
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
-    PINT_CUDA(cudaGetDevice(&dev));
-    PINT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-  }
-  const int tiles = ((ncols + TN - 1) / TN) * ((M + TM - 1) / TM) * nsplit;
-  const int grid = std::min(tiles, std::max(sms, 1));  // persistent: one CTA per SM at most
-  k_wr_umma<<<grid, THREADS, SMEM_BYTES, c->stream>>>(ah, al, bh, bl, M, ncols, Kp / nsplit, nsplit, out, err,
+  const CUtensorMap ah = make_map(Ahi, M, Kp, TM), al = make_map(Alo, M, Kp, TM);
+  const CUtensorMap bh = make_map(Bhi, ncols, Kp, tn), bl = make_map(Blo, ncols, Kp, tn);
+  const int tiles = ((ncols + tn - 1) / tn) * ((M + TM - 1) / TM) * nsplit;
+  const int grid = std::min(tiles, umma_sms());  // persistent: one CTA per SM at most
+  k_wr_umma<<<grid, THREADS, SMEM_BYTES, c->stream>>>(ah, al, bh, bl, M, ncols, Kp / nsplit, nsplit, tn, out, err,
                                                       gate);
   PINT_LAUNCH_CHECK();
   c->launches++;
