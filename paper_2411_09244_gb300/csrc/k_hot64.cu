@@ -1560,6 +1560,17 @@ void mixed_release(Ctx* c) {
   }
 }
 
+// Stopping tolerances of the low-precision solves relative to the largest
+// state norm (the main solve's jumps and WR updates, the correction solve's
+// WR updates): the refinement measures what the main solve leaves, so its
+// tolerances only trade main-solve work against correction work.
+#ifndef PINT_MAIN_REL_TOL
+#define PINT_MAIN_REL_TOL 1e-4
+#endif
+#ifndef PINT_CORR_REL_TOL
+#define PINT_CORR_REL_TOL 1e-6
+#endif
+
 void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const double* amp_dev, double eps,
                  int k_max, double wr_tol, int wr_max, double* u_out, double* coarse_out, pint_stats* st,
                  int n_refine) {
@@ -1615,8 +1626,8 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
     parareal_lp(c, H, M, probe, &f_ms, nullptr, nullptr, 0);
     double sc = state_scale(c, H, H.Xu, H.Xw);
     // the refinement corrects what the low-precision solve leaves: loose tolerances
-    m.eps = std::max(eps, 1e-6 * sc);
-    m.wr_tol = std::max(wr_tol, 1e-6 * sc);
+    m.eps = std::max(eps, PINT_MAIN_REL_TOL * sc);
+    m.wr_tol = std::max(wr_tol, PINT_MAIN_REL_TOL * sc);
     m.have_g0 = true;
   }
   parareal_lp(c, H, M, m, &f_ms, wr_hist, jump_hist, 0);
@@ -1668,7 +1679,7 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
       parareal_lp(c, H, M, probe, &f_ms, nullptr, nullptr, 0);
       double sc = state_scale(c, H, M.Yu, M.Yw);
       y.eps = eps;
-      y.wr_tol = std::max(wr_tol, 1e-6 * sc);
+      y.wr_tol = std::max(wr_tol, PINT_CORR_REL_TOL * sc);
       y.have_g0 = true;
     }
     parareal_lp(c, H, M, y, &f_ms, wr_hist, jump_hist, K1_total);
