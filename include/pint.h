@@ -58,7 +58,7 @@ enum {
 enum { PINT_FP64 = 0, PINT_MIXED = 1, PINT_MIXED_F32 = 2 };
 
 /* flags for pint_assemble_reduced */
-enum { PINT_ALLOW_UNSTABLE = 1, PINT_FINE_SEQUENTIAL = 2 };
+enum { PINT_ALLOW_UNSTABLE = 1, PINT_FINE_SEQUENTIAL = 2, PINT_AUTOTUNE = 4 };
 
 typedef struct {
   int n_f, nc, J, ell;
@@ -135,7 +135,14 @@ pint_status pint_build_multiscale_spaces(pint_ctx* ctx, int nc, int J, int ell,
  *                    propagator of Algorithm 1 is the fine scheme stepped
  *                    P times on all active intervals at once instead of the
  *                    WR all-at-once solve (same fixed point; a comparison
- *                    mode without the paper's counterpart)
+ *                    mode without the paper's counterpart);
+ *                    PINT_AUTOTUNE: on the PINT_MIXED path, the tile width
+ *                    and K split of each tensor-core contraction shape are
+ *                    measured (CUDA events, best of the cost model's top
+ *                    candidates) the first time the shape is met, and kept
+ *                    in the process-wide table of pint_tuning_*; without
+ *                    the flag the cost model's choice (or a loaded entry of
+ *                    the table) is used
  *   info             optional, receives gamma, lambda_max22, dt_max
  * Errors: BAD_ARG, STATE, UNSTABLE_DT (Delta t > dt_max without the flag;
  * info is still filled), SINGULAR, OOM, CUDA.
@@ -153,10 +160,13 @@ pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double 
  *   f_shape     ptr, (n_f+1)^2 source shape g; the source on interval n is
  *               amp[n] * g
  *   amp         ptr or NULL (all ones), N amplitudes
- *   eps         absolute jump tolerance (>= 0)
+ *   eps         jump tolerance: >= 0 absolute; < 0 relative, |eps| times
+ *               the largest M_H norm of the states of the initial G sweep
+ *               (max over n = 1..N)
  *   k_max       maximum F sweeps (1..N)
  *   wr_tol      WR stop: max over intervals and steps of the L2 norm of the
- *               update of u or w (>= 0)
+ *               update of u or w; >= 0 absolute, < 0 relative to the same
+ *               state scale as eps
  *   wr_max      maximum WR iterations per F sweep (>= 1)
  *   u_out       ptr or NULL, N x (n_f+1)^2: u_H at t_1..t_N on the fine grid
  *   coarse_out  ptr or NULL, (N+1) x (d1+d2): (u_n, w_n) coefficients in the
@@ -265,6 +275,30 @@ pint_status pint_get_info(pint_ctx* ctx, pint_space_info* info);
 
 /* pint_destroy -- free every device buffer of the context (NULL is a no-op). */
 pint_status pint_destroy(pint_ctx* ctx);
+
+/*
+ * Autotuner table (process-wide, shared by all contexts and host threads).
+ * One row per contraction shape of the WR fine propagator's two tensor-core
+ * contractions, as 6 ints: M (rows: d1 or d2), Kp (padded K), ncols (active
+ * intervals x P), maxs (largest K split the consumer sums), tn (tile width,
+ * 128..256, a multiple of 32), s (K split, 1..maxs, Kp a multiple of 16 s);
+ * and the measured time of one launch in microseconds (0 when set by hand).
+ * These calls touch no device state and need no GPU.
+ *   pint_tuning_count  number of rows
+ *   pint_tuning_get    copies up to cap rows (host int[cap][6], host
+ *                      float[cap] or NULL) in key order; *count receives the
+ *                      number copied.  Errors: BAD_ARG (NULL rows/count,
+ *                      cap < 0)
+ *   pint_tuning_set    merges count rows (host, same layout; us may be NULL);
+ *                      nothing is merged if any row is invalid.  Errors:
+ *                      BAD_ARG (invalid row, named in pint_last_error)
+ *   pint_tuning_clear  empties the table
+ * The table is read by PINT_MIXED solves whether or not PINT_AUTOTUNE is set.
+ */
+int pint_tuning_count(void);
+pint_status pint_tuning_get(int* rows, float* us, int cap, int* count);
+pint_status pint_tuning_set(const int* rows, const float* us, int count);
+pint_status pint_tuning_clear(void);
 
 /* pint_last_error -- message of the last failing call on this thread. */
 const char* pint_last_error(void);

@@ -21,6 +21,7 @@ STATUS = {0: "OK", -1: "BAD_ARG", -2: "OOM", -3: "CUDA", -4: "UNSTABLE_DT", -5: 
 PINT_FP64, PINT_MIXED, PINT_MIXED_F32 = 0, 1, 2
 PINT_ALLOW_UNSTABLE = 1
 PINT_FINE_SEQUENTIAL = 2
+PINT_AUTOTUNE = 4
 MAX_ITERS = 512
 
 
@@ -77,6 +78,10 @@ SYMBOLS = {
                      C.c_void_p, C.POINTER(C.c_int)],
     "pint_get_info": [C.c_void_p, C.POINTER(SpaceInfo)],
     "pint_destroy": [C.c_void_p],
+    "pint_tuning_count": [],
+    "pint_tuning_get": [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)],
+    "pint_tuning_set": [C.c_void_p, C.c_void_p, C.c_int],
+    "pint_tuning_clear": [],
 }
 
 

@@ -48,6 +48,7 @@ class Pint:
         self.nn = (n_f + 1) ** 2
         k = _f64(kappa_cells, self.device).reshape(-1)
         h = C.c_void_p()
+        self.stream = torch.cuda.current_stream(self.device) if torch.cuda.is_available() else None
         L.check(self.lib.pint_setup_fine_grid(C.byref(h), n_f, L.ptr(k), L.current_stream()))
         self.h = h
         self.info = None
@@ -71,11 +72,14 @@ class Pint:
         return self.info
 
     def assemble_reduced(self, T: float | None, N: int, P: int, alpha: float, precision: int = L.PINT_FP64,
-                         allow_unstable: bool = False, fine_sequential: bool = False) -> dict:
+                         allow_unstable: bool = False, fine_sequential: bool = False,
+                         autotune: bool = False) -> dict:
         """T = None picks the stable final time from gamma and lambda_max.
-        fine_sequential: PINT_FINE_SEQUENTIAL (FP64 path comparison mode)."""
+        fine_sequential: PINT_FINE_SEQUENTIAL (FP64 path comparison mode).
+        autotune: PINT_AUTOTUNE (measured contraction tiles, mixed path)."""
         info = L.SpaceInfo()
-        flags = (L.PINT_ALLOW_UNSTABLE if allow_unstable else 0) | (L.PINT_FINE_SEQUENTIAL if fine_sequential else 0)
+        flags = ((L.PINT_ALLOW_UNSTABLE if allow_unstable else 0) | (L.PINT_FINE_SEQUENTIAL if fine_sequential else 0)
+                 | (L.PINT_AUTOTUNE if autotune else 0))
         if T is None:
             # first pass with a tiny T to obtain gamma and lambda_max
             L.check(self.lib.pint_assemble_reduced(self.h, 1e-30, N, P, alpha, precision, flags,
@@ -196,6 +200,89 @@ class ObservationMisfit(torch.autograd.Function):
     def backward(ctx, grad_out):
         g_u0, g_amp = ctx.saved_tensors
         return grad_out * g_u0, grad_out * g_amp, None, None, None, None, None
+
+
+# -- autotuner table ----------------------------------------------------------
+TUNING_KEYS = ("M", "Kp", "ncols", "maxs", "tn", "s")
+
+
+def tuning_table() -> list[dict]:
+    """Rows of the process-wide contraction tuning table (pint_tuning_get)."""
+    lb = L.lib()
+    n = lb.pint_tuning_count()
+    rows = np.zeros((max(n, 1), 6), dtype=np.int32)
+    us = np.zeros(max(n, 1), dtype=np.float32)
+    got = C.c_int(0)
+    L.check(lb.pint_tuning_get(rows.ctypes.data, us.ctypes.data, n, C.byref(got)))
+    return [dict(zip(TUNING_KEYS, map(int, rows[i])), us=float(us[i])) for i in range(got.value)]
+
+
+def set_tuning(entries) -> None:
+    """Merge rows (dicts with TUNING_KEYS, optional "us") into the table."""
+    entries = list(entries)
+    rows = np.array([[int(e[k]) for k in TUNING_KEYS] for e in entries], dtype=np.int32).reshape(-1, 6)
+    us = np.array([float(e.get("us", 0.0)) for e in entries], dtype=np.float32)
+    L.check(L.lib().pint_tuning_set(rows.ctypes.data if len(entries) else None,
+                                    us.ctypes.data if len(entries) else None, len(entries)))
+
+
+def clear_tuning() -> None:
+    L.check(L.lib().pint_tuning_clear())
+
+
+def save_tuning(path: str, device: str | None = None) -> None:
+    """Write the table as JSON: {"version": 1, "device": ..., "entries": [...]}."""
+    import json
+    if device is None and torch.cuda.is_available():
+        device = torch.cuda.get_device_name()
+    with open(path, "w") as fh:
+        json.dump({"version": 1, "device": device, "entries": tuning_table()}, fh, indent=1)
+
+
+def load_tuning(path: str, device: str | None = None) -> int:
+    """Merge a table written by save_tuning; entries measured on another
+    device name are skipped.  Returns the number of rows merged."""
+    import json
+    with open(path) as fh:
+        doc = json.load(fh)
+    if doc.get("version") != 1:
+        raise ValueError(f"{path}: unknown tuning table version {doc.get('version')!r}")
+    if device is None and torch.cuda.is_available():
+        device = torch.cuda.get_device_name()
+    if device is not None and doc.get("device") not in (None, device):
+        return 0
+    set_tuning(doc["entries"])
+    return len(doc["entries"])
+
+
+def solve_concurrent(pints, problems, eps=None, wr_max=200, want_fine=False):
+    """Solve several independent instances at once: each Pint runs
+    pint_parareal_solve from its own host thread on its own CUDA stream (the
+    stream it was created on), so the GPU overlaps the instances' kernels; an
+    instance's coarse sweep holds one 16-SM cluster, the others' work fills the
+    rest of the GPU.  Returns the per-instance results in order."""
+    import threading
+    out = [None] * len(pints)
+    errs = []
+
+    def run(i):
+        p, prob = pints[i], problems[i]
+        try:
+            with torch.cuda.stream(p.stream):
+                out[i] = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=prob.eps if eps is None else eps,
+                                          wr_max=wr_max, want_fine=want_fine)
+            p.stream.synchronize()
+        except Exception as e:  # surfaced after the join
+            errs.append((i, e))
+
+    ts = [threading.Thread(target=run, args=(i,)) for i in range(len(pints))]
+    for t in ts:
+        t.start()
+    for t in ts:
+        t.join()
+    if errs:
+        raise errs[0][1]
+    return out
 
 
 def from_problem(prob, device="cuda", precision=L.PINT_FP64, T=None):

@@ -3,10 +3,19 @@
 #include <cuda_runtime.h>
 #include <cstdint>
 #include <cstdio>
+#include <mutex>
 #include <string>
 #include <vector>
 
 #include "../../include/pint.h"
+
+// Several contexts may be driven from several host threads at once (one
+// instance per thread and stream); the process-wide lazy initialisations
+// (device attributes, kernel attributes, driver entry points) take this lock.
+inline std::mutex& lazy_init_mutex() {
+  static std::mutex m;
+  return m;
+}
 
 namespace pint {
 
@@ -111,6 +120,7 @@ struct Ctx {
   int N = 0, P = 0, precision = PINT_FP64;
   double T = 0, Dt = 0, dt = 0, alpha = 0;
   bool fine_seq = false;  // PINT_FINE_SEQUENTIAL
+  bool autotune = false;  // PINT_AUTOTUNE: measured contraction tiles
   bool have_time = false;
 
   // hot-path operators (FP64): [-G1 | G2] and [-CM^T | -dt CA^T]
@@ -199,6 +209,11 @@ struct GcArgs {
   double Dt;
 };
 int gc_cluster_size(int d1, int d2);
+// autotuner table of the tensor-core contractions (k_umma.cu)
+int umma_tuning_count();
+int umma_tuning_get(int* rows, float* us, int cap);
+int umma_tuning_set(const int* rows, const float* us, int count);  // -1, or the first invalid row
+void umma_tuning_clear();
 void g_sweep_cluster(Ctx* c, const GcArgs& a, int CL);
 
 }  // namespace pint

@@ -246,6 +246,7 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a, int nb) 
 template <int CL>
 bool gc_feasible(size_t bytes) {
   static int ok = -1;
+  std::lock_guard<std::mutex> lock(lazy_init_mutex());
   if (ok < 0) {
     ok = 0;
     if (cudaFuncSetAttribute(k_g_sweep_cl<CL>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=

@@ -28,6 +28,10 @@
 #include "common.cuh"
 
 #include <algorithm>
+#include <array>
+#include <map>
+#include <mutex>
+#include <vector>
 
 #include <cuda.h>
 #include <cudaTypedefs.h>
@@ -295,6 +299,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  std::lock_guard<std::mutex> lock(lazy_init_mutex());
   if (!fn) {
     void* p = nullptr;
     cudaDriverEntryPointQueryResult q{};
@@ -325,6 +330,7 @@ CUtensorMap make_map(const float* base, int rows, int Kp, int box_rows) {
 
 int umma_sms() {
   static int sms = 0;
+  std::lock_guard<std::mutex> lock(lazy_init_mutex());
   if (!sms) {
     int dev = 0;
     cudaGetDevice(&dev);
@@ -339,6 +345,12 @@ int umma_sms() {
 // set by the busiest SM, ceil(tiles / SMs) tiles of (tn / s) column-K work each,
 // plus the operand bytes each tile streams through L2 (1 / tn + 1 / 128 per
 // output).  nsplit = 1 when the consumer cannot sum K slices.
+static double umma_cost(int M, int ncols, int tn, int s, int sms) {
+  const long long tiles = (long long)((ncols + tn - 1) / tn) * ((M + TM - 1) / TM) * s;
+  const double rounds = (double)((tiles + sms - 1) / sms);
+  return rounds * (double)tn / s * (1.0 + 0.5 * (128.0 / tn + 1.0));
+}
+
 void umma_plan(int M, int Kp, int ncols, int maxs, int* tn_out, int* s_out) {
   const int sms = umma_sms();
   double best = 1e300;
@@ -347,9 +359,7 @@ void umma_plan(int M, int Kp, int ncols, int maxs, int* tn_out, int* s_out) {
   for (int tn = 128; tn <= TNMAX; tn += 32)
     for (int s = 1; s <= maxs; ++s) {
       if (Kp % (KB * s)) continue;
-      const long long tiles = (long long)((ncols + tn - 1) / tn) * ((M + TM - 1) / TM) * s;
-      const double rounds = (double)((tiles + sms - 1) / sms);
-      const double cost = rounds * (double)tn / s * (1.0 + 0.5 * (128.0 / tn + 1.0));
+      const double cost = umma_cost(M, ncols, tn, s, sms);
       if (cost < best * 0.999) {
         best = cost;
         *tn_out = tn;
@@ -365,9 +375,12 @@ void umma_plan(int M, int Kp, int ncols, int maxs, int* tn_out, int* s_out) {
 void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
                       const float* Blo, int ncols, int nsplit, int tn, float* out, int* err, const int* gate) {
   static bool attr = false;
+  {
+  std::lock_guard<std::mutex> lock(lazy_init_mutex());
   if (!attr) {
     PINT_CUDA(cudaFuncSetAttribute(k_wr_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
     attr = true;
+  }
   }
   PINT_REQUIRE(nsplit >= 1 && Kp % (KB * nsplit) == 0, PINT_ERR_BAD_ARG,
                "contraction K not divisible by the split");
@@ -381,6 +394,130 @@ void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp,
                                                       gate);
   PINT_LAUNCH_CHECK();
   c->launches++;
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner.  The cost model above ranks the (tile width, K split) pairs of a
+// contraction shape; the autotuner times the best-ranked few on the live
+// operands with CUDA events on the context's stream and keeps the fastest.
+// Choices live in one process-wide table keyed by (M, Kp, ncols, maxs), so a
+// shape is timed once per process (or never, when the table was loaded).
+// ---------------------------------------------------------------------------
+namespace {
+struct TuneVal {
+  int tn, s;
+  float us;
+};
+std::mutex& tune_mutex() {
+  static std::mutex m;
+  return m;
+}
+std::map<std::array<int, 4>, TuneVal>& tune_table() {
+  static std::map<std::array<int, 4>, TuneVal> t;
+  return t;
+}
+constexpr int TUNE_CANDIDATES = 6;
+constexpr int TUNE_REPS = 3;
+}  // namespace
+
+bool umma_valid_choice(int M, int Kp, int ncols, int maxs, int tn, int s) {
+  return M > 0 && Kp > 0 && ncols > 0 && maxs >= 1 && tn >= 128 && tn <= TNMAX && tn % 32 == 0 && s >= 1 &&
+         s <= maxs && Kp % (KB * s) == 0;
+}
+
+void umma_choose(Ctx* c, bool tune, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
+                 const float* Blo, int ncols, int maxs, float* out, int* err, int* tn_out, int* s_out) {
+  umma_plan(M, Kp, ncols, maxs, tn_out, s_out);
+  if (!tune || ncols <= 0 || M <= 0) return;
+  const std::array<int, 4> key{M, Kp, ncols, maxs};
+  {
+    std::lock_guard<std::mutex> lock(tune_mutex());
+    auto it = tune_table().find(key);
+    if (it != tune_table().end()) {
+      *tn_out = it->second.tn;
+      *s_out = it->second.s;
+      return;
+    }
+  }
+  // candidates ranked by the cost model (its own pick first)
+  const int sms = umma_sms();
+  std::vector<std::pair<double, std::pair<int, int>>> cand;
+  for (int tn = 128; tn <= TNMAX; tn += 32)
+    for (int s = 1; s <= maxs; ++s) {
+      if (!umma_valid_choice(M, Kp, ncols, maxs, tn, s)) continue;
+      const double cost = (tn == *tn_out && s == *s_out) ? -1.0 : umma_cost(M, ncols, tn, s, sms);
+      cand.push_back({cost, {tn, s}});
+    }
+  std::sort(cand.begin(), cand.end());
+  if ((int)cand.size() > TUNE_CANDIDATES) cand.resize(TUNE_CANDIDATES);
+  struct Ev {  // released on every exit, including a thrown failure
+    cudaEvent_t e = nullptr;
+    ~Ev() {
+      if (e) cudaEventDestroy(e);
+    }
+  } e0, e1;
+  PINT_CUDA(cudaEventCreate(&e0.e));
+  PINT_CUDA(cudaEventCreate(&e1.e));
+  float best = 3.4e38f;
+  int btn = *tn_out, bs = *s_out;
+  for (auto& cd : cand) {
+    const int tn = cd.second.first, s = cd.second.second;
+    mx_contract_umma(c, Ahi, Alo, M, Kp, Bhi, Blo, ncols, s, tn, out, err, nullptr);  // warm-up
+    PINT_CUDA(cudaEventRecord(e0.e, c->stream));
+    for (int r = 0; r < TUNE_REPS; ++r) mx_contract_umma(c, Ahi, Alo, M, Kp, Bhi, Blo, ncols, s, tn, out, err, nullptr);
+    PINT_CUDA(cudaEventRecord(e1.e, c->stream));
+    PINT_CUDA(cudaEventSynchronize(e1.e));
+    float ms = 0.f;
+    PINT_CUDA(cudaEventElapsedTime(&ms, e0.e, e1.e));
+    const float us = 1e3f * ms / TUNE_REPS;
+    if (us < best) {
+      best = us;
+      btn = tn;
+      bs = s;
+    }
+  }
+  *tn_out = btn;
+  *s_out = bs;
+  std::lock_guard<std::mutex> lock(tune_mutex());
+  tune_table()[key] = TuneVal{btn, bs, best};
+}
+
+int umma_tuning_count() {
+  std::lock_guard<std::mutex> lock(tune_mutex());
+  return (int)tune_table().size();
+}
+
+int umma_tuning_get(int* rows, float* us, int cap) {
+  std::lock_guard<std::mutex> lock(tune_mutex());
+  int n = 0;
+  for (auto& kv : tune_table()) {
+    if (n >= cap) break;
+    for (int j = 0; j < 4; ++j) rows[6 * n + j] = kv.first[j];
+    rows[6 * n + 4] = kv.second.tn;
+    rows[6 * n + 5] = kv.second.s;
+    if (us) us[n] = kv.second.us;
+    ++n;
+  }
+  return n;
+}
+
+// returns the index of the first invalid row, or -1 when all were merged
+int umma_tuning_set(const int* rows, const float* us, int count) {
+  for (int i = 0; i < count; ++i) {
+    const int* r = rows + 6 * i;
+    if (!umma_valid_choice(r[0], r[1], r[2], r[3], r[4], r[5])) return i;
+  }
+  std::lock_guard<std::mutex> lock(tune_mutex());
+  for (int i = 0; i < count; ++i) {
+    const int* r = rows + 6 * i;
+    tune_table()[{r[0], r[1], r[2], r[3]}] = TuneVal{r[4], r[5], us ? us[i] : 0.f};
+  }
+  return -1;
+}
+
+void umma_tuning_clear() {
+  std::lock_guard<std::mutex> lock(tune_mutex());
+  tune_table().clear();
 }
 
 }  // namespace pint

@@ -250,6 +250,7 @@ pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double 
     c->alpha = alpha;
     c->precision = precision;
     c->fine_seq = (flags & PINT_FINE_SEQUENTIAL) != 0;
+    c->autotune = (flags & PINT_AUTOTUNE) != 0;
     c->Dt = T / N;
     c->dt = c->Dt / P;
     timed_stage(c, 5, [&] { hot_prepare(c); });
@@ -282,7 +283,7 @@ static pint_status solve_common(Ctx* c, const double* u0_nodes, const double* f_
   pint_status s = guarded(c, [&](std::vector<void*>& tmp) {
     PINT_REQUIRE(c->have_time, PINT_ERR_STATE, "pint_assemble_reduced first");
     PINT_REQUIRE(u0_nodes && f_shape, PINT_ERR_BAD_ARG, "u0_nodes and f_shape are required");
-    PINT_REQUIRE(eps >= 0 && wr_tol >= 0, PINT_ERR_BAD_ARG, "eps and wr_tol must be >= 0");
+    PINT_REQUIRE(eps == eps && wr_tol == wr_tol, PINT_ERR_BAD_ARG, "eps and wr_tol must not be NaN");
     PINT_REQUIRE(k_max >= 1 && wr_max >= 1, PINT_ERR_BAD_ARG, "k_max and wr_max must be >= 1");
     const double* du0 = stage_in(c, u0_nodes, c->nn, tmp);
     const double* df = stage_in(c, f_shape, c->nn, tmp);
@@ -483,6 +484,35 @@ pint_status pint_apply_F(pint_ctx* ctx, const double* in, int count, const doubl
     apply_F_dev(c, di, count, df, da, wr_tol, wr_max, o.dev, wr_iters);
     finish_out(c, o);
   });
+}
+
+int pint_tuning_count(void) { return umma_tuning_count(); }
+
+pint_status pint_tuning_get(int* rows, float* us, int cap, int* count) {
+  if (!rows || !count || cap < 0) {
+    set_error("rows and count are required, cap >= 0");
+    return PINT_ERR_BAD_ARG;
+  }
+  *count = umma_tuning_get(rows, us, cap);
+  return PINT_OK;
+}
+
+pint_status pint_tuning_set(const int* rows, const float* us, int count) {
+  if (count < 0 || (count > 0 && !rows)) {
+    set_error("rows required, count >= 0");
+    return PINT_ERR_BAD_ARG;
+  }
+  const int bad = umma_tuning_set(rows, us, count);
+  if (bad >= 0) {
+    set_error("tuning row " + std::to_string(bad) + " is not a valid (M, Kp, ncols, maxs, tn, s)");
+    return PINT_ERR_BAD_ARG;
+  }
+  return PINT_OK;
+}
+
+pint_status pint_tuning_clear(void) {
+  umma_tuning_clear();
+  return PINT_OK;
 }
 
 pint_status pint_get_info(pint_ctx* ctx, pint_space_info* info) {

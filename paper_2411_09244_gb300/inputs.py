@@ -202,6 +202,28 @@ def config_c3(instance: int = 0) -> Problem:
                    f, u0, amp, {"contrast": 1e5, "amp16": a16})
 
 
+def config_c4(instance: int = 0, sizes=(64, 96, 128, 192, 256)) -> Problem:
+    """One instance of the many-instance workload: fine grid drawn uniformly
+    from `sizes`, coarse blocks of 8 fine cells, J in {2, 3, 4}, contrast
+    10^U(3, 6), channel and inclusion counts in {5..50}, N in {16, 32, 64},
+    P = 32, two oversampling layers; f = sum of 10 Gaussians, u0 = 0.
+    The jump tolerance is relative (eps = -1e-10: 1e-10 of the largest
+    G-sweep state): the stable final times of these instances span 1e-7 to
+    1e-2, and so do their solutions' magnitudes."""
+    rng = SplitMix64(SEED_BASE + 3 * 1000 + instance)
+    n_f = sizes[rng.randint(0, len(sizes) - 1)]
+    J = rng.randint(2, 4)
+    contrast = 10.0 ** rng.uniform(3.0, 6.0)
+    n_ch = rng.randint(5, 50)
+    n_in = rng.randint(5, 50)
+    N = (16, 32, 64)[rng.randint(0, 2)]
+    kappa = paint_kappa(rng, n_f, n_ch, contrast, 2, n_incl=n_in, incl_value=contrast)
+    f = gaussian_sum(rng, n_f, 10)
+    nn = (n_f + 1) ** 2
+    return Problem(f"c4_{instance}_{n_f}", n_f, n_f // 8, J, 2, N, 32, 0.1, -1e-10, None, kappa, f,
+                   np.zeros(nn), np.ones(N), {"contrast": contrast, "channels": n_ch, "inclusions": n_in})
+
+
 def config_c5(instance: int = 0) -> Problem:
     """1024x1024 fine, 32x32 coarse, J = 4, four layers; 200 channels and
     400 inclusions of value 1e6; f as in the 256x256 case; N = 256 x P = 32."""
@@ -253,4 +275,4 @@ def observation_nodes(n_f: int, count: int, seed: int) -> np.ndarray:
     return np.array(chosen, dtype=np.int64)
 
 
-CONFIGS = {"c1": config_c1, "c2": config_c2, "c3": config_c3, "c5": config_c5}
+CONFIGS = {"c1": config_c1, "c2": config_c2, "c3": config_c3, "c4": config_c4, "c5": config_c5}
