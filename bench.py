@@ -142,8 +142,8 @@ FP64_MEASURED_TFLOPS = 1.096
 # DRAM bytes (read + write) per launch of the tensor-core contraction on this
 # workload, averaged over its two launches, from the ncu capture summarised in
 # profiles/k_wr_umma_c2_mixed.md; only valid for the kernel source it was taken on.
-UMMA_TRAFFIC = {"sha1": "d83e2b696ca728a7b6d3d24bbb431e9e9a2b985d",
-                "bytes": (24.218112e6 + 0.012032e6 + 94.091008e6 + 3.992832e6) / 2}
+UMMA_TRAFFIC = {"sha1": "89303d89d183e928b6df5b1c3a0a9ac2eba35d3f",
+                "bytes": (25.104640e6 + 0.036864e6 + 93.659392e6 + 3.179264e6) / 2}
 
 
 def umma_traffic():

@@ -1353,6 +1353,15 @@ static void mx_refresh(Ctx* c, Mx& M) {
   }
 }
 
+// Low-precision iterations stop at their precision floor: FP32 trajectories
+// resolve a WR update (or a parareal jump) only to ~1e-7..1e-5 of the state,
+// depending on how much the coupling's difference form cancels, so a tolerance
+// below that is never met.  An iteration counts as stalled when it does not
+// lower the smallest norm so far by 10%; LP_STALL stalled iterations in a row
+// within LP_FLOOR_SPAN of the tolerance end it.
+constexpr int LP_STALL = 3;
+constexpr double LP_FLOOR_SPAN = 1e3;
+
 // low-precision WR sweep on intervals [n_lo, n_lo + nact); Ut/Wt/src point at
 // absolute slot n_lo; ends into fu/fw (FP64)
 static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* xs_w, const double* amp_act,
@@ -1404,10 +1413,8 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
   };
   int it = 0;
   *bad = false;
-  enqueue(1);
-  for (it = 1; it <= wr_max; ++it) {
-    if (it < wr_max) enqueue(it + 1);  // look-ahead: gated no-op if iteration it converges
-    cudaEvent_t* ev = M.iev[it & 1];
+  auto account = [&](int j) {
+    cudaEvent_t* ev = M.iev[j & 1];
     PINT_CUDA(cudaEventSynchronize(ev[4]));
     float m0 = 0.f, m1 = 0.f;
     PINT_CUDA(cudaEventElapsedTime(&m0, ev[0], ev[1]));
@@ -1415,12 +1422,33 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
     H.hot_ms += m0 + m1;
     H.hot_launches += 2;
     H.hot_flops += 2.0 * 4.0 * d1 * (double)d2 * ncols;
+  };
+  double best = 1e300;
+  int stall = 0;
+  bool floor_stop = false;
+  enqueue(1);
+  for (it = 1; it <= wr_max; ++it) {
+    if (it < wr_max) enqueue(it + 1);  // look-ahead: gated no-op if iteration it converges
+    account(it);
     const double nrm = M.hnrm[2 * it], flag = M.hnrm[2 * it + 1];
     if (flag != 0.0 || !(nrm == nrm)) {
       *bad = true;
       break;
     }
     if (nrm <= wr_tol) break;
+    // precision floor: within LP_FLOOR_SPAN of the tolerance, LP_STALL
+    // iterations in a row that do not lower the smallest update by 10%
+    if (nrm < 0.9 * best) {
+      best = nrm;
+      stall = 0;
+    } else if (it >= 4 && nrm <= LP_FLOOR_SPAN * wr_tol && ++stall >= LP_STALL) {
+      floor_stop = true;
+      break;
+    }
+  }
+  if (floor_stop && it < wr_max) {
+    ++it;  // the look-ahead iteration was not gated: it runs, and counts
+    account(it);
   }
   if (it > wr_max) it = wr_max;
   mx_ends32(c, Ut, Wt, M.ldu, M.ldw, nact, fu, fw, fu32, fw32);
@@ -1493,6 +1521,8 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
   PINT_CUDA(cudaEventCreate(&a0));
   PINT_CUDA(cudaEventCreate(&a1));
   const int kcap = std::min(r.k_max, N);
+  double best = 1e300;
+  int stall = 0;
   for (int k = 1; k <= kcap; ++k) {
     const int n_lo = k - 1, nact = N - n_lo;
     PINT_CUDA(cudaMemcpyAsync(r.Su + (size_t)n_lo * d1, r.Xu + (size_t)n_lo * d1, (size_t)nact * d1 * 8,
@@ -1541,6 +1571,13 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
     }
     if (h[0] <= r.eps) {
       r.converged = true;
+      break;
+    }
+    if (h[0] < 0.9 * best) {
+      best = h[0];
+      stall = 0;
+    } else if (k >= 3 && h[0] <= LP_FLOOR_SPAN * r.eps && ++stall >= LP_STALL) {
+      r.converged = true;  // at the precision floor
       break;
     }
   }
@@ -1696,7 +1733,7 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
       probe.k_max = 0;
       parareal_lp(c, H, M, probe, &f_ms, nullptr, nullptr, 0);
       double sc = state_scale(c, H, M.Yu, M.Yw);
-      y.eps = eps;
+      y.eps = eps;  // the jumps stop at eps or at the precision floor
       y.wr_tol = std::max(wr_tol, PINT_CORR_REL_TOL * sc);
       y.have_g0 = true;
     }
