@@ -277,6 +277,41 @@ pint_status pint_get_info(pint_ctx* ctx, pint_space_info* info);
 pint_status pint_destroy(pint_ctx* ctx);
 
 /*
+ * pint_batch_solve -- many independent instances (uneven grids, spaces and
+ * time grids): pint_parareal_solve of every item, each on its own context
+ * and that context's stream, from `workers` host threads inside the
+ * library.  Items are taken longest first (estimated work: fine unknowns x
+ * N x P), so that the uneven instances finish together; the kernels of
+ * different instances overlap on the GPU.
+ *   items    host array of count items; each names a distinct context
+ *            (a context is driven by one thread at a time) and the
+ *            arguments of pint_parareal_solve; status receives the item's
+ *            own result
+ *   count    >= 0
+ *   workers  host threads (<= 0: min(count, 16))
+ * Returns OK when every item is OK, else the first failing item's status
+ * (NOT_CONVERGED only when no item failed otherwise), with "item i: ..." in
+ * pint_last_error.  Errors of the call itself: BAD_ARG (NULL items with
+ * count > 0, NULL or repeated context).
+ */
+typedef struct {
+  pint_ctx* ctx;
+  const double* u0_nodes;
+  const double* f_shape;
+  const double* amp;
+  double eps;
+  int k_max;
+  double wr_tol;
+  int wr_max;
+  double* u_out;
+  double* coarse_out;
+  pint_stats* stats;
+  pint_status status;   /* out */
+} pint_batch_item;
+
+pint_status pint_batch_solve(pint_batch_item* items, int count, int workers);
+
+/*
  * Autotuner table (process-wide, shared by all contexts and host threads).
  * One row per contraction shape of the WR fine propagator's two tensor-core
  * contractions, as 6 ints: M (rows: d1 or d2), Kp (padded K), ncols (active

@@ -51,6 +51,13 @@ class Stats(C.Structure):
                 "hot_launches": self.hot_launches, "hot_ms": self.hot_ms, "hot_flops": self.hot_flops}
 
 
+class BatchItem(C.Structure):
+    _fields_ = [("ctx", C.c_void_p), ("u0_nodes", C.c_void_p), ("f_shape", C.c_void_p), ("amp", C.c_void_p),
+                ("eps", C.c_double), ("k_max", C.c_int), ("wr_tol", C.c_double), ("wr_max", C.c_int),
+                ("u_out", C.c_void_p), ("coarse_out", C.c_void_p), ("stats", C.POINTER(Stats)),
+                ("status", C.c_int)]
+
+
 class PintError(RuntimeError):
     def __init__(self, status: int, msg: str):
         super().__init__(f"{STATUS.get(status, status)}: {msg}")
@@ -78,6 +85,7 @@ SYMBOLS = {
                      C.c_void_p, C.POINTER(C.c_int)],
     "pint_get_info": [C.c_void_p, C.POINTER(SpaceInfo)],
     "pint_destroy": [C.c_void_p],
+    "pint_batch_solve": [C.c_void_p, C.c_int, C.c_int],
     "pint_tuning_count": [],
     "pint_tuning_get": [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)],
     "pint_tuning_set": [C.c_void_p, C.c_void_p, C.c_int],

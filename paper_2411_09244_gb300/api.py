@@ -255,34 +255,66 @@ def load_tuning(path: str, device: str | None = None) -> int:
     return len(doc["entries"])
 
 
-def solve_concurrent(pints, problems, eps=None, wr_max=200, want_fine=False):
-    """Solve several independent instances at once: each Pint runs
-    pint_parareal_solve from its own host thread on its own CUDA stream (the
-    stream it was created on), so the GPU overlaps the instances' kernels; an
-    instance's coarse sweep holds one 16-SM cluster, the others' work fills the
-    rest of the GPU.  Returns the per-instance results in order."""
-    import threading
-    out = [None] * len(pints)
-    errs = []
+class BatchPlan:
+    """Prepared arguments of pint_batch_solve for a list of Pints and their
+    problems: inputs and output buffers are allocated once (on the device,
+    or pinned on the host with host=True, where the library stages the
+    copies), so repeated runs allocate nothing."""
 
-    def run(i):
-        p, prob = pints[i], problems[i]
-        try:
-            with torch.cuda.stream(p.stream):
-                out[i] = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=prob.eps if eps is None else eps,
-                                          wr_max=wr_max, want_fine=want_fine)
-            p.stream.synchronize()
-        except Exception as e:  # surfaced after the join
-            errs.append((i, e))
+    def __init__(self, pints, problems, eps=None, wr_max=200, want_fine=False, host=False):
+        self.n = len(pints)
+        self.items = (L.BatchItem * max(self.n, 1))()
+        self.keep, self.outs = [], []
 
-    ts = [threading.Thread(target=run, args=(i,)) for i in range(len(pints))]
-    for t in ts:
-        t.start()
-    for t in ts:
-        t.join()
-    if errs:
-        raise errs[0][1]
-    return out
+        def buf(shape, p):
+            if host:
+                return torch.empty(shape, dtype=torch.float64).pin_memory()
+            return torch.empty(shape, dtype=torch.float64, device=p.device)
+
+        for i, (p, prob) in enumerate(zip(pints, problems)):
+            if host:
+                u0, f, a = (torch.as_tensor(np.ascontiguousarray(x, dtype=np.float64)).pin_memory()
+                            for x in (prob.u0, prob.f, prob.amp))
+            else:
+                u0, f, a = _f64(prob.u0, p.device), _f64(prob.f, p.device), _f64(prob.amp, p.device)
+            e = prob.eps if eps is None else eps
+            d = p.info["d1"] + p.info["d2"]
+            coarse = buf((p.N + 1, d), p)
+            fine = buf((p.N, p.nn), p) if want_fine else None
+            st = L.Stats()
+            self.keep += [u0, f, a]
+            it = self.items[i]
+            it.ctx = p.h.value
+            it.u0_nodes, it.f_shape, it.amp = L.ptr(u0), L.ptr(f), L.ptr(a)
+            it.eps, it.k_max, it.wr_tol, it.wr_max = e, p.N, 1e-3 * e, wr_max
+            it.u_out, it.coarse_out = L.ptr(fine), L.ptr(coarse)
+            it.stats = C.pointer(st)
+            self.outs.append((coarse, fine, st))
+        self.h2d_bytes = sum(x.numel() * 8 for x in self.keep) if host else 0
+        self.d2h_bytes = sum(c.numel() * 8 + (f.numel() * 8 if f is not None else 0)
+                             for c, f, _ in self.outs) if host else 0
+
+    def run(self, workers=0):
+        """pint_batch_solve over the plan; returns [(coarse, fine, stats)]."""
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()     # inputs staged on the caller's stream are complete
+        status = L.lib().pint_batch_solve(C.cast(self.items, C.c_void_p), self.n, workers)
+        L.check(status, allow=(-5,))
+        res = []
+        for i, (coarse, fine, st) in enumerate(self.outs):
+            dct = st.as_dict()
+            dct["status"] = L.STATUS[self.items[i].status]
+            res.append((coarse, fine, dct))
+        return res
+
+
+def solve_batch(pints, problems, eps=None, wr_max=200, want_fine=False, workers=0, host=False):
+    """Solve several independent instances at once through pint_batch_solve:
+    the library drives each Pint's context on its own CUDA stream (the
+    stream the Pint was created on) from its own worker threads, longest
+    instance first, so the GPU overlaps the instances' kernels.  Returns
+    [(coarse, fine or None, stats)] in the order of `pints`."""
+    return BatchPlan(pints, problems, eps, wr_max, want_fine, host).run(workers)
 
 
 def from_problem(prob, device="cuda", precision=L.PINT_FP64, T=None):

@@ -7,6 +7,9 @@
 #include <cmath>
 #include <chrono>
 #include <cstring>
+#include <atomic>
+#include <set>
+#include <thread>
 
 namespace pint {
 
@@ -311,6 +314,61 @@ pint_status pint_parareal_solve(pint_ctx* ctx, const double* u0_nodes, const dou
                                 double* u_out, double* coarse_out, pint_stats* stats) {
   return solve_common((Ctx*)ctx, u0_nodes, f_shape, amp, eps, k_max, wr_tol, wr_max, u_out, coarse_out,
                       stats, false);
+}
+
+pint_status pint_batch_solve(pint_batch_item* items, int count, int workers) {
+  if (count < 0 || (count > 0 && !items)) {
+    set_error("items required, count >= 0");
+    return PINT_ERR_BAD_ARG;
+  }
+  std::set<pint_ctx*> seen;
+  for (int i = 0; i < count; ++i) {
+    if (!items[i].ctx || !seen.insert(items[i].ctx).second) {
+      set_error("item " + std::to_string(i) + ": NULL or repeated context");
+      return PINT_ERR_BAD_ARG;
+    }
+  }
+  if (count == 0) return PINT_OK;
+  // longest first: fine unknowns x N x P (0 for a context without a time grid)
+  std::vector<int> order(count);
+  std::vector<double> work(count);
+  for (int i = 0; i < count; ++i) {
+    const Ctx* c = (const Ctx*)items[i].ctx;
+    order[i] = i;
+    work[i] = c->have_time ? (double)c->nn * c->N * c->P : 0.0;
+  }
+  std::stable_sort(order.begin(), order.end(), [&](int a, int b) { return work[a] > work[b]; });
+  if (workers <= 0) workers = std::min(count, 16);
+  workers = std::min(workers, count);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::vector<std::string> msg(count);
+  std::atomic<int> next{0};
+  auto run = [&]() {
+    cudaSetDevice(dev);
+    for (int j = next.fetch_add(1); j < count; j = next.fetch_add(1)) {
+      pint_batch_item& it = items[order[j]];
+      it.status = pint_parareal_solve(it.ctx, it.u0_nodes, it.f_shape, it.amp, it.eps, it.k_max, it.wr_tol,
+                                      it.wr_max, it.u_out, it.coarse_out, it.stats);
+      if (it.status != PINT_OK) msg[order[j]] = pint_last_error();
+    }
+  };
+  std::vector<std::thread> pool;
+  for (int w = 1; w < workers; ++w) pool.emplace_back(run);
+  run();  // the calling thread is one of the workers
+  for (auto& t : pool) t.join();
+  pint_status first = PINT_OK;
+  int where = -1;
+  for (int i = 0; i < count; ++i) {
+    const pint_status s = items[i].status;
+    if (s == PINT_OK) continue;
+    if (first == PINT_OK || (first == PINT_ERR_NOT_CONVERGED && s != PINT_ERR_NOT_CONVERGED)) {
+      first = s;
+      where = i;
+    }
+  }
+  if (where >= 0) set_error("item " + std::to_string(where) + ": " + msg[where]);
+  return first;
 }
 
 pint_status pint_sequential_solve(pint_ctx* ctx, const double* u0_nodes, const double* f_shape,

@@ -46,8 +46,10 @@ def test_struct_layouts_match_header(libpint):
 #include <stddef.h>
 #include "pint.h"
 int main(void) {
-  printf("%zu %zu %zu %zu %zu\n", sizeof(pint_space_info), sizeof(pint_stats),
-         offsetof(pint_stats, jumps), offsetof(pint_stats, solve_ms), offsetof(pint_stats, launches));
+  printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu\n", sizeof(pint_space_info), sizeof(pint_stats),
+         offsetof(pint_stats, jumps), offsetof(pint_stats, solve_ms), offsetof(pint_stats, launches),
+         sizeof(pint_batch_item), offsetof(pint_batch_item, wr_tol), offsetof(pint_batch_item, stats),
+         offsetof(pint_batch_item, status));
   return 0;
 }
 '''
@@ -58,7 +60,8 @@ int main(void) {
         subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), src, "-o", exe], check=True)
         out = subprocess.run([exe], capture_output=True, text=True, check=True).stdout.split()
     got = [C.sizeof(_lib.SpaceInfo), C.sizeof(_lib.Stats), _lib.Stats.jumps.offset,
-           _lib.Stats.solve_ms.offset, _lib.Stats.launches.offset]
+           _lib.Stats.solve_ms.offset, _lib.Stats.launches.offset, C.sizeof(_lib.BatchItem),
+           _lib.BatchItem.wr_tol.offset, _lib.BatchItem.stats.offset, _lib.BatchItem.status.offset]
     assert [int(x) for x in out] == got
 
 

@@ -1,7 +1,8 @@
-"""The many-instance workload: its seeded recipe (CPU) and the concurrent
-solve of several independent instances, each on its own context, CUDA stream
-and host thread (GPU): concurrent results equal the one-at-a-time results and
-the oracle's."""
+"""The many-instance workload: its seeded recipe (CPU), pint_batch_solve's
+argument checks (CPU, no device work), and the batch solve of several
+independent instances, each on its own context and CUDA stream, driven by the
+library's worker threads (GPU): batch results equal the one-at-a-time results
+and the oracle's."""
 import numpy as np
 import pytest
 
@@ -37,8 +38,22 @@ def test_recipe_honours_sizes():
         assert config_c4(i, sizes=SIZES).n_f in SIZES
 
 
+def test_batch_arguments_are_checked_without_gpu():
+    import ctypes as C
+    from paper_2411_09244_gb300 import _lib
+    L = _lib.lib()
+    assert L.pint_batch_solve(None, 0, 0) == 0
+    assert L.pint_batch_solve(None, 2, 0) == -1
+    items = (_lib.BatchItem * 2)()
+    assert L.pint_batch_solve(C.cast(items, C.c_void_p), 2, 0) == -1          # NULL contexts
+    assert b"item 0" in L.pint_last_error()
+    items[0].ctx = items[1].ctx = 0x1000                                       # repeated context
+    assert L.pint_batch_solve(C.cast(items, C.c_void_p), 2, 0) == -1
+    assert b"item 1" in L.pint_last_error()
+
+
 @pytest.mark.gpu
-def test_concurrent_equals_sequential_and_oracle():
+def test_batch_equals_sequential_and_oracle():
     torch = pytest.importorskip("torch")
     from paper_2411_09244_gb300 import api
     from paper_2411_09244_gb300._lib import PINT_MIXED, PINT_FP64
@@ -59,7 +74,7 @@ def test_concurrent_equals_sequential_and_oracle():
             with torch.cuda.stream(p.stream):
                 seq.append(p.parareal_solve(prob.u0, prob.f, prob.amp, eps=prob.eps))
             p.stream.synchronize()
-        con = api.solve_concurrent(pints, probs, want_fine=True)
+        con = api.solve_batch(pints, probs, want_fine=True)
         # the reductions use atomics, so the two runs agree to rounding, not bitwise
         for (cs, fs, ss), (cc, fc, sc) in zip(seq, con):
             assert ss["K1"] == sc["K1"]
@@ -85,7 +100,7 @@ def test_concurrent_equals_sequential_and_oracle():
             with torch.cuda.stream(p.stream):
                 p.assemble_reduced(p.T, prob.N, prob.P, prob.alpha, PINT_MIXED)
         torch.cuda.synchronize()
-        mix = api.solve_concurrent(pints, probs, want_fine=True)
+        mix = api.solve_batch(pints, probs, want_fine=True)
         for (_, fs, _), (_, fm, _) in zip(seq, mix):
             assert float(torch.linalg.norm(fm - fs) / torch.linalg.norm(fs)) < 1e-6
         for p, prob in zip(pints, probs):
