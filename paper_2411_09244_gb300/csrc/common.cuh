@@ -199,6 +199,20 @@ void hot_states(Ctx* c, double** Xu, double** Xw);
 void unit_response(Ctx* c, double* su, double* sw);
 
 // FP32 coarse sweep on one thread-block cluster (k_gcluster.cu)
+// WR stopping test fused into the last kernel of a WR iteration (k_mixed.cu):
+// acc holds cnt squared update norms, u parts then w parts, P per interval
+// (cleared again by the test); out gets (norm, non-finite flag); gate is set
+// when norm <= tol; counter holds 3 + nact words (global max bits, flag,
+// intervals done, then one block counter per interval), zero between launches.
+struct WrStop {
+  float* acc;
+  int cnt;
+  double tol;
+  int* gate;
+  double* out;
+  unsigned* counter;
+};
+
 struct GcArgs {
   const float* CA;  // [d1][d2] FP32 coupling
   const double *lam1, *lam2, *b1, *b2, *amp;

@@ -275,38 +275,67 @@ __global__ void k_prolong(const GWin* __restrict__ gw, int n_f, int nc, int bs, 
 
 // k_prolong in double-float arithmetic: thread per node, VB states per thread
 // (the coefficient pairs of the VB states are contiguous), bases as FP32 pairs
+// out[v][node] = sum over the windows containing node and their bases q of
+// a[raw(q)][v] psi_q(node), in double-float arithmetic (bases and coefficients
+// as FP32 pairs).  One CTA per (coarse block, group of VB times).  The block's nodes (the last node row / column joins the last
+// block) share the candidate windows, whose descriptors are staged in shared
+// memory once; every thread walks the same windows and bases (uniform control
+// flow), its node's basis values are read once per time group, and the
+// coefficient pairs of a basis are warp-uniform loads.
+constexpr int PB_MAXW = 19 * 19;  // candidate windows of a block (ell <= 8)
 template <int VB>
-__global__ void k_prolong_df(const GWin* __restrict__ gw, int n_f, int nc, int bs, int ell,
-                             const float* __restrict__ psih, const float* __restrict__ psil,
-                             const float* __restrict__ ah, const float* __restrict__ al, int count,
-                             double* __restrict__ out) {
+__global__ void __launch_bounds__(256) k_prolong_df_blk(const GWin* __restrict__ gw, int n_f, int nc, int bs,
+                                                        int ell, const float* __restrict__ psih,
+                                                        const float* __restrict__ psil,
+                                                        const float2* __restrict__ a2, int count,
+                                                        double* __restrict__ out) {
+  __shared__ GWin sw[PB_MAXW];
   const int nn1 = n_f + 1, nn = nn1 * nn1;
-  const int node = blockIdx.x * blockDim.x + threadIdx.x;
+  const int cx = blockIdx.x % nc, cy = blockIdx.x / nc;
   const int v0 = blockIdx.y * VB;
-  if (node >= nn) return;
-  const int gx = node % nn1, gy = node / nn1;
-  const int cx = min(gx / bs, nc - 1), cy = min(gy / bs, nc - 1);
-  float sh[VB], sl[VB];
+  const int bx0 = max(0, cx - ell - 1), bx1 = min(nc - 1, cx + ell + 1);
+  const int by0 = max(0, cy - ell - 1), by1 = min(nc - 1, cy + ell + 1);
+  const int nwx = bx1 - bx0 + 1, nwin = nwx * (by1 - by0 + 1);
+  for (int e = threadIdx.x; e < nwin; e += blockDim.x) sw[e] = gw[(by0 + e / nwx) * nc + bx0 + e % nwx];
+  __syncthreads();
+  const int gx0 = cx * bs, gy0 = cy * bs;
+  const int tw = bs + (cx == nc - 1 ? 1 : 0), th = bs + (cy == nc - 1 ? 1 : 0);
+  for (int t = threadIdx.x; t < tw * th; t += blockDim.x) {
+    const int gx = gx0 + t % tw, gy = gy0 + t / tw;
+    float sh[VB], sl[VB];
 #pragma unroll
-  for (int v = 0; v < VB; ++v) sh[v] = sl[v] = 0.f;
-  for (int by = max(0, cy - ell - 1); by <= min(nc - 1, cy + ell + 1); ++by)
-    for (int bx = max(0, cx - ell - 1); bx <= min(nc - 1, cx + ell + 1); ++bx) {
-      const GWin W = gw[by * nc + bx];
+    for (int v = 0; v < VB; ++v) sh[v] = sl[v] = 0.f;
+    for (int wi = 0; wi < nwin; ++wi) {
+      const GWin& W = sw[wi];
       const int lx = gx - W.X0, ly = gy - W.Y0;
       if (lx < 0 || lx >= W.wx || ly < 0 || ly >= W.wy) continue;
-      const int l = ly * W.wx + lx;
+      const size_t pi0 = W.psi_off + (size_t)ly * W.wx + lx;
+      const float2* ac = a2 + (size_t)W.raw0 * count + v0;
       for (int q = 0; q < W.kt; ++q) {
-        const size_t pi = W.psi_off + (size_t)q * W.nw + l;
+        const size_t pi = pi0 + (size_t)q * W.nw;
         const float ph = psih[pi], pl = psil[pi];
-        const size_t ai = (size_t)(W.raw0 + q) * count + v0;
 #pragma unroll
         for (int v = 0; v < VB; ++v)
-          if (v0 + v < count) pintd::df_fma(ah[ai + v], al[ai + v], ph, pl, sh[v], sl[v]);
+          if (v0 + v < count) {
+            const float2 c = ac[(size_t)q * count + v];
+            pintd::df_fma(c.x, c.y, ph, pl, sh[v], sl[v]);
+          }
       }
     }
+    const int node = gy * nn1 + gx;
 #pragma unroll
-  for (int v = 0; v < VB; ++v)
-    if (v0 + v < count) out[(size_t)(v0 + v) * nn + node] = (double)sh[v] + (double)sl[v];
+    for (int v = 0; v < VB; ++v)
+      if (v0 + v < count) out[(size_t)(v0 + v) * nn + node] = (double)sh[v] + (double)sl[v];
+  }
+}
+
+// x -> interleaved pairs (fl32(x), fl32(x - fl32(x)))
+__global__ void k_split_pairs2(const double* __restrict__ x, long long n, float2* __restrict__ y) {
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const double v = x[e];
+    const float hv = (float)v;
+    y[e] = make_float2(hv, (float)(v - (double)hv));
+  }
 }
 
 __global__ void k_split_pairs(const double* __restrict__ x, long long n, float* __restrict__ h,
@@ -498,13 +527,17 @@ void prolong_coeffs_df(Ctx* c, const double* u, const double* w, int count, doub
   k_from_reduced<<<count, 256, 0, c->stream>>>(u, w, count, c->n_raw, sd.kind, c->has_bar ? 1.0 / c->L : 0.0,
                                                c->coef, sd.h1, c->d1, sd.h2m, (int)c->h2m.size(), c->has_bar, a);
   PINT_LAUNCH_CHECK();
-  k_split_pairs<<<(unsigned)std::min<size_t>((na + 255) / 256, 4096), 256, 0, c->stream>>>(a, (long long)na, ap,
-                                                                                        ap + na);
+  k_split_pairs2<<<(unsigned)std::min<size_t>((na + 255) / 256, 4096), 256, 0, c->stream>>>(
+      a, (long long)na, reinterpret_cast<float2*>(ap));
   PINT_LAUNCH_CHECK();
-  constexpr int VB = 16;
-  const dim3 grid((unsigned)((c->nn + 127) / 128), (unsigned)((count + VB - 1) / VB));
-  k_prolong_df<VB><<<grid, 128, 0, c->stream>>>((const GWin*)c->d_windesc, c->n_f, c->nc, c->bs, c->ell, psih, psil,
-                                                ap, ap + na, count, out_nodes);
+  constexpr int VB = 17;  // 65 coarse times of a 64-interval solve in four groups
+  const int per = (c->bs + 1) * (c->bs + 1);
+  const int threads = std::min(256, (per + 31) / 32 * 32);
+  PINT_REQUIRE((2 * c->ell + 3) * (2 * c->ell + 3) <= PB_MAXW, PINT_ERR_BAD_ARG, "oversampling too wide");
+  const dim3 grid((unsigned)(c->nc * c->nc), (unsigned)((count + VB - 1) / VB));
+  k_prolong_df_blk<VB><<<grid, threads, 0, c->stream>>>((const GWin*)c->d_windesc, c->n_f, c->nc, c->bs, c->ell,
+                                                        psih, psil, reinterpret_cast<const float2*>(ap), count,
+                                                        out_nodes);
   PINT_LAUNCH_CHECK();
   c->launches += 3;
   dfree(c, a);

@@ -296,30 +296,6 @@ __global__ void k_wr_norm(const T* __restrict__ acc, int cnt, double* __restrict
   }
 }
 
-// WR stopping test of the low-precision sweep without a host round trip:
-// unless *gate is set, out = (sqrt(max acc), non-finite flag) and *gate is
-// set once the update is below tol (or non-finite), which turns the remaining
-// launches of later iterations into no-ops
-__global__ void k_wr_norm_gate(const float* __restrict__ acc, int cnt, double tol, int* __restrict__ gate,
-                               double* __restrict__ out) {
-  if (*gate) return;
-  __shared__ double sh[64];
-  double m = 0.0;
-  bool bad = false;
-  for (int e = threadIdx.x; e < cnt; e += blockDim.x) {
-    const double v = (double)acc[e];
-    if (!(v == v) || v > 1e300) bad = true;
-    m = fmax(m, v);
-  }
-  m = pintd::block_max(m, sh);
-  const double b = pintd::block_max(bad ? 1.0 : 0.0, sh);
-  if (threadIdx.x == 0) {
-    out[0] = sqrt(m);
-    out[1] = b;
-    if (b != 0.0 || sqrt(m) <= tol) *gate = 1;
-  }
-}
-
 // initialise the WR trajectories of intervals [n_lo, n_lo+nact) from their starts
 __global__ void k_wr_init(const double* __restrict__ Xu, const double* __restrict__ Xw, int d1, int d2,
                           int P, int nact, double* __restrict__ Ut, double* __restrict__ Wt) {
@@ -1128,7 +1104,7 @@ void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const
                      const float* bpow, float* accU, float* B1h, float* B1l, const int* gate);
 void mx_w_sweep32(Ctx* c, const float* S, int nsl, size_t slice, int nact, float* Wt, int ldw, const float* lam2,
                   const float* src, const float* b2, const double* amp, float* accW, float* B0h, float* B0l,
-                  const int* gate);
+                  const WrStop& ws);
 void mx_init32(Ctx* c, const double* Xu, const double* Xw, int nact, float* Ut, float* Wt, int ldu, int ldw,
                float* B0h, float* B0l);
 void mx_ends32(Ctx* c, const float* Ut, const float* Wt, int ldu, int ldw, int nact, double* Fu, double* Fw,
@@ -1177,6 +1153,7 @@ struct Mx {
   double *Zu = nullptr, *Zw = nullptr, *R64 = nullptr, *S64 = nullptr, *Cu = nullptr, *Cw = nullptr;
   double *Yu = nullptr, *Yw = nullptr, *zero = nullptr;
   int* gate = nullptr;      // device: WR sweep converged (later launches are no-ops)
+  unsigned* wcount = nullptr;  // device: counters and max of the fused WR stopping test
   double* nrm = nullptr;   // device: (norm, bad) per WR iteration
   double* hnrm = nullptr;  // pinned host copy of nrm
   cudaEvent_t iev[2][5] = {};  // per in-flight iteration: contraction brackets + norm ready
@@ -1256,6 +1233,8 @@ static Mx& mx_prepare(Ctx* c) {
   }
   M.err = (int*)Fa(4);
   M.gate = (int*)Fa(4);
+  M.wcount = (unsigned*)Fa(c->N + 4);  // global max, flag, count; one counter per interval
+  PINT_CUDA(cudaMemsetAsync(M.wcount, 0, (size_t)(c->N + 4) * 4, c->stream));
   M.nrm = Da(2 * PINT_MAX_ITERS + 2);
   if (!M.hnrm) PINT_CUDA(cudaMallocHost(&M.hnrm, (2 * PINT_MAX_ITERS + 2) * sizeof(double)));
   for (auto& row : M.iev)
@@ -1386,12 +1365,14 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
                 &nsl);
   }
   PINT_CUDA(cudaMemsetAsync(M.gate, 0, 4, c->stream));
+  // squared update norms of the first iteration start at zero; the stopping
+  // test at the end of each iteration clears them for the next
+  PINT_CUDA(cudaMemsetAsync(acc32, 0, (size_t)2 * nact * P * 4, c->stream));
   // One WR iteration; every launch is a no-op once the stopping test of an
   // earlier iteration has set the gate, so the host can queue iteration
   // it + 1 before it reads the norm of iteration it (no idle GPU between them).
   auto enqueue = [&](int it) {
     cudaEvent_t* ev = M.iev[it & 1];
-    PINT_CUDA(cudaMemsetAsync(acc32, 0, (size_t)2 * nact * P * 4, c->stream));
     PINT_CUDA(cudaEventRecord(ev[0], c->stream));
     if (tensor) mx_contract_umma(c, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, tn0, M.R, M.err, M.gate);
     else mx_contract32(c, 0, M.AR32, d1, 2 * ldw, Ut, Wt, ldu, ldw, P, ncols, M.R, M.gate);
@@ -1404,10 +1385,8 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
     else mx_contract32(c, 1, M.AS32, d2, 2 * ldu, Ut, Wt, ldu, ldw, P, ncols, M.S, M.gate);
     PINT_CUDA(cudaEventRecord(ev[3], c->stream));
     mx_w_sweep32(c, M.S, tensor ? nsl : 1, (size_t)ncols * d2, nact, Wt, ldw, M.lam2f, srcW, M.b2f, amp_act,
-                 acc32 + (size_t)nact * P, M.B0h, M.B0l, M.gate);
-    k_wr_norm_gate<<<1, 1024, 0, c->stream>>>(acc32, 2 * nact * P, wr_tol, M.gate, M.nrm + 2 * it);
-    PINT_LAUNCH_CHECK();
-    c->launches++;
+                 acc32 + (size_t)nact * P, M.B0h, M.B0l,
+                 WrStop{acc32, 2 * nact * P, wr_tol, M.gate, M.nrm + 2 * it, M.wcount});
     PINT_CUDA(cudaMemcpyAsync(M.hnrm + 2 * it, M.nrm + 2 * it, 16, cudaMemcpyDeviceToHost, c->stream));
     PINT_CUDA(cudaEventRecord(ev[4], c->stream));
   };

@@ -35,7 +35,7 @@ __device__ __forceinline__ void put_split(float* __restrict__ hi, float* __restr
 // max(P / 32, 1) entries (P a power of two), so one atomic instruction per
 // slice entry covers the warp.
 template <int P>
-__device__ __forceinline__ void warp_sum_scatter(float* v, float* __restrict__ acc) {
+__device__ __forceinline__ void warp_sum_scatter(float* v, float* __restrict__ acc, int stride = 1) {
   const int lane = threadIdx.x & 31;
   int off = 0;
   int mask = 16;
@@ -57,7 +57,7 @@ __device__ __forceinline__ void warp_sum_scatter(float* v, float* __restrict__ a
   const int low = (P >= 32) ? 0 : (lane & (32 / P - 1));
   if (low == 0) {
 #pragma unroll
-    for (int k = 0; k < KEEP; ++k) atomicAdd(&acc[off + k], v[k]);
+    for (int k = 0; k < KEEP; ++k) atomicAdd(&acc[(off + k) * stride], v[k]);
   }
 }
 
@@ -338,13 +338,78 @@ __global__ void __launch_bounds__(128) k_time_solve32_t(const float* __restrict_
   warp_sum_scatter<P>(im, accU + (size_t)nloc * P);
 }
 
+// WR stopping test fused into the W recurrence, the last kernel of a WR
+// iteration, in two levels so that no single block walks all entries: the
+// blocks of interval n (blockIdx.y) count themselves done on the interval's
+// counter; the last of them (all atomics of the interval then visible) takes
+// the max of the interval's 2 P squared norms (u and w parts), clears them for
+// the next iteration, folds the max into a global max (non-negative floats
+// order like their bit patterns) and counts the interval done; the last
+// interval writes sqrt(max) and a non-finite flag to out, sets the gate when
+// the update is below tol (or non-finite) and resets the global words.  No
+// block waits on another.
+__device__ void wr_stop_last_block(const WrStop& ws, int P) {
+  __shared__ int s_last;
+  const int nloc = blockIdx.y, nint = gridDim.y;
+  unsigned* cnt_n = ws.counter + 3 + nloc;  // per-interval counters
+  unsigned* gmax = ws.counter;              // [0] max bits, [1] non-finite, [2] intervals done
+  __threadfence();                          // this block's atomics before its count
+  __syncthreads();
+  if (threadIdx.x == 0) s_last = atomicAdd(cnt_n, 1u) == gridDim.x - 1;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  float m = 0.f;
+  int bad = 0;
+  const int half = ws.cnt / 2;  // u part [0, half), w part [half, cnt); interval n owns P of each
+  for (int e = threadIdx.x; e < 2 * P; e += blockDim.x) {
+    const int idx = (e < P) ? nloc * P + e : half + nloc * P + (e - P);
+    const float v = __ldcg(ws.acc + idx);
+    if (!(v <= 3.0e38f)) bad = 1;  // NaN or inf
+    m = fmaxf(m, v);
+    ws.acc[idx] = 0.f;
+  }
+  for (int o = 16; o >= 1; o >>= 1) {
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  __shared__ float s_m[32];
+  __shared__ int s_b[32];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = (blockDim.x + 31) >> 5;
+  if (lane == 0) {
+    s_m[warp] = m;
+    s_b[warp] = bad;
+  }
+  __syncthreads();
+  if (threadIdx.x != 0) return;
+  for (int w = 1; w < nw; ++w) {
+    m = fmaxf(m, s_m[w]);
+    bad |= s_b[w];
+  }
+  *cnt_n = 0u;
+  atomicMax(gmax, __float_as_uint(m));
+  if (bad) atomicOr(gmax + 1, 1u);
+  __threadfence();
+  if (atomicAdd(gmax + 2, 1u) != (unsigned)nint - 1) return;
+  __threadfence();
+  const float mx = __uint_as_float(__ldcg(gmax));
+  const int nf = (int)__ldcg(gmax + 1);
+  const double nrm = sqrt((double)mx);
+  ws.out[0] = nrm;
+  ws.out[1] = nf ? 1.0 : 0.0;
+  if (nf || nrm <= ws.tol) *ws.gate = 1;
+  gmax[0] = 0u;
+  gmax[1] = 0u;
+  gmax[2] = 0u;
+}
+
 __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, int d2, int ldw, int P,
                                                    float* __restrict__ Wt, const float* __restrict__ lam2,
                                                    const float* __restrict__ src, const float* __restrict__ b2,
                                                    const double* __restrict__ amp, float dt, int nsl,
                                                    size_t slice, float* __restrict__ accW,
-                                                   float* __restrict__ B0h, float* __restrict__ B0l, const int* __restrict__ gate) {
-  if (gate && *gate) return;
+                                                   float* __restrict__ B0h, float* __restrict__ B0l, WrStop ws) {
+  if (*ws.gate) return;
   const int nloc = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   float* Wn = Wt + (size_t)nloc * (P + 1) * ldw;
@@ -374,6 +439,7 @@ __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, 
     dw = pintd::warp_sum(dw);
     if ((threadIdx.x & 31) == 0) atomicAdd(&accW[(size_t)nloc * P + p], (float)dw);
   }
+  wr_stop_last_block(ws, P);
 }
 
 // ---------------------------------------------------------------------------
@@ -669,11 +735,13 @@ __global__ void __launch_bounds__(256, 4) k_time_solve32_sq(const float* __restr
 #pragma unroll
   for (int m = 0; m < R; ++m) sT[(g + R * m) * LD + s] = re[m] / ((float)P * bpow[g + R * m]);
   __syncthreads();
-  // new states u_{p+1} (tile row p); the previous iterate is in sO
+  // new states u_{p+1} (tile row p); the previous iterate is in sO.  Row r
+  // of this thread is step p = (tid + 256 r) / NS: the warp's lanes share it
+  float dd[PER];
 #pragma unroll
   for (int r = 0; r < PER; ++r) {
     const int e = tid + 256 * r, p = e / NS, ss = e % NS, ii = i0 + ss;
-    float dd = 0.f;
+    dd[r] = 0.f;
     if (ii < d1) {
       const float uq = sT[p * LD + ss];
       Un[(size_t)(p + 1) * ldu + ii] = uq;
@@ -684,12 +752,11 @@ __global__ void __launch_bounds__(256, 4) k_time_solve32_sq(const float* __restr
         put_split(B1h, B1l, o + ldu, uq);
       }
       const float dv = uq - sO[p * LD + ss];
-      dd = dv * dv;
+      dd[r] = dv * dv;
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) dd += __shfl_xor_sync(0xffffffffu, dd, off);
-    if (lane == 0) atomicAdd(&accU[(size_t)nloc * P + p], dd);  // a warp covers one row segment
   }
+  // one reduce-scatter over the warp for all PER rows (steps tid / NS + r 256 / NS)
+  warp_sum_scatter<PER>(dd, accU + (size_t)nloc * P + (tid - lane) / NS, 256 / NS);
 }
 
 // Register variant for P = 16, 32, 64: the contraction inputs and previous
@@ -701,8 +768,8 @@ __global__ void __launch_bounds__(32) k_w_sweep32_t(const float* __restrict__ S,
                                                     const float* __restrict__ src, const float* __restrict__ b2,
                                                     const double* __restrict__ amp, float dt, int nsl,
                                                     size_t slice, float* __restrict__ accW,
-                                                    float* __restrict__ B0h, float* __restrict__ B0l, const int* __restrict__ gate) {
-  if (gate && *gate) return;
+                                                    float* __restrict__ B0h, float* __restrict__ B0l, WrStop ws) {
+  if (*ws.gate) return;
   constexpr int CH = 16;
   const int nloc = blockIdx.y;
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -747,6 +814,7 @@ __global__ void __launch_bounds__(32) k_w_sweep32_t(const float* __restrict__ S,
     }
     warp_sum_scatter<CH>(dd, accW + (size_t)nloc * P + c0);
   }
+  wr_stop_last_block(ws, P);
 }
 
 // constant initial trajectories; with B0h, also the first-contraction column
@@ -944,20 +1012,21 @@ void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const
 // S holds nsl K-slices of the contraction, slice floats apart (summed here)
 void mx_w_sweep32(Ctx* c, const float* S, int nsl, size_t slice, int nact, float* Wt, int ldw, const float* lam2,
                   const float* src, const float* b2, const double* amp, float* accW, float* B0h, float* B0l,
-                  const int* gate) {
+                  const WrStop& ws) {
+  PINT_REQUIRE(ws.gate && ws.counter && ws.acc && ws.out, PINT_ERR_BAD_ARG, "WR stopping test arguments");
   PINT_REQUIRE(nsl >= 1 && nsl <= MAX_SLICES, PINT_ERR_BAD_ARG, "too many contraction slices");
   const int P = c->P, d2 = c->d2;
   const float dt = (float)c->dt;
   const dim3 g32(nbl(d2, 32), nact);
   if (P == 64)
-    k_w_sweep32_t<64><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l, gate);
+    k_w_sweep32_t<64><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l, ws);
   else if (P == 32)
-    k_w_sweep32_t<32><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l, gate);
+    k_w_sweep32_t<32><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l, ws);
   else if (P == 16)
-    k_w_sweep32_t<16><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l, gate);
+    k_w_sweep32_t<16><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l, ws);
   else
     k_w_sweep32<<<dim3(nbl(d2, 128), nact), 128, 0, c->stream>>>(S, d2, ldw, P, Wt, lam2, src, b2, amp, dt, nsl,
-                                                                 slice, accW, B0h, B0l, gate);
+                                                                 slice, accW, B0h, B0l, ws);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
