@@ -243,6 +243,282 @@ __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a, int nb) 
   }
 }
 
+// ---------------------------------------------------------------------------
+// Register-resident variant for couplings of up to 16 x 6 rows and 9 x 32
+// columns per CTA (16 CTAs, 16 warps each).  Profiling the shared-memory
+// kernel above showed each step bound by shared-memory bandwidth and issue:
+// CA was read from shared memory twice per step (the products CA w and
+// CA^T u'), and w once per row.  Here each warp keeps its RT rows of CA in
+// registers for the whole sweep (lane l holds columns l + 32 k), w is read
+// once per step into registers, and one pass over the rows forms u' and the
+// warp's share of CA^T u' together; the warps' shares meet in shared memory,
+// the CTAs' in each CTA's receive buffer (as above, one cluster barrier per
+// step, every CTA forms the whole w').
+// ---------------------------------------------------------------------------
+constexpr int GR_WARPS = 16;
+constexpr int GR_THREADS = 32 * GR_WARPS;
+constexpr int GR_CL = 16;
+
+struct GrLayout {
+  int rpc, spc, d2p, nb;
+  size_t xw, wsum, recv, ia, cb, fw, cw, su, sg, sw, sh, n;  // float offsets
+  size_t bytes;
+};
+
+__host__ __device__ inline GrLayout gr_layout(int d1, int d2, int nk, int nb) {
+  GrLayout L{};
+  L.nb = nb;
+  L.rpc = (d1 + GR_CL - 1) / GR_CL;
+  L.spc = (d2 + GR_CL - 1) / GR_CL;
+  L.d2p = 32 * nk;
+  size_t o = 0;
+  auto take = [&](size_t n) {
+    const size_t at = o;
+    o += (n + 3) / 4 * 4;
+    return at;
+  };
+  L.xw = take(L.d2p);                               // the whole w, identical in every CTA
+  L.wsum = take((size_t)GR_WARPS * L.d2p);          // the warps' shares of CA^T u'
+  L.recv = take((size_t)2 * GR_CL * L.d2p);         // two halves of the CTAs' slots
+  L.ia = take(L.rpc);                               // 1 / (1 + Dt lambda1)
+  L.cb = take(L.rpc);                               // Dt b1 / (1 + Dt lambda1)
+  L.fw = take(L.d2p);                               // 1 - Dt lambda2
+  L.cw = take(L.d2p);                               // Dt b2
+  L.su = take((size_t)nb * L.rpc);                  // staged X_u, G_u rows and X_w, G_w slices
+  L.sg = take((size_t)nb * L.rpc);
+  L.sw = take((size_t)nb * L.spc);
+  L.sh = take((size_t)nb * L.spc);
+  L.n = o;
+  L.bytes = o * 4;
+  return L;
+}
+
+template <int RT, int NK>
+__global__ void __launch_bounds__(GR_THREADS, 1) k_g_sweep_clr(GcArgs a, int nb) {
+  extern __shared__ __align__(16) unsigned char gsm[];
+  const int d1 = a.d1, d2 = a.d2;
+  const GrLayout L = gr_layout(d1, d2, NK, nb);
+  const int d2p = L.d2p;
+  float* fs = reinterpret_cast<float*>(gsm);
+  float *xw = fs + L.xw, *wsum = fs + L.wsum, *recv = fs + L.recv, *ia = fs + L.ia, *cb = fs + L.cb,
+        *fw = fs + L.fw, *cw = fs + L.cw, *stXu = fs + L.su, *stGu = fs + L.sg, *stXw = fs + L.sw,
+        *stGw = fs + L.sh;
+  const int rank = (int)cl_rank();
+  const int r0 = rank * L.rpc, nr = max(0, min(d1, r0 + L.rpc) - r0);
+  const int j0 = rank * L.spc, ns = max(0, min(d2, j0 + L.spc) - j0);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const float Dt = (float)a.Dt;
+  const size_t n0 = (size_t)a.n_lo;
+  // this warp's rows q = warp + 16 t of CA, lane l holding columns l + 32 k
+  float ca[RT][NK], xu[RT];
+#pragma unroll
+  for (int t = 0; t < RT; ++t) {
+    const int q = warp + GR_WARPS * t;
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+      const int j = lane + 32 * k;
+      ca[t][k] = (q < nr && j < d2) ? a.CA[(size_t)(r0 + q) * d2 + j] : 0.f;
+    }
+    xu[t] = q < nr ? (float)a.Xu[n0 * d1 + r0 + q] : 0.f;
+  }
+  for (int j = tid; j < d2p; j += GR_THREADS) {
+    xw[j] = j < d2 ? (float)a.Xw[n0 * d2 + j] : 0.f;
+    fw[j] = j < d2 ? (float)(1.0 - a.Dt * a.lam2[j]) : 0.f;
+    cw[j] = j < d2 ? (float)(a.Dt * a.b2[j]) : 0.f;
+  }
+  for (int q = tid; q < nr; q += GR_THREADS) {
+    const int i = r0 + q;
+    ia[q] = (float)(1.0 / (1.0 + a.Dt * a.lam1[i]));
+    cb[q] = (float)(a.Dt * a.b1[i] / (1.0 + a.Dt * a.lam1[i]));
+  }
+  __syncthreads();
+  cl_sync();  // every CTA of the cluster is resident before any DSMEM access
+  // inputs of a step that do not depend on the sweep, fetched one step ahead
+  // and already combined: F_n - G_old_n (+ c_{n+1}) for the warp's rows (the
+  // same values in every lane) and for column tid
+  auto fetch = [&](int n, float* pu, float& pw, float& am) {
+    am = 0.f;
+    pw = 0.f;
+#pragma unroll
+    for (int t = 0; t < RT; ++t) pu[t] = 0.f;
+    if (n >= a.n_hi) return;
+    am = (float)a.amp[n];
+#pragma unroll
+    for (int t = 0; t < RT; ++t) {
+      const int q = warp + GR_WARPS * t;
+      if (q < nr) {
+        const int i = r0 + q;
+        if (!a.first) pu[t] = a.Fu[(size_t)n * d1 + i] - a.Gu[(size_t)n * d1 + i];
+        if (a.Cu) pu[t] += a.Cu[(size_t)(n + 1) * d1 + i];
+      }
+    }
+    if (tid < d2) {
+      if (!a.first) pw = a.Fw[(size_t)n * d2 + tid] - a.Gw[(size_t)n * d2 + tid];
+      if (a.Cw) pw += a.Cw[(size_t)(n + 1) * d2 + tid];
+    }
+  };
+  float npu[RT], npw, nam;
+  fetch(a.n_lo, npu, npw, nam);
+  int nbase = a.n_lo;
+  for (int n = a.n_lo; n < a.n_hi; ++n) {
+    const int sl = n - nbase;  // staging slot of this step
+    float pu[RT];
+#pragma unroll
+    for (int t = 0; t < RT; ++t) pu[t] = npu[t];
+    const float pw = npw, am = nam;
+    // G_old of step n + 1 is read here, before this sweep rewrites it: this
+    // step writes G_old of step n only (staged), so the read sees the old value
+    fetch(n + 1, npu, npw, nam);
+    float wl[NK], part[NK];
+#pragma unroll
+    for (int k = 0; k < NK; ++k) {
+      wl[k] = xw[lane + 32 * k];
+      part[k] = 0.f;
+    }
+    // one pass over the warp's rows: u' = G's u step, then its CA^T u' share
+#pragma unroll
+    for (int t = 0; t < RT; ++t) {
+      const int q = warp + GR_WARPS * t;
+      if (q < nr) {  // warp-uniform
+        float acc = 0.f;
+#pragma unroll
+        for (int k = 0; k < NK; ++k) acc = fmaf(ca[t][k], wl[k], acc);
+        acc = pintd::warp_sumf(acc);
+        const float g = xu[t] * ia[q] - Dt * ia[q] * acc + am * cb[q];
+        const float v = g + pu[t];
+        if (lane == 0) {
+          stXu[(size_t)sl * L.rpc + q] = v;
+          stGu[(size_t)sl * L.rpc + q] = g;
+        }
+        xu[t] = v;
+#pragma unroll
+        for (int k = 0; k < NK; ++k) part[k] = fmaf(ca[t][k], g, part[k]);
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < NK; ++k) wsum[(size_t)warp * d2p + lane + 32 * k] = part[k];
+    __syncthreads();
+    // this CTA's CA^T u' into its slot of every CTA's receive half
+    float* rh = recv + (size_t)((n - a.n_lo) & 1) * GR_CL * d2p;
+    if (tid < d2) {
+      float sum = 0.f;
+#pragma unroll
+      for (int w = 0; w < GR_WARPS; ++w) sum += wsum[(size_t)w * d2p + tid];
+      const float* slot = rh + (size_t)rank * d2p + tid;
+#pragma unroll
+      for (int r = 0; r < GR_CL; ++r) st_dsmem(dsmem_addr(slot, (uint32_t)r), sum);
+    }
+    cl_sync();  // every CTA's shares delivered to every CTA
+    // the whole w' in every CTA, slots summed in rank order (identical copies)
+    if (tid < d2) {
+      float sum = 0.f;
+#pragma unroll
+      for (int r = 0; r < GR_CL; ++r) sum += rh[(size_t)r * d2p + tid];
+      const float g = fw[tid] * xw[tid] - Dt * sum + am * cw[tid];
+      const float v = g + pw;
+      xw[tid] = v;
+      if (tid >= j0 && tid < j0 + ns) {
+        stXw[(size_t)sl * L.spc + (tid - j0)] = v;
+        stGw[(size_t)sl * L.spc + (tid - j0)] = g;
+      }
+    }
+    __syncthreads();  // new w before the next step; wsum free again
+    if (sl + 1 == nb || n + 1 == a.n_hi) {  // write the staged chunk out (states in FP64)
+      const int cnt = sl + 1;
+      for (int e = tid; e < cnt * nr; e += GR_THREADS) {
+        const int st = e / nr, q = e - st * nr;
+        a.Xu[(size_t)(nbase + st + 1) * d1 + r0 + q] = (double)stXu[(size_t)st * L.rpc + q];
+        a.Gu[(size_t)(nbase + st) * d1 + r0 + q] = stGu[(size_t)st * L.rpc + q];
+      }
+      for (int e = tid; e < cnt * ns; e += GR_THREADS) {
+        const int st = e / ns, q = e - st * ns;
+        a.Xw[(size_t)(nbase + st + 1) * d2 + j0 + q] = (double)stXw[(size_t)st * L.spc + q];
+        a.Gw[(size_t)(nbase + st) * d2 + j0 + q] = stGw[(size_t)st * L.spc + q];
+      }
+      __syncthreads();
+      nbase = n + 1;
+    }
+  }
+}
+
+// instantiated shapes: rows per warp RT and column blocks NK (d2 <= 32 NK)
+template <int RT, int NK>
+bool gr_feasible(size_t bytes) {
+  static int ok = -1;
+  std::lock_guard<std::mutex> lock(lazy_init_mutex());
+  if (ok < 0) {
+    ok = 0;
+    if (cudaFuncSetAttribute(k_g_sweep_clr<RT, NK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_g_sweep_clr<RT, NK>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) !=
+            cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    cudaLaunchConfig_t cfg{};
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = GR_CL;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(GR_CL);
+    cfg.blockDim = dim3(GR_THREADS);
+    cfg.dynamicSmemBytes = GC_SMEM;
+    cfg.attrs = at;
+    cfg.numAttrs = 1;
+    int nclusters = 0;
+    if (cudaOccupancyMaxActiveClusters(&nclusters, k_g_sweep_clr<RT, NK>, &cfg) != cudaSuccess) {
+      cudaGetLastError();
+      return false;
+    }
+    ok = nclusters >= 1 ? 1 : 0;
+  }
+  return ok == 1 && bytes <= GC_SMEM;
+}
+
+template <int RT, int NK>
+bool gr_launch(Ctx* c, const GcArgs& a) {
+  const GrLayout L1 = gr_layout(a.d1, a.d2, NK, 1), L0 = gr_layout(a.d1, a.d2, NK, 0);
+  if (!gr_feasible<RT, NK>(L1.bytes)) return false;
+  const size_t per = L1.bytes - L0.bytes;
+  const int nb = (int)std::min<size_t>((size_t)std::max(a.n_hi - a.n_lo, 1), 1 + (GC_SMEM - L1.bytes) / per);
+  const GrLayout L = gr_layout(a.d1, a.d2, NK, nb);
+  cudaLaunchConfig_t cfg{};
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeClusterDimension;
+  at[0].val.clusterDim.x = GR_CL;
+  at[0].val.clusterDim.y = 1;
+  at[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(GR_CL);
+  cfg.blockDim = dim3(GR_THREADS);
+  cfg.dynamicSmemBytes = L.bytes;
+  cfg.stream = c->stream;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  PINT_CUDA(cudaLaunchKernelEx(&cfg, k_g_sweep_clr<RT, NK>, a, nb));
+  c->launches++;
+  return true;
+}
+
+// the register variant when an instantiated shape covers the coupling
+template <int NK>
+bool gr_try_rt(Ctx* c, const GcArgs& a, int rt) {
+  if (rt <= 2) return gr_launch<2, NK>(c, a);
+  if (rt <= 4) return gr_launch<4, NK>(c, a);
+  if (rt <= 6) return gr_launch<6, NK>(c, a);
+  return false;
+}
+
+bool gr_try(Ctx* c, const GcArgs& a) {
+  const int rpc = (a.d1 + GR_CL - 1) / GR_CL, rt = (rpc + GR_WARPS - 1) / GR_WARPS;
+  const int nk = (a.d2 + 31) / 32;
+  if (a.d2 > GR_THREADS) return false;
+  if (nk <= 3) return gr_try_rt<3>(c, a, rt);
+  if (nk <= 5) return gr_try_rt<5>(c, a, rt);
+  if (nk <= 9) return gr_try_rt<9>(c, a, rt);
+  return false;
+}
+
 template <int CL>
 bool gc_feasible(size_t bytes) {
   static int ok = -1;
@@ -326,6 +602,7 @@ int gc_cluster_size(int d1, int d2) {
 
 void g_sweep_cluster(Ctx* c, const GcArgs& a, int CL) {
   if (a.n_lo >= a.n_hi) return;
+  if (CL == 16 && gr_try(c, a)) return;
   if (CL == 16)
     gc_launch<16>(c, a);
   else if (CL == 8)
