@@ -259,11 +259,25 @@ constexpr int GR_WARPS = 16;
 constexpr int GR_THREADS = 32 * GR_WARPS;
 constexpr int GR_CL = 16;
 
+// one half of the prefetch area: amp (a double, then 2 pad floats), then
+// Fu, Gu, Cu (rpc each) and Fw, Gw, Cw (d2p each); a multiple of 4 floats
+__host__ __device__ inline size_t gr_half(int rpc, int d2p) {
+  return ((size_t)4 + 3 * (size_t)rpc + 3 * (size_t)d2p + 3) / 4 * 4;
+}
+
 struct GrLayout {
   int rpc, spc, d2p, nb;
-  size_t xw, wsum, recv, ia, cb, fw, cw, su, sg, sw, sh, n;  // float offsets
+  size_t xw, wsum, recv, ia, cb, fw, cw, pre, su, sg, sw, sh, n;  // float offsets
   size_t bytes;
 };
+
+__device__ __forceinline__ void gr_cp4(float* sdst, const float* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void gr_cp8(void* sdst, const void* gsrc) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(smem_u32(sdst)), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void gr_cp_wait() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
 __host__ __device__ inline GrLayout gr_layout(int d1, int d2, int nk, int nb) {
   GrLayout L{};
@@ -284,6 +298,7 @@ __host__ __device__ inline GrLayout gr_layout(int d1, int d2, int nk, int nb) {
   L.cb = take(L.rpc);                               // Dt b1 / (1 + Dt lambda1)
   L.fw = take(L.d2p);                               // 1 - Dt lambda2
   L.cw = take(L.d2p);                               // Dt b2
+  L.pre = take((size_t)2 * gr_half(L.rpc, L.d2p));  // next step's inputs, two halves
   L.su = take((size_t)nb * L.rpc);                  // staged X_u, G_u rows and X_w, G_w slices
   L.sg = take((size_t)nb * L.rpc);
   L.sw = take((size_t)nb * L.spc);
@@ -333,68 +348,96 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_g_sweep_clr(GcArgs a, int nb)
   }
   __syncthreads();
   cl_sync();  // every CTA of the cluster is resident before any DSMEM access
-  // inputs of a step that do not depend on the sweep, fetched one step ahead
-  // and already combined: F_n - G_old_n (+ c_{n+1}) for the warp's rows (the
-  // same values in every lane) and for column tid
-  auto fetch = [&](int n, float* pu, float& pw, float& am) {
-    am = 0.f;
-    pw = 0.f;
-#pragma unroll
-    for (int t = 0; t < RT; ++t) pu[t] = 0.f;
+  // inputs of a step that do not depend on the sweep (F ends, old G values,
+  // jumps, amplitude) are copied one step ahead into the other half of `pre`
+  // by asynchronous copies, so no register waits on their global loads:
+  // half layout [Fu | Gu | Cu] (rpc each), [Fw | Gw | Cw] (d2p each), amp (2)
+  float* pre = fs + L.pre;
+  const size_t half = gr_half(L.rpc, d2p);
+  auto fetch = [&](int n, int h) {
+    float* b = pre + (size_t)h * half;
+    double* bam = reinterpret_cast<double*>(b);
+    float *bFu = b + 4, *bGu = bFu + L.rpc, *bCu = bGu + L.rpc, *bFw = bCu + L.rpc, *bGw = bFw + d2p,
+          *bCw = bGw + d2p;
     if (n >= a.n_hi) return;
-    am = (float)a.amp[n];
-#pragma unroll
-    for (int t = 0; t < RT; ++t) {
-      const int q = warp + GR_WARPS * t;
-      if (q < nr) {
-        const int i = r0 + q;
-        if (!a.first) pu[t] = a.Fu[(size_t)n * d1 + i] - a.Gu[(size_t)n * d1 + i];
-        if (a.Cu) pu[t] += a.Cu[(size_t)(n + 1) * d1 + i];
+    for (int q = tid; q < nr; q += GR_THREADS) {
+      const size_t i = (size_t)r0 + q;
+      if (!a.first) {
+        gr_cp4(bFu + q, a.Fu + (size_t)n * d1 + i);
+        gr_cp4(bGu + q, a.Gu + (size_t)n * d1 + i);
+      } else {
+        bFu[q] = 0.f;
+        bGu[q] = 0.f;
       }
+      if (a.Cu) gr_cp4(bCu + q, a.Cu + (size_t)(n + 1) * d1 + i);
+      else bCu[q] = 0.f;
     }
     if (tid < d2) {
-      if (!a.first) pw = a.Fw[(size_t)n * d2 + tid] - a.Gw[(size_t)n * d2 + tid];
-      if (a.Cw) pw += a.Cw[(size_t)(n + 1) * d2 + tid];
+      if (!a.first) {
+        gr_cp4(bFw + tid, a.Fw + (size_t)n * d2 + tid);
+        gr_cp4(bGw + tid, a.Gw + (size_t)n * d2 + tid);
+      } else {
+        bFw[tid] = 0.f;
+        bGw[tid] = 0.f;
+      }
+      if (a.Cw) gr_cp4(bCw + tid, a.Cw + (size_t)(n + 1) * d2 + tid);
+      else bCw[tid] = 0.f;
     }
+    if (tid == 0) gr_cp8(bam, a.amp + n);
   };
-  float npu[RT], npw, nam;
-  fetch(a.n_lo, npu, npw, nam);
+  fetch(a.n_lo, 0);
+  gr_cp_wait();
+  __syncthreads();
   int nbase = a.n_lo;
   for (int n = a.n_lo; n < a.n_hi; ++n) {
     const int sl = n - nbase;  // staging slot of this step
-    float pu[RT];
-#pragma unroll
-    for (int t = 0; t < RT; ++t) pu[t] = npu[t];
-    const float pw = npw, am = nam;
+    const int h = (n - a.n_lo) & 1;
+    const float* b = pre + (size_t)h * half;
+    const float *bFu = b + 4, *bGu = bFu + L.rpc, *bCu = bGu + L.rpc, *bFw = bCu + L.rpc, *bGw = bFw + d2p,
+                *bCw = bGw + d2p;
+    const float am = (float)*reinterpret_cast<const double*>(b);
     // G_old of step n + 1 is read here, before this sweep rewrites it: this
     // step writes G_old of step n only (staged), so the read sees the old value
-    fetch(n + 1, npu, npw, nam);
+    fetch(n + 1, h ^ 1);
     float wl[NK], part[NK];
 #pragma unroll
     for (int k = 0; k < NK; ++k) {
       wl[k] = xw[lane + 32 * k];
       part[k] = 0.f;
     }
-    // one pass over the warp's rows: u' = G's u step, then its CA^T u' share
+    // one pass over the warp's rows: u' = G's u step, then its CA^T u' share.
+    // The RT rows are independent: their products and butterfly reductions
+    // are interleaved so that the warp has RT chains in flight, not one.
+    float acc[RT], gr[RT];
+#pragma unroll
+    for (int t = 0; t < RT; ++t) {
+      acc[t] = 0.f;
+#pragma unroll
+      for (int k = 0; k < NK; ++k) acc[t] = fmaf(ca[t][k], wl[k], acc[t]);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+      for (int t = 0; t < RT; ++t) acc[t] += __shfl_xor_sync(0xffffffffu, acc[t], o);
 #pragma unroll
     for (int t = 0; t < RT; ++t) {
       const int q = warp + GR_WARPS * t;
+      gr[t] = 0.f;  // rows past nr: zero coupling rows, no u' and no share
       if (q < nr) {  // warp-uniform
-        float acc = 0.f;
-#pragma unroll
-        for (int k = 0; k < NK; ++k) acc = fmaf(ca[t][k], wl[k], acc);
-        acc = pintd::warp_sumf(acc);
-        const float g = xu[t] * ia[q] - Dt * ia[q] * acc + am * cb[q];
-        const float v = g + pu[t];
+        const float g = xu[t] * ia[q] - Dt * ia[q] * acc[t] + am * cb[q];
+        const float v = g + ((bFu[q] - bGu[q]) + bCu[q]);
         if (lane == 0) {
           stXu[(size_t)sl * L.rpc + q] = v;
           stGu[(size_t)sl * L.rpc + q] = g;
         }
         xu[t] = v;
-#pragma unroll
-        for (int k = 0; k < NK; ++k) part[k] = fmaf(ca[t][k], g, part[k]);
+        gr[t] = g;
       }
     }
+#pragma unroll
+    for (int t = 0; t < RT; ++t)
+#pragma unroll
+      for (int k = 0; k < NK; ++k) part[k] = fmaf(ca[t][k], gr[t], part[k]);
 #pragma unroll
     for (int k = 0; k < NK; ++k) wsum[(size_t)warp * d2p + lane + 32 * k] = part[k];
     __syncthreads();
@@ -415,14 +458,15 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_g_sweep_clr(GcArgs a, int nb)
 #pragma unroll
       for (int r = 0; r < GR_CL; ++r) sum += rh[(size_t)r * d2p + tid];
       const float g = fw[tid] * xw[tid] - Dt * sum + am * cw[tid];
-      const float v = g + pw;
+      const float v = g + ((bFw[tid] - bGw[tid]) + bCw[tid]);
       xw[tid] = v;
       if (tid >= j0 && tid < j0 + ns) {
         stXw[(size_t)sl * L.spc + (tid - j0)] = v;
         stGw[(size_t)sl * L.spc + (tid - j0)] = g;
       }
     }
-    __syncthreads();  // new w before the next step; wsum free again
+    gr_cp_wait();     // this thread's copies of the next step's inputs
+    __syncthreads();  // new w and the next inputs before the next step; wsum free again
     if (sl + 1 == nb || n + 1 == a.n_hi) {  // write the staged chunk out (states in FP64)
       const int cnt = sl + 1;
       for (int e = tid; e < cnt * nr; e += GR_THREADS) {
