@@ -837,7 +837,7 @@ static void stage_amp(Ctx* c, Hot& H, const double* amp_dev, int count) {
     k_fill<<<nb_(count, 256), 256, 0, c->stream>>>(H.amp, count, 1.0);
 }
 
-static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw);
+static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw, const float* CM32);
 
 void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const double* amp_dev, double eps,
                 int k_max, double wr_tol, int wr_max, double* u_out, double* coarse_out, pint_stats* st,
@@ -901,7 +901,7 @@ void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const dou
     g_sweep(c, H, H.Xu, H.Xw, H.amp, nullptr, nullptr, nullptr, nullptr, 0, true);
     g_sweep_check(c, H);
     if (eps < 0 || wr_tol < 0) {  // relative tolerances: scale of the G-sweep states
-      const double sc = state_scale(c, H, H.Xu, H.Xw);
+      const double sc = state_scale(c, H, H.Xu, H.Xw, nullptr);
       if (eps < 0) eps = -eps * sc;
       if (wr_tol < 0) wr_tol = -wr_tol * sc;
     }
@@ -1116,6 +1116,7 @@ void mx_residual(Ctx* c, const double* Zu, const double* Zw, const double* R64, 
                  const double* b1, const double* b2, const double* amp, float* srcU, float* srcW);
 void mx_continuity(Ctx* c, const double* Zu, const double* Zw, double* Cu, double* Cw);
 void mx_ar_diff(Ctx* c, int ld, float* a32, float* hi, float* lo);
+void mx_gemm_df_nt(Ctx* c, const double* A, const double* B, int m, int n, int K, double* C);
 void mx_split_df(Ctx* c, const double* x, long long n, float* h, float* l);
 void mx_wr_gemm_df(Ctx* c, int mode, const float* Ah, const float* Al, int M, int K, const float* Uh,
                    const float* Ul, const float* Wh, const float* Wl, int ncols, double* out);
@@ -1341,6 +1342,7 @@ static void mx_refresh(Ctx* c, Mx& M) {
 constexpr int LP_STALL = 3;
 constexpr double LP_FLOOR_SPAN = 1e3;
 
+
 // low-precision WR sweep on intervals [n_lo, n_lo + nact); Ut/Wt/src point at
 // absolute slot n_lo; ends into fu/fw (FP64)
 static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* xs_w, const double* amp_act,
@@ -1510,10 +1512,11 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
                               cudaMemcpyDeviceToDevice, c->stream));
     PINT_CUDA(cudaEventRecord(a0, c->stream));
     bool bad = false;
+    const double wtol = r.wr_tol;
     int it = wr_sweep_lp(c, H, M, r.Xu + (size_t)n_lo * d1, r.Xw + (size_t)n_lo * d2, r.amp + n_lo, nact,
                          r.srcU ? r.srcU + (size_t)n_lo * P * d1 : nullptr,
                          r.srcW ? r.srcW + (size_t)n_lo * P * d2 : nullptr, r.Ut + (size_t)n_lo * (P + 1) * M.ldu,
-                         r.Wt + (size_t)n_lo * (P + 1) * M.ldw, r.wr_tol, r.wr_max, H.Fu + (size_t)n_lo * d1,
+                         r.Wt + (size_t)n_lo * (P + 1) * M.ldw, wtol, r.wr_max, H.Fu + (size_t)n_lo * d1,
                          H.Fw + (size_t)n_lo * d2, M.Fu32 ? M.Fu32 + (size_t)n_lo * d1 : nullptr,
                          M.Fw32 ? M.Fw32 + (size_t)n_lo * d2 : nullptr, &bad);
     PINT_CUDA(cudaEventRecord(a1, c->stream));
@@ -1566,12 +1569,16 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
 }
 
 // max_n ||x_n||_{M_H} (n = 0..N) into *out (host)
-static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw) {
+static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw, const float* CM32) {
   const int N = c->N, d1 = c->d1, d2 = c->d2;
   PINT_CUDA(cudaMemsetAsync(H.tmp1, 0, (size_t)(N + 1) * std::max(d1, d2) * 8, c->stream));
-  // k_jump measures rows 1..N against the zero rows of tmp1
+  // k_jump measures rows 1..N against the zero rows of tmp1 (a scale for the
+  // relative tolerances: the FP32 coupling serves as well as the FP64 one)
   PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
-  k_jump<double><<<dim3(N, JS), 256, 0, c->stream>>>(Xu, Xw, H.tmp1, H.tmp1, c->CM, d1, d2, H.red + 8);
+  if (CM32)
+    k_jump<float><<<dim3(N, JS), 256, 0, c->stream>>>(Xu, Xw, H.tmp1, H.tmp1, CM32, d1, d2, H.red + 8);
+  else
+    k_jump<double><<<dim3(N, JS), 256, 0, c->stream>>>(Xu, Xw, H.tmp1, H.tmp1, c->CM, d1, d2, H.red + 8);
   k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
   PINT_LAUNCH_CHECK();
   double h[2];
@@ -1656,7 +1663,7 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
     LpRun probe = m;
     probe.k_max = 0;
     parareal_lp(c, H, M, probe, &f_ms, nullptr, nullptr, 0);
-    double sc = state_scale(c, H, H.Xu, H.Xw);
+    double sc = state_scale(c, H, H.Xu, H.Xw, M.CM32);
     if (eps < 0) eps = -eps * sc;  // relative tolerances
     if (wr_tol < 0) wr_tol = -wr_tol * sc;
     // the refinement corrects what the low-precision solve leaves: loose tolerances
@@ -1711,7 +1718,7 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
       LpRun probe = y;
       probe.k_max = 0;
       parareal_lp(c, H, M, probe, &f_ms, nullptr, nullptr, 0);
-      double sc = state_scale(c, H, M.Yu, M.Yw);
+      double sc = state_scale(c, H, M.Yu, M.Yw, M.CM32);
       y.eps = eps;  // the jumps stop at eps or at the precision floor
       y.wr_tol = std::max(wr_tol, PINT_CORR_REL_TOL * sc);
       y.have_g0 = true;
@@ -1740,7 +1747,9 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
   cudaEvent_t eP0, eP1;
   PINT_CUDA(cudaEventCreate(&eP0));
   PINT_CUDA(cudaEventCreate(&eP1));
-  from_spectral(c, H.Xu, H.Xw, N + 1, H.tmp1, H.tmp2);
+  // out of the spectral coordinates (x Q^T, x Q2^T) in double-float
+  mx_gemm_df_nt(c, H.Xu, c->Q, N + 1, d1, d1, H.tmp1);
+  mx_gemm_df_nt(c, H.Xw, c->Q2, N + 1, d2, d2, H.tmp2);
   if (coarse_out) {
     PINT_CUDA(cudaMemcpy2DAsync(coarse_out, (size_t)(d1 + d2) * 8, H.tmp1, (size_t)d1 * 8, (size_t)d1 * 8, N + 1,
                                 cudaMemcpyDeviceToDevice, c->stream));

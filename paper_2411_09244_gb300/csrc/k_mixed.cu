@@ -525,6 +525,56 @@ __global__ void __launch_bounds__(256) k_wr_gemm_df(const float* __restrict__ Ah
     }
 }
 
+// C[i][j] = sum_k A[i][k] B[j][k] (FP64 in and out, row-major) in
+// double-float arithmetic on the FP32 pipe: the operands are split into FP32
+// pairs as they are staged in shared memory, the products accumulated as in
+// k_wr_gemm_df.  For the conversions of coarse states out of the spectral
+// coordinates (a few rows against d x d), which the FP64 pipe would take
+// ten times longer to do.
+template <int T>
+__global__ void __launch_bounds__(256) k_gemm_df_nt(const double* __restrict__ A, const double* __restrict__ B,
+                                                    int m, int n, int K, double* __restrict__ C) {
+  constexpr int R = T / 16;
+  __shared__ float Ash[16][T + 1], Asl[16][T + 1], Bsh[16][T + 1], Bsl[16][T + 1];
+  const int i0 = blockIdx.y * T, j0 = blockIdx.x * T;
+  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  float sh[R][R] = {}, sl[R][R] = {};
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    for (int e = threadIdx.x; e < 16 * T; e += 256) {
+      const int kk = e % 16, r = e / 16, kg = k0 + kk;
+      const double a = (kg < K && i0 + r < m) ? A[(size_t)(i0 + r) * K + kg] : 0.0;
+      const double b = (kg < K && j0 + r < n) ? B[(size_t)(j0 + r) * K + kg] : 0.0;
+      const float ah = (float)a, bh = (float)b;
+      Ash[kk][r] = ah;
+      Asl[kk][r] = (float)(a - (double)ah);
+      Bsh[kk][r] = bh;
+      Bsl[kk][r] = (float)(b - (double)bh);
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < 16; ++kk) {
+      float a_h[R], a_l[R], b_h[R], b_l[R];
+#pragma unroll
+      for (int q = 0; q < R; ++q) {
+        a_h[q] = Ash[kk][ty * R + q];
+        a_l[q] = Asl[kk][ty * R + q];
+        b_h[q] = Bsh[kk][tx * R + q];
+        b_l[q] = Bsl[kk][tx * R + q];
+      }
+#pragma unroll
+      for (int p = 0; p < R; ++p)
+#pragma unroll
+        for (int q = 0; q < R; ++q) pintd::df_fma(a_h[p], a_l[p], b_h[q], b_l[q], sh[p][q], sl[p][q]);
+    }
+    __syncthreads();
+  }
+  for (int p = 0; p < R; ++p)
+    for (int q = 0; q < R; ++q) {
+      const int i = i0 + ty * R + p, j = j0 + tx * R + q;
+      if (i < m && j < n) C[(size_t)i * n + j] = (double)sh[p][q] + (double)sl[p][q];
+    }
+}
+
 // x -> (h, l) with h = fl32(x), l = fl32(x - h)
 __global__ void k_split_df(const double* __restrict__ x, long long n, float* __restrict__ h, float* __restrict__ l) {
   for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
@@ -817,6 +867,125 @@ __global__ void __launch_bounds__(32) k_w_sweep32_t(const float* __restrict__ S,
   wr_stop_last_block(ws, P);
 }
 
+// One block per interval for d2 <= 512 (thread j = column j): the squared
+// updates of the interval's w steps meet in shared memory instead of global
+// atomics, and the block itself takes the interval's max over its 2 P
+// squared norms (the u part left in accU by the time solve), so the fused
+// stopping test needs one counter per launch, not one per interval.
+template <int P>
+__global__ void __launch_bounds__(512) k_w_sweep32_b(const float* __restrict__ S, int d2, int ldw,
+                                                      float* __restrict__ Wt, const float* __restrict__ lam2,
+                                                      const float* __restrict__ src, const float* __restrict__ b2,
+                                                      const double* __restrict__ amp, float dt, int nsl,
+                                                      size_t slice, float* __restrict__ B0h,
+                                                      float* __restrict__ B0l, WrStop ws) {
+  if (*ws.gate) return;
+  constexpr int CH = 16;
+  __shared__ float sW[16][P];  // per-warp sums of the squared w updates
+  __shared__ float s_m[32];
+  __shared__ int s_b[32];
+  const int nloc = blockIdx.x;
+  const int j = threadIdx.x, lane = j & 31, warp = j >> 5, nw = (blockDim.x + 31) >> 5;
+  const bool act = j < d2;
+  float* Wn = Wt + (size_t)nloc * (P + 1) * ldw;
+  const float fac = act ? 1.f - dt * lam2[j] : 0.f;
+  const float cs = (act && !src) ? dt * b2[j] * (float)amp[nloc] : 0.f;
+  float w = act ? Wn[j] : 0.f;
+#pragma unroll 1
+  for (int c0 = 0; c0 < P; c0 += CH) {
+    float sv[CH], ov[CH], dd[CH];
+    if (act) {
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const size_t o = ((size_t)nloc * P + c0 + q) * d2 + j;
+        float a = src ? src[o] : cs;
+#pragma unroll
+        for (int z = 0; z < MAX_SLICES; ++z)
+          if (z < nsl) a += S[(size_t)z * slice + o];
+        sv[q] = a;
+        ov[q] = Wn[(size_t)(c0 + q + 1) * ldw + j];
+      }
+#pragma unroll
+      for (int q = 0; q < CH; ++q) {
+        const int p = c0 + q;
+        const float wn = fac * w + sv[q];
+        Wn[(size_t)(p + 1) * ldw + j] = wn;
+        if (B0h && p + 1 < P) {  // first-contraction column map of step p + 1: [w_{p+1} ; w_{p+1} - w_p]
+          const size_t o = ((size_t)nloc * P + p + 1) * 2 * ldw + j;
+          put_split(B0h, B0l, o, wn);
+          put_split(B0h, B0l, o + ldw, wn - w);
+        }
+        const float d = wn - ov[q];
+        dd[q] = d * d;
+        w = wn;
+      }
+    } else {
+#pragma unroll
+      for (int q = 0; q < CH; ++q) dd[q] = 0.f;
+    }
+    // butterfly reduce-scatter over the warp: lane pairs (2 l, 2 l + 1) end
+    // with the warp's sum for step c0 + off of the chunk
+    int off = 0;
+    int mask = 16;
+#pragma unroll
+    for (int C = CH; C > 1; C >>= 1, mask >>= 1) {
+      const int half = C / 2;
+      const bool upper = (lane & mask) != 0;
+#pragma unroll
+      for (int k = 0; k < half; ++k) {
+        const float send = upper ? dd[k] : dd[k + half];
+        const float keep = upper ? dd[k + half] : dd[k];
+        dd[k] = keep + __shfl_xor_sync(0xffffffffu, send, mask);
+      }
+      if (upper) off += half;
+    }
+    dd[0] += __shfl_xor_sync(0xffffffffu, dd[0], 1);
+    if ((lane & 1) == 0) sW[warp][c0 + off] = dd[0];
+  }
+  __syncthreads();
+  // the interval's max over its u and w squared norms; clear the u sums
+  float m = 0.f;
+  int bad = 0;
+  for (int p = j; p < P; p += blockDim.x) {
+    float sw = 0.f;
+    for (int g = 0; g < nw; ++g) sw += sW[g][p];
+    float* au = ws.acc + (size_t)nloc * P + p;
+    const float su = __ldcg(au);
+    *au = 0.f;
+    if (!(sw <= 3.0e38f) || !(su <= 3.0e38f)) bad = 1;  // NaN or inf
+    m = fmaxf(m, fmaxf(sw, su));
+  }
+  for (int o = 16; o >= 1; o >>= 1) {
+    m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    bad |= __shfl_xor_sync(0xffffffffu, bad, o);
+  }
+  if (lane == 0) {
+    s_m[warp] = m;
+    s_b[warp] = bad;
+  }
+  __syncthreads();
+  if (j != 0) return;
+  for (int g = 1; g < nw; ++g) {
+    m = fmaxf(m, s_m[g]);
+    bad |= s_b[g];
+  }
+  unsigned* gmax = ws.counter;  // [0] max bits, [1] non-finite, [2] intervals done
+  atomicMax(gmax, __float_as_uint(m));
+  if (bad) atomicOr(gmax + 1, 1u);
+  __threadfence();
+  if (atomicAdd(gmax + 2, 1u) != gridDim.x - 1) return;
+  __threadfence();
+  const float mx = __uint_as_float(__ldcg(gmax));
+  const int nf = (int)__ldcg(gmax + 1);
+  const double nrm = sqrt((double)mx);
+  ws.out[0] = nrm;
+  ws.out[1] = nf ? 1.0 : 0.0;
+  if (nf || nrm <= ws.tol) *ws.gate = 1;
+  gmax[0] = 0u;
+  gmax[1] = 0u;
+  gmax[2] = 0u;
+}
+
 // constant initial trajectories; with B0h, also the first-contraction column
 // map [w_p ; w_p - w_{p-1}] = [x_w ; 0] of every step
 __global__ void k_init32(const double* __restrict__ Xu, const double* __restrict__ Xw, int d1, int d2, int ldu,
@@ -1018,7 +1187,15 @@ void mx_w_sweep32(Ctx* c, const float* S, int nsl, size_t slice, int nact, float
   const int P = c->P, d2 = c->d2;
   const float dt = (float)c->dt;
   const dim3 g32(nbl(d2, 32), nact);
-  if (P == 64)
+  const int tb = (d2 + 31) / 32 * 32;
+  if (d2 <= 512 && (P == 64 || P == 32 || P == 16)) {  // one block per interval; accW unused
+    if (P == 64)
+      k_w_sweep32_b<64><<<nact, tb, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, B0h, B0l, ws);
+    else if (P == 32)
+      k_w_sweep32_b<32><<<nact, tb, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, B0h, B0l, ws);
+    else
+      k_w_sweep32_b<16><<<nact, tb, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, B0h, B0l, ws);
+  } else if (P == 64)
     k_w_sweep32_t<64><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l, ws);
   else if (P == 32)
     k_w_sweep32_t<32><<<g32, 32, 0, c->stream>>>(S, d2, ldw, Wt, lam2, src, b2, amp, dt, nsl, slice, accW, B0h, B0l, ws);
@@ -1117,6 +1294,14 @@ void mx_wr_gemm_df(Ctx* c, int mode, const float* Ah, const float* Al, int M, in
     else
       k_wr_gemm_df<1, 32><<<grid, 256, 0, c->stream>>>(Ah, Al, M, K, Uh, Ul, Wh, Wl, d1, d2, P, ncols, out);
   }
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+}
+
+void mx_gemm_df_nt(Ctx* c, const double* A, const double* B, int m, int n, int K, double* C) {
+  if (m <= 0 || n <= 0) return;
+  const dim3 grid(nbl(n, 32), nbl(m, 32));
+  k_gemm_df_nt<32><<<grid, 256, 0, c->stream>>>(A, B, m, n, K, C);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
