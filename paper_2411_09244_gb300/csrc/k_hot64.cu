@@ -1720,7 +1720,9 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
       parareal_lp(c, H, M, probe, &f_ms, nullptr, nullptr, 0);
       double sc = state_scale(c, H, M.Yu, M.Yw, M.CM32);
       y.eps = eps;  // the jumps stop at eps or at the precision floor
-      y.wr_tol = std::max(wr_tol, PINT_CORR_REL_TOL * sc);
+      // WR to 1e-6 of the correction's scale, but no tighter than a tenth of
+      // the jump tolerance the correction solve stops at
+      y.wr_tol = std::max(wr_tol, std::max(PINT_CORR_REL_TOL * sc, 0.1 * eps));
       y.have_g0 = true;
     }
     parareal_lp(c, H, M, y, &f_ms, wr_hist, jump_hist, K1_total);
