@@ -648,29 +648,34 @@ __device__ __forceinline__ void small_dft(float* re, float* im) {
   }
 }
 
-// Transpose within each R-lane group (lane g holds X_g[0..R); afterwards it
-// holds X_0[g] .. X_{R-1}[g]) through shared memory: lane g writes its values
-// as row g of the group's R x R tile (rows padded to R + 1
-// floats, tiles R (R + 1) floats apart: no bank conflicts for R = 4, 8) and
-// reads column g back.  `tile` is this warp's area of 2 (32 / R) R (R + 1)
-// floats (real parts, then imaginary parts).
+// a[t] <- a[(t - g) mod R] for the lane's own g, as log2(R) selected rotations
 template <int R>
-__device__ __forceinline__ void tile_transpose(float* re, float* im, float* tile, int grp, int g) {
-  constexpr int TS = R * (R + 1);
-  float* tr = tile + grp * TS;
-  float* ti = tr + (32 / R) * TS;
-  __syncwarp();  // the previous use of the tile is read out
+__device__ __forceinline__ void rotate_right(float* a, int g) {
 #pragma unroll
-  for (int m = 0; m < R; ++m) {
-    tr[g * (R + 1) + m] = re[m];
-    ti[g * (R + 1) + m] = im[m];
-  }
-  __syncwarp();
+  for (int b = 1; b < R; b <<= 1) {
+    const bool on = (g & b) != 0;
+    float t2[R];
 #pragma unroll
-  for (int m = 0; m < R; ++m) {
-    re[m] = tr[m * (R + 1) + g];
-    im[m] = ti[m * (R + 1) + g];
+    for (int t = 0; t < R; ++t) t2[t] = a[(t - b + R) % R];
+#pragma unroll
+    for (int t = 0; t < R; ++t) a[t] = on ? t2[t] : a[t];
   }
+}
+
+// lane g of an R-lane group (first lane `base`) holds X_g[0..R); afterwards
+// it holds X_0[g] .. X_{R-1}[g].  Round t reads lane (g + t) mod R, which
+// sends X_{g+t}[g] once its registers are reversed and rotated by its g.
+template <int R>
+__device__ __forceinline__ void group_transpose(float* v, int g, int base) {
+  float a[R];
+#pragma unroll
+  for (int t = 0; t < R; ++t) a[t] = v[(R - t) % R];
+  rotate_right<R>(a, g);
+#pragma unroll
+  for (int t = 0; t < R; ++t) a[t] = __shfl_sync(0xffffffffu, a[t], base + ((g + t) & (R - 1)));
+  rotate_right<R>(a, g);
+#pragma unroll
+  for (int t = 0; t < R; ++t) v[t] = a[t];
 }
 
 __device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
@@ -698,7 +703,6 @@ __global__ void __launch_bounds__(256, 4) k_time_solve32_sq(const float* __restr
   __shared__ float sT[P * LD];   // right-hand sides, then the new states
   __shared__ float sO[P * LD];   // previous iterate u_{p+1}
   __shared__ float su0[NS];
-  __shared__ float sX[8][64 * (R + 1)];  // per-warp transpose tiles: 2 (32 / R) R (R + 1) floats
   const int nloc = blockIdx.y, i0 = blockIdx.x * NS;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float* Un = Ut + (size_t)nloc * (P + 1) * ldu;
@@ -734,7 +738,7 @@ __global__ void __launch_bounds__(256, 4) k_time_solve32_sq(const float* __restr
   __syncthreads();
   // one series per R-lane group; series s = warp + 8 j keeps the tile reads
   // free of bank conflicts for R = 8
-  const int g = lane % R, j = lane / R, s = warp + 8 * j;
+  const int g = lane % R, j = lane / R, s = warp + 8 * j, base = lane - g;
   const int i = i0 + s;
   const float li = (i < d1) ? lam1[i] : 0.f;
   float re[R], im[R], twr[R], twi[R];
@@ -756,7 +760,8 @@ __global__ void __launch_bounds__(256, 4) k_time_solve32_sq(const float* __restr
     re[a] = xr;
     im[a] = xi;
   }
-  tile_transpose<R>(re, im, sX[warp], j, g);
+  group_transpose<R>(re, g, base);
+  group_transpose<R>(im, g, base);
   small_dft<R, -1>(re, im);  // lane g: Y[g + R b]
 #pragma unroll
   for (int b = 0; b < R; ++b) {
@@ -773,7 +778,8 @@ __global__ void __launch_bounds__(256, 4) k_time_solve32_sq(const float* __restr
     re[a] = xr;
     im[a] = xi;
   }
-  tile_transpose<R>(re, im, sX[warp], j, g);
+  group_transpose<R>(re, g, base);
+  group_transpose<R>(im, g, base);
   small_dft<R, 1>(re, im);  // lane g: P y[g + R m]
   __syncthreads();          // every read of the right-hand sides is done
 #pragma unroll
