@@ -410,88 +410,6 @@ __global__ void k_jump(const double* __restrict__ Xu, const double* __restrict__
 }
 
 // max over n of sqrt(max(x_n, 0)) (x = squared jumps), flags non-finite values
-// The same jumps for all N coarse times in one pass over CM (FP32 coupling):
-// the w differences of every time sit in shared memory, each warp takes rows
-// of CM into registers (lane l: columns l + 32 k) and forms their products
-// with all N differences; lane l accumulates times n - 1 = l + 32 q.  CM is
-// read once instead of once per coarse time.  NPL = times per lane (N <= 32
-// NPL), NK = column blocks (d2 <= 32 NK).
-template <int NPL, int NK>
-__global__ void __launch_bounds__(256) k_jump_all(const double* __restrict__ Xu, const double* __restrict__ Xw,
-                                                  const double* __restrict__ Ou, const double* __restrict__ Ow,
-                                                  const float* __restrict__ CM, int d1, int d2, int N,
-                                                  double* __restrict__ jump2) {
-  extern __shared__ float sdw[];  // [N][d2]: w differences of times 1..N
-  __shared__ float sacc[8][32 * NPL];
-  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  for (int e = tid; e < N * d2; e += blockDim.x) {
-    const int n = e / d2 + 1, j = e - (n - 1) * d2;
-    sdw[e] = (float)(Xw[(size_t)n * d2 + j] - Ow[(size_t)n * d2 + j]);
-  }
-  __syncthreads();
-  float acc[NPL];
-#pragma unroll
-  for (int q = 0; q < NPL; ++q) acc[q] = 0.f;
-  if (blockIdx.x == 0) {  // ||dw||^2 per time
-#pragma unroll
-    for (int q = 0; q < NPL; ++q) {
-      const int n0 = lane + 32 * q;
-      if (warp == 0 && n0 < N)
-        for (int j = 0; j < d2; ++j) acc[q] = fmaf(sdw[(size_t)n0 * d2 + j], sdw[(size_t)n0 * d2 + j], acc[q]);
-    }
-  }
-  for (int i = blockIdx.x * 8 + warp; i < d1; i += gridDim.x * 8) {
-    float cm[NK];
-#pragma unroll
-    for (int k = 0; k < NK; ++k) {
-      const int j = lane + 32 * k;
-      cm[k] = j < d2 ? CM[(size_t)i * d2 + j] : 0.f;
-    }
-    float du[NPL];
-#pragma unroll
-    for (int q = 0; q < NPL; ++q) {
-      const int n = lane + 32 * q + 1;
-      du[q] = n <= N ? (float)(Xu[(size_t)n * d1 + i] - Ou[(size_t)n * d1 + i]) : 0.f;
-      acc[q] = fmaf(du[q], du[q], acc[q]);
-    }
-    // products with all N differences, four times at once
-    for (int n0 = 0; n0 < N; n0 += 4) {
-      float t[4];
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        t[h] = 0.f;
-        const int n = n0 + h;
-        if (n < N)
-#pragma unroll
-          for (int k = 0; k < NK; ++k) {
-            const int j = lane + 32 * k;
-            if (j < d2) t[h] = fmaf(cm[k], sdw[(size_t)n * d2 + j], t[h]);
-          }
-      }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int h = 0; h < 4; ++h) t[h] += __shfl_xor_sync(0xffffffffu, t[h], o);
-#pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const int n = n0 + h;  // time n + 1, owned by lane n % 32
-#pragma unroll
-        for (int q = 0; q < NPL; ++q)
-          if (n == lane + 32 * q) acc[q] = fmaf(2.f * du[q], t[h], acc[q]);
-      }
-    }
-  }
-#pragma unroll
-  for (int q = 0; q < NPL; ++q) sacc[warp][lane + 32 * q] = acc[q];
-  __syncthreads();
-  for (int n = tid; n < N; n += blockDim.x) {
-    float sum = 0.f;
-#pragma unroll
-    for (int w = 0; w < 8; ++w) sum += sacc[w][n];
-    atomicAdd(&jump2[n], (double)sum);
-  }
-}
-
 __global__ void k_max_fin(const double* __restrict__ x, int n, double* __restrict__ out) {
   __shared__ double sh[64];
   double m = 0.0, bad = 0.0;
@@ -917,45 +835,6 @@ static void stage_amp(Ctx* c, Hot& H, const double* amp_dev, int count) {
     PINT_CUDA(cudaMemcpyAsync(H.amp, amp_dev, (size_t)count * 8, cudaMemcpyDeviceToDevice, c->stream));
   else
     k_fill<<<nb_(count, 256), 256, 0, c->stream>>>(H.amp, count, 1.0);
-}
-
-// jumps of times 1..N into jump2 (zeroed by the caller) with the FP32
-// coupling: one pass over CM when an instantiated shape covers (N, d2) and the
-// differences fit in shared memory, else the per-time kernel
-static void jumps_f32(Ctx* c, const double* Xu, const double* Xw, const double* Ou, const double* Ow,
-                      const float* CM32, double* jump2) {
-  const int N = c->N, d1 = c->d1, d2 = c->d2;
-  const size_t smem = (size_t)N * d2 * 4;
-  const int blocks = std::min(64, (d1 + 7) / 8);
-  auto go = [&](auto kern) {
-    // raise each instantiation's shared-memory limit once (the instantiations
-    // share one function type, so they are told apart by address)
-    static std::vector<const void*> raised;
-    {
-      std::lock_guard<std::mutex> lock(lazy_init_mutex());
-      const void* key = reinterpret_cast<const void*>(kern);
-      if (std::find(raised.begin(), raised.end(), key) == raised.end()) {
-        PINT_CUDA(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-        raised.push_back(key);
-      }
-    }
-    kern<<<blocks, 256, smem, c->stream>>>(Xu, Xw, Ou, Ow, CM32, d1, d2, N, jump2);
-  };
-  if (smem <= 200 * 1024 && N <= 64 && d2 <= 288) {
-    const int nk = (d2 + 31) / 32;
-    if (N <= 32) {
-      if (nk <= 3) go(k_jump_all<1, 3>);
-      else if (nk <= 5) go(k_jump_all<1, 5>);
-      else go(k_jump_all<1, 9>);
-    } else {
-      if (nk <= 3) go(k_jump_all<2, 3>);
-      else if (nk <= 5) go(k_jump_all<2, 5>);
-      else go(k_jump_all<2, 9>);
-    }
-  } else {
-    k_jump<float><<<dim3(N, JS), 256, 0, c->stream>>>(Xu, Xw, Ou, Ow, CM32, d1, d2, jump2);
-  }
-  PINT_LAUNCH_CHECK();
 }
 
 static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw, const float* CM32);
@@ -1656,7 +1535,7 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
     g_sweep_lp(c, H, M, r.Xu, r.Xw, r.amp, H.Fu, H.Fw, r.Cu, r.Cw, n_lo, false);
     PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
     if (M.CM32)
-      jumps_f32(c, r.Xu, r.Xw, H.Ou, H.Ow, M.CM32, H.red + 8);
+      k_jump<float><<<dim3(N, JS), 256, 0, c->stream>>>(r.Xu, r.Xw, H.Ou, H.Ow, M.CM32, d1, d2, H.red + 8);
     else
       k_jump<double><<<dim3(N, JS), 256, 0, c->stream>>>(r.Xu, r.Xw, H.Ou, H.Ow, c->CM, d1, d2, H.red + 8);
     k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
@@ -1697,7 +1576,7 @@ static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw, co
   // relative tolerances: the FP32 coupling serves as well as the FP64 one)
   PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
   if (CM32)
-    jumps_f32(c, Xu, Xw, H.tmp1, H.tmp1, CM32, H.red + 8);
+    k_jump<float><<<dim3(N, JS), 256, 0, c->stream>>>(Xu, Xw, H.tmp1, H.tmp1, CM32, d1, d2, H.red + 8);
   else
     k_jump<double><<<dim3(N, JS), 256, 0, c->stream>>>(Xu, Xw, H.tmp1, H.tmp1, c->CM, d1, d2, H.red + 8);
   k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
