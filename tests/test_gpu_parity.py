@@ -190,3 +190,23 @@ def test_sequential_batched_fine_propagator(pair):
     u, w = orc.sequential()
     ref = orc.fine_field(u, w)[1:]
     assert rel(fs.cpu().numpy(), ref) < 1e-10
+
+
+def test_paper_example_shape_non_power_of_two_P():
+    """The paper's first experiment uses P = 30 fine steps per interval (N = 20): the
+    time solve then runs the generic (non power-of-two) DFT kernels on both paths.
+    Algorithm 1 must reach the sequential fine scheme: FP64 to 1e-10, mixed to 1e-6."""
+    from paper_2411_09244_gb300._lib import PINT_MIXED, PINT_FP64
+    prob = config_small(n_f=40, nc=4, J=2, ell=2, N=20, P=30, channels=3, contrast=1e4, f_kind="gauss")
+    orc = OracleRun(prob)
+    u, w = orc.sequential()
+    ref = orc.fine_field(u, w)[1:]
+    p = api.from_problem(prob, device="cuda", T=orc.T)
+    try:
+        _, f64, st = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-13, wr_tol=1e-15, wr_max=400)
+        assert rel(f64.cpu().numpy(), ref) < 1e-10
+        p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=PINT_MIXED)
+        _, fm, _ = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-13, wr_max=400)
+        assert rel(fm.cpu().numpy(), ref) < 1e-6
+    finally:
+        p.close()
