@@ -44,6 +44,8 @@ def parse():
     ap.add_argument("--tuning", default=None,
                     help="JSON tuning table: loaded before the run if present, written after it")
     ap.add_argument("--batch", type=int, default=16, help="instances of the many-instance workload (c4)")
+    ap.add_argument("--workers", type=int, default=0,
+                    help="host worker threads of the many-instance batch (0: min(instances, 16))")
     ap.add_argument("--batch-sizes", default="64,96,128",
                     help="fine grid sizes drawn for the c4 instances (comma separated)")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "mixed_f32"])
@@ -437,7 +439,7 @@ def run_batch(args, rank, world):
     plan = api.BatchPlan(pints, probs, want_fine=True)
 
     def concurrent():
-        return plan.run()
+        return plan.run(args.workers)
 
     for _ in range(args.warmup):
         timed(sequential)                       # first: the autotuner times each shape alone
@@ -462,7 +464,7 @@ def run_batch(args, rank, world):
     for it in range(args.warmup + args.steps):
         torch.cuda.synchronize()
         t0 = time.perf_counter()
-        hplan.run()
+        hplan.run(args.workers)
         torch.cuda.synchronize()
         if it >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
@@ -494,8 +496,9 @@ def run_batch(args, rank, world):
                        "accuracy_note": "rel_l2_vs_fp64: over each instance's whole trajectory, max over "
                                         "instances; _max_t: per coarse time (u0 = 0, so the first states "
                                         "are orders of magnitude below the solver's state scale)",
-                       "schedule": "pint_batch_solve: one context and CUDA stream per instance, library worker "
-                                   "threads taking the longest instance first; contraction tiles per shape "
+                       "schedule": f"pint_batch_solve: one context and CUDA stream per instance, "
+                                   f"{args.workers or min(args.batch, 16)} library worker threads taking the longest "
+                                   "instance first; contraction tiles per shape "
                                    + ("from the launch cost model" if args.no_autotune else
                                       f"measured by the autotuner ({len(api.tuning_table())} shapes)"),
                        "parallelism": "replicas" if world > 1 else "single GPU"},
