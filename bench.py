@@ -330,6 +330,7 @@ def run_ours(args, rank, world):
         "config": {"workload": f"{prob.name}: {prob.n_f}x{prob.n_f} fine, {prob.nc}x{prob.nc} coarse, "
                                f"J={prob.J}, ell={prob.ell}, N={prob.N} x P={prob.P}, T={p.T:g}",
                    "d1": info["d1"], "d2": info["d2"], "gamma": info["gamma"],
+                   "reduced_dof_steps_per_s": world * (info["d1"] + info["d2"]) * prob.N * prob.P / t_step,
                    "lambda_max22": info["lambda_max22"], "precision": args.precision,
                    "K1": st["K1"], "wr_total": st["wr_total"], "wr_iters": st["wr_iters"],
                    "rel_l2_vs_fp64_max_t": rel_err, "fp64_gpu_value": dofsteps / (st64["solve_ms"] / 1e3),
