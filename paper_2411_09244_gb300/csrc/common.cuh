@@ -140,6 +140,8 @@ struct Ctx {
   // scratch for solves (grown on demand)
   std::vector<std::pair<void*, size_t>> scratch;
   int launches = 0;
+  unsigned graph_epoch = 0;            // bumped whenever hot-path buffers are reallocated
+  cudaStream_t cap_stream = nullptr;   // private stream for capturing CUDA graphs
 };
 
 void* dalloc(Ctx* c, size_t bytes);

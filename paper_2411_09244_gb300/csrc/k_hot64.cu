@@ -21,7 +21,10 @@
 #include <cstring>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <cstdint>
+#include <map>
 
 namespace pint {
 
@@ -474,6 +477,7 @@ static void ensure(Ctx* c, Hot& H, int cap) {
   // ones until pint_destroy, which only happens when the time grid changes
   const int N = c->N, P = c->P, d1 = c->d1, d2 = c->d2;
   cap = std::max(cap, N);
+  c->graph_epoch++;  // captured graphs refer to the old buffers
   auto A = [&](size_t n) { return (double*)dalloc(c, std::max<size_t>(n, 1) * 8); };
   H.N = N;
   H.P = P;
@@ -1097,6 +1101,7 @@ void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* 
 void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
                       const float* Blo, int ncols, int nsplit, int tn, float* out, int* err, const int* gate);
 void umma_plan(int M, int Kp, int ncols, int maxs, int* tn, int* s);
+void umma_prepare();
 void umma_choose(Ctx* c, bool tune, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
                  const float* Blo, int ncols, int maxs, float* out, int* err, int* tn, int* s);
 void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const float* lam1, const float* src,
@@ -1158,6 +1163,11 @@ struct Mx {
   double* nrm = nullptr;   // device: (norm, bad) per WR iteration
   double* hnrm = nullptr;  // pinned host copy of nrm
   cudaEvent_t iev[2][5] = {};  // per in-flight iteration: contraction brackets + norm ready
+  // one WR iteration as a CUDA graph per (sweep shape, parity); value: the
+  // instantiated graph and the kernel launches it holds
+  std::map<std::array<uintptr_t, 9>, std::pair<cudaGraphExec_t, int>> graphs;
+  unsigned graph_epoch = 0;
+  bool graphs_off = false;  // capture failed once: issue the iterations directly
   float* CA32 = nullptr;  // FP32 coupling of the cluster coarse sweep
   float* CM32 = nullptr;  // FP32 coupling of the jump norms
   // FP32 copies for the cluster coarse sweep: F ends, old G values, jumps
@@ -1173,13 +1183,20 @@ struct Mx {
   std::vector<void*> bufs;  // every device buffer above
 };
 
+static void mx_drop_graphs(Mx& M) {
+  for (auto& g : M.graphs) cudaGraphExecDestroy(g.second.first);
+  M.graphs.clear();
+}
+
 static Mx& mx_prepare(Ctx* c) {
   if (c->scratch.empty()) c->scratch.push_back({new Mx(), 0});
   Mx& M = *reinterpret_cast<Mx*>(c->scratch[0].first);
   const int N = c->N, P = c->P, d1 = c->d1, d2 = c->d2;
   const bool tensor = (c->precision == PINT_MIXED);
   if (M.ready && M.N == N && M.P == P && M.d1 == d1 && M.d2 == d2 && M.tensor == tensor) return M;
+  c->graph_epoch++;  // captured graphs refer to the old buffers
   if (M.ready) {  // shapes or precision changed: release the old buffers (keep host-side resources)
+    mx_drop_graphs(M);
     for (void* b : M.bufs) dfree(c, b);
     double* hn = M.hnrm;
     cudaEvent_t ev[2][5];
@@ -1366,6 +1383,7 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
     umma_choose(c, c->autotune, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, MX_MAX_SPLIT, M.S, M.err, &tn1,
                 &nsl);
   }
+  if (tensor) umma_prepare();  // before any capture
   PINT_CUDA(cudaMemsetAsync(M.gate, 0, 4, c->stream));
   // squared update norms of the first iteration start at zero; the stopping
   // test at the end of each iteration clears them for the next
@@ -1373,24 +1391,87 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
   // One WR iteration; every launch is a no-op once the stopping test of an
   // earlier iteration has set the gate, so the host can queue iteration
   // it + 1 before it reads the norm of iteration it (no idle GPU between them).
-  auto enqueue = [&](int it) {
-    cudaEvent_t* ev = M.iev[it & 1];
-    PINT_CUDA(cudaEventRecord(ev[0], c->stream));
+  // Iterations of equal parity are identical stream work (norm slots and
+  // events alternate), so each is captured once as a CUDA graph and replayed:
+  // one launch per iteration instead of ten stream operations.
+  auto body = [&](int par, bool capturing) {
+    cudaEvent_t* ev = M.iev[par];
+    auto rec = [&](cudaEvent_t e) {
+      if (capturing) PINT_CUDA(cudaEventRecordWithFlags(e, c->stream, cudaEventRecordExternal));
+      else PINT_CUDA(cudaEventRecord(e, c->stream));
+    };
+    rec(ev[0]);
     if (tensor) mx_contract_umma(c, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, tn0, M.R, M.err, M.gate);
     else mx_contract32(c, 0, M.AR32, d1, 2 * ldw, Ut, Wt, ldu, ldw, P, ncols, M.R, M.gate);
-    PINT_CUDA(cudaEventRecord(ev[1], c->stream));
+    rec(ev[1]);
     mx_time_solve32(c, M.R, nact, Ut, ldu, M.lam1f, srcU, M.b1f, amp_act, M.twf, M.dshf, M.dshbr, M.bpowf, acc32,
                     M.B1h, M.B1l, M.gate);
-    PINT_CUDA(cudaEventRecord(ev[2], c->stream));
+    rec(ev[2]);
     if (tensor)
       mx_contract_umma(c, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, nsl, tn1, M.S, M.err, M.gate);
     else mx_contract32(c, 1, M.AS32, d2, 2 * ldu, Ut, Wt, ldu, ldw, P, ncols, M.S, M.gate);
-    PINT_CUDA(cudaEventRecord(ev[3], c->stream));
+    rec(ev[3]);
     mx_w_sweep32(c, M.S, tensor ? nsl : 1, (size_t)ncols * d2, nact, Wt, ldw, M.lam2f, srcW, M.b2f, amp_act,
                  acc32 + (size_t)nact * P, M.B0h, M.B0l,
-                 WrStop{acc32, 2 * nact * P, wr_tol, M.gate, M.nrm + 2 * it, M.wcount});
-    PINT_CUDA(cudaMemcpyAsync(M.hnrm + 2 * it, M.nrm + 2 * it, 16, cudaMemcpyDeviceToHost, c->stream));
-    PINT_CUDA(cudaEventRecord(ev[4], c->stream));
+                 WrStop{acc32, 2 * nact * P, wr_tol, M.gate, M.nrm + 2 * par, M.wcount});
+    PINT_CUDA(cudaMemcpyAsync(M.hnrm + 2 * par, M.nrm + 2 * par, 16, cudaMemcpyDeviceToHost, c->stream));
+    rec(ev[4]);
+  };
+  uint64_t tol_bits = 0;
+  std::memcpy(&tol_bits, &wr_tol, 8);
+  auto enqueue = [&](int it) {
+    const int par = it & 1;
+    if (M.graphs_off) {
+      body(par, false);
+      return;
+    }
+    if (M.graph_epoch != c->graph_epoch) {
+      mx_drop_graphs(M);
+      M.graph_epoch = c->graph_epoch;
+    }
+    const std::array<uintptr_t, 9> key{(uintptr_t)Ut, (uintptr_t)Wt, (uintptr_t)srcU, (uintptr_t)srcW,
+                                       (uintptr_t)amp_act, (uintptr_t)nact,
+                                       (uintptr_t)(tn0 | (tn1 << 10) | (nsl << 20) | ((tensor ? 1 : 0) << 24)),
+                                       (uintptr_t)tol_bits, (uintptr_t)par};
+    auto f = M.graphs.find(key);
+    if (f == M.graphs.end()) {
+      // capture on a private stream (the caller's may be the legacy stream,
+      // which cannot be captured); the graph is then launched on the caller's
+      if (!c->cap_stream) PINT_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
+      cudaStream_t user = c->stream;
+      const int l0 = c->launches;
+      cudaGraph_t g = nullptr;
+      c->stream = c->cap_stream;
+      cudaError_t e = cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal);
+      if (e == cudaSuccess) {
+        try {
+          body(par, true);
+        } catch (...) {
+          cudaStreamEndCapture(c->stream, &g);
+          if (g) cudaGraphDestroy(g);
+          c->stream = user;
+          c->launches = l0;
+          cudaGetLastError();
+          throw;
+        }
+        e = cudaStreamEndCapture(c->stream, &g);
+      }
+      c->stream = user;
+      const int kernels = c->launches - l0;  // the kernels the body launched while capturing
+      c->launches = l0;
+      cudaGraphExec_t ex = nullptr;
+      if (e == cudaSuccess) e = cudaGraphInstantiate(&ex, g, 0);
+      if (g) cudaGraphDestroy(g);
+      if (e != cudaSuccess) {  // not capturable here: issue the stream work directly from now on
+        cudaGetLastError();
+        M.graphs_off = true;
+        body(par, false);
+        return;
+      }
+      f = M.graphs.emplace(key, std::make_pair(ex, kernels)).first;
+    }
+    PINT_CUDA(cudaGraphLaunch(f->second.first, c->stream));
+    c->launches += f->second.second;
   };
   int it = 0;
   *bad = false;
@@ -1411,7 +1492,7 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
   for (it = 1; it <= wr_max; ++it) {
     if (it < wr_max) enqueue(it + 1);  // look-ahead: gated no-op if iteration it converges
     account(it);
-    const double nrm = M.hnrm[2 * it], flag = M.hnrm[2 * it + 1];
+    const double nrm = M.hnrm[2 * (it & 1)], flag = M.hnrm[2 * (it & 1) + 1];
     if (flag != 0.0 || !(nrm == nrm)) {
       *bad = true;
       break;
@@ -1590,12 +1671,17 @@ static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw, co
 void mixed_release(Ctx* c) {
   if (!c->scratch.empty()) {
     Mx* M = reinterpret_cast<Mx*>(c->scratch[0].first);
+    mx_drop_graphs(*M);
     if (M->hnrm) cudaFreeHost(M->hnrm);
     for (auto& row : M->iev)
       for (auto& e : row)
         if (e) cudaEventDestroy(e);
     delete M;
     c->scratch.clear();
+  }
+  if (c->cap_stream) {
+    cudaStreamDestroy(c->cap_stream);
+    c->cap_stream = nullptr;
   }
 }
 

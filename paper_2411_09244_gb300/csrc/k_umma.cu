@@ -372,16 +372,24 @@ void umma_plan(int M, int Kp, int ncols, int maxs, int* tn_out, int* s_out) {
 // ([M][Kp]), B = Bhi + Blo ([ncols][Kp]), TF32 pairs in FP32 containers, both
 // 16-byte aligned with Kp a multiple of 32 nsplit.  gate (device, may be
 // null): the launch does nothing when *gate != 0.
-void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
-                      const float* Blo, int ncols, int nsplit, int tn, float* out, int* err, const int* gate) {
+// one-time setup of the contraction (kernel attribute, driver entry point):
+// callers that capture the launches into a CUDA graph run it beforehand
+void umma_prepare() {
   static bool attr = false;
   {
-  std::lock_guard<std::mutex> lock(lazy_init_mutex());
-  if (!attr) {
-    PINT_CUDA(cudaFuncSetAttribute(k_wr_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
-    attr = true;
+    std::lock_guard<std::mutex> lock(lazy_init_mutex());
+    if (!attr) {
+      PINT_CUDA(cudaFuncSetAttribute(k_wr_umma, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+      attr = true;
+    }
   }
-  }
+  (void)encode_fn();
+  (void)umma_sms();
+}
+
+void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
+                      const float* Blo, int ncols, int nsplit, int tn, float* out, int* err, const int* gate) {
+  umma_prepare();
   PINT_REQUIRE(nsplit >= 1 && Kp % (KB * nsplit) == 0, PINT_ERR_BAD_ARG,
                "contraction K not divisible by the split");
   PINT_REQUIRE(tn >= 32 && tn <= TNMAX && tn % 32 == 0, PINT_ERR_BAD_ARG, "contraction tile width");
