@@ -210,3 +210,28 @@ def test_paper_example_shape_non_power_of_two_P():
         assert rel(fm.cpu().numpy(), ref) < 1e-6
     finally:
         p.close()
+
+
+def test_mixed_solve_after_reassembly_matches_fresh_context():
+    """The WR iterations of the mixed path are replayed from captured CUDA graphs
+    that refer to the context's buffers; re-assembling with another time grid
+    reallocates them, and the next solve must equal a fresh context's."""
+    from paper_2411_09244_gb300._lib import PINT_MIXED
+    prob = config_small(n_f=24, nc=4, J=3, ell=2, N=6, P=16, channels=3, contrast=1e4, f_kind="gauss")
+    orc = OracleRun(prob)
+    p = api.from_problem(prob, device="cuda", T=orc.T)
+    q = api.from_problem(prob, device="cuda", T=orc.T)
+    try:
+        p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=PINT_MIXED)
+        p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-12)          # captures graphs
+        p.assemble_reduced(orc.T, 4, 32, prob.alpha, precision=PINT_MIXED)  # other grid
+        p.parareal_solve(prob.u0, prob.f, np.ones(4), eps=1e-12)
+        p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=PINT_MIXED)
+        _, fp, sp = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-12)
+        q.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=PINT_MIXED)
+        _, fq, sq = q.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-12)
+        assert sp["K1"] == sq["K1"] and sp["wr_total"] == sq["wr_total"]
+        assert rel(fp.cpu().numpy(), fq.cpu().numpy()) < 1e-9
+    finally:
+        p.close()
+        q.close()
