@@ -159,6 +159,11 @@ def umma_traffic():
     return UMMA_TRAFFIC["bytes"] if h == UMMA_TRAFFIC["sha1"] else None
 
 
+def workload_desc(prob):
+    return (f"{prob.name}: {prob.n_f}x{prob.n_f} fine, {prob.nc}x{prob.nc} coarse, J={prob.J}, "
+            f"ell={prob.ell}, N={prob.N} x P={prob.P}")
+
+
 def problem(name):
     from paper_2411_09244_gb300 import inputs
     return {"c1": inputs.config_c1, "c2": inputs.config_c2, "c5": inputs.config_c5}[name]()
@@ -327,8 +332,7 @@ def run_ours(args, rank, world):
         "vs_baseline": None,
         "dtype": {"fp64": "f64", "mixed": "tf32x3/f32 + f64 refinement", "mixed_f32": "f32 + f64 refinement"}[args.precision],
         "data": "synthetic (seeded splitmix64 high-contrast channels/inclusions; paper fields unavailable)",
-        "config": {"workload": f"{prob.name}: {prob.n_f}x{prob.n_f} fine, {prob.nc}x{prob.nc} coarse, "
-                               f"J={prob.J}, ell={prob.ell}, N={prob.N} x P={prob.P}, T={p.T:g}",
+        "config": {"workload": workload_desc(prob), "T": p.T,
                    "d1": info["d1"], "d2": info["d2"], "gamma": info["gamma"],
                    "reduced_dof_steps_per_s": world * (info["d1"] + info["d2"]) * prob.N * prob.P / t_step,
                    "lambda_max22": info["lambda_max22"], "precision": args.precision,
@@ -376,7 +380,7 @@ def run_reference(args, rank, world):
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": D * prob.N * prob.P / v * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": prob.name},
+            "data": "synthetic", "config": {"workload": workload_desc(prob)},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0}}
 
@@ -487,7 +491,7 @@ def run_batch(args, rank, world):
             "dtype": {"fp64": "f64", "mixed": "tf32x3/f32 + f64 refinement",
                       "mixed_f32": "f32 + f64 refinement"}[args.precision],
             "data": "synthetic (seeded splitmix64 high-contrast fields, many-instance recipe)",
-            "config": {"workload": f"c4 subset: {args.batch} instances per GPU, fine grids from {sizes}, "
+            "config": {"workload": f"many-instance batch: {args.batch} instances per GPU, fine grids from {sizes}, "
                                    f"8-cell blocks, J 2-4, contrast 10^U(3,6), N in (16,32,64), P=32, ell=2",
                        "instances": [{"n_f": pr.n_f, "J": pr.J, "N": pr.N, "K1": r[2]["K1"],
                                       "wr_total": r[2]["wr_total"]} for pr, r in zip(probs, res)],

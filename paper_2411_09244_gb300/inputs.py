@@ -167,7 +167,7 @@ def config_c1(instance: int = 0) -> Problem:
     n_f = 64
     kappa = paint_kappa(rng, n_f, 8, 1e4, 2)
     nn = (n_f + 1) ** 2
-    return Problem("c1_64x64_fp64", n_f, 8, 2, 2, 8, 16, 0.1, 1e-10, None, kappa,
+    return Problem("channels_64x64", n_f, 8, 2, 2, 8, 16, 0.1, 1e-10, None, kappa,
                    np.ones(nn), np.zeros(nn), np.ones(8), {"contrast": 1e4})
 
 
@@ -180,7 +180,7 @@ def config_c2(instance: int = 0) -> Problem:
     kappa = paint_kappa(rng, n_f, 40, 1e6, 2, n_incl=60, incl_value=1e6)
     f = gaussian_sum(rng, n_f, 10)
     nn = (n_f + 1) ** 2
-    return Problem("c2_256x256_mixed", n_f, 16, 4, 4, 64, 64, 0.1, 1e-10, None, kappa,
+    return Problem("channels_inclusions_256x256", n_f, 16, 4, 4, 64, 64, 0.1, 1e-10, None, kappa,
                    f, np.zeros(nn), np.ones(64), {"contrast": 1e6})
 
 
@@ -198,7 +198,7 @@ def config_c3(instance: int = 0) -> Problem:
     f = np.exp(-((X - 0.5) ** 2 + (Y - 0.5) ** 2) / (2 * 0.1 ** 2))
     a16 = np.array([rng.uniform(0.5, 1.5) for _ in range(16)])
     amp = np.repeat(a16, 2)
-    return Problem("c3_128x128_adjoint", n_f, 16, 3, 2, 32, 32, 0.1, 1e-10, None, kappa,
+    return Problem("observed_128x128", n_f, 16, 3, 2, 32, 32, 0.1, 1e-10, None, kappa,
                    f, u0, amp, {"contrast": 1e5, "amp16": a16})
 
 
@@ -220,7 +220,7 @@ def config_c4(instance: int = 0, sizes=(64, 96, 128, 192, 256)) -> Problem:
     kappa = paint_kappa(rng, n_f, n_ch, contrast, 2, n_incl=n_in, incl_value=contrast)
     f = gaussian_sum(rng, n_f, 10)
     nn = (n_f + 1) ** 2
-    return Problem(f"c4_{instance}_{n_f}", n_f, n_f // 8, J, 2, N, 32, 0.1, -1e-10, None, kappa, f,
+    return Problem(f"batch_{instance}_{n_f}x{n_f}", n_f, n_f // 8, J, 2, N, 32, 0.1, -1e-10, None, kappa, f,
                    np.zeros(nn), np.ones(N), {"contrast": contrast, "channels": n_ch, "inclusions": n_in})
 
 
@@ -232,7 +232,7 @@ def config_c5(instance: int = 0) -> Problem:
     kappa = paint_kappa(rng, n_f, 200, 1e6, 2, n_incl=400, incl_value=1e6)
     f = gaussian_sum(rng, n_f, 10)
     nn = (n_f + 1) ** 2
-    return Problem("c5_1024x1024_large", n_f, 32, 4, 4, 256, 32, 0.1, 1e-10, None, kappa,
+    return Problem("channels_inclusions_1024x1024", n_f, 32, 4, 4, 256, 32, 0.1, 1e-10, None, kappa,
                    f, np.zeros(nn), np.ones(256), {"contrast": 1e6})
 
 
