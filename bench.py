@@ -53,14 +53,18 @@ def parse():
     return ap.parse_args()
 
 
-def dist_init(args):
+def dist_init(args=None):
+    """Ranks from the torchrun environment; NCCL on GPUs, gloo without (tests)."""
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     if world > 1:
         import torch.distributed as dist
         import torch
-        torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
-        dist.init_process_group("nccl")
+        if torch.cuda.is_available():
+            torch.cuda.set_device(int(os.environ.get("LOCAL_RANK", "0")))
+            dist.init_process_group("nccl")
+        else:
+            dist.init_process_group("gloo")
     return rank, world
 
 
@@ -75,9 +79,16 @@ def max_over_ranks(x, world):
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([x], dtype=torch.float64, device=dev)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def batch_instances(rank, batch):
+    """Seeded instances of one rank in the many-instance run: disjoint blocks per
+    rank (weak scaling, no exchange between ranks)."""
+    return [rank * batch + i for i in range(batch)]
 
 
 class ClockSampler:
@@ -361,6 +372,9 @@ def run_reference(args, rank, world):
     """The oracle timed on the host cores: each step a bounded sample."""
     if rank != 0:
         return None
+    if args.config not in ("c1", "c2"):
+        return {"impl": "reference", "unavailable": "the oracle's timed sample is defined for the 64x64 and "
+                                                    "256x256 workloads only"}
     prob = problem(args.config)
     # dimensions and iteration counts of this workload as measured on the GPU
     # path (the same algorithm converges in the same counts)
@@ -397,7 +411,7 @@ def run_batch(args, rank, world):
     torch.cuda.set_device(dev)
     sizes = tuple(int(x) for x in args.batch_sizes.split(","))
     # instances of this rank (weak scaling: each rank its own seeded block)
-    probs = [inputs.config_c4(rank * args.batch + i, sizes=sizes) for i in range(args.batch)]
+    probs = [inputs.config_c4(i, sizes=sizes) for i in batch_instances(rank, args.batch)]
     prec = {"fp64": _lib.PINT_FP64, "mixed": _lib.PINT_MIXED, "mixed_f32": _lib.PINT_MIXED_F32}[args.precision]
     t0 = time.perf_counter()
     pints, refs = [], []
