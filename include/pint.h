@@ -23,8 +23,14 @@
  *   - All GPU work runs on the stream given to pint_setup_fine_grid (a
  *     cudaStream_t passed as void*; NULL = legacy default stream).  Calls
  *     that return host-visible results synchronise that stream before
- *     returning.
- *   - One context is not thread-safe; distinct contexts are independent.
+ *     returning.  The solves read convergence norms on the host between
+ *     launches, so they cannot themselves be captured into a caller's CUDA
+ *     graph; internally the PINT_MIXED solve captures each WR iteration once
+ *     (on a private stream of the context) and launches the graph on the
+ *     context's stream.
+ *   - One context is not thread-safe; distinct contexts are independent and
+ *     may be driven from different host threads at once (pint_batch_solve
+ *     does so).
  */
 #ifndef PINT_H
 #define PINT_H
