@@ -392,15 +392,26 @@ __global__ void k_jump(const double* __restrict__ Xu, const double* __restrict__
     for (int j = threadIdx.x; j < d2; j += blockDim.x) s += dw[j] * dw[j];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
   for (int i0 = part + JS * 32 * warp; i0 < d1; i0 += JS * 32 * nwarp) {
-    // 32 rows per warp pass; lane r keeps row i0 + JS r's product
+    // 32 rows per warp pass, four at a time (their loads and reductions
+    // interleaved); lane r keeps row i0 + JS r's product
     T mine = 0;
-    for (int r = 0; r < 32; ++r) {
-      const int i = i0 + JS * r;
-      if (i >= d1) break;
-      T t = 0;
-      for (int j = lane; j < d2; j += 32) t += CM[(size_t)i * d2 + j] * dw[j];
-      for (int o = 16; o > 0; o >>= 1) t += __shfl_xor_sync(0xffffffffu, t, o);
-      if (lane == r) mine = t;
+    for (int r0 = 0; r0 < 32; r0 += 4) {
+      if (i0 + JS * r0 >= d1) break;
+      T t[4];
+#pragma unroll
+      for (int h = 0; h < 4; ++h) {
+        const int i = i0 + JS * (r0 + h);
+        t[h] = 0;
+        if (i < d1)
+          for (int j = lane; j < d2; j += 32) t[h] += CM[(size_t)i * d2 + j] * dw[j];
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1)
+#pragma unroll
+        for (int h = 0; h < 4; ++h) t[h] += __shfl_xor_sync(0xffffffffu, t[h], o);
+#pragma unroll
+      for (int h = 0; h < 4; ++h)
+        if (lane == r0 + h) mine = t[h];
     }
     const int i = i0 + JS * lane;
     if (i < d1) {
