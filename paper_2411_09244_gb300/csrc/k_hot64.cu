@@ -45,6 +45,7 @@ struct Hot {
   double* nodes = nullptr;
   cudaEvent_t ev[4] = {nullptr, nullptr, nullptr, nullptr};
   unsigned* gsync = nullptr;  // grid-barrier counter, generation, error flag
+  std::vector<void*> bufs;    // the buffers above that ensure() sized
   double hot_ms = 0, hot_flops = 0;
   int hot_launches = 0;
 };
@@ -484,12 +485,18 @@ void hot_release(Ctx* c) {
 
 static void ensure(Ctx* c, Hot& H, int cap) {
   if (H.N == c->N && H.P == c->P && H.d1 == c->d1 && H.d2 == c->d2 && H.cap >= cap) return;
-  // buffers are owned by the context allocation list; resizing leaks the old
-  // ones until pint_destroy, which only happens when the time grid changes
+  // a new time grid or size: the old buffers go back to the pool (stream-ordered,
+  // after the work that used them)
+  for (void* b : H.bufs) dfree(c, b);
+  H.bufs.clear();
   const int N = c->N, P = c->P, d1 = c->d1, d2 = c->d2;
   cap = std::max(cap, N);
   c->graph_epoch++;  // captured graphs refer to the old buffers
-  auto A = [&](size_t n) { return (double*)dalloc(c, std::max<size_t>(n, 1) * 8); };
+  auto A = [&](size_t n) {
+    double* p = (double*)dalloc(c, std::max<size_t>(n, 1) * 8);
+    H.bufs.push_back(p);
+    return p;
+  };
   H.N = N;
   H.P = P;
   H.d1 = d1;
