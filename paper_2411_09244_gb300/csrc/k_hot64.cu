@@ -1778,6 +1778,7 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
   parareal_lp(c, H, M, m, &f_ms, wr_hist, jump_hist, 0);
   PINT_REQUIRE(!m.nonfinite, PINT_ERR_NONFINITE, "non-finite WR update or parareal jump");
   int K1_total = m.K1, wr_total = m.wr_total;
+  bool corr_converged = true;  // the correction solve met eps (the result's accuracy)
   // -- 2.-4. refinement ------------------------------------------------------
   PINT_CUDA(cudaEventRecord(r0, c->stream));
   for (int ref = 0; ref < n_refine; ++ref) {
@@ -1831,6 +1832,7 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
     }
     parareal_lp(c, H, M, y, &f_ms, wr_hist, jump_hist, K1_total);
     PINT_REQUIRE(!y.nonfinite, PINT_ERR_NONFINITE, "non-finite WR update or jump in the refinement");
+    if (!y.converged) corr_converged = false;
     K1_total += y.K1;
     wr_total += y.wr_total;
     // x_n = s_n + y_n
@@ -1878,7 +1880,7 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
   cudaEventDestroy(eP1);
   if (st) {
     st->K1 = K1_total;
-    st->converged = 1;
+    st->converged = corr_converged ? 1 : 0;
     st->wr_total = wr_total;
     st->solve_ms = ms;
     st->f_ms = f_ms;
@@ -1889,6 +1891,7 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
     st->hot_ms = H.hot_ms;
     st->hot_flops = H.hot_flops;
   }
+  PINT_REQUIRE(corr_converged, PINT_ERR_NOT_CONVERGED, "correction solve stopped at k_max above eps");
 }
 
 }  // namespace pint

@@ -235,3 +235,31 @@ def test_mixed_solve_after_reassembly_matches_fresh_context():
     finally:
         p.close()
         q.close()
+
+
+@pytest.mark.parametrize("mixed", [False, True])
+def test_not_converged_and_nonfinite_statuses(mixed):
+    """Failure statuses without any device fault: k_max below what eps needs
+    returns NOT_CONVERGED with the outputs and the jump history written; a
+    non-finite source makes the WR update norm non-finite and the solve
+    returns NONFINITE."""
+    from paper_2411_09244_gb300._lib import PINT_MIXED, PintError
+    prob = config_small(n_f=16, nc=4, J=2, ell=1, N=6, P=8, f_kind="gauss")
+    orc = OracleRun(prob)
+    p = api.from_problem(prob, device="cuda", T=orc.T)
+    try:
+        if mixed:
+            p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=PINT_MIXED)
+        coarse, fine, st = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-300, k_max=1)
+        assert st["status"] == "NOT_CONVERGED" and not st["converged"]
+        assert st["jumps"][0] > 0 and np.isfinite(coarse.cpu().numpy()).all()
+        assert np.isfinite(fine.cpu().numpy()).all()
+        bad = np.array(prob.f, dtype=np.float64)
+        bad[len(bad) // 2] = np.nan
+        with pytest.raises(PintError, match="NONFINITE"):
+            p.parareal_solve(prob.u0, bad, prob.amp, eps=1e-10)
+        # the context stays usable
+        _, _, st2 = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-10)
+        assert st2["converged"]
+    finally:
+        p.close()
