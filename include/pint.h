@@ -178,8 +178,10 @@ pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double 
  *   coarse_out  ptr or NULL, (N+1) x (d1+d2): (u_n, w_n) coefficients in the
  *               V_H1 / V_H2 bases at t_0..t_N
  *   stats       optional
- * Errors: BAD_ARG, STATE, NOT_CONVERGED (outputs still written), NONFINITE,
- * OOM, CUDA.
+ * Errors: BAD_ARG, STATE, NOT_CONVERGED (outputs and stats still written; on
+ * PINT_MIXED it means the correction solve stopped at k_max above eps),
+ * NONFINITE (a non-finite WR update or jump; the context stays usable),
+ * TIMEOUT (a bounded device wait ran out), OOM, CUDA.
  */
 pint_status pint_parareal_solve(pint_ctx* ctx, const double* u0_nodes, const double* f_shape,
                                 const double* amp, double eps, int k_max, double wr_tol,
