@@ -263,3 +263,26 @@ def test_not_converged_and_nonfinite_statuses(mixed):
         assert st2["converged"]
     finally:
         p.close()
+
+
+def test_wr_alpha_trade_off_on_the_gpu():
+    """The FP64 WR fine propagator on the GPU shows the oracle's alpha trade-off
+    (tests/test_oracle_wr_alpha.py): fewer iterations for alpha = 1e-4 than
+    1e-1, and a round-off floor far above the 1e-1 error at alpha = 1e-6."""
+    prob = config_small(n_f=16, nc=4, J=2, ell=1, N=4, P=8)
+    orc = OracleRun(prob)
+    x = np.concatenate([orc.u0, orc.w0])[None, :]
+    us, ws = orc.sch.F_seq(orc.u0, orc.w0, orc.F1, orc.F2)
+    ref = np.concatenate([us, ws])
+    p = api.from_problem(prob, device="cuda", T=orc.T)
+    res = {}
+    try:
+        for alpha in (1e-1, 1e-4, 1e-6):
+            p.assemble_reduced(orc.T, prob.N, prob.P, alpha)
+            F, it = p.apply_F(x, prob.f, np.ones(1), wr_tol=1e-13, wr_max=200)
+            res[alpha] = (it, rel(F.cpu().numpy()[0], ref))
+    finally:
+        p.close()
+    assert res[1e-4][0] < res[1e-1][0] < 200
+    assert res[1e-1][1] < 1e-11
+    assert res[1e-6][1] > 10 * res[1e-1][1]
