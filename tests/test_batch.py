@@ -109,3 +109,34 @@ def test_batch_equals_sequential_and_oracle():
     finally:
         for p in pints:
             p.close()
+
+
+@pytest.mark.gpu
+def test_batch_reports_the_failing_item():
+    """An item whose context has no time grid fails with STATE; the others are
+    solved, and the call returns the failing item's status and index."""
+    torch = pytest.importorskip("torch")
+    from paper_2411_09244_gb300 import api, _lib
+    probs = [config_c4(i, sizes=(32,)) for i in range(2)]
+    pints = []
+    try:
+        for k, prob in enumerate(probs):
+            s = torch.cuda.Stream()
+            with torch.cuda.stream(s):
+                p = api.Pint(prob.n_f, prob.kappa)
+                p.build_multiscale_spaces(prob.nc, prob.J, prob.ell)
+                if k == 0:
+                    p.assemble_reduced(None, prob.N, prob.P, prob.alpha)
+                else:  # no time grid yet: N, P and d for the outputs taken from the first
+                    p.info = dict(pints[0].info)
+                    p.N, p.P = probs[0].N, probs[0].P
+            pints.append(p)
+        probs[1].amp = probs[0].amp
+        plan = api.BatchPlan(pints, probs)
+        with pytest.raises(_lib.PintError, match="STATE") as ei:
+            plan.run()
+        assert "item 1" in str(ei.value)
+        assert plan.items[0].status == 0 and plan.items[1].status == -8
+    finally:
+        for p in pints:
+            p.close()
