@@ -99,6 +99,11 @@ __device__ __forceinline__ float ld_dsmem(uint32_t a) {
 __device__ __forceinline__ void st_dsmem(uint32_t a, float v) {
   asm volatile("st.shared::cluster.f32 [%0], %1;" ::"r"(a), "f"(v) : "memory");
 }
+__device__ __forceinline__ void st_dsmem4(uint32_t a, float4 v) {  // a 16-byte aligned
+  asm volatile("st.shared::cluster.v4.f32 [%0], {%1, %2, %3, %4};" ::"r"(a), "f"(v.x), "f"(v.y), "f"(v.z),
+               "f"(v.w)
+               : "memory");
+}
 
 template <int CL>
 __global__ void __launch_bounds__(GC_THREADS, 1) k_g_sweep_cl(GcArgs a, int nb) {
@@ -443,13 +448,19 @@ __global__ void __launch_bounds__(GR_THREADS, 1) k_g_sweep_clr(GcArgs a, int nb)
     __syncthreads();
     // this CTA's CA^T u' into its slot of every CTA's receive half
     float* rh = recv + (size_t)((n - a.n_lo) & 1) * GR_CL * d2p;
-    if (tid < d2) {
-      float sum = 0.f;
+    if (4 * tid < d2) {  // four columns per thread, 16-byte stores (rows are 16-byte aligned)
+      float4 sum = make_float4(0.f, 0.f, 0.f, 0.f);
 #pragma unroll
-      for (int w = 0; w < GR_WARPS; ++w) sum += wsum[(size_t)w * d2p + tid];
-      const float* slot = rh + (size_t)rank * d2p + tid;
+      for (int w = 0; w < GR_WARPS; ++w) {
+        const float4 t = reinterpret_cast<const float4*>(wsum + (size_t)w * d2p)[tid];
+        sum.x += t.x;
+        sum.y += t.y;
+        sum.z += t.z;
+        sum.w += t.w;
+      }
+      const float* slot = rh + (size_t)rank * d2p + 4 * tid;
 #pragma unroll
-      for (int r = 0; r < GR_CL; ++r) st_dsmem(dsmem_addr(slot, (uint32_t)r), sum);
+      for (int r = 0; r < GR_CL; ++r) st_dsmem4(dsmem_addr(slot, (uint32_t)r), sum);
     }
     cl_sync();  // every CTA's shares delivered to every CTA
     // the whole w' in every CTA, slots summed in rank order (identical copies)
