@@ -1201,6 +1201,8 @@ struct Mx {
   std::vector<void*> bufs;  // every device buffer above
 };
 
+constexpr size_t MX_MAX_GRAPHS = 512;  // captured WR iterations kept per context
+
 static void mx_drop_graphs(Mx& M) {
   for (auto& g : M.graphs) cudaGraphExecDestroy(g.second.first);
   M.graphs.clear();
@@ -1453,6 +1455,12 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
                                        (uintptr_t)tol_bits, (uintptr_t)par};
     auto f = M.graphs.find(key);
     if (f == M.graphs.end()) {
+      // the tolerance is part of the key and follows the solution's scale, so
+      // solves with ever new inputs keep adding graphs: bound the cache
+      if (M.graphs.size() >= MX_MAX_GRAPHS) {
+        PINT_CUDA(cudaStreamSynchronize(c->stream));  // no launch of a dropped graph in flight
+        mx_drop_graphs(M);
+      }
       // capture on a private stream (the caller's may be the legacy stream,
       // which cannot be captured); the graph is then launched on the caller's
       if (!c->cap_stream) PINT_CUDA(cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking));
