@@ -46,6 +46,9 @@ Steps, in the paper's order:
 """
 from __future__ import annotations
 
+import os
+from concurrent.futures import ThreadPoolExecutor
+
 import numpy as np
 import scipy.linalg as sla
 import scipy.sparse as sp
@@ -234,29 +237,45 @@ def cem_window(fp: FineProblem, blocks: dict, win: Window, target):
     return sol[:gid.size, :]
 
 
+def default_workers() -> int:
+    """Host threads for the independent per-block and per-window problems."""
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)
+
+
+def _map(fn, items, workers):
+    """[fn(x) for x in items], in order; the blocks and windows are
+    independent problems, so they may run on several threads (SciPy's sparse
+    LU and LAPACK release the GIL).  The result does not depend on workers."""
+    if workers <= 1 or len(items) <= 1:
+        return [fn(x) for x in items]
+    with ThreadPoolExecutor(max_workers=workers) as ex:
+        return list(ex.map(fn, items))
+
+
 class Spaces:
     """All bases and the V_H1 / V_H2 split for one FineProblem."""
 
-    def __init__(self, fp: FineProblem, J: int, ell: int):
+    def __init__(self, fp: FineProblem, J: int, ell: int, workers: int | None = None):
         self.fp = fp
         nc = fp.nc
         self.J, self.ell = J, ell
-        self.blocks = {}
-        for by in range(nc):
-            for bx in range(nc):
-                self.blocks[(bx, by)] = Block(fp, bx, by, J)
+        workers = default_workers() if workers is None else workers
+        keys = [(bx, by) for by in range(nc) for bx in range(nc)]
+        self.blocks = dict(zip(keys, _map(lambda k: Block(fp, k[0], k[1], J), keys, workers)))
         gpos = -np.ones((fp.n_f + 1) ** 2, dtype=np.int64)
         gpos[fp.interior] = np.arange(fp.D)
+        wins = {k: Window(fp, k[0], k[1], ell) for k in keys}
+        phis = _map(lambda k: cem_window(fp, self.blocks, wins[k], k), keys, workers)
         cols, kind, owner = [], [], []
-        for by in range(nc):
-            for bx in range(nc):
-                win = Window(fp, bx, by, ell)
-                phi = cem_window(fp, self.blocks, win, (bx, by))
-                full = np.zeros((fp.D, phi.shape[1]))
-                full[gpos[win.gid], :] = phi
-                cols.extend(full[:, c] for c in range(phi.shape[1]))
-                kind.extend(self.blocks[(bx, by)].kinds)
-                owner.extend([by * nc + bx] * phi.shape[1])
+        for (bx, by), phi in zip(keys, phis):
+            full = np.zeros((fp.D, phi.shape[1]))
+            full[gpos[wins[(bx, by)].gid], :] = phi
+            cols.extend(full[:, c] for c in range(phi.shape[1]))
+            kind.extend(self.blocks[(bx, by)].kinds)
+            owner.extend([by * nc + bx] * phi.shape[1])
         self.Psi_all = np.column_stack(cols)
         self.kind = np.array(kind)
         self.owner = np.array(owner)
