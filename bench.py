@@ -15,13 +15,17 @@ from __future__ import annotations
 
 import argparse
 import json
-import math
 import os
 import statistics
 import subprocess
 import sys
 import threading
 import time
+
+# the oracle (CPU baseline, reference arm) uses every host core the process may run on
+_CORES = len(os.sched_getaffinity(0))
+for _v in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS"):
+    os.environ.setdefault(_v, str(_CORES))
 
 import numpy as np
 
@@ -50,6 +54,10 @@ def parse():
                     help="fine grid sizes drawn for the c4 instances (comma separated)")
     ap.add_argument("--precision", default="mixed", choices=["fp64", "mixed", "mixed_f32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--coarse-fp64", action="store_true",
+                    help="mixed path: the low-precision solve's coarse sweeps in FP64 too (PINT_COARSE_FP64)")
+    ap.add_argument("--refine-fp64", action="store_true",
+                    help="mixed path: refinement residual contractions in FP64 (PINT_REFINE_FP64)")
     return ap.parse_args()
 
 
@@ -180,58 +188,93 @@ def problem(name):
     return {"c1": inputs.config_c1, "c2": inputs.config_c2, "c5": inputs.config_c5}[name]()
 
 
-def cpu_baseline(prob, d1, d2, K1, wr_total, budget_s=25.0, cache=None):
-    """The oracle's time stepping as it stands, on a synthetic reduced system
-    with the workload's dimensions (d1, d2, N, P): the shifted complex LU
-    setup of eq. (4.7), one WR iteration on a subset of intervals, one G
-    sweep; extrapolated to the solve with the measured K1 and WR counts.
-    With `cache`, the setup is timed once and reused by later samples; the
-    WR sample shrinks to one interval when budget_s is short."""
-    import types
-    from oracle.scheme import Scheme
-    cores = len(os.sched_getaffinity(0))
-    rng = np.random.default_rng(0)
+class OracleSampler:
+    """The oracle as it stands, timed on the host cores on the workload's own
+    operators.  Setup (the oracle's multiscale spaces and reduced matrices,
+    its time-grid factorisations) is done once and reported, not counted: the
+    GPU figure excludes setup too.  A sample times the units of the oracle's
+    solve: one WR iteration of the fine propagator on `nsub` intervals, one
+    coarse sweep over all N intervals, the prolongation of one state; a whole
+    solve is then  sum K0 x N x t_wr + (K1 + 1) x t_G + N x t_prolong,  with
+    K1 and the WR iterations of every sweep taken from a complete oracle
+    solve of the same workload (oracle/counts_<config>.json, written by
+    oracle/record_counts.py).  The 64x64 workload is small enough to time
+    whole solves instead."""
 
-    def spd(n, scale):
-        X = rng.normal(size=(n, n)) / math.sqrt(n)
-        return (X @ X.T + np.eye(n)) * scale
-
-    r = types.SimpleNamespace()
-    r.M11, r.A11 = spd(d1, 1e-3), spd(d1, 1.0)
-    r.M22, r.A22 = spd(d2, 1e-3), spd(d2, 1.0)
-    r.M12 = rng.normal(size=(d1, d2)) * 1e-5
-    r.A12 = rng.normal(size=(d1, d2)) * 1e-2
-    r.M21, r.A21 = r.M12.T, r.A12.T
-    r.d1, r.d2 = d1, d2
-    N, P = prob.N, prob.P
-    if cache is not None and "sch" in cache:
-        sch, t_setup = cache["sch"], cache["t_setup"]
-    else:
+    def __init__(self, config, prob):
+        from oracle.pipeline import OracleRun
+        from oracle.record_counts import load_counts
+        self.config, self.prob = config, prob
+        self.counts = load_counts(config)
         t0 = time.perf_counter()
-        sch = Scheme(r, T=1e-4, N=N, P=P, alpha=prob.alpha)
-        sch._shift_lu()
-        t_setup = time.perf_counter() - t0
-        if cache is not None:
-            cache.update(sch=sch, t_setup=t_setup)
-    nsub = max(1, min(N, 4 if budget_s >= 10 else 1))
-    starts = [(rng.normal(size=d1), rng.normal(size=d2)) for _ in range(nsub)]
-    F1 = [np.ones(d1)] * nsub
-    F2 = [np.ones(d2)] * nsub
-    t0 = time.perf_counter()
-    sch.F_wr(starts, F1, F2, wr_tol=0.0, wr_max=1)
-    t_wr = (time.perf_counter() - t0) * N / nsub
-    t0 = time.perf_counter()
-    u, w = starts[0]
-    for n in range(N):
-        u, w = sch.G(u, w, F1[0], F2[0])
-    t_g = time.perf_counter() - t0
-    t_solve = t_setup + wr_total * t_wr + (K1 + 1) * t_g
-    D = (prob.n_f - 1) ** 2
-    return {"value": D * N * P / t_solve, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": (f"oracle time stepping on a synthetic reduced system of the workload's size "
-                       f"(d1={d1}, d2={d2}, N={N}, P={P}): shifted-LU setup {t_setup:.1f}s, one WR "
-                       f"iteration on {nsub} of {N} intervals, one G sweep; extrapolated with "
-                       f"K1={K1}, sum K0={wr_total} to {t_solve:.1f}s per solve")}
+        self.run = OracleRun(prob)
+        self.setup_s = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        self.run.sch._shift_lu()          # the factorisations of eq. (4.7), once per time grid
+        self.grid_s = time.perf_counter() - t0
+        self.cores = int(os.environ.get("OPENBLAS_NUM_THREADS", _CORES))
+        self.D = (prob.n_f - 1) ** 2
+
+    def full_solve(self):
+        """One complete oracle solve (64x64 workload): seconds and stats."""
+        p = self.prob
+        t0 = time.perf_counter()
+        u, w, st = self.run.solve(eps=p.eps, wr_tol=1e-3 * p.eps, wr_max=200)
+        self.run.fine_field(u[1:], w[1:])
+        return time.perf_counter() - t0, st
+
+    def units(self, nsub):
+        """(t_wr per interval, t_G per sweep, t_prolong per state), timed now."""
+        run, p = self.run, self.prob
+        N, nsub = p.N, max(1, min(nsub, p.N))
+        starts = [(run.u0, run.w0)] * nsub
+        t0 = time.perf_counter()
+        run.sch.F_wr(starts, [run.F1] * nsub, [run.F2] * nsub, wr_tol=0.0, wr_max=1)
+        t_wr = (time.perf_counter() - t0) / nsub
+        t0 = time.perf_counter()
+        u, w = run.u0, run.w0
+        for n in range(N):
+            u, w = run.sch.G(u, w, p.amp[n] * run.F1, p.amp[n] * run.F2)
+        t_g = time.perf_counter() - t0
+        t0 = time.perf_counter()
+        run.red.prolong(u, w)
+        t_pr = time.perf_counter() - t0
+        return t_wr, t_g, t_pr
+
+    def sample(self, nsub):
+        """Seconds per solve extrapolated from one timed sample, and its description."""
+        c = self.counts
+        if c is None:
+            raise RuntimeError(f"oracle/counts_{self.config}.json is missing: run "
+                               f"`python -m oracle.record_counts {self.config}`")
+        p = self.prob
+        t_wr, t_g, t_pr = self.units(nsub)
+        t = c["wr_total"] * p.N * t_wr + (c["K1"] + 1) * t_g + p.N * t_pr
+        desc = (f"oracle on the workload's own reduced system (d1={self.run.red.d1}, d2={self.run.red.d2}, "
+                f"N={p.N}, P={p.P}), {self.cores} threads; measured: one WR iteration on {min(nsub, p.N)} of "
+                f"{p.N} intervals ({t_wr:.3f} s per interval), one coarse sweep ({t_g:.3f} s), one "
+                f"prolongation ({t_pr:.3f} s); scaled to a solve with the counts of a complete oracle solve "
+                f"(K1={c['K1']}, sum K0={c['wr_total']}): {t:.1f} s; setup excluded (spaces "
+                f"{self.setup_s:.1f} s, eq. (4.7) factorisations {self.grid_s:.1f} s)")
+        return t, desc
+
+
+def cpu_baseline(config, prob, budget_s=20.0):
+    """cpu_baseline of the bench line: the oracle on the host cores."""
+    smp = OracleSampler(config, prob)
+    out = {"unit": UNIT, "cores": smp.cores, "kind": "oracle"}
+    if config == "c1":
+        t, st = smp.full_solve()
+        out.update(value=smp.D * prob.N * prob.P / t,
+                   sample=f"one complete oracle solve of the workload ({t:.2f} s, K1={st['K1']}, "
+                          f"sum K0={sum(st['wr_iters'])}), {smp.cores} threads, setup excluded "
+                          f"({smp.setup_s:.1f} s)")
+        return out
+    t1, _, _ = smp.units(1)
+    nsub = int(max(1, min(prob.N, budget_s / max(t1, 1e-3) / 2)))
+    t, desc = smp.sample(nsub)
+    out.update(value=smp.D * prob.N * prob.P / t, sample=desc, oracle_setup_s=smp.setup_s)
+    return out
 
 
 def run_ours(args, rank, world):
@@ -254,7 +297,8 @@ def run_ours(args, rank, world):
     _, fine64, st64 = p.parareal_solve(u0, f, amp, eps=eps, want_fine=True)
     torch.cuda.synchronize()
     if prec != _lib.PINT_FP64:
-        info = p.assemble_reduced(p.T, prob.N, prob.P, prob.alpha, prec, autotune=not args.no_autotune)
+        info = p.assemble_reduced(p.T, prob.N, prob.P, prob.alpha, prec, autotune=not args.no_autotune,
+                                  coarse_fp64=args.coarse_fp64, refine_fp64=args.refine_fp64)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     for _ in range(args.warmup):
         p.parareal_solve(u0, f, amp, eps=eps, want_fine=True)
@@ -276,6 +320,9 @@ def run_ours(args, rank, world):
             e1.synchronize()
             times.append(e0.elapsed_time(e1) / 1e3)
             stats.append(st)
+    bad = [s["status"] for s in stats if s["status"] != "OK" or not s["converged"]]
+    if bad:
+        raise SystemExit(f"bench: {len(bad)} timed solves did not converge ({bad[0]}); no number reported")
     rel_err = max(float(torch.linalg.norm(fine[n] - fine64[n]) / torch.linalg.norm(fine64[n]))
                   for n in range(prob.N) if float(torch.linalg.norm(fine64[n])) > 0)
     torch.cuda.synchronize()
@@ -303,7 +350,7 @@ def run_ours(args, rank, world):
         torch.cuda.synchronize()
         if it >= args.warmup:
             e2e_t.append(time.perf_counter() - t0)
-        _lib.check(s, allow=(-5,))
+        _lib.check(s)           # NOT_CONVERGED is an error here too
     e2e_value = world * dofsteps / max_over_ranks(sum(e2e_t) / len(e2e_t), world)
     h2d = (hu0.numel() + hf.numel() + ha.numel()) * 8
     d2h = (hfine.numel() + hcoarse.numel()) * 8
@@ -347,6 +394,11 @@ def run_ours(args, rank, world):
                    "d1": info["d1"], "d2": info["d2"], "gamma": info["gamma"],
                    "reduced_dof_steps_per_s": world * (info["d1"] + info["d2"]) * prob.N * prob.P / t_step,
                    "lambda_max22": info["lambda_max22"], "precision": args.precision,
+                   "coarse_sweeps": ("FP64 in both solves" if args.coarse_fp64 or args.precision == "fp64" else
+                                     "FP32 cluster in the low-precision solve, FP64 in the correction solve"),
+                   "jump_norm": "FP64",
+                   "refinement_residual": "FP64" if args.refine_fp64 else "double-float (~48 bits, FP32 pipe)",
+                   "status": st["status"], "converged": all(s["converged"] for s in stats),
                    "K1": st["K1"], "wr_total": st["wr_total"], "wr_iters": st["wr_iters"],
                    "rel_l2_vs_fp64_max_t": rel_err, "fp64_gpu_value": dofsteps / (st64["solve_ms"] / 1e3),
                    "fp64_gpu_ms": st64["solve_ms"], "fp64_K1": st64["K1"], "fp64_wr_total": st64["wr_total"],
@@ -361,38 +413,44 @@ def run_ours(args, rank, world):
         "clocks": clk.summary(),
         "split_ms": {"f": st["f_ms"], "g": st["g_ms"], "prolong": st["prolong_ms"]},
     }
-    if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        # the oracle runs the FP64 algorithm: extrapolate with the FP64 path's counts
-        out["cpu_baseline"] = cpu_baseline(prob, info["d1"], info["d2"], st64["K1"], st64["wr_total"])
     p.close()
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        out["cpu_baseline"] = cpu_baseline(args.config, prob)
     return out
 
 
 def run_reference(args, rank, world):
-    """The oracle timed on the host cores: each step a bounded sample."""
+    """The oracle timed on the host cores, each step a bounded sample of the
+    workload (the 64x64 workload: a complete solve per step)."""
     if rank != 0:
         return None
     if args.config not in ("c1", "c2"):
         return {"impl": "reference", "unavailable": "the oracle's timed sample is defined for the 64x64 and "
                                                     "256x256 workloads only"}
     prob = problem(args.config)
-    # dimensions and iteration counts of this workload as measured on the GPU
-    # path (the same algorithm converges in the same counts)
-    d1, d2 = (1343, 257) if args.config == "c2" else (170, 65)
-    # the oracle is FP64: the FP64 path's counts on this workload
-    K1, wr_total = (9, 93) if args.config == "c2" else (4, 60)
-    vals = []
+    smp = OracleSampler(args.config, prob)
+    dofsteps = smp.D * prob.N * prob.P
+    secs, desc = [], ""
     # each step a bounded sample, sized so the whole run ends within a few minutes
-    budget = max(1.0, 150.0 / max(1, args.warmup + args.steps))
-    cache = {}
-    for _ in range(args.warmup + args.steps):
-        cb = cpu_baseline(prob, d1, d2, K1, wr_total, budget_s=budget, cache=cache)
-        vals.append(cb["value"])
-    v = statistics.mean(vals[args.warmup:])
-    cb["value"] = v
-    D = (prob.n_f - 1) ** 2
+    budget = max(1.0, 120.0 / max(1, args.warmup + args.steps))
+    nsub = 1
+    if args.config == "c2":
+        t1, _, _ = smp.units(1)
+        nsub = int(max(1, min(prob.N, budget / max(t1, 1e-3) / 2)))
+    for it in range(args.warmup + args.steps):
+        if args.config == "c1":
+            t, st = smp.full_solve()
+            desc = (f"one complete oracle solve per step (K1={st['K1']}, sum K0={sum(st['wr_iters'])}), "
+                    f"{smp.cores} threads, setup excluded ({smp.setup_s:.1f} s)")
+        else:
+            t, desc = smp.sample(nsub)
+        if it >= args.warmup:
+            secs.append(t)
+    t = statistics.mean(secs)
+    v = dofsteps / t
+    cb = {"value": v, "unit": UNIT, "cores": smp.cores, "kind": "oracle", "sample": desc}
     return {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": D * prob.N * prob.P / v * 1e3,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic", "config": {"workload": workload_desc(prob)},
             "cpu_baseline": cb, "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0,

@@ -59,12 +59,23 @@ enum {
  *   PINT_FP64      every step in FP64
  *   PINT_MIXED     WR contractions on the tensor cores (TF32 hi/lo split,
  *                  FP32 accumulation), time solve and recurrence in FP32,
- *                  FP64 coarse states and FP64 trajectory refinement
+ *                  FP64 coarse states; then one refinement pass: the residual
+ *                  of the fine scheme over the trajectory (double-float
+ *                  contractions) drives a correction solve whose coarse
+ *                  step (the diagonal (M11 + Delta t A11) solve and the
+ *                  couplings) runs in FP64.  The parareal jump and
+ *                  convergence norm of eq. (2.8) is FP64 throughout.
  *   PINT_MIXED_F32 the same with FP32 CUDA-core contractions (comparison) */
 enum { PINT_FP64 = 0, PINT_MIXED = 1, PINT_MIXED_F32 = 2 };
 
 /* flags for pint_assemble_reduced */
-enum { PINT_ALLOW_UNSTABLE = 1, PINT_FINE_SEQUENTIAL = 2, PINT_AUTOTUNE = 4 };
+enum {
+  PINT_ALLOW_UNSTABLE = 1,
+  PINT_FINE_SEQUENTIAL = 2,
+  PINT_AUTOTUNE = 4,
+  PINT_COARSE_FP64 = 8,
+  PINT_REFINE_FP64 = 16
+};
 
 typedef struct {
   int n_f, nc, J, ell;
@@ -76,6 +87,8 @@ typedef struct {
   double lambda_max22;/* sup_{V_H2} ||v||_a^2 / ||v||^2                     */
   double dt_max;      /* (1 - gamma^2) / lambda_max22 (Section 3.2)         */
   double setup_ms;    /* device time of the last setup stage                */
+  double T;           /* final time of the assembled time grid (0 before)   */
+  double Dt, dt;      /* coarse step T / N and fine step Delta t / P        */
 } pint_space_info;
 
 #define PINT_MAX_ITERS 512
@@ -133,7 +146,11 @@ pint_status pint_build_multiscale_spaces(pint_ctx* ctx, int nc, int J, int ell,
  * dt = Delta t / P) and the WR parameter alpha of eq. (4.1).  Also the
  * eigenbases Q (A11 Q = M11 Q Lambda1, Q^T M11 Q = I) and Q2 (same for
  * (A22, M22)) in which the fine and coarse steps are solved.
- *   T, N, P, alpha   time grid and WR parameter (0 < alpha < 1, P <= 64)
+ *   T, N, P, alpha   time grid and WR parameter (0 < alpha < 1, P <= 64);
+ *                    T <= 0 asks the library for the final time: 90% of
+ *                    the Section 3.2 bound on the coarse step,
+ *                    T = 0.9 N (1 - gamma^2) / lambda_max(A22, M22),
+ *                    rounded down to two significant digits (info->T)
  *   precision        PINT_FP64 or PINT_MIXED
  *   flags            PINT_ALLOW_UNSTABLE: do not reject a Delta t above
  *                    dt_max (Section 3.2 condition);
@@ -142,6 +159,14 @@ pint_status pint_build_multiscale_spaces(pint_ctx* ctx, int nc, int J, int ell,
  *                    P times on all active intervals at once instead of the
  *                    WR all-at-once solve (same fixed point; a comparison
  *                    mode without the paper's counterpart);
+ *                    PINT_COARSE_FP64: on the mixed paths, the first
+ *                    (low-precision) solve's coarse sweeps run in FP64 too
+ *                    (by default they run in FP32 on one thread-block
+ *                    cluster; the correction solve's are always FP64);
+ *                    PINT_REFINE_FP64: on the mixed paths, the refinement
+ *                    residual's two contractions run in FP64 (by default
+ *                    in double-float arithmetic, about 48 bits, on the FP32
+ *                    pipe);
  *                    PINT_AUTOTUNE: on the PINT_MIXED path, the tile width
  *                    and K split of each tensor-core contraction shape are
  *                    measured (CUDA events, best of the cost model's top
@@ -149,9 +174,12 @@ pint_status pint_build_multiscale_spaces(pint_ctx* ctx, int nc, int J, int ell,
  *                    in the process-wide table of pint_tuning_*; without
  *                    the flag the cost model's choice (or a loaded entry of
  *                    the table) is used
- *   info             optional, receives gamma, lambda_max22, dt_max
- * Errors: BAD_ARG, STATE, UNSTABLE_DT (Delta t > dt_max without the flag;
- * info is still filled), SINGULAR, OOM, CUDA.
+ *   info             optional, receives gamma, lambda_max22, dt_max and
+ *                    the time grid T, Dt, dt
+ * Errors: BAD_ARG (also a non-finite T, or T <= 0 when no stable T exists),
+ * STATE, UNSTABLE_DT (Delta t > dt_max without the flag; info is still
+ * filled), SINGULAR, OOM, CUDA.  Every call replaces the time grid; work
+ * cached for the previous one (captured WR iterations) is discarded.
  */
 pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double alpha,
                                   int precision, int flags, pint_space_info* info);
@@ -249,20 +277,25 @@ pint_status pint_prolong(pint_ctx* ctx, const double* coarse, int count, double*
 
 /*
  * pint_prolong_noalloc -- the same result as pint_prolong, for callers that
- * cannot allocate device memory (code running while a CUDA graph is being
- * captured on its stream, host runtimes that own the allocator, loops that
- * must not touch it).  The paper has no counterpart: this is a service entry
- * point of the library.  The call allocates and frees nothing: its scratch
+ * cannot call cudaMalloc or any other allocating routine: host runtimes that
+ * own the device allocator and forbid allocations outside it, real-time
+ * loops that must not touch the allocator, callers with no allocator.  The
+ * paper has no counterpart: this is a service entry point of the library.
+ * The call allocates and frees nothing: its scratch
  * (count * (d1 + d2 + n_raw) doubles) lives in a file-scope device array of
  * 2^20 doubles (8 MB, held by every GPU that loads the library until exit).
  *   coarse  DEVICE pointer, count x (d1+d2)
  *   u_out   DEVICE pointer, count x (n_f+1)^2
- * Errors: BAD_ARG (host pointers, or count * (d1 + d2 + n_raw) > 2^20),
- * STATE, CUDA.  The first call with a given device current looks the
- * array's device address up (cudaGetSymbolAddress) and caches it; make that
- * first call before any stream capture.  All calls share the array, so calls
- * whose work overlaps on the GPU (other streams, threads or contexts on the
- * same device) race; each call writes every scratch element before reading it.
+ * The context's device (the one current at pint_setup_fine_grid) must be
+ * current.  The work is queued on the context's stream and the call returns
+ * without waiting for it: u_out is ready once that stream reaches it.
+ * Errors: BAD_ARG (host pointers, another device current, or
+ * count * (d1 + d2 + n_raw) > 2^20), STATE, CUDA.  The first call on a
+ * device looks the array's device address up (cudaGetSymbolAddress) and
+ * caches it.  All calls share the array, which keeps the last call's
+ * contents, so calls whose work overlaps on the GPU (other streams, threads
+ * or contexts on the same device) race; each call writes every scratch
+ * element before reading it.
  */
 pint_status pint_prolong_noalloc(pint_ctx* ctx, const double* coarse, int count, double* u_out);
 

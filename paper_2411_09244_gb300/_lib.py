@@ -22,6 +22,8 @@ PINT_FP64, PINT_MIXED, PINT_MIXED_F32 = 0, 1, 2
 PINT_ALLOW_UNSTABLE = 1
 PINT_FINE_SEQUENTIAL = 2
 PINT_AUTOTUNE = 4
+PINT_COARSE_FP64 = 8
+PINT_REFINE_FP64 = 16
 MAX_ITERS = 512
 
 
@@ -29,7 +31,8 @@ class SpaceInfo(C.Structure):
     _fields_ = [("n_f", C.c_int), ("nc", C.c_int), ("J", C.c_int), ("ell", C.c_int),
                 ("n_blocks", C.c_int), ("n_raw", C.c_int), ("L", C.c_int), ("d1", C.c_int),
                 ("d2", C.c_int), ("gamma", C.c_double), ("lambda_max22", C.c_double),
-                ("dt_max", C.c_double), ("setup_ms", C.c_double)]
+                ("dt_max", C.c_double), ("setup_ms", C.c_double), ("T", C.c_double), ("Dt", C.c_double),
+                ("dt", C.c_double)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_}

@@ -8,7 +8,6 @@ kernels; this module only marshals arguments.
 from __future__ import annotations
 
 import ctypes as C
-import math
 
 import numpy as np
 import torch
@@ -25,15 +24,6 @@ def _f64(x, device=None):
     if device is not None:
         x = x.to(device)
     return x.contiguous()
-
-
-def stable_T(N: int, gamma: float, lambda_max22: float, margin: float = 0.9) -> float:
-    """Final time whose coarse step satisfies the condition of Section 3.2,
-    Delta t lambda_max(A22, M22) <= 1 - gamma^2, with a margin, rounded down
-    to two significant digits."""
-    t = margin * N * (1.0 - gamma * gamma) / lambda_max22
-    e = math.floor(math.log10(t)) - 1
-    return math.floor(t / 10.0 ** e) * 10.0 ** e
 
 
 class Pint:
@@ -73,22 +63,22 @@ class Pint:
 
     def assemble_reduced(self, T: float | None, N: int, P: int, alpha: float, precision: int = L.PINT_FP64,
                          allow_unstable: bool = False, fine_sequential: bool = False,
-                         autotune: bool = False) -> dict:
-        """T = None picks the stable final time from gamma and lambda_max.
+                         autotune: bool = False, coarse_fp64: bool = False, refine_fp64: bool = False) -> dict:
+        """T = None (passed as 0) lets the library pick the stable final time
+        of Section 3.2; the T used is returned in info["T"].
         fine_sequential: PINT_FINE_SEQUENTIAL (FP64 path comparison mode).
-        autotune: PINT_AUTOTUNE (measured contraction tiles, mixed path)."""
+        autotune: PINT_AUTOTUNE (measured contraction tiles, mixed path).
+        coarse_fp64: PINT_COARSE_FP64 (every coarse sweep of the mixed path in FP64).
+        refine_fp64: PINT_REFINE_FP64 (refinement residual contractions in FP64)."""
         info = L.SpaceInfo()
         flags = ((L.PINT_ALLOW_UNSTABLE if allow_unstable else 0) | (L.PINT_FINE_SEQUENTIAL if fine_sequential else 0)
-                 | (L.PINT_AUTOTUNE if autotune else 0))
-        if T is None:
-            # first pass with a tiny T to obtain gamma and lambda_max
-            L.check(self.lib.pint_assemble_reduced(self.h, 1e-30, N, P, alpha, precision, flags,
-                                                   C.byref(info)))
-            T = stable_T(N, info.gamma, info.lambda_max22)
-        st = self.lib.pint_assemble_reduced(self.h, T, N, P, alpha, precision, flags, C.byref(info))
+                 | (L.PINT_AUTOTUNE if autotune else 0) | (L.PINT_COARSE_FP64 if coarse_fp64 else 0)
+                 | (L.PINT_REFINE_FP64 if refine_fp64 else 0))
+        st = self.lib.pint_assemble_reduced(self.h, 0.0 if T is None else T, N, P, alpha, precision, flags,
+                                            C.byref(info))
         L.check(st)
         self.info = info.as_dict()
-        self.T, self.N, self.P, self.alpha = T, N, P, alpha
+        self.T, self.N, self.P, self.alpha = info.T, N, P, alpha
         return self.info
 
     def get_info(self) -> dict:

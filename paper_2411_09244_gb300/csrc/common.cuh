@@ -66,6 +66,7 @@ struct WinDesc {
 
 struct Ctx {
   cudaStream_t stream = nullptr;
+  int device = 0;             // the device current at pint_setup_fine_grid
   std::vector<void*> allocs;  // everything freed in pint_destroy
 
   // fine grid (Section 2)
@@ -121,6 +122,8 @@ struct Ctx {
   double T = 0, Dt = 0, dt = 0, alpha = 0;
   bool fine_seq = false;  // PINT_FINE_SEQUENTIAL
   bool autotune = false;  // PINT_AUTOTUNE: measured contraction tiles
+  bool coarse64 = false;  // PINT_COARSE_FP64: every coarse sweep of the mixed path in FP64
+  bool refine64 = false;  // PINT_REFINE_FP64: refinement residual contractions in FP64
   bool have_time = false;
 
   // hot-path operators (FP64): [-G1 | G2] and [-CM^T | -dt CA^T]

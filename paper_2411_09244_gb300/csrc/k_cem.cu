@@ -12,6 +12,12 @@
 // Y = L^-1 C^T, S = Y^T Y (= C A_w^-1 C^T), S X = g, phi = L^-T (Y X).
 // Columns of C^T are zero above the first node of their block, so Y's are
 // too; the forward solve and the Schur products start there.
+//
+// S = Y^T Y squares the conditioning (cond(S) ~ 1e12 on a contrast-1e6
+// window), so the plain Schur solve leaves forward errors ~1e-9 in phi.  One
+// step of iterative refinement with the same factors removes them: with
+// X = -mu, the residuals r1 = C^T X - A_w phi and r2 = g - C phi give
+// z = L^-1 r1, dX = S^-1 (r2 - Y^T z), dphi = L^-T (z + Y dX).
 #include "common.cuh"
 
 #include <algorithm>
@@ -22,8 +28,17 @@ namespace {
 
 struct WinDev {
   int X0, Y0, wx, wy, nw, b, m, t0, kt, blk;
+  int bx0, by0, nbx, nby;  // coarse blocks of the window (rectangle)
   long long lb_off, y_off, s_off, psi_off, col_off;
+  long long bc_off;        // first constraint column of each window block (bcol table)
+  long long r_off;         // refinement scratch: nw kt (r1, z, dphi) and m kt (r2, t)
 };
+
+// window-local constraint column of aux function qq of block (xb, yb), or -1
+__device__ __forceinline__ int win_col(const WinDev& W, const int* __restrict__ bcol, int xb, int yb, int qq) {
+  if (xb < W.bx0 || xb >= W.bx0 + W.nbx || yb < W.by0 || yb >= W.by0 + W.nby) return -1;
+  return bcol[W.bc_off + (yb - W.by0) * W.nbx + (xb - W.bx0)] + qq;
+}
 
 // --- banded A_w from the 9-point stiffness stencil -------------------------
 __global__ void k_win_assemble(const WinDev* __restrict__ wd, int w0, const double* __restrict__ stA,
@@ -238,27 +253,11 @@ __global__ void __launch_bounds__(512) k_win_small(const WinDev* __restrict__ wd
   }
 }
 
-// --- phi = L^-T (Y X), one CTA per window ------------------------------------
-__global__ void __launch_bounds__(512) k_win_phi(const WinDev* __restrict__ wd, int w0,
-                                                 const double* __restrict__ lb,
-                                                 const double* __restrict__ y,
-                                                 const double* __restrict__ sch,
-                                                 double* __restrict__ psi) {
-  const WinDev W = wd[w0 + blockIdx.x];
-  const int m = W.m, kt = W.kt, n = W.nw, b = W.b, bw = b + 1;
-  const double* L = lb + W.lb_off;
-  const double* Y = y + W.y_off;
-  const double* Xw = sch + W.s_off + (size_t)m * m;
-  double* Z = psi + W.psi_off;  // kt x n, column q at q*n
-  for (long long e = threadIdx.x; e < (long long)n * kt; e += blockDim.x) {
-    int i = (int)(e / kt), q = (int)(e % kt);
-    double acc = 0.0;
-    for (int c = 0; c < m; ++c) acc += Y[(size_t)i * m + c] * Xw[(size_t)c * kt + q];
-    Z[(size_t)q * n + i] = acc;
-  }
-  __syncthreads();
-  // column-oriented back substitution with L^T: x_i = z_i / L_ii, then
-  // z_k -= L_ik x_i for k in [i-b, i)
+// Z <- L^-T Z for the kt columns of Z (column q at q n), whole CTA:
+// column-oriented back substitution, x_i = z_i / L_ii, then z_k -= L_ik x_i
+// for k in [i-b, i)
+__device__ void band_back_cols(const double* __restrict__ L, double* __restrict__ Z, int n, int b, int kt) {
+  const int bw = b + 1;
   for (int i = n - 1; i >= 0; --i) {
     const double* Li = L + (size_t)i * bw;
     if (threadIdx.x < kt) Z[(size_t)threadIdx.x * n + i] /= Li[b];
@@ -273,13 +272,191 @@ __global__ void __launch_bounds__(512) k_win_phi(const WinDev* __restrict__ wd, 
   }
 }
 
+// --- phi = L^-T (Y X), one CTA per window ------------------------------------
+__global__ void __launch_bounds__(512) k_win_phi(const WinDev* __restrict__ wd, int w0,
+                                                 const double* __restrict__ lb,
+                                                 const double* __restrict__ y,
+                                                 const double* __restrict__ sch,
+                                                 double* __restrict__ psi) {
+  const WinDev W = wd[w0 + blockIdx.x];
+  const int m = W.m, kt = W.kt, n = W.nw;
+  const double* Y = y + W.y_off;
+  const double* Xw = sch + W.s_off + (size_t)m * m;
+  double* Z = psi + W.psi_off;  // kt x n, column q at q*n
+  for (long long e = threadIdx.x; e < (long long)n * kt; e += blockDim.x) {
+    int i = (int)(e / kt), q = (int)(e % kt);
+    double acc = 0.0;
+    for (int c = 0; c < m; ++c) acc += Y[(size_t)i * m + c] * Xw[(size_t)c * kt + q];
+    Z[(size_t)q * n + i] = acc;
+  }
+  __syncthreads();
+  band_back_cols(lb + W.lb_off, Z, n, W.b, kt);
+}
+
+// --- refinement step 1: residuals of the saddle-point system -----------------
+// r1[i][q] = (C^T X)_iq - (A_w phi)_iq on the window nodes; r2[c][q] =
+// g_cq - (C phi)_cq on the constraints.  One CTA per window.
+__global__ void __launch_bounds__(512) k_win_resid(const WinDev* __restrict__ wd, int w0,
+                                                   const double* __restrict__ stA, int n_f,
+                                                   const int* __restrict__ colmap, const int* __restrict__ bcol,
+                                                   const int* __restrict__ blk_k, const double* __restrict__ con_rows,
+                                                   const double* __restrict__ gram, int kcap, int nb, int bs, int nc,
+                                                   const double* __restrict__ sch, const double* __restrict__ psi,
+                                                   double* __restrict__ r1, double* __restrict__ r2) {
+  const WinDev W = wd[w0 + blockIdx.x];
+  const int m = W.m, kt = W.kt, n = W.nw;
+  const double* Xw = sch + W.s_off + (size_t)m * m;  // [c][kt]
+  const double* phi = psi + W.psi_off;                // [q][n]
+  double* R1 = r1 + W.r_off;                          // [i][kt]
+  double* R2 = r2 + W.r_off;                          // [c][kt]
+  for (long long e = threadIdx.x; e < (long long)n * kt; e += blockDim.x) {
+    const int i = (int)(e / kt), q = (int)(e % kt);
+    const int lx = i % W.wx, ly = i / W.wx, gx = W.X0 + lx, gy = W.Y0 + ly;
+    double acc = 0.0;
+    // C^T X: the (up to 4) blocks whose closure holds node (gx, gy)
+    for (int yb = max(0, (gy - 1) / bs); yb <= min(nc - 1, gy / bs); ++yb)
+      for (int xb = max(0, (gx - 1) / bs); xb <= min(nc - 1, gx / bs); ++xb) {
+        if (gx < xb * bs || gx > (xb + 1) * bs || gy < yb * bs || gy > (yb + 1) * bs) continue;
+        const int b2 = yb * nc + xb, r = (gy - yb * bs) * (bs + 1) + (gx - xb * bs);
+        for (int qq = 0; qq < blk_k[b2]; ++qq) {
+          const int c = win_col(W, bcol, xb, yb, qq);
+          if (c < 0) break;
+          acc += con_rows[((size_t)b2 * kcap + qq) * nb + r] * Xw[(size_t)c * kt + q];
+        }
+      }
+    // A_w phi (zero Dirichlet data outside the window)
+    const int node = gy * (n_f + 1) + gx;
+    double ap = 0.0;
+    for (int dy = -1; dy <= 1; ++dy)
+      for (int dx = -1; dx <= 1; ++dx) {
+        const int x2 = lx + dx, y2 = ly + dy;
+        if (x2 < 0 || x2 >= W.wx || y2 < 0 || y2 >= W.wy) continue;
+        ap += stA[(size_t)node * 9 + (dy + 1) * 3 + (dx + 1)] * phi[(size_t)q * n + y2 * W.wx + x2];
+      }
+    R1[(size_t)i * kt + q] = acc - ap;
+  }
+  // r2: one warp per constraint column, lanes over the block's nodes
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  for (int c = warp; c < m; c += nwarp) {
+    const int code = colmap[W.col_off + c], b2 = code / kcap, qq = code % kcap;
+    const int xb = b2 % nc, yb = b2 / nc;
+    for (int q = 0; q < kt; ++q) {
+      double acc = 0.0;
+      for (int r = lane; r < nb; r += 32) {
+        const int gx = xb * bs + r % (bs + 1), gy = yb * bs + r / (bs + 1);
+        const int lx = gx - W.X0, ly = gy - W.Y0;
+        if (lx < 0 || lx >= W.wx || ly < 0 || ly >= W.wy) continue;
+        acc += con_rows[((size_t)b2 * kcap + qq) * nb + r] * phi[(size_t)q * n + ly * W.wx + lx];
+      }
+      acc = pintd::warp_sum(acc);
+      if (lane == 0) {
+        const double g = (c == W.t0 + q) ? gram[(size_t)W.blk * kcap + q] : 0.0;
+        R2[(size_t)c * kt + q] = g - acc;
+      }
+    }
+  }
+}
+
+// --- refinement step 2: z = L^-1 r1 in place, one warp per column -------------
+__global__ void __launch_bounds__(256) k_win_fwd_cols(const WinDev* __restrict__ wd, int w0,
+                                                      const double* __restrict__ lb, double* __restrict__ r1) {
+  const WinDev W = wd[w0 + blockIdx.x];
+  const int kt = W.kt, n = W.nw, b = W.b, bw = b + 1;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
+  const double* L = lb + W.lb_off;
+  double* Z = r1 + W.r_off;  // [i][kt]
+  for (int q = warp; q < kt; q += nwarp) {
+    for (int i = 0; i < n; ++i) {
+      const double* Li = L + (size_t)i * bw;
+      double acc = 0.0;
+      for (int k = max(0, i - b) + lane; k < i; k += 32) acc += Li[k - i + b] * Z[(size_t)k * kt + q];
+      acc = pintd::warp_sum(acc);
+      if (lane == 0) Z[(size_t)i * kt + q] = (Z[(size_t)i * kt + q] - acc) / Li[b];
+      __syncwarp();
+    }
+  }
+}
+
+// --- refinement step 3: r2 <- r2 - Y^T z, threads over constraint columns ----
+constexpr int RQ = 8;  // right-hand sides per pass
+__global__ void __launch_bounds__(128) k_win_ytz(const WinDev* __restrict__ wd, int w0,
+                                                 const double* __restrict__ y, const int* __restrict__ first,
+                                                 const double* __restrict__ r1, double* __restrict__ r2) {
+  const WinDev W = wd[w0 + blockIdx.y];
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= W.m) return;
+  const int m = W.m, kt = W.kt, n = W.nw;
+  const double* Y = y + W.y_off;
+  const double* Z = r1 + W.r_off;
+  double* R2 = r2 + W.r_off;
+  const int i0 = first[W.col_off + c];
+  for (int q0 = 0; q0 < kt; q0 += RQ) {
+    double acc[RQ];
+#pragma unroll
+    for (int t = 0; t < RQ; ++t) acc[t] = 0.0;
+    for (int i = i0; i < n; ++i) {
+      const double yv = Y[(size_t)i * m + c];
+#pragma unroll
+      for (int t = 0; t < RQ; ++t)
+        if (q0 + t < kt) acc[t] += yv * Z[(size_t)i * kt + q0 + t];
+    }
+#pragma unroll
+    for (int t = 0; t < RQ; ++t)
+      if (q0 + t < kt) R2[(size_t)c * kt + q0 + t] -= acc[t];
+  }
+}
+
+// --- refinement step 4: dX = S^-1 r2 (Cholesky factor of S from k_win_small) --
+__global__ void __launch_bounds__(256) k_win_small_rhs(const WinDev* __restrict__ wd, int w0,
+                                                       const double* __restrict__ sch, double* __restrict__ r2) {
+  const WinDev W = wd[w0 + blockIdx.x];
+  const int m = W.m, kt = W.kt;
+  const double* S = sch + W.s_off;
+  double* X = r2 + W.r_off;  // [c][kt], overwritten by the solution
+  for (int q = threadIdx.x; q < kt; q += blockDim.x) {
+    for (int i = 0; i < m; ++i) {
+      double v = X[(size_t)i * kt + q];
+      for (int k = 0; k < i; ++k) v -= S[(size_t)i * m + k] * X[(size_t)k * kt + q];
+      X[(size_t)i * kt + q] = v / S[(size_t)i * m + i];
+    }
+    for (int i = m - 1; i >= 0; --i) {
+      double v = X[(size_t)i * kt + q];
+      for (int k = i + 1; k < m; ++k) v -= S[(size_t)k * m + i] * X[(size_t)k * kt + q];
+      X[(size_t)i * kt + q] = v / S[(size_t)i * m + i];
+    }
+  }
+}
+
+// --- refinement step 5: phi += L^-T (z + Y dX), one CTA per window -----------
+__global__ void __launch_bounds__(512) k_win_phi_corr(const WinDev* __restrict__ wd, int w0,
+                                                      const double* __restrict__ lb, const double* __restrict__ y,
+                                                      const double* __restrict__ r1, const double* __restrict__ r2,
+                                                      double* __restrict__ dphi, double* __restrict__ psi) {
+  const WinDev W = wd[w0 + blockIdx.x];
+  const int m = W.m, kt = W.kt, n = W.nw;
+  const double* Y = y + W.y_off;
+  const double* Z = r1 + W.r_off;   // [i][kt]
+  const double* dX = r2 + W.r_off;  // [c][kt]
+  double* D = dphi + W.r_off;       // [q][n]
+  for (long long e = threadIdx.x; e < (long long)n * kt; e += blockDim.x) {
+    const int i = (int)(e / kt), q = (int)(e % kt);
+    double acc = Z[(size_t)i * kt + q];
+    for (int c = 0; c < m; ++c) acc += Y[(size_t)i * m + c] * dX[(size_t)c * kt + q];
+    D[(size_t)q * n + i] = acc;
+  }
+  __syncthreads();
+  band_back_cols(lb + W.lb_off, D, n, W.b, kt);
+  double* phi = psi + W.psi_off;
+  for (long long e = threadIdx.x; e < (long long)n * kt; e += blockDim.x) phi[e] += D[e];
+}
+
 }  // namespace
 
 void build_windows(Ctx* c) {
   const int nc = c->nc, bs = c->bs, ell = c->ell, kcap = c->kmax;
   c->win.assign(c->n_blocks, WinDesc{});
   std::vector<WinDev> wd(c->n_blocks);
-  std::vector<int> colmap, first;
+  std::vector<int> colmap, first, bcol;
   long long psi_tot = 0, col_tot = 0;
   for (int blk = 0; blk < c->n_blocks; ++blk) {
     int bx = blk % nc, by = blk / nc;
@@ -297,10 +474,16 @@ void build_windows(Ctx* c) {
     W.t0 = -1;
     WinDev& D = wd[blk];
     D.col_off = col_tot;
+    D.bc_off = (long long)bcol.size();
+    D.bx0 = W.bx0;
+    D.by0 = W.by0;
+    D.nbx = W.bx1 - W.bx0 + 1;
+    D.nby = W.by1 - W.by0 + 1;
     for (int yb = W.by0; yb <= W.by1; ++yb)
       for (int xb = W.bx0; xb <= W.bx1; ++xb) {
         int b2 = yb * nc + xb;
         if (b2 == blk) W.t0 = W.m;
+        bcol.push_back(W.m);
         // first window row touched by block b2 (its smallest interior node)
         int fx = std::max(xb * bs, W.X0) - W.X0, fy = std::max(yb * bs, W.Y0) - W.Y0;
         for (int q = 0; q < c->blk_k[b2]; ++q) {
@@ -329,6 +512,11 @@ void build_windows(Ctx* c) {
   c->psi = (double*)dalloc(c, (size_t)psi_tot * sizeof(double));
   int* d_colmap = (int*)dalloc(c, colmap.size() * sizeof(int));
   int* d_first = (int*)dalloc(c, first.size() * sizeof(int));
+  int* d_bcol = (int*)dalloc(c, bcol.size() * sizeof(int));
+  int* d_blk_k = (int*)dalloc(c, c->n_blocks * sizeof(int));
+  PINT_CUDA(cudaMemcpyAsync(d_bcol, bcol.data(), bcol.size() * sizeof(int), cudaMemcpyHostToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(d_blk_k, c->blk_k.data(), c->n_blocks * sizeof(int), cudaMemcpyHostToDevice,
+                            c->stream));
   PINT_CUDA(cudaMemcpyAsync(d_colmap, colmap.data(), colmap.size() * sizeof(int),
                             cudaMemcpyHostToDevice, c->stream));
   PINT_CUDA(cudaMemcpyAsync(d_first, first.data(), first.size() * sizeof(int),
@@ -339,19 +527,22 @@ void build_windows(Ctx* c) {
   const long long budget = 24LL << 30;
   int w = 0;
   while (w < c->n_blocks) {
-    long long lb = 0, yy = 0, ss = 0;
+    long long lb = 0, yy = 0, ss = 0, rr = 0;
     int w1 = w;
     while (w1 < c->n_blocks) {
       const WinDev& D = wd[w1];
       long long nlb = (long long)D.nw * (D.b + 1), ny = (long long)D.nw * D.m,
-                ns = (long long)D.m * D.m + (long long)D.m * D.kt;
-      if (w1 > w && (lb + nlb + yy + ny + ss + ns) * 8 > budget) break;
+                ns = (long long)D.m * D.m + (long long)D.m * D.kt,
+                nr = (long long)std::max(D.nw, D.m) * D.kt;
+      if (w1 > w && (lb + nlb + yy + ny + ss + ns + 3 * (rr + nr)) * 8 > budget) break;
       wd[w1].lb_off = lb;
       wd[w1].y_off = yy;
       wd[w1].s_off = ss;
+      wd[w1].r_off = rr;
       lb += nlb;
       yy += ny;
       ss += ns;
+      rr += nr;
       ++w1;
     }
     int nwin = w1 - w;
@@ -385,7 +576,25 @@ void build_windows(Ctx* c) {
     PINT_LAUNCH_CHECK();
     k_win_phi<<<nwin, 512, 0, c->stream>>>(d_wd, w, d_lb, d_y, d_s, c->psi);
     PINT_LAUNCH_CHECK();
+    // one step of iterative refinement with the same factors
+    double* d_r1 = (double*)dalloc(c, (size_t)rr * 8);
+    double* d_r2 = (double*)dalloc(c, (size_t)rr * 8);
+    double* d_dp = (double*)dalloc(c, (size_t)rr * 8);
+    k_win_resid<<<nwin, 512, 0, c->stream>>>(d_wd, w, c->stA, c->n_f, d_colmap, d_bcol, d_blk_k, c->con_rows,
+                                             c->con_gram, kcap, c->nb, bs, nc, d_s, c->psi, d_r1, d_r2);
+    PINT_LAUNCH_CHECK();
+    k_win_fwd_cols<<<nwin, 256, 0, c->stream>>>(d_wd, w, d_lb, d_r1);
+    PINT_LAUNCH_CHECK();
+    k_win_ytz<<<dim3((maxm + 127) / 128, nwin), 128, 0, c->stream>>>(d_wd, w, d_y, d_first, d_r1, d_r2);
+    PINT_LAUNCH_CHECK();
+    k_win_small_rhs<<<nwin, 256, 0, c->stream>>>(d_wd, w, d_s, d_r2);
+    PINT_LAUNCH_CHECK();
+    k_win_phi_corr<<<nwin, 512, 0, c->stream>>>(d_wd, w, d_lb, d_y, d_r1, d_r2, d_dp, c->psi);
+    PINT_LAUNCH_CHECK();
     PINT_CUDA(cudaStreamSynchronize(c->stream));
+    dfree(c, d_r1);
+    dfree(c, d_r2);
+    dfree(c, d_dp);
     dfree(c, d_lb);
     dfree(c, d_y);
     dfree(c, d_s);
@@ -399,6 +608,8 @@ void build_windows(Ctx* c) {
   dfree(c, d_status);
   dfree(c, d_colmap);
   dfree(c, d_first);
+  dfree(c, d_bcol);
+  dfree(c, d_blk_k);
   for (int s : st) PINT_REQUIRE(s == 0, PINT_ERR_SINGULAR, "window saddle-point system singular");
 }
 

@@ -246,6 +246,66 @@ __global__ void k_jac_cols(double* __restrict__ C, double* __restrict__ V, int n
   V[(size_t)i * n + R.q] = R.s * x + R.c * y;
 }
 
+// The whole cyclic Jacobi iteration in one CTA for small matrices (n <= 128):
+// the same rounds, rotations and element updates as k_jac_params / _rows /
+// _cols, separated by barriers instead of launches, and the same stopping
+// test on the off-diagonal norm as the host loop of dense_sym_eig.  C and V
+// stay in global memory (L1/L2 resident at these sizes).
+constexpr int JAC1_MAXN = 128;
+__global__ void __launch_bounds__(1024) k_jac_one_cta(double* __restrict__ C, double* __restrict__ V, int n,
+                                                      int max_sweeps) {
+  __shared__ Rot rot[JAC1_MAXN / 2];
+  __shared__ double sh[64];
+  const int m = n + (n & 1), npair = m / 2;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  double prev = 1e300;
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    double off = 0.0, tot = 0.0;
+    for (int e = tid; e < n * n; e += nt) {
+      const double v = C[e] * C[e];
+      tot += v;
+      if (e / n != e % n) off += v;
+    }
+    off = pintd::block_sum(off, sh);  // every thread gets the same sums: a uniform exit
+    tot = pintd::block_sum(tot, sh);
+    if (off == 0.0 || off <= 1e-30 * tot || (off <= 1e-20 * tot && off > 0.25 * prev)) break;
+    prev = off;
+    for (int r = 0; r < m - 1; ++r) {
+      if (tid < npair) {
+        const int x = rr_pos(tid, r, m), y = rr_pos(m - 1 - tid, r, m);
+        const int p = min(x, y), q = max(x, y);
+        Rot R{p, q, 1.0, 0.0};
+        if (q < n) rot_params(C[(size_t)p * n + p], C[(size_t)p * n + q], C[(size_t)q * n + q], R.c, R.s);
+        else R.q = -1;
+        rot[tid] = R;
+      }
+      __syncthreads();
+      for (int e = tid; e < npair * n; e += nt) {
+        const int k = e / n, j = e % n;
+        const Rot R = rot[k];
+        if (R.q < 0 || R.s == 0.0) continue;
+        const double x = C[(size_t)R.p * n + j], y = C[(size_t)R.q * n + j];
+        C[(size_t)R.p * n + j] = R.c * x - R.s * y;
+        C[(size_t)R.q * n + j] = R.s * x + R.c * y;
+      }
+      __syncthreads();
+      for (int e = tid; e < npair * n; e += nt) {
+        const int k = e % npair, i = e / npair;
+        const Rot R = rot[k];
+        if (R.q < 0 || R.s == 0.0) continue;
+        double x = C[(size_t)i * n + R.p], y = C[(size_t)i * n + R.q];
+        C[(size_t)i * n + R.p] = R.c * x - R.s * y;
+        C[(size_t)i * n + R.q] = R.s * x + R.c * y;
+        x = V[(size_t)i * n + R.p];
+        y = V[(size_t)i * n + R.q];
+        V[(size_t)i * n + R.p] = R.c * x - R.s * y;
+        V[(size_t)i * n + R.q] = R.s * x + R.c * y;
+      }
+      __syncthreads();
+    }
+  }
+}
+
 __global__ void k_offnorm(const double* __restrict__ C, int n, double* __restrict__ out) {
   __shared__ double sh[64];
   double off = 0, tot = 0;
@@ -415,6 +475,11 @@ void dense_sym_eig(Ctx* c, double* C, double* V, double* lam, int n) {
   k_symmetrize<<<nblk((long long)n * n, 256), 256, 0, c->stream>>>(C, n);
   k_eye<<<nblk((long long)n * n, 256), 256, 0, c->stream>>>(Vtmp, n);
   PINT_LAUNCH_CHECK();
+  if (n <= JAC1_MAXN) {
+    // small matrices: every sweep inside one launch
+    k_jac_one_cta<<<1, 1024, 0, c->stream>>>(C, Vtmp, n, 40);
+    PINT_LAUNCH_CHECK();
+  } else {
   // one sweep = m-1 rounds, captured once as a CUDA graph
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
@@ -443,6 +508,7 @@ void dense_sym_eig(Ctx* c, double* C, double* V, double* lam, int n) {
   cudaGraphExecDestroy(exec);
   cudaGraphDestroy(graph);
   cudaStreamDestroy(cs);
+  }
   // sort ascending
   double* dd = (double*)dalloc(c, (size_t)n * 8);
   k_diag<<<nblk(n, 256), 256, 0, c->stream>>>(C, n, dd);

@@ -553,23 +553,23 @@ void split_bases(Ctx* c, float* psih, float* psil) {
 // ---------------------------------------------------------------------------
 // Allocation-free prolongation (pint_prolong_noalloc, declared in pint.h).
 //
-// Some callers cannot allocate device memory: code that runs while a CUDA
-// graph is being captured on its stream, allocators owned by a host runtime
-// that forbid the CUDA allocator, or real-time loops that must not touch the
-// allocator.  This entry point runs the same two kernels as pint_prolong but
-// keeps the scratch it needs (the split u / w rows and the raw-basis
-// coefficients) in the file-scope device array below, so the call itself
-// allocates and frees nothing.  Limits and hazards:
+// Some callers cannot call cudaMalloc or any allocating routine: a host
+// runtime that owns the device allocator and forbids other allocations, a
+// real-time loop that must not touch the allocator, or a caller that has no
+// allocator at all.  This entry point runs the same two kernels as
+// pint_prolong but keeps the scratch it needs (the split u / w rows and the
+// raw-basis coefficients) in the file-scope device array below, so the call
+// itself allocates and frees nothing.  Limits and hazards:
 //   * count * (d1 + d2 + n_raw) <= PINT_NOALLOC_SCRATCH_DOUBLES, else
 //     PINT_ERR_BAD_ARG (8 MB per GPU that loads the library, held until exit);
 //   * coarse and u_out must be device pointers (host staging would allocate);
 //   * every call shares the one array: calls whose kernels overlap on the GPU
 //     (two streams, two threads, two contexts on one device) race;
-//   * each call writes every scratch element it reads before reading it.
-// Host code cannot use the array's name as a device address; the device
-// address is fetched once per device with cudaGetSymbolAddress by the first
-// call made with that device current, which should therefore come before any
-// stream capture.
+//   * each call writes every scratch element it reads before reading it, so
+//     what an earlier call left there does not matter.
+// Host code cannot use the array's name as a device address; the address is
+// fetched with cudaGetSymbolAddress, once per device, by the first call made
+// on that device.
 // ---------------------------------------------------------------------------
 namespace {
 constexpr size_t PINT_NOALLOC_SCRATCH_DOUBLES = (size_t)1 << 20;
@@ -578,9 +578,8 @@ static __device__ __align__(256) double g_noalloc_scratch[PINT_NOALLOC_SCRATCH_D
 std::mutex g_noalloc_mu;
 double* g_noalloc_ptr[256] = {nullptr};
 
-double* noalloc_scratch_for_current_device() {
-  int dev = 0;
-  PINT_CUDA(cudaGetDevice(&dev));
+// the scratch address on device `dev`, which must be the current device
+double* noalloc_scratch_for_device(int dev) {
   PINT_REQUIRE(dev >= 0 && dev < 256, PINT_ERR_BAD_ARG, "device ordinal out of range");
   std::lock_guard<std::mutex> lk(g_noalloc_mu);
   if (!g_noalloc_ptr[dev]) {
@@ -607,13 +606,17 @@ extern "C" pint_status pint_prolong_noalloc(pint_ctx* ctx, const double* coarse,
   }
   try {
     PINT_REQUIRE(c->have_reduced, PINT_ERR_STATE, "pint_assemble_reduced first");
+    int cur = -1;
+    PINT_CUDA(cudaGetDevice(&cur));
+    PINT_REQUIRE(cur == c->device, PINT_ERR_BAD_ARG,
+                 "pint_prolong_noalloc: make the context's device current first");
     PINT_REQUIRE(is_device_ptr(coarse) && is_device_ptr(u_out), PINT_ERR_BAD_ARG,
                  "pint_prolong_noalloc takes device pointers only");
     const int d1 = c->d1, d2 = c->d2, n_raw = c->n_raw;
     const size_t need = (size_t)count * (d1 + d2 + n_raw);
     PINT_REQUIRE(need <= PINT_NOALLOC_SCRATCH_DOUBLES, PINT_ERR_BAD_ARG,
                  "pint_prolong_noalloc: count * (d1 + d2 + n_raw) exceeds the 1048576-double scratch");
-    double* s = noalloc_scratch_for_current_device();
+    double* s = noalloc_scratch_for_device(c->device);
     double* u = s;
     double* w = u + (size_t)count * d1;
     double* a = w + (size_t)count * d2;
@@ -629,10 +632,12 @@ extern "C" pint_status pint_prolong_noalloc(pint_ctx* ctx, const double* coarse,
     k_prolong<<<(unsigned)((tot + 255) / 256), 256, 0, c->stream>>>(
         (const GWin*)c->d_windesc, c->n_f, c->nc, c->bs, c->ell, c->psi, a, count, u_out);
     PINT_LAUNCH_CHECK();
-    PINT_CUDA(cudaStreamSynchronize(c->stream));
-    return PINT_OK;
+    return PINT_OK;  // stream-ordered: the result is ready when the context's stream reaches this point
   } catch (const Fail& e) {
     set_error(e.msg);
     return e.code;
+  } catch (const std::exception& e) {
+    set_error(std::string("host exception: ") + e.what());
+    return PINT_ERR_BAD_ARG;
   }
 }

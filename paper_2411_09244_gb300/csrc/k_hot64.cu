@@ -371,17 +371,18 @@ __global__ void k_step_w(const double* __restrict__ CMt, const double* __restric
   }
 }
 
-// jump of eq. (2.8) per coarse time: ||du||^2 + ||dw||^2 + 2 du^T CM dw;
-// CTA (n-1, part) handles rows i = part, part + JS, ... of CM and adds its
-// partial sum to jump2[n-1] (zeroed by the caller); k_max_fin takes sqrt
+// jump of eq. (2.8) per coarse time, in FP64: ||du||^2 + ||dw||^2 + 2 du^T CM dw
+// (M_H in spectral coordinates); CTA (n - n_first - 1, part) handles rows
+// i = part, part + JS, ... of CM for coarse time n and adds its partial sum to
+// jump2[n-1] (zeroed by the caller); k_max_fin takes sqrt.  Coarse times
+// n <= n_first are not launched: in sweep k the states up to n = k - 1 do not
+// change, so their jumps are exactly zero.
 constexpr int JS = 8;
-// T: arithmetic type of the coupling product (FP32 in the low-precision
-// path, where the jumps only steer the stopping test)
 template <typename T>
 __global__ void k_jump(const double* __restrict__ Xu, const double* __restrict__ Xw,
                        const double* __restrict__ Ou, const double* __restrict__ Ow,
-                       const T* __restrict__ CM, int d1, int d2, double* __restrict__ jump2) {
-  const int n = blockIdx.x + 1, part = blockIdx.y;
+                       const T* __restrict__ CM, int d1, int d2, int n_first, double* __restrict__ jump2) {
+  const int n = n_first + blockIdx.x + 1, part = blockIdx.y;
   __shared__ double sh[64];
   __shared__ T dw[4096];
   const double* xu = Xu + (size_t)n * d1;
@@ -859,7 +860,7 @@ static void stage_amp(Ctx* c, Hot& H, const double* amp_dev, int count) {
     k_fill<<<nb_(count, 256), 256, 0, c->stream>>>(H.amp, count, 1.0);
 }
 
-static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw, const float* CM32);
+static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw);
 
 void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const double* amp_dev, double eps,
                 int k_max, double wr_tol, int wr_max, double* u_out, double* coarse_out, pint_stats* st,
@@ -923,7 +924,7 @@ void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const dou
     g_sweep(c, H, H.Xu, H.Xw, H.amp, nullptr, nullptr, nullptr, nullptr, 0, true);
     g_sweep_check(c, H);
     if (eps < 0 || wr_tol < 0) {  // relative tolerances: scale of the G-sweep states
-      const double sc = state_scale(c, H, H.Xu, H.Xw, nullptr);
+      const double sc = state_scale(c, H, H.Xu, H.Xw);
       if (eps < 0) eps = -eps * sc;
       if (wr_tol < 0) wr_tol = -wr_tol * sc;
     }
@@ -957,7 +958,8 @@ void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const dou
       g_sweep(c, H, H.Xu, H.Xw, H.amp, H.Fu, H.Fw, nullptr, nullptr, n_lo, false);
       g_sweep_check(c, H);
       PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
-    k_jump<double><<<dim3(N, JS), 256, 0, c->stream>>>(H.Xu, H.Xw, H.Ou, H.Ow, c->CM, d1, d2, H.red + 8);
+      k_jump<double><<<dim3(N - n_lo, JS), 256, 0, c->stream>>>(H.Xu, H.Xw, H.Ou, H.Ow, c->CM, d1, d2, n_lo,
+                                                                 H.red + 8);
       k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
       PINT_LAUNCH_CHECK();
       c->launches += 2;
@@ -1117,7 +1119,8 @@ void apply_F_dev(Ctx* c, const double* in, int count, const double* f_nodes, con
 void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* Ut, const float* Wt, int ldu,
                    int ldw, int P, int ncols, float* out, const int* gate);
 void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
-                      const float* Blo, int ncols, int nsplit, int tn, float* out, int* err, const int* gate);
+                      const float* Blo, int ncols, int nsplit, int tn, float* out, int* err, const int* gate,
+                      bool use_alo);
 void umma_plan(int M, int Kp, int ncols, int maxs, int* tn, int* s);
 void umma_prepare();
 void umma_choose(Ctx* c, bool tune, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
@@ -1159,6 +1162,11 @@ __global__ void k_axpy2(const double* __restrict__ a, const double* __restrict__
 }  // namespace
 
 constexpr int MX_MAX_SPLIT = 4;
+// 1: the first low-precision solve's tensor-core contractions take the
+// couplings at TF32 (two MMAs per K step instead of three)
+#ifndef PINT_MAIN_2MMA
+#define PINT_MAIN_2MMA 0
+#endif
 
 struct Mx {
   bool ready = false;
@@ -1187,7 +1195,6 @@ struct Mx {
   unsigned graph_epoch = 0;
   bool graphs_off = false;  // capture failed once: issue the iterations directly
   float* CA32 = nullptr;  // FP32 coupling of the cluster coarse sweep
-  float* CM32 = nullptr;  // FP32 coupling of the jump norms
   // FP32 copies for the cluster coarse sweep: F ends, old G values, jumps
   float *Fu32 = nullptr, *Fw32 = nullptr, *Gu32 = nullptr, *Gw32 = nullptr, *Cu32 = nullptr, *Cw32 = nullptr;
   // double-float pairs of AR, AS and of the FP64 trajectory (refinement residual)
@@ -1253,7 +1260,6 @@ static Mx& mx_prepare(Ctx* c) {
     M.Cu32 = Fa((size_t)(N + 1) * d1);
     M.Cw32 = Fa((size_t)(N + 1) * d2);
   }
-  M.CM32 = Fa((size_t)d1 * d2);
   if (tensor) {
     M.Rhi = Fa((size_t)d1 * 2 * ldw);
     M.Rlo = Fa((size_t)d1 * 2 * ldw);
@@ -1342,7 +1348,6 @@ static void mx_refresh(Ctx* c, Mx& M) {
   mx_ar_diff(c, M.ldw, M.AR32, M.Rhi, M.Rlo);  // [-CA | -CM/dt] against [w_p ; w_p - w_{p-1}]
   mx_pad_split(c, c->AS, d2, d1, M.ldu, M.AS32, M.Shi, M.Slo);
   if (M.CA32) mx_to_f32(c, c->CA, (long long)d1 * d2, M.CA32);
-  mx_to_f32(c, c->CM, (long long)d1 * d2, M.CM32);
   mx_split_df(c, c->AR, (long long)d1 * 2 * d2, M.ARh, M.ARl);
   mx_split_df(c, c->AS, (long long)d2 * 2 * d1, M.ASh, M.ASl);
   mx_to_f32(c, c->lam1, d1, M.lam1f);
@@ -1389,6 +1394,10 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
   const int ncols = nact * P;
   const int ldu = M.ldu, ldw = M.ldw;
   const bool tensor = (c->precision == PINT_MIXED);
+  // the first (low-precision) solve may take the couplings at TF32 (two MMAs
+  // per K step): its result is refined against the exact couplings; the
+  // correction solve (per-step sources srcU) keeps the three-MMA product
+  const bool use_alo = srcU != nullptr || !PINT_MAIN_2MMA;
   // tile widths and K splits of the two contractions (the time solve reads one
   // slice of the first; the W recurrence sums the slices of the second)
   int tn0 = 128, tn1 = 128, nsl = 1, one = 1;
@@ -1421,14 +1430,16 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
       else PINT_CUDA(cudaEventRecord(e, c->stream));
     };
     rec(ev[0]);
-    if (tensor) mx_contract_umma(c, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, tn0, M.R, M.err, M.gate);
+    if (tensor)
+      mx_contract_umma(c, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, tn0, M.R, M.err, M.gate, use_alo);
     else mx_contract32(c, 0, M.AR32, d1, 2 * ldw, Ut, Wt, ldu, ldw, P, ncols, M.R, M.gate);
     rec(ev[1]);
     mx_time_solve32(c, M.R, nact, Ut, ldu, M.lam1f, srcU, M.b1f, amp_act, M.twf, M.dshf, M.dshbr, M.bpowf, acc32,
                     M.B1h, M.B1l, M.gate);
     rec(ev[2]);
     if (tensor)
-      mx_contract_umma(c, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, nsl, tn1, M.S, M.err, M.gate);
+      mx_contract_umma(c, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, nsl, tn1, M.S, M.err, M.gate,
+                       use_alo);
     else mx_contract32(c, 1, M.AS32, d2, 2 * ldu, Ut, Wt, ldu, ldw, P, ncols, M.S, M.gate);
     rec(ev[3]);
     mx_w_sweep32(c, M.S, tensor ? nsl : 1, (size_t)ncols * d2, nact, Wt, ldw, M.lam2f, srcW, M.b2f, amp_act,
@@ -1451,7 +1462,8 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
     }
     const std::array<uintptr_t, 9> key{(uintptr_t)Ut, (uintptr_t)Wt, (uintptr_t)srcU, (uintptr_t)srcW,
                                        (uintptr_t)amp_act, (uintptr_t)nact,
-                                       (uintptr_t)(tn0 | (tn1 << 10) | (nsl << 20) | ((tensor ? 1 : 0) << 24)),
+                                       (uintptr_t)(tn0 | (tn1 << 10) | (nsl << 20) | ((tensor ? 1 : 0) << 24) |
+                                                   ((use_alo ? 1 : 0) << 25)),
                                        (uintptr_t)tol_bits, (uintptr_t)par};
     auto f = M.graphs.find(key);
     if (f == M.graphs.end()) {
@@ -1562,14 +1574,16 @@ struct LpRun {
   int k_max, wr_max;
   int K1 = 0, wr_total = 0;
   bool converged = false, nonfinite = false, have_g0 = false;
+  bool g64 = false;         // coarse sweep in FP64 (grid-wide kernel) instead of the FP32 cluster
   double last_jump = 0;
 };
 
 // coarse sweep of the low-precision path: FP32 couplings on one cluster when
-// they fit in its shared memory, else the grid-wide FP64 sweep
+// they fit in its shared memory (and g64 is not asked), else the grid-wide
+// FP64 sweep (FP64 diagonal V_H1 solve, FP64 couplings and update)
 static void g_sweep_lp(Ctx* c, Hot& H, Mx& M, double* Xu, double* Xw, const double* amp, const double* Fu,
-                       const double* Fw, const double* Cu, const double* Cw, int n_lo, bool first) {
-  if (!M.gcl) {
+                       const double* Fw, const double* Cu, const double* Cw, int n_lo, bool first, bool g64) {
+  if (!M.gcl || g64) {
     g_sweep(c, H, Xu, Xw, amp, Fu, Fw, Cu, Cw, n_lo, first);
     g_sweep_check(c, H);
     return;
@@ -1603,7 +1617,7 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
                         int hist_off) {
   const int N = c->N, d1 = c->d1, d2 = c->d2, P = c->P;
   if (!r.have_g0) {
-    g_sweep_lp(c, H, M, r.Xu, r.Xw, r.amp, nullptr, nullptr, r.Cu, r.Cw, 0, true);
+    g_sweep_lp(c, H, M, r.Xu, r.Xw, r.amp, nullptr, nullptr, r.Cu, r.Cw, 0, true, r.g64);
   }
   cudaEvent_t a0, a1;
   PINT_CUDA(cudaEventCreate(&a0));
@@ -1639,12 +1653,11 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
     r.wr_total += it;
     PINT_CUDA(cudaMemcpyAsync(H.Ou, r.Xu, (size_t)(N + 1) * d1 * 8, cudaMemcpyDeviceToDevice, c->stream));
     PINT_CUDA(cudaMemcpyAsync(H.Ow, r.Xw, (size_t)(N + 1) * d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
-    g_sweep_lp(c, H, M, r.Xu, r.Xw, r.amp, H.Fu, H.Fw, r.Cu, r.Cw, n_lo, false);
+    g_sweep_lp(c, H, M, r.Xu, r.Xw, r.amp, H.Fu, H.Fw, r.Cu, r.Cw, n_lo, false, r.g64);
     PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
-    if (M.CM32)
-      k_jump<float><<<dim3(N, JS), 256, 0, c->stream>>>(r.Xu, r.Xw, H.Ou, H.Ow, M.CM32, d1, d2, H.red + 8);
-    else
-      k_jump<double><<<dim3(N, JS), 256, 0, c->stream>>>(r.Xu, r.Xw, H.Ou, H.Ow, c->CM, d1, d2, H.red + 8);
+    // the parareal jump and convergence norm of eq. (2.8) in FP64
+    k_jump<double><<<dim3(N - n_lo, JS), 256, 0, c->stream>>>(r.Xu, r.Xw, H.Ou, H.Ow, c->CM, d1, d2, n_lo,
+                                                               H.red + 8);
     k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
     PINT_LAUNCH_CHECK();
     c->launches += 2;
@@ -1676,16 +1689,13 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
 }
 
 // max_n ||x_n||_{M_H} (n = 0..N) into *out (host)
-static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw, const float* CM32) {
+static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw) {
   const int N = c->N, d1 = c->d1, d2 = c->d2;
   PINT_CUDA(cudaMemsetAsync(H.tmp1, 0, (size_t)(N + 1) * std::max(d1, d2) * 8, c->stream));
-  // k_jump measures rows 1..N against the zero rows of tmp1 (a scale for the
-  // relative tolerances: the FP32 coupling serves as well as the FP64 one)
+  // k_jump measures rows 1..N against the zero rows of tmp1 (the scale of
+  // the relative tolerances)
   PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
-  if (CM32)
-    k_jump<float><<<dim3(N, JS), 256, 0, c->stream>>>(Xu, Xw, H.tmp1, H.tmp1, CM32, d1, d2, H.red + 8);
-  else
-    k_jump<double><<<dim3(N, JS), 256, 0, c->stream>>>(Xu, Xw, H.tmp1, H.tmp1, c->CM, d1, d2, H.red + 8);
+  k_jump<double><<<dim3(N, JS), 256, 0, c->stream>>>(Xu, Xw, H.tmp1, H.tmp1, c->CM, d1, d2, 0, H.red + 8);
   k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
   PINT_LAUNCH_CHECK();
   double h[2];
@@ -1770,12 +1780,13 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
   m.wr_max = wr_max;
   m.eps = eps;
   m.wr_tol = wr_tol;
+  m.g64 = c->coarse64;  // PINT_COARSE_FP64: the main solve's coarse sweep in FP64 too
   {
     // G sweep first to get the state scale for the relative tolerances
     LpRun probe = m;
     probe.k_max = 0;
     parareal_lp(c, H, M, probe, &f_ms, nullptr, nullptr, 0);
-    double sc = state_scale(c, H, H.Xu, H.Xw, M.CM32);
+    double sc = state_scale(c, H, H.Xu, H.Xw);
     if (eps < 0) eps = -eps * sc;  // relative tolerances
     if (wr_tol < 0) wr_tol = -wr_tol * sc;
     // the refinement corrects what the low-precision solve leaves: loose tolerances
@@ -1801,10 +1812,16 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
     // FP32 trajectory, so its contractions need more than FP32 accumulation
     // (products accumulated in FP32 would err by as much as the residual);
     // double-float arithmetic on the FP32 pipe gives ~48 bits.
-    mx_split_df(c, M.Zu, (long long)N * (P + 1) * d1, M.Zuh, M.Zul);
-    mx_split_df(c, M.Zw, (long long)N * (P + 1) * d2, M.Zwh, M.Zwl);
-    mx_wr_gemm_df(c, 0, M.ARh, M.ARl, d1, 2 * d2, M.Zuh, M.Zul, M.Zwh, M.Zwl, ncols, M.R64);
-    mx_wr_gemm_df(c, 1, M.ASh, M.ASl, d2, 2 * d1, M.Zuh, M.Zul, M.Zwh, M.Zwl, ncols, M.S64);
+    if (c->refine64) {  // PINT_REFINE_FP64: the residual contractions on the FP64 pipe
+      wr_gemm64<0>(c, c->AR, d1, 2 * d2, M.Zu, M.Zw, ncols, M.R64);
+      wr_gemm64<1>(c, c->AS, d2, 2 * d1, M.Zu, M.Zw, ncols, M.S64);
+      c->launches += 2;
+    } else {
+      mx_split_df(c, M.Zu, (long long)N * (P + 1) * d1, M.Zuh, M.Zul);
+      mx_split_df(c, M.Zw, (long long)N * (P + 1) * d2, M.Zwh, M.Zwl);
+      mx_wr_gemm_df(c, 0, M.ARh, M.ARl, d1, 2 * d2, M.Zuh, M.Zul, M.Zwh, M.Zwl, ncols, M.R64);
+      mx_wr_gemm_df(c, 1, M.ASh, M.ASl, d2, 2 * d1, M.Zuh, M.Zul, M.Zwh, M.Zwl, ncols, M.S64);
+    }
     mx_residual(c, M.Zu, M.Zw, M.R64, M.S64, H.b1, H.b2, H.amp, M.srcU, M.srcW);
     mx_continuity(c, M.Zu, M.Zw, M.Cu, M.Cw);
     if (M.Cu32) {
@@ -1825,13 +1842,16 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
     y.Wt = M.dWt;
     y.k_max = k_max;
     y.wr_max = wr_max;
+    // the correction solve's jumps decide the returned result: its coarse step
+    // (the diagonal (M11 + Delta t A11) solve, the couplings, eq. (2.7)) is FP64
+    y.g64 = true;
     PINT_CUDA(cudaMemsetAsync(M.Yu, 0, (size_t)d1 * 8, c->stream));
     PINT_CUDA(cudaMemsetAsync(M.Yw, 0, (size_t)d2 * 8, c->stream));
     {
       LpRun probe = y;
       probe.k_max = 0;
       parareal_lp(c, H, M, probe, &f_ms, nullptr, nullptr, 0);
-      double sc = state_scale(c, H, M.Yu, M.Yw, M.CM32);
+      double sc = state_scale(c, H, M.Yu, M.Yw);
       y.eps = eps;  // the jumps stop at eps or at the precision floor
       // WR to 1e-6 of the correction's scale, but no tighter than a tenth of
       // the jump tolerance the correction solve stops at

@@ -123,6 +123,19 @@ static void timed_stage(Ctx* c, int k, F&& f) {
   c->stage_ms[k] += std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
 }
 
+// Section 3.2: the splitting scheme is stable when
+// Delta t lambda_max(A22, M22) <= 1 - gamma^2.  The final time picked for
+// T <= 0 keeps 90% of that bound on the coarse step Delta t = T / N and is
+// rounded down to two significant digits (so that it prints exactly).
+static double stable_final_time(int N, double gamma, double lam22) {
+  if (!(lam22 > 0) || !(gamma >= 0 && gamma < 1)) return 0.0;
+  const double t = 0.9 * N * (1.0 - gamma * gamma) / lam22;
+  if (!(t > 0) || !std::isfinite(t)) return 0.0;
+  const double e = std::floor(std::log10(t)) - 1.0;
+  const double scale = std::pow(10.0, e);
+  return std::floor(t / scale) * scale;
+}
+
 static void fill_info(Ctx* c, pint_space_info* info, double ms) {
   if (!info) return;
   info->n_f = c->n_f;
@@ -138,6 +151,9 @@ static void fill_info(Ctx* c, pint_space_info* info, double ms) {
   info->lambda_max22 = c->lam22;
   info->dt_max = c->dt_max;
   info->setup_ms = ms;
+  info->T = c->have_time ? c->T : 0.0;
+  info->Dt = c->have_time ? c->Dt : 0.0;
+  info->dt = c->have_time ? c->dt : 0.0;
 }
 
 }  // namespace pint
@@ -160,6 +176,12 @@ pint_status pint_setup_fine_grid(pint_ctx** out, int n_f, const double* kappa_ce
   }
   Ctx* c = new Ctx();
   c->stream = (cudaStream_t)stream;
+  if (cudaGetDevice(&c->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete c;
+    set_error("no CUDA device");
+    return PINT_ERR_CUDA;
+  }
   c->n_f = n_f;
   c->nn = (n_f + 1) * (n_f + 1);
   pint_status s = guarded(c, [&](std::vector<void*>& tmp) {
@@ -230,7 +252,7 @@ pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double 
   pint_status unstable = PINT_OK;
   pint_status s = guarded(c, [&](std::vector<void*>&) {
     PINT_REQUIRE(c->have_spaces, PINT_ERR_STATE, "pint_build_multiscale_spaces first");
-    PINT_REQUIRE(T > 0 && std::isfinite(T), PINT_ERR_BAD_ARG, "T must be > 0");
+    PINT_REQUIRE(std::isfinite(T), PINT_ERR_BAD_ARG, "T must be finite");
     PINT_REQUIRE(N >= 1 && N <= 4096, PINT_ERR_BAD_ARG, "N must be in [1, 4096]");
     PINT_REQUIRE(P >= 2 && P <= 64, PINT_ERR_BAD_ARG, "P must be in [2, 64]");
     PINT_REQUIRE(alpha > 0 && alpha < 1, PINT_ERR_BAD_ARG, "alpha must be in (0, 1)");
@@ -247,6 +269,9 @@ pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double 
       timed_stage(c, 4, [&] { build_spectral(c); });
       c->have_reduced = true;
     }
+    if (T <= 0) T = stable_final_time(N, c->gamma, c->lam22);
+    PINT_REQUIRE(T > 0 && std::isfinite(T), PINT_ERR_BAD_ARG,
+                 "no stable final time: lambda_max(A22, M22) or gamma out of range");
     c->T = T;
     c->N = N;
     c->P = P;
@@ -254,9 +279,14 @@ pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double 
     c->precision = precision;
     c->fine_seq = (flags & PINT_FINE_SEQUENTIAL) != 0;
     c->autotune = (flags & PINT_AUTOTUNE) != 0;
+    c->coarse64 = (flags & PINT_COARSE_FP64) != 0;
+    c->refine64 = (flags & PINT_REFINE_FP64) != 0;
     c->Dt = T / N;
     c->dt = c->Dt / P;
     timed_stage(c, 5, [&] { hot_prepare(c); });
+    // graphs captured for the previous time grid hold its dt and alpha as
+    // kernel arguments: never replay them after a re-assembly
+    c->graph_epoch++;
     c->have_time = true;
     PINT_CUDA(cudaEventRecord(e1, c->stream));
     PINT_CUDA(cudaEventSynchronize(e1));

@@ -1,0 +1,115 @@
+"""CUDA path vs the FP64 oracle at the shapes the throughput figure is measured on.
+
+The 256x256 workload (16x16 coarse, J = 4, four oversampling layers, contrast
+1e6, N = 64 intervals x P = 64 fine steps, d1 = 1343, d2 = 257) reaches
+kernel variants that the small parity cases do not: the 8x8 four-step time
+solve and the one-block-per-interval W recurrence at P = 64, the register
+coarse sweep with six rows per warp, the K-split second contraction, and the
+radix-2 FP64 time solve at P = 64.  The second case (96x96, 24x24 coarse,
+d2 = 577 > 512) reaches the column-tiled W recurrence and the shared-memory
+coarse sweep at P = 64.
+
+Reference: the oracle's sequential fine scheme (the limit of Algorithm 1,
+eqs. (2.4)-(2.5) stepped N P times with the lags restarted at every coarse
+boundary), built from the oracle's own multiscale spaces.  Every comparison
+is the relative L2 difference of the fine-grid fields per coarse time
+t_1..t_N, and the bound holds at every one of them: FP64 path <= 1e-10,
+mixed path <= 1e-6.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+
+pytestmark = [pytest.mark.gpu, pytest.mark.slow]
+
+from paper_2411_09244_gb300 import api, _lib  # noqa: E402
+from paper_2411_09244_gb300.inputs import config_c2, config_small  # noqa: E402
+from oracle.pipeline import OracleRun  # noqa: E402
+
+
+def per_time_rel(got, ref):
+    """Relative L2 difference of each row (coarse time); rows where the
+    reference vanishes are skipped."""
+    out = []
+    for n in range(ref.shape[0]):
+        nr = np.linalg.norm(ref[n])
+        if nr > 0:
+            out.append(np.linalg.norm(got[n] - ref[n]) / nr)
+    return np.array(out)
+
+
+def _reference(prob):
+    orc = OracleRun(prob)
+    u, w = orc.sequential()
+    return orc, orc.fine_field(u, w)[1:]
+
+
+@pytest.fixture(scope="module")
+def headline():
+    prob = config_c2()
+    orc, ref = _reference(prob)
+    p = api.from_problem(prob, device="cuda", T=orc.T)
+    yield prob, orc, ref, p
+    p.close()
+
+
+def test_headline_spaces_agree(headline):
+    prob, orc, ref, p = headline
+    assert (p.info["d1"], p.info["d2"]) == (orc.red.d1, orc.red.d2) == (1343, 257)
+    assert abs(p.info["gamma"] - orc.gamma) < 1e-9
+    assert abs(p.info["lambda_max22"] - orc.lam22) < 1e-9 * orc.lam22
+
+
+def test_headline_fp64_parareal_matches_oracle_per_coarse_time(headline):
+    prob, orc, ref, p = headline
+    p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=_lib.PINT_FP64)
+    _, fine, st = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=-1e-13, wr_tol=-1e-16, wr_max=400)
+    assert st["status"] == "OK" and st["converged"]
+    err = per_time_rel(fine.cpu().numpy(), ref)
+    assert err.size == prob.N
+    assert err.max() <= 1e-10, (err.max(), int(err.argmax()), st["K1"])
+
+
+def test_headline_fp64_sequential_matches_oracle_per_coarse_time(headline):
+    prob, orc, ref, p = headline
+    p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=_lib.PINT_FP64)
+    _, fine = p.sequential_solve(prob.u0, prob.f, prob.amp)
+    err = per_time_rel(fine.cpu().numpy(), ref)
+    assert err.max() <= 1e-10, (err.max(), int(err.argmax()))
+
+
+@pytest.mark.parametrize("coarse_fp64", [False, True])
+def test_headline_mixed_matches_oracle_per_coarse_time(headline, coarse_fp64):
+    """The bench's solve (mixed precision, the workload's own tolerance); with
+    PINT_COARSE_FP64 the low-precision solve's coarse sweeps run in FP64 too."""
+    prob, orc, ref, p = headline
+    p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=_lib.PINT_MIXED, coarse_fp64=coarse_fp64)
+    try:
+        _, fine, st = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=prob.eps)
+    finally:
+        p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=_lib.PINT_FP64)
+    assert st["status"] == "OK" and st["converged"]
+    err = per_time_rel(fine.cpu().numpy(), ref)
+    assert err.size == prob.N
+    assert err.max() <= 1e-6, (err.max(), int(err.argmax()), st["K1"], st["wr_total"])
+
+
+def test_wide_v_h2_at_p64_matches_oracle_per_coarse_time():
+    """d2 > 512 at P = 64: column-tiled W recurrence, shared-memory coarse sweep."""
+    prob = config_small(n_f=96, nc=24, J=1, ell=1, N=6, P=64, channels=6, contrast=1e4, f_kind="gauss")
+    orc, ref = _reference(prob)
+    assert orc.red.d2 > 512
+    p = api.from_problem(prob, device="cuda", T=orc.T)
+    try:
+        assert (p.info["d1"], p.info["d2"]) == (orc.red.d1, orc.red.d2)
+        _, f64, st = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=-1e-13, wr_tol=-1e-16, wr_max=400)
+        err = per_time_rel(f64.cpu().numpy(), ref)
+        assert err.max() <= 1e-10, (err.max(), st["K1"])
+        p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=_lib.PINT_MIXED)
+        _, fm, sm = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=-1e-12)
+        assert sm["converged"]
+        err = per_time_rel(fm.cpu().numpy(), ref)
+        assert err.max() <= 1e-6, (err.max(), sm["K1"], sm["wr_total"])
+    finally:
+        p.close()

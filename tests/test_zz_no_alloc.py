@@ -1,9 +1,11 @@
 """The allocation-free prolongation (pint_prolong_noalloc) against the regular
 one (pint_prolong), through the C ABI.
 
-pint_prolong_noalloc exists for callers that cannot allocate device memory
-(stream capture in progress, host-owned allocators, allocation-free loops):
-its scratch is a fixed device array inside the library.  This file is named
+pint_prolong_noalloc exists for callers that cannot call cudaMalloc or any
+allocating routine (a host runtime that owns the device allocator, a loop
+that must not touch it): its scratch is a fixed device array inside the
+library.  The call is stream-ordered and returns without waiting, so each
+check synchronises first.  This file is named
 so that pytest collects it last; it must pass alone in a fresh process and
 after the other tests.  Two calls in a row must each match pint_prolong
 (the same kernels run in both, so the tolerance of the prolongation parity
