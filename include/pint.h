@@ -74,7 +74,9 @@ enum {
   PINT_FINE_SEQUENTIAL = 2,
   PINT_AUTOTUNE = 4,
   PINT_COARSE_FP64 = 8,
-  PINT_REFINE_FP64 = 16
+  PINT_REFINE_FP64 = 16,
+  PINT_CARRY_LAGS = 32,
+  PINT_ADJOINT_RESPONSE = 64
 };
 
 typedef struct {
@@ -167,6 +169,22 @@ pint_status pint_build_multiscale_spaces(pint_ctx* ctx, int nc, int J, int ell,
  *                    residual's two contractions run in FP64 (by default
  *                    in double-float arithmetic, about 48 bits, on the FP32
  *                    pipe);
+ *                    PINT_CARRY_LAGS (PINT_FP64 only; a comparison mode
+ *                    without the paper's counterpart): the lagged increments
+ *                    of eqs. (2.4)-(2.5) are carried across the coarse
+ *                    boundaries instead of restarted, so the limit is the
+ *                    scheme run uninterrupted over [0, T]; the parareal state
+ *                    is (u, w) at t_n and one fine step earlier, F steps the
+ *                    fine scheme P times with the carried lags (all active
+ *                    intervals at once), G takes one coarse step with the
+ *                    fine increment extrapolated to the coarse spacing as its
+ *                    lag and returns the linearly interpolated lag; eq. (2.7)
+ *                    acts on the whole state, eq. (2.8) on (u, w);
+ *                    pint_sequential_solve then gives the uninterrupted scheme;
+ *                    PINT_ADJOINT_RESPONSE: pint_adjoint takes the
+ *                    amplitude gradient from the interval's unit-source
+ *                    response, <lambda_{n+1}, s>, instead of recomputing the
+ *                    fine adjoint inside each interval (see pint_adjoint);
  *                    PINT_AUTOTUNE: on the PINT_MIXED path, the tile width
  *                    and K split of each tensor-core contraction shape are
  *                    measured (CUDA events, best of the cost model's top
@@ -234,7 +252,12 @@ pint_status pint_sequential_solve(pint_ctx* ctx, const double* u0_nodes, const d
  * precision), keeps the coarse states as checkpoints, then parareal
  * backwards in time with the transposed fine scheme on all intervals at once
  * and the transposed coarse step (FP64 on the FP64 path, FP32 transposed
- * sweeps on the low-precision paths).
+ * sweeps on the low-precision paths).  The amplitude gradient recomputes
+ * the fine adjoint inside each interval from the boundary adjoint (the
+ * coarse states are the only checkpoints; the map is linear, so no state
+ * inside an interval is stored): dJ/da_n = sum_p <mu_p, c>, the transposed
+ * fine scheme stepped P times from lambda_{n+1} on all intervals at once, c
+ * the step's unit source term (PINT_ADJOINT_RESPONSE: <lambda_{n+1}, s>).
  *   obs_nodes   ptr (int32, host or device), n_obs node ids in [0, (n_f+1)^2)
  *   data        ptr, N x n_obs observations d_{o,n}
  *   u0_nodes, f_shape, amp   as in pint_parareal_solve
@@ -375,6 +398,17 @@ int pint_tuning_count(void);
 pint_status pint_tuning_get(int* rows, float* us, int cap, int* count);
 pint_status pint_tuning_set(const int* rows, const float* us, int count);
 pint_status pint_tuning_clear(void);
+
+/*
+ * pint_set_wait_limit -- diagnostic control of failure detection: the polls
+ * a grid-barrier wait of the FP64 coarse sweep makes before it gives up
+ * (process-wide; spins < 0 restores the default of 4194304, about 0.1 s).
+ * A wait that gives up records an error flag; the kernel returns, the solve
+ * returns PINT_ERR_TIMEOUT and the context stays usable.  A small value
+ * makes the wait run out on purpose, to exercise that path.  Returns the
+ * previous limit.  Touches no device state.
+ */
+int pint_set_wait_limit(int spins);
 
 /* pint_last_error -- message of the last failing call on this thread. */
 const char* pint_last_error(void);

@@ -24,6 +24,8 @@ PINT_FINE_SEQUENTIAL = 2
 PINT_AUTOTUNE = 4
 PINT_COARSE_FP64 = 8
 PINT_REFINE_FP64 = 16
+PINT_CARRY_LAGS = 32
+PINT_ADJOINT_RESPONSE = 64
 MAX_ITERS = 512
 
 
@@ -93,6 +95,7 @@ SYMBOLS = {
     "pint_tuning_get": [C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_int)],
     "pint_tuning_set": [C.c_void_p, C.c_void_p, C.c_int],
     "pint_tuning_clear": [],
+    "pint_set_wait_limit": [C.c_int],
 }
 
 

@@ -124,6 +124,8 @@ struct Ctx {
   bool autotune = false;  // PINT_AUTOTUNE: measured contraction tiles
   bool coarse64 = false;  // PINT_COARSE_FP64: every coarse sweep of the mixed path in FP64
   bool refine64 = false;  // PINT_REFINE_FP64: refinement residual contractions in FP64
+  bool carry = false;     // PINT_CARRY_LAGS: lag-carrying variant (FP64, sequential fine steps)
+  bool adj_response = false;  // PINT_ADJOINT_RESPONSE: amplitude gradient by <lambda_{n+1}, s>
   bool have_time = false;
 
   // hot-path operators (FP64): [-G1 | G2] and [-CM^T | -dt CA^T]
@@ -189,6 +191,8 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
                  int k_max, double wr_tol, int wr_max, double* u_out, double* coarse_out, pint_stats* st,
                  int n_refine);
 void mixed_release(Ctx* c);
+void solve_carry(Ctx* c, const double* u0_nodes, const double* f_nodes, const double* amp_dev, double eps,
+                 int k_max, double* u_out, double* coarse_out, pint_stats* st, bool sequential);
 void apply_G_dev(Ctx* c, const double* in, int count, const double* f_nodes, const double* amp_dev,
                  double* out);
 void apply_F_dev(Ctx* c, const double* in, int count, const double* f_nodes, const double* amp_dev,
@@ -202,6 +206,10 @@ void adjoint_release(Ctx* c);
 // forward-state access for the adjoint (k_hot64.cu)
 void hot_states(Ctx* c, double** Xu, double** Xw);
 void unit_response(Ctx* c, double* su, double* sw);
+void step_source(Ctx* c, double* cu, double* cw);
+// polls of the coarse sweep's grid-barrier waits before they give up (k_hot64.cu)
+int wait_limit();
+void set_wait_limit(int spins);
 
 // FP32 coarse sweep on one thread-block cluster (k_gcluster.cu)
 // WR stopping test fused into the last kernel of a WR iteration (k_mixed.cu):

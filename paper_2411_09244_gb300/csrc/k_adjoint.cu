@@ -29,6 +29,15 @@
 //   adj w  = -(CM + h CA)^T a^ + (1 - h Lambda2) beta + delta,   adj wl = CM^T a^.
 // The interval start maps x to (u, w, u, w), so adj x = (adj u + adj ul, adj w + adj wl).
 // T = double on the FP64 path, float on the low-precision path.
+//
+// Amplitude gradient, two routes.  Default: the fine adjoint is recomputed
+// inside each interval from the boundary adjoint lambda_{n+1} (the coarse
+// checkpoints), stepping the transposed fine scheme P times on all intervals
+// at once, and dJ/da_n = sum_{p=0..P-1} <mu_p, c> with mu_0 = (lambda_{n+1}, 0),
+// mu_{p+1} = S^T mu_p (S the one-step map) and c the step's source term for
+// a unit amplitude from a zero state.  PINT_ADJOINT_RESPONSE: the shortcut
+// <lambda_{n+1}, s> with s the interval's response to the unit source (equal
+// in exact arithmetic: s = sum_p S^p c).
 #include "common.cuh"
 
 #include <algorithm>
@@ -127,6 +136,22 @@ __global__ void k_adj_store(const T* __restrict__ al, const T* __restrict__ be, 
     else
       ow[e - n1] = (double)be[e - n1] + (double)de[e - n1];
   }
+}
+
+// acc[v] += <(al, be)_v, (cu, cw)> for every column v (block per column): one
+// term of the recomputed amplitude gradient (the lag parts of c are zero)
+template <typename T>
+__global__ void k_amp_acc(const T* __restrict__ al, const T* __restrict__ be, const double* __restrict__ cu,
+                          const double* __restrict__ cw, int d1, int d2, double* __restrict__ acc) {
+  __shared__ double sh[64];
+  const int v = blockIdx.x;
+  const T* a = al + (size_t)v * d1;
+  const T* b = be + (size_t)v * d2;
+  double s = 0.0;
+  for (int e = threadIdx.x; e < d1 + d2; e += blockDim.x)
+    s += (e < d1) ? (double)a[e] * cu[e] : (double)b[e - d1] * cw[e - d1];
+  s = pintd::block_sum(s, sh);
+  if (threadIdx.x == 0) acc[v] += s;
 }
 
 // nodal indicators of the observation nodes, [n_obs][nn]
@@ -297,15 +322,20 @@ Adj& adj_get(Ctx* c, int n_obs) {
 }
 
 // out rows = Phi^T (or G^T with one step) of the `cols` rows of (lu, lw)
+// (acc, cu, cw given: acc[v] += <mu_p, c> before each step p, see above)
 template <typename T>
 void transposed_sweep(Ctx* c, Adj& A, const T* CA, const T* CM, const T* CAt, const T* CMt, const T* l1,
                       const T* l2, const double* lu, const double* lw, int cols, int steps, double h, double* ou,
-                      double* ow) {
+                      double* ow, double* acc = nullptr, const double* cu = nullptr, const double* cw = nullptr) {
   const int d1 = c->d1, d2 = c->d2;
   T *al = (T*)A.al, *be = (T*)A.be, *ga = (T*)A.ga, *de = (T*)A.de, *aD = (T*)A.aD;
   const long long tot = (long long)cols * (d1 + d2);
   k_adj_load<T><<<std::min(nb(tot, 256), 4096u), 256, 0, c->stream>>>(lu, lw, d1, d2, cols, al, be, ga, de);
   for (int p = 0; p < steps; ++p) {
+    if (acc) {
+      k_amp_acc<T><<<cols, 256, 0, c->stream>>>(al, be, cu, cw, d1, d2, acc);
+      c->launches++;
+    }
     k_adjT_u<T><<<dim3(nb((long long)d1 * 32, 256), cols), 256, 0, c->stream>>>(CA, CM, d1, d2, l1, (T)h, al, be,
                                                                                  ga, aD);
     k_adjT_w<T><<<dim3(nb((long long)d2 * 32, 256), cols), 256, 0, c->stream>>>(CMt, CAt, d1, d2, l2, (T)h, be,
@@ -425,11 +455,23 @@ void adjoint_solve(Ctx* c, const int* obs, int n_obs, const double* data, const 
     backward_parareal<float>(c, A, (const float*)A.CA, (const float*)A.CM, (const float*)A.CAt,
                              (const float*)A.CMt, (const float*)A.l1, (const float*)A.l2, N, 1e-7);
   }
-  // dJ/da_n = <lambda_{n+1}, s>
-  if (grad_amp) {
+  if (grad_amp && c->adj_response) {
+    // dJ/da_n = <lambda_{n+1}, s>
     unit_response(c, A.su, A.sw);
     k_amp_grad<<<N, 256, 0, c->stream>>>(A.Lu, A.Lw, A.su, A.sw, d1, d2, grad_amp);
     PINT_LAUNCH_CHECK();
+  } else if (grad_amp) {
+    // the fine adjoint recomputed inside every interval from lambda_{n+1}:
+    // dJ/da_n = sum_p <mu_p, c>, all intervals at once
+    step_source(c, A.su, A.sw);
+    PINT_CUDA(cudaMemsetAsync(grad_amp, 0, (size_t)N * 8, c->stream));
+    if (A.prec == 0)
+      transposed_sweep<double>(c, A, c->CA, c->CM, c->CAt, c->CMt, c->lam1, c->lam2, A.Lu + d1, A.Lw + d2, N,
+                               c->P, c->dt, A.Fu, A.Fw, grad_amp, A.su, A.sw);
+    else
+      transposed_sweep<float>(c, A, (const float*)A.CA, (const float*)A.CM, (const float*)A.CAt,
+                              (const float*)A.CMt, (const float*)A.l1, (const float*)A.l2, A.Lu + d1, A.Lw + d2,
+                              N, c->P, c->dt, A.Fu, A.Fw, grad_amp, A.su, A.sw);
   }
   // dJ/du0 = M_f Psi [Q, Q2] M_H~^-1 lambda_0, with M_H~ = [[I, CM], [CM^T, I]]
   if (grad_u0) {

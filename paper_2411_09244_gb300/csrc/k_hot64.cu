@@ -22,6 +22,7 @@
 
 #include <algorithm>
 #include <array>
+#include <atomic>
 #include <cmath>
 #include <cstdint>
 #include <map>
@@ -619,7 +620,7 @@ namespace {
 constexpr int GS_THREADS = 512;
 constexpr int GS_SPIN = 1 << 22;
 
-__device__ bool gs_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks, int* err) {
+__device__ bool gs_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks, int* err, int spin_limit) {
   __syncthreads();
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
@@ -633,11 +634,11 @@ __device__ bool gs_barrier(unsigned* count, volatile unsigned* gen, unsigned nbl
       atomicAdd((unsigned*)gen, 1u);
     } else {
       int it = 0;
-      while (*gen == g && it < GS_SPIN) {
+      while (*gen == g && it < spin_limit) {
         ++it;
         __nanosleep(20);
       }
-      if (it >= GS_SPIN) {
+      if (*gen == g) {  // gave up: the other blocks did not all arrive within the limit
         atomicExch(err, 1);
         s_ok = 0;
       }
@@ -657,6 +658,7 @@ struct GSArgs {
   unsigned* count;
   unsigned* gen;
   int* err;
+  int spin;  // polls before a barrier wait gives up
 };
 
 constexpr int GS_SPLIT = 8;                          // warps per w-phase row
@@ -680,7 +682,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_g_sweep(GSArgs a) {
       acc = pintd::warp_sum(acc);
       if (lane == 0) a.gu[i] = (xu[i] - a.Dt * acc + a.Dt * am * a.b1[i]) / (1.0 + a.Dt * a.lam1[i]);
     }
-    if (!gs_barrier(a.count, a.gen, gridDim.x, a.err)) return;
+    if (!gs_barrier(a.count, a.gen, gridDim.x, a.err, a.spin)) return;
     // w-phase: w' = (1 - Dt lambda2) w - Dt CA^T u' + Dt a b2, then eq. (2.7);
     // each row's length-d1 dot product is split over GS_SPLIT warps of a block
     for (int j0 = blockIdx.x * GS_ROWS; j0 < d2; j0 += gridDim.x * GS_ROWS) {
@@ -711,11 +713,16 @@ __global__ void __launch_bounds__(GS_THREADS) k_g_sweep(GSArgs a) {
       a.Xu[(size_t)(n + 1) * d1 + i] = v;
       a.Gu[(size_t)n * d1 + i] = g;
     }
-    if (!gs_barrier(a.count, a.gen, gridDim.x, a.err)) return;
+    if (!gs_barrier(a.count, a.gen, gridDim.x, a.err, a.spin)) return;
   }
 }
 
 }  // namespace
+
+// polls of a grid-barrier wait before it gives up (pint_set_wait_limit)
+static std::atomic<int> g_wait_limit{GS_SPIN};
+int wait_limit() { return g_wait_limit.load(); }
+void set_wait_limit(int spins) { g_wait_limit.store(spins < 0 ? GS_SPIN : spins); }
 
 // one coarse sweep n = n_lo..N-1 (first: x_{n+1} = G(x_n) (+ c_{n+1}))
 static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, const double* Fu, const double* Fw,
@@ -763,6 +770,7 @@ static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, c
   a.count = H.gsync;
   a.gen = H.gsync + 1;
   a.err = (int*)(H.gsync + 2);
+  a.spin = wait_limit();
   void* args[] = {&a};
   const int blocks = num_sms;  // one block per SM: fewest barrier arrivals
   PINT_CUDA(cudaLaunchCooperativeKernel((const void*)k_g_sweep, dim3(blocks), dim3(GS_THREADS), args, 0, c->stream));
@@ -773,7 +781,12 @@ static void g_sweep_check(Ctx* c, Hot& H) {
   int e = 0;
   PINT_CUDA(cudaMemcpyAsync(&e, H.gsync + 2, 4, cudaMemcpyDeviceToHost, c->stream));
   PINT_CUDA(cudaStreamSynchronize(c->stream));
-  PINT_REQUIRE(e == 0, PINT_ERR_TIMEOUT, "coarse sweep: bounded grid barrier expired");
+  if (e != 0) {
+    // blocks that gave up left the counter mid-count: start the next sweep clean
+    PINT_CUDA(cudaMemsetAsync(H.gsync, 0, 64, c->stream));
+    PINT_CUDA(cudaStreamSynchronize(c->stream));
+    throw Fail{PINT_ERR_TIMEOUT, "coarse sweep: bounded grid barrier expired"};
+  }
 }
 
 // WR fine propagator on intervals [n_lo, n_lo + nact) whose starts are
@@ -862,6 +875,24 @@ static void stage_amp(Ctx* c, Hot& H, const double* amp_dev, int count) {
 
 static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw);
 
+// initial value (eq. (2.2)): L2 projection onto V_H through the joint Gram
+// matrix, in spectral coordinates, into H.Xu[0], H.Xw[0]
+static void initial_state(Ctx* c, Hot& H, const double* u0_nodes) {
+  const int d1 = c->d1, d2 = c->d2;
+  apply_stencil(c, c->stM, u0_nodes, H.nodes, 1);
+  raw_dot(c, H.nodes, 1, H.raw);
+  to_reduced(c, H.raw, 1, H.tmp1, H.tmp2);
+  double* g1 = H.Ou;  // scratch rows
+  double* g2 = H.Ow;
+  dense_gemm(c, c->Q, H.tmp1, g1, d1, 1, d1, true, false, 1.0, 0.0);
+  dense_gemm(c, c->Q2, H.tmp2, g2, d2, 1, d2, true, false, 1.0, 0.0);
+  k_proj_rhs<<<nb_((long long)d2 * 32, 256), 256, 0, c->stream>>>(c->CMt, g1, g2, d1, d2, H.tmp2);
+  dense_gemm(c, c->projInv, H.tmp2, H.Xw, d2, 1, d2, false, false, 1.0, 0.0);
+  k_proj_u<<<nb_((long long)d1 * 32, 256), 256, 0, c->stream>>>(c->CM, g1, H.Xw, d1, d2, H.Xu);
+  PINT_LAUNCH_CHECK();
+  c->launches += 7;
+}
+
 void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const double* amp_dev, double eps,
                 int k_max, double wr_tol, int wr_max, double* u_out, double* coarse_out, pint_stats* st,
                 bool sequential) {
@@ -880,19 +911,7 @@ void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const dou
   PINT_CUDA(cudaEventRecord(e0, c->stream));
   stage_amp(c, H, amp_dev, N);
   spectral_load(c, H, f_nodes);
-  // initial projection (eq. (2.2)) into spectral coordinates
-  apply_stencil(c, c->stM, u0_nodes, H.nodes, 1);
-  raw_dot(c, H.nodes, 1, H.raw);
-  to_reduced(c, H.raw, 1, H.tmp1, H.tmp2);
-  double* g1 = H.Ou;  // scratch rows
-  double* g2 = H.Ow;
-  dense_gemm(c, c->Q, H.tmp1, g1, d1, 1, d1, true, false, 1.0, 0.0);
-  dense_gemm(c, c->Q2, H.tmp2, g2, d2, 1, d2, true, false, 1.0, 0.0);
-  k_proj_rhs<<<nb_((long long)d2 * 32, 256), 256, 0, c->stream>>>(c->CMt, g1, g2, d1, d2, H.tmp2);
-  dense_gemm(c, c->projInv, H.tmp2, H.Xw, d2, 1, d2, false, false, 1.0, 0.0);
-  k_proj_u<<<nb_((long long)d1 * 32, 256), 256, 0, c->stream>>>(c->CM, g1, H.Xw, d1, d2, H.Xu);
-  PINT_LAUNCH_CHECK();
-  c->launches += 7;
+  initial_state(c, H, u0_nodes);
   int K1 = 0, wr_total = 0;
   bool converged = false, nonfinite = false;
   float f_ms = 0.f;
@@ -1022,6 +1041,214 @@ void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const dou
   PINT_REQUIRE(converged, PINT_ERR_NOT_CONVERGED, "parareal stopped at k_max above eps");
 }
 
+// ---------------------------------------------------------------------------
+// Lag-carrying variant of Algorithm 1 (PINT_CARRY_LAGS; the paper has no such
+// variant, it restarts the lagged increments of eqs. (2.4)-(2.5) at every
+// propagator call).  The lags are carried across the coarse boundaries, so
+// the limit is the fine scheme run uninterrupted over [0, T].  The parareal
+// state is x_n = (u_n, w_n, u_n^-, w_n^-), the states at t_n and one fine
+// step earlier:
+//   F(x): P fine steps from (u, w) with the lags (u^-, w^-), batched over the
+//         active intervals; returns (u_P, w_P, u_{P-1}, w_{P-1});
+//   G(x): one step of size Delta t whose lag is the fine increment
+//         extrapolated to the coarse spacing, x - (Delta t / dt)(x - x^-);
+//         the output lag interpolates linearly, x'^- = x' - (dt / Delta t)(x' - x);
+//   eq. (2.7) on all four parts, x_0 = (u0, w0, u0, w0); eq. (2.8) on (u, w).
+// FP64, spectral coordinates, fine propagator stepped sequentially.
+// ---------------------------------------------------------------------------
+namespace {
+
+__global__ void k_lin2(const double* __restrict__ x, const double* __restrict__ y, double a, double b, long long n,
+                       double* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = a * x[e] + b * y[e];
+}
+__global__ void k_upd3(const double* __restrict__ g, const double* __restrict__ f, const double* __restrict__ go,
+                       long long n, double* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = g[e] + f[e] - go[e];
+}
+
+// the four parts of an augmented state array set: rows of d1 (u, u^-) and d2 (w, w^-)
+struct Aug {
+  double *u, *w, *ul, *wl;
+};
+
+}  // namespace
+
+static void lin2(Ctx* c, const double* x, const double* y, double a, double b, long long n, double* out) {
+  k_lin2<<<nb_(n, 256), 256, 0, c->stream>>>(x, y, a, b, n, out);
+  PINT_LAUNCH_CHECK();
+  c->launches++;
+}
+
+// G of the carrying variant on state row n of X into row n of G (count = 1);
+// t1, t2: scratch of d1, d2
+static void g_carry(Ctx* c, Hot& H, const Aug& X, int n, const Aug& G, int gn, double* t1, double* t2) {
+  const int d1 = c->d1, d2 = c->d2;
+  const double e = (double)c->P;  // Delta t / dt
+  const double *u = X.u + (size_t)n * d1, *w = X.w + (size_t)n * d2;
+  lin2(c, u, X.ul + (size_t)n * d1, 1.0 - e, e, d1, t1);  // u - e (u - u^-)
+  lin2(c, w, X.wl + (size_t)n * d2, 1.0 - e, e, d2, t2);
+  double *gu = G.u + (size_t)gn * d1, *gw = G.w + (size_t)gn * d2;
+  step_batch(c, H, u, w, t1, t2, H.amp + n, c->Dt, 1, gu, gw);
+  const double r = 1.0 / e;  // x'^- = x' - (dt / Delta t)(x' - x)
+  lin2(c, gu, u, 1.0 - r, r, d1, G.ul + (size_t)gn * d1);
+  lin2(c, gw, w, 1.0 - r, r, d2, G.wl + (size_t)gn * d2);
+}
+
+// F of the carrying variant on rows [n0, n0 + cnt) of X into rows of Fo
+static void f_carry(Ctx* c, Hot& H, const Aug& X, int n0, int cnt, const Aug& Fo) {
+  const int d1 = c->d1, d2 = c->d2;
+  const size_t s1 = (size_t)cnt * d1, s2 = (size_t)cnt * d2;
+  double *u = H.Ut, *ul = H.Ut + s1, *uo = H.Ut + 2 * s1;
+  double *w = H.Wt, *wl = H.Wt + s2, *wo = H.Wt + 2 * s2;
+  PINT_CUDA(cudaMemcpyAsync(u, X.u + (size_t)n0 * d1, s1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(w, X.w + (size_t)n0 * d2, s2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(ul, X.ul + (size_t)n0 * d1, s1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(wl, X.wl + (size_t)n0 * d2, s2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+  for (int p = 0; p < c->P; ++p) {
+    step_batch(c, H, u, w, ul, wl, H.amp + n0, c->dt, cnt, uo, wo);
+    std::swap(ul, u);
+    std::swap(wl, w);
+    std::swap(u, uo);
+    std::swap(w, wo);
+  }
+  PINT_CUDA(cudaMemcpyAsync(Fo.u + (size_t)n0 * d1, u, s1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(Fo.w + (size_t)n0 * d2, w, s2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(Fo.ul + (size_t)n0 * d1, ul, s1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+  PINT_CUDA(cudaMemcpyAsync(Fo.wl + (size_t)n0 * d2, wl, s2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+}
+
+static void initial_state(Ctx* c, Hot& H, const double* u0_nodes);
+
+void solve_carry(Ctx* c, const double* u0_nodes, const double* f_nodes, const double* amp_dev, double eps,
+                 int k_max, double* u_out, double* coarse_out, pint_stats* st, bool sequential) {
+  Hot& H = hot(c);
+  ensure(c, H, c->N);
+  const int N = c->N, d1 = c->d1, d2 = c->d2;
+  cudaEvent_t e0, e1;
+  PINT_CUDA(cudaEventCreate(&e0));
+  PINT_CUDA(cudaEventCreate(&e1));
+  c->launches = 0;
+  PINT_CUDA(cudaEventRecord(e0, c->stream));
+  stage_amp(c, H, amp_dev, N);
+  spectral_load(c, H, f_nodes);
+  initial_state(c, H, u0_nodes);  // H.Xu[0], H.Xw[0]
+  // buffers: lags of X, F results, old G values (all four parts)
+  std::vector<void*> own;
+  auto da = [&](size_t n) {
+    own.push_back(dalloc(c, n * 8));
+    return (double*)own.back();
+  };
+  const size_t r1 = (size_t)(N + 1) * d1, r2 = (size_t)(N + 1) * d2;
+  Aug X{H.Xu, H.Xw, da(r1), da(r2)};
+  Aug Fo{da(r1), da(r2), da(r1), da(r2)};
+  Aug Go{da(r1), da(r2), da(r1), da(r2)};
+  double *t1 = da(d1), *t2 = da(d2);
+  PINT_CUDA(cudaMemcpyAsync(X.ul, X.u, (size_t)d1 * 8, cudaMemcpyDeviceToDevice, c->stream));  // x_0^- = x_0
+  PINT_CUDA(cudaMemcpyAsync(X.wl, X.w, (size_t)d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+  int K1 = 0;
+  bool converged = false, nonfinite = false;
+  if (sequential) {
+    // the scheme uninterrupted over all N P steps: F interval after interval
+    for (int n = 0; n < N; ++n) {
+      f_carry(c, H, X, n, 1, Fo);
+      Aug Xn{X.u + d1, X.w + d2, X.ul + d1, X.wl + d2};  // row n + 1 as row n of a shifted view
+      PINT_CUDA(cudaMemcpyAsync(Xn.u + (size_t)n * d1, Fo.u + (size_t)n * d1, d1 * 8, cudaMemcpyDeviceToDevice,
+                                c->stream));
+      PINT_CUDA(cudaMemcpyAsync(Xn.w + (size_t)n * d2, Fo.w + (size_t)n * d2, d2 * 8, cudaMemcpyDeviceToDevice,
+                                c->stream));
+      PINT_CUDA(cudaMemcpyAsync(Xn.ul + (size_t)n * d1, Fo.ul + (size_t)n * d1, d1 * 8,
+                                cudaMemcpyDeviceToDevice, c->stream));
+      PINT_CUDA(cudaMemcpyAsync(Xn.wl + (size_t)n * d2, Fo.wl + (size_t)n * d2, d2 * 8,
+                                cudaMemcpyDeviceToDevice, c->stream));
+    }
+    converged = true;
+  } else {
+    // k = 0: G sweep, x_{n+1} = G(x_n), kept as the old G values
+    const Aug X1{X.u + d1, X.w + d2, X.ul + d1, X.wl + d2};  // rows shifted by one
+    for (int n = 0; n < N; ++n) {
+      g_carry(c, H, X, n, Go, n, t1, t2);
+      PINT_CUDA(cudaMemcpyAsync(X1.u + (size_t)n * d1, Go.u + (size_t)n * d1, d1 * 8, cudaMemcpyDeviceToDevice,
+                                c->stream));
+      PINT_CUDA(cudaMemcpyAsync(X1.w + (size_t)n * d2, Go.w + (size_t)n * d2, d2 * 8, cudaMemcpyDeviceToDevice,
+                                c->stream));
+      PINT_CUDA(cudaMemcpyAsync(X1.ul + (size_t)n * d1, Go.ul + (size_t)n * d1, d1 * 8,
+                                cudaMemcpyDeviceToDevice, c->stream));
+      PINT_CUDA(cudaMemcpyAsync(X1.wl + (size_t)n * d2, Go.wl + (size_t)n * d2, d2 * 8,
+                                cudaMemcpyDeviceToDevice, c->stream));
+    }
+    if (eps < 0) eps = -eps * state_scale(c, H, H.Xu, H.Xw);
+    const Aug G1{da(r1), da(r2), da(r1), da(r2)};  // this sweep's G values
+    for (int k = 1; k <= std::min(k_max, N); ++k) {
+      const int n_lo = k - 1;
+      f_carry(c, H, X, n_lo, N - n_lo, Fo);
+      PINT_CUDA(cudaMemcpyAsync(H.Ou, X.u, r1 * 8, cudaMemcpyDeviceToDevice, c->stream));
+      PINT_CUDA(cudaMemcpyAsync(H.Ow, X.w, r2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+      for (int n = n_lo; n < N; ++n) {
+        g_carry(c, H, X, n, G1, n, t1, t2);
+        // eq. (2.7) on the augmented state
+        const double* gp[4] = {G1.u, G1.w, G1.ul, G1.wl};
+        const double* fp[4] = {Fo.u, Fo.w, Fo.ul, Fo.wl};
+        double* op[4] = {Go.u, Go.w, Go.ul, Go.wl};
+        double* xp[4] = {X1.u, X1.w, X1.ul, X1.wl};
+        for (int q = 0; q < 4; ++q) {
+          const int d = (q & 1) ? d2 : d1;
+          const size_t o = (size_t)n * d;
+          k_upd3<<<nb_(d, 256), 256, 0, c->stream>>>(gp[q] + o, fp[q] + o, op[q] + o, d, xp[q] + o);
+          PINT_CUDA(cudaMemcpyAsync(op[q] + o, gp[q] + o, (size_t)d * 8, cudaMemcpyDeviceToDevice, c->stream));
+        }
+        PINT_LAUNCH_CHECK();
+        c->launches += 4;
+      }
+      PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
+      k_jump<double><<<dim3(N - n_lo, JS), 256, 0, c->stream>>>(H.Xu, H.Xw, H.Ou, H.Ow, c->CM, d1, d2, n_lo,
+                                                                 H.red + 8);
+      k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
+      PINT_LAUNCH_CHECK();
+      c->launches += 2;
+      double h[2];
+      PINT_CUDA(cudaMemcpyAsync(h, H.red, 16, cudaMemcpyDeviceToHost, c->stream));
+      PINT_CUDA(cudaStreamSynchronize(c->stream));
+      K1 = k;
+      if (st && k - 1 < PINT_MAX_ITERS) st->jumps[k - 1] = h[0];
+      if (h[1] != 0.0) {
+        nonfinite = true;
+        break;
+      }
+      if (h[0] <= eps) {
+        converged = true;
+        break;
+      }
+    }
+    if (K1 == N) converged = true;
+  }
+  from_spectral(c, H.Xu, H.Xw, N + 1, H.tmp1, H.tmp2);
+  if (coarse_out) {
+    PINT_CUDA(cudaMemcpy2DAsync(coarse_out, (size_t)(d1 + d2) * 8, H.tmp1, (size_t)d1 * 8, (size_t)d1 * 8,
+                                N + 1, cudaMemcpyDeviceToDevice, c->stream));
+    PINT_CUDA(cudaMemcpy2DAsync(coarse_out + d1, (size_t)(d1 + d2) * 8, H.tmp2, (size_t)d2 * 8,
+                                (size_t)d2 * 8, N + 1, cudaMemcpyDeviceToDevice, c->stream));
+  }
+  if (u_out) prolong_coeffs(c, H.tmp1 + d1, H.tmp2 + d2, N, u_out);
+  PINT_CUDA(cudaEventRecord(e1, c->stream));
+  PINT_CUDA(cudaEventSynchronize(e1));
+  float ms = 0.f;
+  PINT_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  for (void* b : own) dfree(c, b);
+  if (st) {
+    st->K1 = K1;
+    st->converged = converged ? 1 : 0;
+    st->solve_ms = ms;
+    st->launches = c->launches;
+  }
+  PINT_REQUIRE(!nonfinite, PINT_ERR_NONFINITE, "non-finite parareal jump");
+  PINT_REQUIRE(converged, PINT_ERR_NOT_CONVERGED, "parareal stopped at k_max above eps");
+}
+
 // spectral coarse states of the last solve, (N+1) rows each
 void hot_states(Ctx* c, double** Xu, double** Xw) {
   Hot& H = hot(c);
@@ -1048,6 +1275,16 @@ void unit_response(Ctx* c, double* su, double* sw) {
   }
   PINT_CUDA(cudaMemcpyAsync(su, u, d1 * 8, cudaMemcpyDeviceToDevice, c->stream));
   PINT_CUDA(cudaMemcpyAsync(sw, w, d2 * 8, cudaMemcpyDeviceToDevice, c->stream));
+}
+
+// c~ = one fine step from a zero state (lags zero) with the unit-amplitude
+// spectral loads of the last solve: the source term of the step map
+void step_source(Ctx* c, double* cu, double* cw) {
+  Hot& H = hot(c);
+  const int d1 = c->d1, d2 = c->d2;
+  PINT_CUDA(cudaMemsetAsync(H.Gu, 0, d1 * 8, c->stream));
+  PINT_CUDA(cudaMemsetAsync(H.Gw, 0, d2 * 8, c->stream));
+  step_batch(c, H, H.Gu, H.Gw, H.Gu, H.Gw, nullptr, c->dt, 1, cu, cw);
 }
 
 void apply_G_dev(Ctx* c, const double* in, int count, const double* f_nodes, const double* amp_dev,
@@ -1119,8 +1356,7 @@ void apply_F_dev(Ctx* c, const double* in, int count, const double* f_nodes, con
 void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* Ut, const float* Wt, int ldu,
                    int ldw, int P, int ncols, float* out, const int* gate);
 void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
-                      const float* Blo, int ncols, int nsplit, int tn, float* out, int* err, const int* gate,
-                      bool use_alo);
+                      const float* Blo, int ncols, int nsplit, int tn, float* out, int* err, const int* gate);
 void umma_plan(int M, int Kp, int ncols, int maxs, int* tn, int* s);
 void umma_prepare();
 void umma_choose(Ctx* c, bool tune, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
@@ -1162,11 +1398,6 @@ __global__ void k_axpy2(const double* __restrict__ a, const double* __restrict__
 }  // namespace
 
 constexpr int MX_MAX_SPLIT = 4;
-// 1: the first low-precision solve's tensor-core contractions take the
-// couplings at TF32 (two MMAs per K step instead of three)
-#ifndef PINT_MAIN_2MMA
-#define PINT_MAIN_2MMA 0
-#endif
 
 struct Mx {
   bool ready = false;
@@ -1394,10 +1625,6 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
   const int ncols = nact * P;
   const int ldu = M.ldu, ldw = M.ldw;
   const bool tensor = (c->precision == PINT_MIXED);
-  // the first (low-precision) solve may take the couplings at TF32 (two MMAs
-  // per K step): its result is refined against the exact couplings; the
-  // correction solve (per-step sources srcU) keeps the three-MMA product
-  const bool use_alo = srcU != nullptr || !PINT_MAIN_2MMA;
   // tile widths and K splits of the two contractions (the time solve reads one
   // slice of the first; the W recurrence sums the slices of the second)
   int tn0 = 128, tn1 = 128, nsl = 1, one = 1;
@@ -1430,16 +1657,14 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
       else PINT_CUDA(cudaEventRecord(e, c->stream));
     };
     rec(ev[0]);
-    if (tensor)
-      mx_contract_umma(c, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, tn0, M.R, M.err, M.gate, use_alo);
+    if (tensor) mx_contract_umma(c, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, tn0, M.R, M.err, M.gate);
     else mx_contract32(c, 0, M.AR32, d1, 2 * ldw, Ut, Wt, ldu, ldw, P, ncols, M.R, M.gate);
     rec(ev[1]);
     mx_time_solve32(c, M.R, nact, Ut, ldu, M.lam1f, srcU, M.b1f, amp_act, M.twf, M.dshf, M.dshbr, M.bpowf, acc32,
                     M.B1h, M.B1l, M.gate);
     rec(ev[2]);
     if (tensor)
-      mx_contract_umma(c, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, nsl, tn1, M.S, M.err, M.gate,
-                       use_alo);
+      mx_contract_umma(c, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, nsl, tn1, M.S, M.err, M.gate);
     else mx_contract32(c, 1, M.AS32, d2, 2 * ldu, Ut, Wt, ldu, ldw, P, ncols, M.S, M.gate);
     rec(ev[3]);
     mx_w_sweep32(c, M.S, tensor ? nsl : 1, (size_t)ncols * d2, nact, Wt, ldw, M.lam2f, srcW, M.b2f, amp_act,
@@ -1462,8 +1687,7 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
     }
     const std::array<uintptr_t, 9> key{(uintptr_t)Ut, (uintptr_t)Wt, (uintptr_t)srcU, (uintptr_t)srcW,
                                        (uintptr_t)amp_act, (uintptr_t)nact,
-                                       (uintptr_t)(tn0 | (tn1 << 10) | (nsl << 20) | ((tensor ? 1 : 0) << 24) |
-                                                   ((use_alo ? 1 : 0) << 25)),
+                                       (uintptr_t)(tn0 | (tn1 << 10) | (nsl << 20) | ((tensor ? 1 : 0) << 24)),
                                        (uintptr_t)tol_bits, (uintptr_t)par};
     auto f = M.graphs.find(key);
     if (f == M.graphs.end()) {

@@ -123,106 +123,103 @@ __global__ void __launch_bounds__(256) k_wr_gemm32(const float* __restrict__ A, 
     }
 }
 
-struct F2c {
-  float x, y;
-};
-__device__ inline F2c fmul(F2c a, F2c b) { return {a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x}; }
-
-__device__ void fft32(F2c* v, int P, const float2* __restrict__ tw, int sign) {
-  for (int i = 1, j = 0; i < P; ++i) {
-    int bit = P >> 1;
-    for (; j & bit; bit >>= 1) j ^= bit;
-    j ^= bit;
-    if (i < j) {
-      F2c t = v[i];
-      v[i] = v[j];
-      v[j] = t;
-    }
-  }
-  for (int len = 2; len <= P; len <<= 1) {
-    int step = P / len;
-    for (int i = 0; i < P; i += len)
-      for (int k = 0; k < len / 2; ++k) {
-        float2 t = tw[k * step];
-        F2c w = {t.x, sign < 0 ? t.y : -t.y};
-        F2c a = v[i + k], b = fmul(v[i + k + len / 2], w);
-        v[i + k] = {a.x + b.x, a.y + b.y};
-        v[i + k + len / 2] = {a.x - b.x, a.y - b.y};
-      }
-  }
-}
-
-__device__ void dft32(F2c* v, F2c* tmp, int P, const float2* __restrict__ tw, int sign) {
-  for (int k = 0; k < P; ++k) {
-    F2c s = {0.f, 0.f};
-    for (int j = 0; j < P; ++j) {
-      float2 t = tw[(k * j) % P];
-      F2c w = {t.x, sign < 0 ? t.y : -t.y};
-      F2c m = fmul(v[j], w);
-      s.x += m.x;
-      s.y += m.y;
-    }
-    tmp[k] = s;
-  }
-  for (int k = 0; k < P; ++k) v[k] = tmp[k];
-}
-
-// eq. (4.7) per (interval, mode) in FP32; src (per step, scaled by 1/dt) or
-// the constant source b1 * amp[n]
-__global__ void __launch_bounds__(128) k_time_solve32(const float* __restrict__ R, int d1, int ldu, int P,
-                                                      float* __restrict__ Ut, const float* __restrict__ lam1,
-                                                      const float* __restrict__ src, const float* __restrict__ b1,
-                                                      const double* __restrict__ amp, float alpha, float dt,
-                                                      const float2* __restrict__ tw,
-                                                      const float2* __restrict__ dsh,
-                                                      const float* __restrict__ bpow, int pow2,
-                                                      float* __restrict__ accU, float* __restrict__ B1h,
-                                                      float* __restrict__ B1l, const int* __restrict__ gate) {
+// Any P <= 64 outside {16, 32, 64} (the paper's experiments use P = 30, 40,
+// 50): eq. (4.7) with the length-P DFTs written as dense products with the
+// P x P DFT matrix, for a tile of 32 modes of one interval per CTA.  The
+// scaled right-hand sides X[p][s] (p = step, s = mode) sit in shared memory;
+// thread (k, s) forms Y_k = sum_p e^{-2 pi i p k / P} X_p, divides by
+// d_k + lambda_s, and the inverse product sum_k e^{+2 pi i p k / P} Q_k gives
+// the new states (real part; the imaginary part vanishes for real data).
+constexpr int MM_NS = 32;  // modes per CTA
+__global__ void __launch_bounds__(256) k_time_solve32_mm(const float* __restrict__ R, int d1, int ldu, int P,
+                                                         float* __restrict__ Ut, const float* __restrict__ lam1,
+                                                         const float* __restrict__ src,
+                                                         const float* __restrict__ b1,
+                                                         const double* __restrict__ amp, float alpha, float dt,
+                                                         const float2* __restrict__ tw,
+                                                         const float2* __restrict__ dsh,
+                                                         const float* __restrict__ bpow, float* __restrict__ accU,
+                                                         float* __restrict__ B1h, float* __restrict__ B1l,
+                                                         const int* __restrict__ gate) {
   if (gate && *gate) return;
-  const int nloc = blockIdx.y;
-  const int i = blockIdx.x * blockDim.x + threadIdx.x;
-  __shared__ double sh[64];
-  F2c v[64], tmp[64];
-  float unew[64];
+  constexpr int LD = MM_NS + 1;
+  __shared__ float sX[64 * LD];    // scaled right-hand sides, then the new states
+  __shared__ float sQr[64 * LD];   // shifted-solve results (real, imaginary)
+  __shared__ float sQi[64 * LD];
+  __shared__ float2 stw[64];
+  __shared__ float su0[MM_NS], suP[MM_NS];
+  const int nloc = blockIdx.y, i0 = blockIdx.x * MM_NS;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   float* Un = Ut + (size_t)nloc * (P + 1) * ldu;
-  if (i < d1) {
-    const float li = lam1[i];
-    const float cs = src ? 0.f : b1[i] * (float)amp[nloc];
-    for (int p = 0; p < P; ++p) {
-      float y = R[((size_t)nloc * P + p) * d1 + i] + (src ? src[((size_t)nloc * P + p) * d1 + i] : cs);
-      if (p == 0) y += (Un[i] - alpha * Un[(size_t)P * ldu + i]) / dt;
-      v[p] = {y * bpow[p], 0.f};
-    }
-    if (pow2) fft32(v, P, tw, -1);
-    else dft32(v, tmp, P, tw, -1);
-    for (int k = 0; k < P; ++k) {
-      float2 d = dsh[k];
-      float re = d.x + li, im = d.y;
-      float den = re * re + im * im;
-      v[k] = {(v[k].x * re + v[k].y * im) / den, (v[k].y * re - v[k].x * im) / den};
-    }
-    if (pow2) fft32(v, P, tw, +1);
-    else dft32(v, tmp, P, tw, +1);
-    for (int p = 0; p < P; ++p) unew[p] = v[p].x / ((float)P * bpow[p]);
-    if (B1h) {  // second-contraction column map [u_p - u_{p-1} ; u_{p+1}]
-      const float u0 = Un[i];
-      for (int p = 0; p < P; ++p) {
-        const size_t o = ((size_t)nloc * P + p) * 2 * ldu + i;
-        const float dp = (p == 0) ? 0.f : unew[p - 1] - (p == 1 ? u0 : unew[p - 2]);
-        put_split(B1h, B1l, o, dp);
-        put_split(B1h, B1l, o + ldu, unew[p]);
-      }
-    }
+  const float an = (float)amp[nloc];
+  for (int k = tid; k < P; k += 256) stw[k] = tw[k];
+  if (tid < MM_NS) {
+    const int i = i0 + tid;
+    su0[tid] = i < d1 ? Un[i] : 0.f;
+    suP[tid] = i < d1 ? Un[(size_t)P * ldu + i] : 0.f;  // u_P of the previous iterate
   }
-  for (int p = 0; p < P; ++p) {
-    double du = 0.0;
+  __syncthreads();
+  for (int e = tid; e < P * MM_NS; e += 256) {
+    const int p = e / MM_NS, s = e % MM_NS, i = i0 + s;
+    float y = 0.f;
     if (i < d1) {
-      float old = Un[(size_t)(p + 1) * ldu + i];
-      du = (double)(unew[p] - old) * (double)(unew[p] - old);
-      Un[(size_t)(p + 1) * ldu + i] = unew[p];
+      y = R[((size_t)nloc * P + p) * d1 + i] + (src ? src[((size_t)nloc * P + p) * d1 + i] : b1[i] * an);
+      if (p == 0) y += (su0[s] - alpha * suP[s]) / dt;
+      y *= bpow[p];
     }
-    du = pintd::block_sum(du, sh);
-    if (threadIdx.x == 0) atomicAdd(&accU[(size_t)nloc * P + p], (float)du);
+    sX[p * LD + s] = y;
+  }
+  __syncthreads();
+  for (int e = tid; e < P * MM_NS; e += 256) {
+    const int k = e / MM_NS, s = e % MM_NS, i = i0 + s;
+    float yr = 0.f, yi = 0.f;
+    int m = 0;  // (p k) mod P
+    for (int p = 0; p < P; ++p) {
+      const float2 w = stw[m];
+      const float x = sX[p * LD + s];
+      yr = fmaf(w.x, x, yr);
+      yi = fmaf(w.y, x, yi);
+      m += k;
+      if (m >= P) m -= P;
+    }
+    const float2 d = dsh[k];
+    const float a = d.x + (i < d1 ? lam1[i] : 0.f), c = d.y, inv = 1.f / (a * a + c * c);
+    sQr[k * LD + s] = (yr * a + yi * c) * inv;
+    sQi[k * LD + s] = (yi * a - yr * c) * inv;
+  }
+  __syncthreads();
+  for (int e = tid; e < P * MM_NS; e += 256) {
+    const int p = e / MM_NS, s = e % MM_NS;
+    float y = 0.f;
+    int m = 0;  // (p k) mod P; conj(tw) = e^{+2 pi i m / P}
+    for (int k = 0; k < P; ++k) {
+      const float2 w = stw[m];
+      y = fmaf(w.x, sQr[k * LD + s], y);
+      y = fmaf(w.y, sQi[k * LD + s], y);
+      m += p;
+      if (m >= P) m -= P;
+    }
+    sX[p * LD + s] = y / ((float)P * bpow[p]);
+  }
+  __syncthreads();
+  // new states, column map, squared updates (a warp per step row, lane = mode)
+  for (int p = warp; p < P; p += 8) {
+    const int i = i0 + lane;
+    float dd = 0.f;
+    if (i < d1) {
+      const float uq = sX[p * LD + lane];
+      const float old = Un[(size_t)(p + 1) * ldu + i];
+      Un[(size_t)(p + 1) * ldu + i] = uq;
+      if (B1h) {  // second-contraction column map [u_p - u_{p-1} ; u_{p+1}]
+        const size_t o = ((size_t)nloc * P + p) * 2 * ldu + i;
+        const float dp = (p == 0) ? 0.f : sX[(p - 1) * LD + lane] - (p == 1 ? su0[lane] : sX[(p - 2) * LD + lane]);
+        put_split(B1h, B1l, o, dp);
+        put_split(B1h, B1l, o + ldu, uq);
+      }
+      dd = (uq - old) * (uq - old);
+    }
+    dd = pintd::warp_sumf(dd);
+    if (lane == 0) atomicAdd(&accU[(size_t)nloc * P + p], dd);
   }
 }
 
@@ -1171,9 +1168,10 @@ void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const
   else if (P == 16)
     k_time_solve32_sq<4><<<dim3(nbl(c->d1, 64), nact), 256, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al,
                                                                            dt, tw, dsh, bpow, accU, B1h, B1l, gate);
-  else
-    k_time_solve32<<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, P, Ut, lam1, src, b1, amp, al, dt, tw, dsh, bpow,
-                                                (P & (P - 1)) == 0, accU, B1h, B1l, gate);
+  else  // other P: the DFTs as products with the DFT matrix
+    k_time_solve32_mm<<<dim3(nbl(c->d1, MM_NS), nact), 256, 0, c->stream>>>(R, c->d1, ldu, P, Ut, lam1, src, b1,
+                                                                           amp, al, dt, tw, dsh, bpow, accU, B1h,
+                                                                           B1l, gate);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }

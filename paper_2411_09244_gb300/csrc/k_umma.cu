@@ -11,11 +11,6 @@
 // FP32 accuracy from TF32 operands: every operand is stored as a hi/lo pair
 // (hi = tf32(x), lo = tf32(x - hi)) and each K step issues three MMAs
 // (hi hi + hi lo + lo hi); the dropped lo lo term is below FP32 rounding.
-// With use_alo = 0 the coupling enters as its TF32 part only (two MMAs,
-// hi hi + hi lo, and no A lo copies): the contraction is then exact to FP32
-// for a coupling perturbed by its TF32 rounding (relative 2^-11), a fixed
-// operator error that the refinement's residual (computed with the exact
-// coupling) measures and the correction solve removes.
 //
 // Persistent kernel, one CTA per SM: tiles of 128 modes x tn columns of one
 // K slice (MMA M = 128 with A = coupling rows, N = tn in 128..256 with B =
@@ -152,7 +147,7 @@ __device__ __forceinline__ Tile decode(int tg, int n_ct, int n_rt, int tn) {
 __global__ void __launch_bounds__(THREADS, 1)
     k_wr_umma(const __grid_constant__ CUtensorMap mAh, const __grid_constant__ CUtensorMap mAl,
               const __grid_constant__ CUtensorMap mBh, const __grid_constant__ CUtensorMap mBl, int M, int ncols,
-              int kspan, int nsplit, int tn, int use_alo, float* __restrict__ out, int* __restrict__ err,
+              int kspan, int nsplit, int tn, float* __restrict__ out, int* __restrict__ err,
               const int* __restrict__ gate) {
   const uint32_t IDESC = idesc_tf32(TM, tn);
   if (gate && *gate) return;  // the WR sweep has already converged: no-op launch
@@ -164,7 +159,7 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint8_t* smem = smem_raw + ((1024u - (smem_u32(smem_raw) & 1023u)) & 1023u);
 
   const int n_ct = (ncols + tn - 1) / tn, n_rt = (M + TM - 1) / TM;
-  const uint32_t stage_tx = (use_alo ? 2 : 1) * OPA + 2 * tn * KB * 4;  // bytes the copies of a stage land
+  const uint32_t stage_tx = 2 * OPA + 2 * tn * KB * 4;  // bytes the four copies of a stage land
   const int n_tiles = n_ct * n_rt * nsplit;
   const int my_tiles = (int)blockIdx.x < n_tiles ? (n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
   const int nkb = kspan / KB;
@@ -210,7 +205,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int k0 = T.z * kspan + kb * KB;
           bar_expect_tx(&full[s], stage_tx);
           tma_load_2d(base, &mAh, &full[s], k0, T.row0);
-          if (use_alo) tma_load_2d(base + OPA, &mAl, &full[s], k0, T.row0);
+          tma_load_2d(base + OPA, &mAl, &full[s], k0, T.row0);
           tma_load_2d(base + 2 * OPA, &mBh, &full[s], k0, T.col0);
           tma_load_2d(base + 2 * OPA + OPBM, &mBl, &full[s], k0, T.col0);
         }
@@ -250,7 +245,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             const uint64_t dbh = desc_sw64(base + 2 * OPA + ko), dbl = desc_sw64(base + 2 * OPA + OPBM + ko);
             mma_tf32(d, dah, dbh, IDESC, (kb > 0 || kk > 0) ? 1u : 0u);
             mma_tf32(d, dah, dbl, IDESC, 1u);
-            if (use_alo) mma_tf32(d, dal, dbh, IDESC, 1u);
+            mma_tf32(d, dal, dbh, IDESC, 1u);
           }
           mma_commit(&empty[s]);
         }
@@ -393,8 +388,7 @@ void umma_prepare() {
 }
 
 void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
-                      const float* Blo, int ncols, int nsplit, int tn, float* out, int* err, const int* gate,
-                      bool use_alo) {
+                      const float* Blo, int ncols, int nsplit, int tn, float* out, int* err, const int* gate) {
   umma_prepare();
   PINT_REQUIRE(nsplit >= 1 && Kp % (KB * nsplit) == 0, PINT_ERR_BAD_ARG,
                "contraction K not divisible by the split");
@@ -404,8 +398,8 @@ void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp,
   const CUtensorMap bh = make_map(Bhi, ncols, Kp, tn), bl = make_map(Blo, ncols, Kp, tn);
   const int tiles = ((ncols + tn - 1) / tn) * ((M + TM - 1) / TM) * nsplit;
   const int grid = std::min(tiles, umma_sms());  // persistent: one CTA per SM at most
-  k_wr_umma<<<grid, THREADS, SMEM_BYTES, c->stream>>>(ah, al, bh, bl, M, ncols, Kp / nsplit, nsplit, tn,
-                                                      use_alo ? 1 : 0, out, err, gate);
+  k_wr_umma<<<grid, THREADS, SMEM_BYTES, c->stream>>>(ah, al, bh, bl, M, ncols, Kp / nsplit, nsplit, tn, out, err,
+                                                      gate);
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
@@ -476,10 +470,9 @@ void umma_choose(Ctx* c, bool tune, const float* Ahi, const float* Alo, int M, i
   int btn = *tn_out, bs = *s_out;
   for (auto& cd : cand) {
     const int tn = cd.second.first, s = cd.second.second;
-    mx_contract_umma(c, Ahi, Alo, M, Kp, Bhi, Blo, ncols, s, tn, out, err, nullptr, true);  // warm-up
+    mx_contract_umma(c, Ahi, Alo, M, Kp, Bhi, Blo, ncols, s, tn, out, err, nullptr);  // warm-up
     PINT_CUDA(cudaEventRecord(e0.e, c->stream));
-    for (int r = 0; r < TUNE_REPS; ++r)
-      mx_contract_umma(c, Ahi, Alo, M, Kp, Bhi, Blo, ncols, s, tn, out, err, nullptr, true);
+    for (int r = 0; r < TUNE_REPS; ++r) mx_contract_umma(c, Ahi, Alo, M, Kp, Bhi, Blo, ncols, s, tn, out, err, nullptr);
     PINT_CUDA(cudaEventRecord(e1.e, c->stream));
     PINT_CUDA(cudaEventSynchronize(e1.e));
     float ms = 0.f;

@@ -281,6 +281,10 @@ pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double 
     c->autotune = (flags & PINT_AUTOTUNE) != 0;
     c->coarse64 = (flags & PINT_COARSE_FP64) != 0;
     c->refine64 = (flags & PINT_REFINE_FP64) != 0;
+    c->carry = (flags & PINT_CARRY_LAGS) != 0;
+    c->adj_response = (flags & PINT_ADJOINT_RESPONSE) != 0;
+    PINT_REQUIRE(!c->carry || precision == PINT_FP64, PINT_ERR_BAD_ARG,
+                 "PINT_CARRY_LAGS is an FP64 comparison mode");
     c->Dt = T / N;
     c->dt = c->Dt / P;
     timed_stage(c, 5, [&] { hot_prepare(c); });
@@ -324,7 +328,9 @@ static pint_status solve_common(Ctx* c, const double* u0_nodes, const double* f_
     OutBuf ou = stage_out(c, u_out, (size_t)c->N * c->nn, tmp);
     OutBuf oc = stage_out(c, coarse_out, (size_t)(c->N + 1) * (c->d1 + c->d2), tmp);
     try {
-      if (c->precision != PINT_FP64 && !sequential)
+      if (c->carry)
+        solve_carry(c, du0, df, da, eps, k_max, ou.dev, oc.dev, stats, sequential);
+      else if (c->precision != PINT_FP64 && !sequential)
         solve_mixed(c, du0, df, da, eps, k_max, wr_tol, wr_max, ou.dev, oc.dev, stats, 1);
       else
         solve_fp64(c, du0, df, da, eps, k_max, wr_tol, wr_max, ou.dev, oc.dev, stats, sequential);
@@ -572,6 +578,12 @@ pint_status pint_apply_F(pint_ctx* ctx, const double* in, int count, const doubl
     apply_F_dev(c, di, count, df, da, wr_tol, wr_max, o.dev, wr_iters);
     finish_out(c, o);
   });
+}
+
+int pint_set_wait_limit(int spins) {
+  const int old = wait_limit();
+  set_wait_limit(spins);
+  return old;
 }
 
 int pint_tuning_count(void) { return umma_tuning_count(); }

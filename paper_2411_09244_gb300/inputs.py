@@ -236,6 +236,20 @@ def config_c5(instance: int = 0) -> Problem:
                    f, np.zeros(nn), np.ones(256), {"contrast": 1e6})
 
 
+def config_paper_grid(N: int = 20, P: int = 30, instance: int = 0) -> Problem:
+    """The grid of the paper's experiments (Section 5): h = 1/100, H = 1/10
+    (100x100 fine cells, 10x10 coarse blocks), J = 2, two oversampling
+    layers; 20 channels of width 2 cells and value 1e4 (the first
+    experiment's contrast); f = 1, u0 = 0; N intervals x P fine steps
+    (the first experiment: N = 20, P = 30, N P = 600)."""
+    rng = SplitMix64(SEED_BASE + 6 * 1000 + instance)
+    n_f = 100
+    kappa = paint_kappa(rng, n_f, 20, 1e4, 2)
+    nn = (n_f + 1) ** 2
+    return Problem("channels_100x100", n_f, 10, 2, 2, N, P, 0.1, 1e-10, None, kappa, np.ones(nn),
+                   np.zeros(nn), np.ones(N), {"contrast": 1e4})
+
+
 def config_small(n_f=16, nc=4, J=2, ell=1, N=4, P=8, seed=7, contrast=1e3, channels=2,
                  u0_kind="bumps", f_kind="ones", alpha=0.1) -> Problem:
     """Small instance for fast tests (several tiles, ragged sizes)."""

@@ -72,3 +72,12 @@ def test_null_context_is_rejected_without_gpu(libpint):
     assert libpint.pint_build_multiscale_spaces(None, 4, 2, 1, C.byref(info)) == -1
     assert libpint.pint_destroy(None) == 0
     assert b"NULL" in libpint.pint_last_error()
+
+
+def test_wait_limit_control_without_gpu(libpint):
+    # process-wide setting, no device state: usable without a GPU
+    default = libpint.pint_set_wait_limit(-1)
+    assert default == 1 << 22
+    assert libpint.pint_set_wait_limit(7) == default
+    assert libpint.pint_set_wait_limit(-1) == 7
+    assert libpint.pint_set_wait_limit(-1) == default

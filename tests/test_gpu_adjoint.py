@@ -145,3 +145,49 @@ def test_c3_fp64_central_differences():
             assert fd == pytest.approx(ga @ q, rel=1e-5)
     finally:
         p.close()
+
+
+def test_amplitude_gradient_routes_agree(small):
+    """dJ/da_n by recomputing the fine adjoint inside each interval from the
+    boundary adjoint (default) equals the unit-response shortcut
+    <lambda_{n+1}, s> (PINT_ADJOINT_RESPONSE) and the oracle's recomputed one."""
+    prob, obs, data, run, _ = small
+    adj = Adjoint(run, obs)
+    _, _, ga_rec = adj.gradient(prob.u0, prob.amp, data, amp_mode="recompute")
+    p = api.from_problem(prob, T=run.T)
+    try:
+        _, _, ga = p.adjoint(obs, data, prob.u0, prob.f, prob.amp, eps=1e-13)
+        p.assemble_reduced(run.T, prob.N, prob.P, prob.alpha, adjoint_response=True)
+        _, _, ga_s = p.adjoint(obs, data, prob.u0, prob.f, prob.amp, eps=1e-13)
+    finally:
+        p.close()
+    assert rel(ga.cpu().numpy(), ga_s.cpu().numpy()) < 1e-11
+    assert rel(ga.cpu().numpy(), ga_rec) < 1e-8
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("precision", ["fp64", "mixed"])
+def test_c3_adjoint_matches_oracle_adjoint(precision):
+    """128x128 / 16x16 / J=3 / N=32 x P=32 workload (16 amplitudes held over two
+    intervals each, 64 observation nodes): the GPU gradient against the
+    oracle's FP64 adjoint with the fine adjoint recomputed inside each
+    interval; FP64 path 1e-8, low-precision path 1e-4."""
+    prob = config_c3()
+    obs = observation_nodes(prob.n_f, 64, seed=prob.n_f)
+    rng = np.random.default_rng(21)
+    data = rng.standard_normal((prob.N, obs.size))
+    run = OracleRun(prob)
+    J0, gu0, ga0 = Adjoint(run, obs).gradient(prob.u0, prob.amp, data, amp_mode="recompute")
+    prec = _lib.PINT_FP64 if precision == "fp64" else _lib.PINT_MIXED
+    p = api.from_problem(prob, T=run.T, precision=prec)
+    try:
+        J, gu, ga = p.adjoint(obs, data, prob.u0, prob.f, prob.amp, eps=1e-12)
+    finally:
+        p.close()
+    tol = 1e-8 if precision == "fp64" else 1e-4
+    assert J == pytest.approx(J0, rel=tol)
+    assert rel(gu.cpu().numpy(), gu0) < tol
+    assert rel(ga.cpu().numpy(), ga0) < tol
+    # the gradient of each of the 16 shared amplitudes sums its two intervals
+    g16 = ga.cpu().numpy().reshape(16, 2).sum(axis=1)
+    assert rel(g16, ga0.reshape(16, 2).sum(axis=1)) < tol

@@ -13,8 +13,14 @@ Reference: the oracle's sequential fine scheme (the limit of Algorithm 1,
 eqs. (2.4)-(2.5) stepped N P times with the lags restarted at every coarse
 boundary), built from the oracle's own multiscale spaces.  Every comparison
 is the relative L2 difference of the fine-grid fields per coarse time
-t_1..t_N, and the bound holds at every one of them: FP64 path <= 1e-10,
-mixed path <= 1e-6.
+t_1..t_N, and the bound holds at every one of them: mixed path <= 1e-6;
+FP64 path <= 1e-10, or, on the 256x256 workload, twice the oracle's own
+FP64 spread if that is larger.  At contrast 1e6 the small eigenvectors of
+the auxiliary eigenproblems (eq. (3.1)) are fixed by FP64 only to about
+eps kappa_max / gap, so two FP64 oracles that differ only in the LAPACK
+driver of those eigenproblems already differ by ~1e-10 in the solution
+(2.5e-11..1.3e-10 per coarse time measured); the module measures that
+spread and bounds the GPU by it.
 """
 import numpy as np
 import pytest
@@ -45,45 +51,72 @@ def _reference(prob):
     return orc, orc.fine_field(u, w)[1:]
 
 
+def _oracle_driver_spread(prob, orc, ref):
+    """Largest per-coarse-time difference between the oracle and the same
+    oracle with the eq. (3.1) eigenproblems solved by another LAPACK driver."""
+    import oracle.spaces as spaces
+    eigh = spaces.sla.eigh
+
+    def eigh_gv(a, b=None, **kw):
+        kw.setdefault("driver", "gv")
+        return eigh(a, b, **kw)
+
+    spaces.sla.eigh = eigh_gv
+    try:
+        alt = OracleRun(prob, T=orc.T)
+    finally:
+        spaces.sla.eigh = eigh
+    u, w = alt.sequential()
+    return float(per_time_rel(alt.fine_field(u, w)[1:], ref).max())
+
+
 @pytest.fixture(scope="module")
 def headline():
     prob = config_c2()
     orc, ref = _reference(prob)
+    spread = _oracle_driver_spread(prob, orc, ref)
     p = api.from_problem(prob, device="cuda", T=orc.T)
-    yield prob, orc, ref, p
+    yield prob, orc, ref, p, max(1e-10, 2.0 * spread)
     p.close()
 
 
+def test_headline_oracle_spread_is_small(headline):
+    """The FP64 floor of the setup on this workload: well below the mixed
+    path's bound, and not far above 1e-10."""
+    bound = headline[-1]
+    assert bound <= 1e-9, bound
+
+
 def test_headline_spaces_agree(headline):
-    prob, orc, ref, p = headline
+    prob, orc, ref, p, _ = headline
     assert (p.info["d1"], p.info["d2"]) == (orc.red.d1, orc.red.d2) == (1343, 257)
     assert abs(p.info["gamma"] - orc.gamma) < 1e-9
     assert abs(p.info["lambda_max22"] - orc.lam22) < 1e-9 * orc.lam22
 
 
 def test_headline_fp64_parareal_matches_oracle_per_coarse_time(headline):
-    prob, orc, ref, p = headline
+    prob, orc, ref, p, bound = headline
     p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=_lib.PINT_FP64)
     _, fine, st = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=-1e-13, wr_tol=-1e-16, wr_max=400)
     assert st["status"] == "OK" and st["converged"]
     err = per_time_rel(fine.cpu().numpy(), ref)
     assert err.size == prob.N
-    assert err.max() <= 1e-10, (err.max(), int(err.argmax()), st["K1"])
+    assert err.max() <= bound, (err.max(), bound, int(err.argmax()), st["K1"])
 
 
 def test_headline_fp64_sequential_matches_oracle_per_coarse_time(headline):
-    prob, orc, ref, p = headline
+    prob, orc, ref, p, bound = headline
     p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=_lib.PINT_FP64)
     _, fine = p.sequential_solve(prob.u0, prob.f, prob.amp)
     err = per_time_rel(fine.cpu().numpy(), ref)
-    assert err.max() <= 1e-10, (err.max(), int(err.argmax()))
+    assert err.max() <= bound, (err.max(), bound, int(err.argmax()))
 
 
 @pytest.mark.parametrize("coarse_fp64", [False, True])
 def test_headline_mixed_matches_oracle_per_coarse_time(headline, coarse_fp64):
     """The bench's solve (mixed precision, the workload's own tolerance); with
     PINT_COARSE_FP64 the low-precision solve's coarse sweeps run in FP64 too."""
-    prob, orc, ref, p = headline
+    prob, orc, ref, p, _ = headline
     p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=_lib.PINT_MIXED, coarse_fp64=coarse_fp64)
     try:
         _, fine, st = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=prob.eps)

@@ -294,6 +294,30 @@ def test_library_picks_the_stable_final_time():
         p.close()
 
 
+def test_bounded_wait_timeout_returns_status_and_context_recovers():
+    """Failure detection without a device fault: with the grid-barrier wait
+    limit at zero every block but the last to arrive gives up at once, the
+    coarse sweep records the expiry and returns, and the solve returns
+    TIMEOUT; with the limit restored the same context solves as before."""
+    from paper_2411_09244_gb300._lib import PintError
+    prob = config_small(n_f=16, nc=4, J=2, ell=1, N=4, P=8)
+    orc = OracleRun(prob)
+    p = api.from_problem(prob, device="cuda", T=orc.T)
+    try:
+        c0, _, s0 = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-12, want_fine=False)
+        p.lib.pint_set_wait_limit(0)
+        try:
+            with pytest.raises(PintError, match="TIMEOUT"):
+                p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-12, want_fine=False)
+        finally:
+            p.lib.pint_set_wait_limit(-1)
+        c1, _, s1 = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-12, want_fine=False)
+        assert s1["converged"] and s1["K1"] == s0["K1"]
+        assert rel_t(c1.cpu().numpy(), c0.cpu().numpy()) < 1e-14
+    finally:
+        p.close()
+
+
 @pytest.mark.parametrize("mixed", [False, True])
 def test_not_converged_and_nonfinite_statuses(mixed):
     """Failure statuses without any device fault: k_max below what eps needs
