@@ -136,6 +136,237 @@ __device__ double apply_sb_row(const BlkArgs& g, int bx, int by, int r, const do
   return acc;
 }
 
+// y = A_b x with A_b the block-local stiffness (only this block's cells)
+__device__ double apply_ab_row(const BlkArgs& g, int bx, int by, int r, const double* x) {
+  int bs = g.bs, w = bs + 1;
+  int a = r % w, b = r / w;
+  double acc = 0.0;
+  for (int cj = b - 1; cj <= b; ++cj) {
+    if (cj < 0 || cj >= bs) continue;
+    for (int ci = a - 1; ci <= a; ++ci) {
+      if (ci < 0 || ci >= bs) continue;
+      double kap = cell_kappa(g, bx, by, ci, cj);
+      int lx = a - ci, ly = b - cj;
+      int ca = (ly == 0) ? (lx == 0 ? 0 : 1) : (lx == 1 ? 2 : 3);
+      for (int cb = 0; cb < 4; ++cb) {
+        int col = (cj + pintd::corner_y(cb)) * w + ci + pintd::corner_x(cb);
+        acc += kap * q1s(ca, cb) * x[col];
+      }
+    }
+  }
+  return acc;
+}
+
+// ---------------------------------------------------------------------------
+// Large blocks (nb > SI_MIN_NB nodes): the J + 1 smallest pairs of eq. (3.1)
+// by shift-invert subspace iteration instead of the dense Jacobi (whose
+// O(nb^3) sweeps dominate setup for 32-cell blocks).  K = A_b + sigma S_b is
+// banded (9-point stencil, half-bandwidth bs + 2) and factored once, K = L L^T;
+// each iteration solves K Y = S_b X for the m columns of X and runs
+// Rayleigh-Ritz with the exact A_b and S_b, so the Ritz vectors come out
+// S-orthonormal and sorted.  The iteration stops when the leading m - 2 pairs
+// have residuals ||A x - theta S x|| below 1e-12 (||A x|| + |theta| ||S x||)
+// + 1e-15 lambda_max ||S x||.  lambda_max (the cluster rule's absolute scale)
+// is the element bound 24 (H/h)^2: kappa cancels between A_b and the
+// kappa_tilde mass, so every cell's pencil has that largest eigenvalue, and a
+// uniform block attains it.
+// ---------------------------------------------------------------------------
+constexpr int SI_MIN_NB = 400;
+constexpr int SI_EXTRA = 6;      // Ritz vectors beyond the J + 1 wanted
+constexpr int SI_MAXIT = 400;
+constexpr double SI_SIGMA = 1.0; // the pencil's eigenvalues are O(pi^2 (a^2 + b^2)), bs-independent
+
+__device__ inline double si_hash(int r, int j) {
+  unsigned long long z = 0x9E3779B97F4A7C15ull * (unsigned long long)(r * 64 + j + 1);
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  z ^= z >> 31;
+  return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+}
+
+// returns the iterations done; Ritz values into th[0..m), vectors (S-orthonormal,
+// ascending) into X (column j at j nb); sets *status = 1 for a non-positive pivot
+__device__ int si_eigs(const BlkArgs& g, int bx, int by, int m, double* Kb, double* X, double* Y, double* Z,
+                       double* AX, double* sm, double* th, double* sh, int* status) {
+  const int nb = g.nb, bs = g.bs, w1 = bs + 1, hw = bs + 2, bw = hw + 1;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nwarp = BT / 32;
+  __shared__ double s_piv;
+  __shared__ int s_done;
+  double* Am = sm;             // m x m
+  double* Sm = Am + KCAP * KCAP;
+  double* Lm = Sm + KCAP * KCAP;
+  double* Wm = Lm + KCAP * KCAP;
+  double* Vm = Wm + KCAP * KCAP;
+  // ---- banded K = A_b + sigma S_b (row r, slot k <-> column r - hw + k) ----
+  for (int e = tid; e < nb * bw; e += BT) Kb[e] = 0.0;
+  __syncthreads();
+  for (int r = tid; r < nb; r += BT) {
+    const int a = r % w1, b = r / w1;
+    for (int cj = b - 1; cj <= b; ++cj) {
+      if (cj < 0 || cj >= bs) continue;
+      for (int ci = a - 1; ci <= a; ++ci) {
+        if (ci < 0 || ci >= bs) continue;
+        const double kap = cell_kappa(g, bx, by, ci, cj), kt = kap * g.kt_scale * g.h2;
+        const int lx = a - ci, ly = b - cj;
+        const int ca = (ly == 0) ? (lx == 0 ? 0 : 1) : (lx == 1 ? 2 : 3);
+        for (int cb = 0; cb < 4; ++cb) {
+          const int col = (cj + pintd::corner_y(cb)) * w1 + ci + pintd::corner_x(cb);
+          if (col <= r) Kb[(size_t)r * bw + (col - r + hw)] += kap * q1s(ca, cb) + SI_SIGMA * kt * q1m(ca, cb);
+        }
+      }
+    }
+  }
+  __syncthreads();
+  // ---- banded Cholesky, right-looking -------------------------------------------
+  for (int k = 0; k < nb; ++k) {
+    if (tid == 0) {
+      double d = Kb[(size_t)k * bw + hw];
+      if (!(d > 0.0)) {
+        *status = 1;
+        d = 1.0;
+      }
+      s_piv = sqrt(d);
+      Kb[(size_t)k * bw + hw] = s_piv;
+    }
+    __syncthreads();
+    const int rem = min(hw, nb - 1 - k);
+    for (int t = tid; t < rem; t += BT) Kb[(size_t)(k + 1 + t) * bw + (k - (k + 1 + t) + hw)] /= s_piv;
+    __syncthreads();
+    for (int t = tid; t < rem * rem; t += BT) {
+      const int i = k + 1 + t / rem, j = k + 1 + t % rem;
+      if (j <= i)
+        Kb[(size_t)i * bw + (j - i + hw)] -= Kb[(size_t)i * bw + (k - i + hw)] * Kb[(size_t)j * bw + (k - j + hw)];
+    }
+    __syncthreads();
+  }
+  // ---- start: seeded pseudo-random columns ----------------------------------
+  for (int e = tid; e < nb * m; e += BT) X[e] = si_hash(e % nb, e / nb);
+  __syncthreads();
+  const double lmax = 24.0 * bs * bs;
+  const int need = m - 2;
+  int it = 0;
+  for (it = 1; it <= SI_MAXIT; ++it) {
+    // Z = S X; Y = K^-1 Z (a warp per column: forward then backward, row by row)
+    for (int e = tid; e < nb * m; e += BT) Z[e] = apply_sb_row(g, bx, by, e % nb, X + (size_t)(e / nb) * nb);
+    __syncthreads();
+    for (int j = warp; j < m; j += nwarp) {
+      double* y = Y + (size_t)j * nb;
+      const double* z = Z + (size_t)j * nb;
+      for (int i = 0; i < nb; ++i) {
+        const double* Li = Kb + (size_t)i * bw;
+        double acc = 0.0;
+        for (int k = max(0, i - hw) + lane; k < i; k += 32) acc += Li[k - i + hw] * y[k];
+        acc = pintd::warp_sum(acc);
+        if (lane == 0) y[i] = (z[i] - acc) / Li[hw];
+        __syncwarp();
+      }
+      for (int i = nb - 1; i >= 0; --i) {
+        double acc = 0.0;
+        for (int k = i + 1 + lane; k <= min(nb - 1, i + hw); k += 32) acc += Kb[(size_t)k * bw + (i - k + hw)] * y[k];
+        acc = pintd::warp_sum(acc);
+        if (lane == 0) y[i] = (y[i] - acc) / Kb[(size_t)i * bw + hw];
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // Rayleigh-Ritz on span(Y): AX = A Y, Z = S Y, Am = Y^T A Y, Sm = Y^T S Y
+    for (int e = tid; e < nb * m; e += BT) {
+      const double* yc = Y + (size_t)(e / nb) * nb;
+      AX[e] = apply_ab_row(g, bx, by, e % nb, yc);
+      Z[e] = apply_sb_row(g, bx, by, e % nb, yc);
+    }
+    __syncthreads();
+    for (int pq = warp; pq < m * m; pq += nwarp) {
+      const int p = pq / m, q = pq % m;
+      if (q < p) continue;
+      double aa = 0.0, ss = 0.0;
+      for (int r = lane; r < nb; r += 32) {
+        const double yp = Y[(size_t)p * nb + r];
+        aa += yp * AX[(size_t)q * nb + r];
+        ss += yp * Z[(size_t)q * nb + r];
+      }
+      aa = pintd::warp_sum(aa);
+      ss = pintd::warp_sum(ss);
+      if (lane == 0) {
+        Am[p * m + q] = Am[q * m + p] = aa;
+        Sm[p * m + q] = Sm[q * m + p] = ss;
+      }
+    }
+    __syncthreads();
+    if (tid == 0) {
+      // Sm = L L^T, C = L^-1 Am L^-T, C = W diag(th) W^T, V = L^-T W
+      for (int k = 0; k < m; ++k) {
+        double d = Sm[k * m + k];
+        for (int t = 0; t < k; ++t) d -= Lm[k * m + t] * Lm[k * m + t];
+        d = sqrt(fmax(d, 1e-300));
+        Lm[k * m + k] = d;
+        for (int i = k + 1; i < m; ++i) {
+          double v = Sm[i * m + k];
+          for (int t = 0; t < k; ++t) v -= Lm[i * m + t] * Lm[k * m + t];
+          Lm[i * m + k] = v / d;
+        }
+        for (int i = 0; i < k; ++i) Lm[i * m + k] = 0.0;
+      }
+      for (int col = 0; col < m; ++col)  // Wm = L^-1 Am (column col)
+        for (int i = 0; i < m; ++i) {
+          double v = Am[i * m + col];
+          for (int t = 0; t < i; ++t) v -= Lm[i * m + t] * Wm[t * m + col];
+          Wm[i * m + col] = v / Lm[i * m + i];
+        }
+      for (int col = 0; col < m; ++col)  // C = L^-1 (L^-1 Am)^T, symmetric
+        for (int i = 0; i < m; ++i) {
+          double v = Wm[col * m + i];
+          for (int t = 0; t < i; ++t) v -= Lm[i * m + t] * Am[t * m + col];
+          Am[i * m + col] = v / Lm[i * m + i];
+        }
+      for (int i = 0; i < m; ++i)
+        for (int j = i + 1; j < m; ++j) {
+          const double v = 0.5 * (Am[i * m + j] + Am[j * m + i]);
+          Am[i * m + j] = Am[j * m + i] = v;
+        }
+      small_eig(Am, Wm, th, m);
+      for (int col = 0; col < m; ++col)  // V = L^-T W
+        for (int i = m - 1; i >= 0; --i) {
+          double v = Wm[i * m + col];
+          for (int t = i + 1; t < m; ++t) v -= Lm[t * m + i] * Vm[t * m + col];
+          Vm[i * m + col] = v / Lm[i * m + i];
+        }
+    }
+    __syncthreads();
+    // X = Y V; the residuals of the new Ritz pairs from A Y V and S Y V
+    for (int e = tid; e < nb * m; e += BT) {
+      const int r = e % nb, j = e / nb;
+      double x = 0.0;
+      for (int t = 0; t < m; ++t) x += Y[(size_t)t * nb + r] * Vm[t * m + j];
+      X[e] = x;
+    }
+    if (tid == 0) s_done = 1;
+    __syncthreads();
+    for (int j = 0; j < need; ++j) {
+      double rr = 0.0, a2 = 0.0, s2 = 0.0;
+      for (int r = tid; r < nb; r += BT) {
+        double ax = 0.0, sx = 0.0;
+        for (int t = 0; t < m; ++t) {
+          ax += AX[(size_t)t * nb + r] * Vm[t * m + j];
+          sx += Z[(size_t)t * nb + r] * Vm[t * m + j];
+        }
+        const double res = ax - th[j] * sx;
+        rr += res * res;
+        a2 += ax * ax;
+        s2 += sx * sx;
+      }
+      rr = pintd::block_sum(rr, sh);
+      a2 = pintd::block_sum(a2, sh);
+      s2 = pintd::block_sum(s2, sh);
+      const double tol = 1e-12 * (sqrt(a2) + fabs(th[j]) * sqrt(s2)) + 1e-15 * lmax * sqrt(s2);
+      if (tid == 0 && !(sqrt(rr) <= tol)) s_done = 0;
+    }
+    __syncthreads();
+    if (s_done) break;
+  }
+  return min(it, SI_MAXIT);
+}
+
 __device__ inline int rr_player(int k, int r, int m) {
   // circle method: position k of round r (player 0 fixed)
   return k == 0 ? 0 : 1 + ((k - 1 + r) % (m - 1));
@@ -167,6 +398,28 @@ __global__ void __launch_bounds__(BT) k_block_setup(BlkArgs g) {
   __shared__ int s_keep[KCAP];
 
   if (tid == 0) s_status = 0;
+  const bool use_si = nb > SI_MIN_NB;
+  const int m_si = min(nb, g.J + 1 + SI_EXTRA);
+  int sweeps = 0;
+  if (use_si) {
+    // ---- large block: shift-invert subspace iteration (see si_eigs) ---------
+    if (g.J > 0) {
+      double* X = Lm;
+      double* Y = X + (size_t)nb * m_si;
+      double* Z = Y + (size_t)nb * m_si;
+      double* AXs = Z + (size_t)nb * m_si;
+      sweeps = si_eigs(g, bx, by, m_si, Cm, X, Y, Z, AXs, Vm, lam, sh, &s_status);
+      for (int e = tid; e < nb * m_si; e += BT) {
+        const int r = e % nb, j = e / nb;
+        Tm[(size_t)r * nb + j] = X[e];
+      }
+      for (int j = tid; j < m_si; j += BT) {
+        perm[j] = j;
+        lsort[j] = lam[j];
+      }
+    }
+    __syncthreads();
+  } else {
   // ---- assemble dense A_b and S_b (eq. (3.1)), one row per thread --------
   for (size_t e = tid; e < (size_t)nb * nb; e += BT) {
     Cm[e] = 0.0;
@@ -243,7 +496,6 @@ __global__ void __launch_bounds__(BT) k_block_setup(BlkArgs g) {
   // ---- parallel cyclic Jacobi ----------------------------------------------
   const int m = nb + (nb & 1);
   const int npair = m / 2;
-  int sweeps = 0;
   double prev_off = 1e300;
   for (; sweeps < 40; ++sweeps) {
     double off = 0.0, tot = 0.0;
@@ -320,13 +572,17 @@ __global__ void __launch_bounds__(BT) k_block_setup(BlkArgs g) {
     lsort[rk] = li;
   }
   __syncthreads();
+  }  // dense path
   // ---- selection with cluster completion; continua by flood fill ------------
   if (tid == 0) {
-    int nsel = (g.J > 0) ? min(g.J + 1, nb) : 0;
-    double lmax = fabs(lsort[nb - 1]);
-    while (nsel > 0 && nsel < nb &&
+    // eigenpairs available to the rule: all (dense) or the converged Ritz pairs
+    const int navail = use_si ? m_si - 2 : nb;
+    int nsel = (g.J > 0) ? min(g.J + 1, navail) : 0;
+    const double lmax = use_si ? 24.0 * bs * bs : fabs(lsort[nb - 1]);
+    while (nsel > 0 && nsel < navail &&
            lsort[nsel] - lsort[nsel - 1] <= 1e-8 * fabs(lsort[nsel]) + 1e-12 * lmax)
       ++nsel;
+    if (use_si && g.J > 0 && nsel >= navail) s_status = 3;  // a cluster wider than the Ritz pairs
     s_nsel = nsel;
     int hasm = 0;
     for (int c = 0; c < bs * bs; ++c) {
@@ -599,6 +855,8 @@ void build_blocks(Ctx* c) {
     const int* inf = &info[(size_t)b * 8];
     PINT_REQUIRE(inf[4] != 1, PINT_ERR_SINGULAR, "block s-mass matrix not positive definite");
     PINT_REQUIRE(inf[4] != 2, PINT_ERR_BAD_ARG, "too many continua + enrichment functions in a block");
+    PINT_REQUIRE(inf[4] != 3, PINT_ERR_BAD_ARG,
+                 "eigenvalue cluster of a block wider than its subspace iteration (raise J or use smaller blocks)");
     c->blk_k[b] = inf[0];
     c->blk_kind_off[b] = off;
     off += inf[0];

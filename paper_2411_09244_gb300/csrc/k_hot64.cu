@@ -40,6 +40,7 @@ struct Hot {
   double* acc = nullptr;                    // 2 x cap x P squared update norms
   double* red = nullptr;                    // scalars
   double *b1 = nullptr, *b2 = nullptr;      // spectral loads of the source shape
+  double* qb = nullptr;                     // (CA^T D) b1, d2 (the folded coarse step's source term)
   double* amp = nullptr;                    // N
   double *tmp1 = nullptr, *tmp2 = nullptr;  // staging
   double* raw = nullptr;
@@ -372,58 +373,74 @@ __global__ void k_step_w(const double* __restrict__ CMt, const double* __restric
   }
 }
 
-// jump of eq. (2.8) per coarse time, in FP64: ||du||^2 + ||dw||^2 + 2 du^T CM dw
-// (M_H in spectral coordinates); CTA (n - n_first - 1, part) handles rows
-// i = part, part + JS, ... of CM for coarse time n and adds its partial sum to
-// jump2[n-1] (zeroed by the caller); k_max_fin takes sqrt.  Coarse times
-// n <= n_first are not launched: in sweep k the states up to n = k - 1 do not
-// change, so their jumps are exactly zero.
-constexpr int JS = 8;
-template <typename T>
-__global__ void k_jump(const double* __restrict__ Xu, const double* __restrict__ Xw,
-                       const double* __restrict__ Ou, const double* __restrict__ Ow,
-                       const T* __restrict__ CM, int d1, int d2, int n_first, double* __restrict__ jump2) {
-  const int n = n_first + blockIdx.x + 1, part = blockIdx.y;
+// jump of eq. (2.8) per coarse time, in FP64 (M_H in spectral coordinates):
+// ||du_n||^2 + ||dw_n||^2 + 2 du_n^T CM dw_n.  Coarse times n <= n_first are not
+// launched: in sweep k the states up to n = k - 1 do not change, so their
+// jumps are exactly zero.
+// One read of the coupling per launch: CTA (row tile,
+// group of JT_G coarse times) forms (CM dw_n)_i for its JT_R rows and JT_G
+// times at once, reading CM^T (d2 x d1) coalesced along the rows and reusing
+// each element for the JT_G times; dw_n is staged in shared memory in chunks
+// of JT_J columns.  Its partial sums of du_n^2 + 2 du_n (CM dw_n) over its rows,
+// plus ||dw_n||^2 from the first row tile, go to jump2[n-1] (zeroed by the
+// caller).  FP64 throughout.
+constexpr int JT_R = 128, JT_G = 4, JT_J = 512;
+__global__ void __launch_bounds__(JT_R) k_jump_tiled(const double* __restrict__ Xu, const double* __restrict__ Xw,
+                                                     const double* __restrict__ Ou, const double* __restrict__ Ow,
+                                                     const double* __restrict__ CMt, int d1, int d2, int n_first,
+                                                     int N, double* __restrict__ jump2) {
+  __shared__ double sdw[JT_G][JT_J];
   __shared__ double sh[64];
-  __shared__ T dw[4096];
-  const double* xu = Xu + (size_t)n * d1;
-  const double* ou = Ou + (size_t)n * d1;
-  for (int j = threadIdx.x; j < d2; j += blockDim.x) dw[j] = (T)(Xw[(size_t)n * d2 + j] - Ow[(size_t)n * d2 + j]);
-  __syncthreads();
-  T s = 0;
-  if (part == 0)
-    for (int j = threadIdx.x; j < d2; j += blockDim.x) s += dw[j] * dw[j];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nwarp = blockDim.x >> 5;
-  for (int i0 = part + JS * 32 * warp; i0 < d1; i0 += JS * 32 * nwarp) {
-    // 32 rows per warp pass, four at a time (their loads and reductions
-    // interleaved); lane r keeps row i0 + JS r's product
-    T mine = 0;
-    for (int r0 = 0; r0 < 32; r0 += 4) {
-      if (i0 + JS * r0 >= d1) break;
-      T t[4];
+  const int i = blockIdx.x * JT_R + threadIdx.x;
+  const int n0 = n_first + 1 + blockIdx.y * JT_G;  // first coarse time of the group
+  const int ng = min(JT_G, N + 1 - n0);
+  double acc[JT_G], w2[JT_G];
 #pragma unroll
-      for (int h = 0; h < 4; ++h) {
-        const int i = i0 + JS * (r0 + h);
-        t[h] = 0;
-        if (i < d1)
-          for (int j = lane; j < d2; j += 32) t[h] += CM[(size_t)i * d2 + j] * dw[j];
+  for (int g = 0; g < JT_G; ++g) acc[g] = w2[g] = 0.0;
+  for (int j0 = 0; j0 < d2; j0 += JT_J) {
+    const int nj = min(JT_J, d2 - j0);
+    __syncthreads();
+    for (int e = threadIdx.x; e < JT_G * JT_J; e += JT_R) {
+      const int g = e / JT_J, j = e % JT_J;
+      double v = 0.0;
+      if (g < ng && j < nj) {
+        const size_t o = (size_t)(n0 + g) * d2 + j0 + j;
+        v = Xw[o] - Ow[o];
       }
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1)
-#pragma unroll
-        for (int h = 0; h < 4; ++h) t[h] += __shfl_xor_sync(0xffffffffu, t[h], o);
-#pragma unroll
-      for (int h = 0; h < 4; ++h)
-        if (lane == r0 + h) mine = t[h];
+      sdw[g][j] = v;
     }
-    const int i = i0 + JS * lane;
-    if (i < d1) {
-      const T du = (T)(xu[i] - ou[i]);
-      s += du * du + 2 * du * mine;
-    }
+    __syncthreads();
+    if (blockIdx.x == 0)  // ||dw_n||^2, once per time
+      for (int e = threadIdx.x; e < JT_G * nj; e += JT_R) {
+        const int g = e / nj, j = e % nj;
+        w2[g] += sdw[g][j] * sdw[g][j];
+      }
+    if (i < d1)
+      for (int j = 0; j < nj; ++j) {
+        const double c = CMt[(size_t)(j0 + j) * d1 + i];
+#pragma unroll
+        for (int g = 0; g < JT_G; ++g) acc[g] = fma(c, sdw[g][j], acc[g]);
+      }
   }
-  const double sd = pintd::block_sum((double)s, sh);
-  if (threadIdx.x == 0) atomicAdd(&jump2[n - 1], sd);
+#pragma unroll
+  for (int g = 0; g < JT_G; ++g) {
+    double v = w2[g];
+    if (i < d1 && g < ng) {
+      const double du = Xu[(size_t)(n0 + g) * d1 + i] - Ou[(size_t)(n0 + g) * d1 + i];
+      v += du * du + 2.0 * du * acc[g];
+    }
+    v = pintd::block_sum(v, sh);
+    if (threadIdx.x == 0 && g < ng) atomicAdd(&jump2[n0 + g - 1], v);
+  }
+}
+
+static void jumps_fp64(Ctx* c, const double* Xu, const double* Xw, const double* Ou, const double* Ow, int n_first,
+                       double* jump2) {
+  const int N = c->N, nt = N - n_first;
+  if (nt <= 0) return;
+  k_jump_tiled<<<dim3(nb_(c->d1, JT_R), nb_(nt, JT_G)), JT_R, 0, c->stream>>>(Xu, Xw, Ou, Ow, c->CMt, c->d1, c->d2,
+                                                                              n_first, N, jump2);
+  PINT_LAUNCH_CHECK();
 }
 
 // max over n of sqrt(max(x_n, 0)) (x = squared jumps), flags non-finite values
@@ -529,6 +546,14 @@ static void ensure(Ctx* c, Hot& H, int cap) {
     if (!e) PINT_CUDA(cudaEventCreate(&e));
 }
 
+// out[j][i] = CAt[j][i] / (1 + Dt lambda1_i)  (d2 x d1)
+__global__ void k_scale_cols(const double* __restrict__ CAt, const double* __restrict__ lam1, double Dt, int d2,
+                             int d1, double* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)d2 * d1) return;
+  out[e] = CAt[e] / (1.0 + Dt * lam1[e % d1]);
+}
+
 void hot_prepare(Ctx* c) {
   const int d1 = c->d1, d2 = c->d2, P = c->P;
   auto A = [&](size_t n) { return (double*)dalloc(c, n * 8); };
@@ -556,6 +581,14 @@ void hot_prepare(Ctx* c) {
   }
   PINT_CUDA(cudaMemcpyAsync(c->AR, AR.data(), AR.size() * 8, cudaMemcpyHostToDevice, c->stream));
   PINT_CUDA(cudaMemcpyAsync(c->AS, AS.data(), AS.size() * 8, cudaMemcpyHostToDevice, c->stream));
+  // the folded coarse step (k_g_sweep): GCD = CA^T D, GE = CA^T D CA, D = (1 + Dt Lambda1)^-1
+  if (!c->GE) {
+    c->GE = A((size_t)d2 * d2);
+    c->GCD = A((size_t)d2 * d1);
+  }
+  k_scale_cols<<<nb_((long long)d2 * d1, 256), 256, 0, c->stream>>>(c->CAt, c->lam1, c->Dt, d2, d1, c->GCD);
+  PINT_LAUNCH_CHECK();
+  dense_gemm(c, c->GCD, c->CA, c->GE, d2, d2, d1, false, false, 1.0, 0.0);
   std::vector<double2> tw(64), ds(64);
   std::vector<double> bp(65);
   const double beta = std::pow(c->alpha, 1.0 / P);
@@ -579,7 +612,9 @@ static void spectral_load(Ctx* c, Hot& H, const double* f_nodes) {
   to_reduced(c, H.raw, 1, H.tmp1, H.tmp2);
   dense_gemm(c, c->Q, H.tmp1, H.b1, c->d1, 1, c->d1, true, false, 1.0, 0.0);
   dense_gemm(c, c->Q2, H.tmp2, H.b2, c->d2, 1, c->d2, true, false, 1.0, 0.0);
-  c->launches += 2;
+  if (!H.qb) H.qb = (double*)dalloc(c, (size_t)c->d2 * 8);
+  dense_gemm(c, c->GCD, H.b1, H.qb, c->d2, 1, c->d1, false, false, 1.0, 0.0);
+  c->launches += 3;
 }
 
 // original coordinates -> spectral: u~ = Q^T M11 u, w~ = Q2^T M22 w (count vectors)
@@ -620,28 +655,26 @@ namespace {
 constexpr int GS_THREADS = 512;
 constexpr int GS_SPIN = 1 << 22;
 
-__device__ bool gs_barrier(unsigned* count, volatile unsigned* gen, unsigned nblocks, int* err, int spin_limit) {
+// Grid barrier on a counter that only grows within a launch (cleared before
+// each launch): barrier number b is passed once it reaches (b + 1) x blocks.
+// One arrival atomic per block and no reset or generation word; the wait
+// polls at most spin_limit times and then records the expiry and gives up.
+__device__ bool gs_barrier(unsigned* count, unsigned target, int* err, int spin_limit) {
   __syncthreads();
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
     s_ok = 1;
-    const unsigned g = *gen;
-    __threadfence();
-    const unsigned arrived = atomicAdd(count, 1u);
-    if (arrived == nblocks - 1) {
-      *count = 0;
-      __threadfence();
-      atomicAdd((unsigned*)gen, 1u);
-    } else {
-      int it = 0;
-      while (*gen == g && it < spin_limit) {
-        ++it;
-        __nanosleep(20);
-      }
-      if (*gen == g) {  // gave up: the other blocks did not all arrive within the limit
-        atomicExch(err, 1);
-        s_ok = 0;
-      }
+    __threadfence();  // this block's writes are visible before its arrival
+    atomicAdd(count, 1u);
+    volatile unsigned* vc = count;
+    int it = 0;
+    while (*vc < target && it < spin_limit) {
+      ++it;
+      __nanosleep(20);
+    }
+    if (*vc < target) {  // gave up: the other blocks did not all arrive within the limit
+      atomicExch(err, 1);
+      s_ok = 0;
     }
     __threadfence();
   }
@@ -650,70 +683,76 @@ __device__ bool gs_barrier(unsigned* count, volatile unsigned* gen, unsigned nbl
 }
 
 struct GSArgs {
-  const double *CA, *CAt, *lam1, *lam2, *b1, *b2, *amp;
+  const double *CA, *lam1, *lam2, *b1, *b2, *qb, *amp;
+  const double *GE, *GCD;  // CA^T D CA (d2 x d2) and CA^T D (d2 x d1), D = (1 + Dt Lambda1)^-1
   const double *Fu, *Fw, *Cu, *Cw;
-  double *Xu, *Xw, *Gu, *Gw, *gu, *gw;
+  double *Xu, *Xw, *Gu, *Gw;
   int d1, d2, n_lo, n_hi, first;
+  int ublocks;  // blocks [0, ublocks) take the u rows, the others the w rows
   double Dt;
-  unsigned* count;
-  unsigned* gen;
+  unsigned* count;  // barrier arrivals, zero at launch
   int* err;
   int spin;  // polls before a barrier wait gives up
 };
 
-constexpr int GS_SPLIT = 8;                          // warps per w-phase row
-constexpr int GS_ROWS = GS_THREADS / 32 / GS_SPLIT;   // w-phase rows per block and pass
-
+// One coarse step in spectral coordinates (lags restarted), D = (1 + Dt Lambda1)^-1:
+//   u' = D (u - Dt CA w + Dt a b1)
+//   w' = (1 - Dt Lambda2) w - Dt CA^T u' + Dt a b2
+//      = (1 - Dt Lambda2) w + Dt^2 (CA^T D CA) w - Dt (CA^T D) u + Dt a (b2 - Dt CA^T D b1),
+// so both halves depend on (u, w) only and the step needs one grid barrier:
+// blocks [0, ublocks) form u' a warp per row; the others form w' a block per
+// row, its 16 warps splitting the row of [Dt^2 CA^T D CA | -Dt CA^T D] against
+// [w ; u].  Each half applies eq. (2.7) to its rows at once.
 __global__ void __launch_bounds__(GS_THREADS) k_g_sweep(GSArgs a) {
   __shared__ double s_part[GS_THREADS / 32];
-  const int lane = threadIdx.x & 31;
-  const int gwarp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int nwarps = (gridDim.x * blockDim.x) >> 5;
-  const int gtid = blockIdx.x * blockDim.x + threadIdx.x, gthreads = gridDim.x * blockDim.x;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
   const int d1 = a.d1, d2 = a.d2;
+  const double Dt = a.Dt;
+  const bool ublock = (int)blockIdx.x < a.ublocks;
+  const int uwarps = a.ublocks * (GS_THREADS / 32), uw = blockIdx.x * (GS_THREADS / 32) + wib;
+  const int wblocks = gridDim.x - a.ublocks, wb = blockIdx.x - a.ublocks;
+  const int kw = d2 + d1, piece = (kw + GS_THREADS / 32 - 1) / (GS_THREADS / 32);
+  unsigned target = 0;  // arrivals the next barrier waits for
   for (int n = a.n_lo; n < a.n_hi; ++n) {
     const double* xu = a.Xu + (size_t)n * d1;
     const double* xw = a.Xw + (size_t)n * d2;
     const double am = a.amp[n];
-    // u-phase: u' = (u - Dt CA w + Dt a b1) / (1 + Dt lambda1)
-    for (int i = gwarp; i < d1; i += nwarps) {
-      double acc = 0.0;
-      for (int j = lane; j < d2; j += 32) acc += a.CA[(size_t)i * d2 + j] * xw[j];
-      acc = pintd::warp_sum(acc);
-      if (lane == 0) a.gu[i] = (xu[i] - a.Dt * acc + a.Dt * am * a.b1[i]) / (1.0 + a.Dt * a.lam1[i]);
-    }
-    if (!gs_barrier(a.count, a.gen, gridDim.x, a.err, a.spin)) return;
-    // w-phase: w' = (1 - Dt lambda2) w - Dt CA^T u' + Dt a b2, then eq. (2.7);
-    // each row's length-d1 dot product is split over GS_SPLIT warps of a block
-    for (int j0 = blockIdx.x * GS_ROWS; j0 < d2; j0 += gridDim.x * GS_ROWS) {
-      const int wib = threadIdx.x >> 5, slot = wib / GS_SPLIT, piece = wib % GS_SPLIT;
-      const int j = j0 + slot;
-      double acc = 0.0;
-      if (j < d2)
-        for (int i = piece * 32 + lane; i < d1; i += GS_SPLIT * 32) acc += a.CAt[(size_t)j * d1 + i] * a.gu[i];
-      acc = pintd::warp_sum(acc);
-      if (lane == 0) s_part[wib] = acc;
-      __syncthreads();
-      if (threadIdx.x < GS_ROWS && j0 + (int)threadIdx.x < d2) {
-        const int jj = j0 + threadIdx.x;
-        double dot = 0.0;
-        for (int q = 0; q < GS_SPLIT; ++q) dot += s_part[threadIdx.x * GS_SPLIT + q];
-        const double g = (1.0 - a.Dt * a.lam2[jj]) * xw[jj] - a.Dt * dot + a.Dt * am * a.b2[jj];
-        double v = a.first ? g : g + a.Fw[(size_t)n * d2 + jj] - a.Gw[(size_t)n * d2 + jj];
-        if (a.Cw) v += a.Cw[(size_t)(n + 1) * d2 + jj];
-        a.Xw[(size_t)(n + 1) * d2 + jj] = v;
-        a.Gw[(size_t)n * d2 + jj] = g;
+    if (ublock) {
+      for (int i = uw; i < d1; i += uwarps) {
+        double acc = 0.0;
+        for (int j = lane; j < d2; j += 32) acc += a.CA[(size_t)i * d2 + j] * xw[j];
+        acc = pintd::warp_sum(acc);
+        if (lane == 0) {
+          const double g = (xu[i] - Dt * acc + Dt * am * a.b1[i]) / (1.0 + Dt * a.lam1[i]);
+          double v = a.first ? g : g + a.Fu[(size_t)n * d1 + i] - a.Gu[(size_t)n * d1 + i];
+          if (a.Cu) v += a.Cu[(size_t)(n + 1) * d1 + i];
+          a.Xu[(size_t)(n + 1) * d1 + i] = v;
+          a.Gu[(size_t)n * d1 + i] = g;
+        }
       }
-      __syncthreads();
+    } else {
+      for (int j = wb; j < d2; j += wblocks) {
+        const int k0 = wib * piece, k1 = min(kw, k0 + piece);
+        double acc = 0.0;
+        for (int k = k0 + lane; k < k1; k += 32)
+          acc += (k < d2) ? Dt * Dt * a.GE[(size_t)j * d2 + k] * xw[k] : -Dt * a.GCD[(size_t)j * d1 + (k - d2)] * xu[k - d2];
+        acc = pintd::warp_sum(acc);
+        if (lane == 0) s_part[wib] = acc;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+          double dot = 0.0;
+          for (int q = 0; q < GS_THREADS / 32; ++q) dot += s_part[q];
+          const double g = (1.0 - Dt * a.lam2[j]) * xw[j] + dot + Dt * am * (a.b2[j] - Dt * a.qb[j]);
+          double v = a.first ? g : g + a.Fw[(size_t)n * d2 + j] - a.Gw[(size_t)n * d2 + j];
+          if (a.Cw) v += a.Cw[(size_t)(n + 1) * d2 + j];
+          a.Xw[(size_t)(n + 1) * d2 + j] = v;
+          a.Gw[(size_t)n * d2 + j] = g;
+        }
+        __syncthreads();
+      }
     }
-    for (int i = gtid; i < d1; i += gthreads) {
-      const double g = a.gu[i];
-      double v = a.first ? g : g + a.Fu[(size_t)n * d1 + i] - a.Gu[(size_t)n * d1 + i];
-      if (a.Cu) v += a.Cu[(size_t)(n + 1) * d1 + i];
-      a.Xu[(size_t)(n + 1) * d1 + i] = v;
-      a.Gu[(size_t)n * d1 + i] = g;
-    }
-    if (!gs_barrier(a.count, a.gen, gridDim.x, a.err, a.spin)) return;
+    target += gridDim.x;
+    if (!gs_barrier(a.count, target, a.err, a.spin)) return;
   }
 }
 
@@ -745,11 +784,13 @@ static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, c
   }
   GSArgs a;
   a.CA = c->CA;
-  a.CAt = c->CAt;
+  a.GE = c->GE;
+  a.GCD = c->GCD;
   a.lam1 = c->lam1;
   a.lam2 = c->lam2;
   a.b1 = H.b1;
   a.b2 = H.b2;
+  a.qb = H.qb;
   a.amp = amp;
   a.Fu = Fu;
   a.Fw = Fw;
@@ -759,8 +800,6 @@ static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, c
   a.Xw = Xw;
   a.Gu = H.Gu;
   a.Gw = H.Gw;
-  a.gu = H.tmp1;
-  a.gw = H.tmp2;
   a.d1 = c->d1;
   a.d2 = c->d2;
   a.n_lo = n_lo;
@@ -768,11 +807,26 @@ static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, c
   a.first = first ? 1 : 0;
   a.Dt = c->Dt;
   a.count = H.gsync;
-  a.gen = H.gsync + 1;
   a.err = (int*)(H.gsync + 2);
   a.spin = wait_limit();
-  void* args[] = {&a};
+  PINT_CUDA(cudaMemsetAsync(H.gsync, 0, 4, c->stream));  // the arrival counter
   const int blocks = num_sms;  // one block per SM: fewest barrier arrivals
+  // split the blocks between u rows and w rows so that the longest per-warp
+  // dot product (the step's latency) is as short as possible
+  {
+    const int W = GS_THREADS / 32, d1 = c->d1, d2 = c->d2;
+    long long best = -1;
+    for (int ub = 1; ub < blocks; ++ub) {
+      const long long lu = (long long)((d1 + ub * W - 1) / (ub * W)) * ((d2 + 31) / 32);
+      const long long lw = (long long)((d2 + blocks - ub - 1) / (blocks - ub)) * (((d1 + d2 + W - 1) / W + 31) / 32);
+      const long long l = std::max(lu, lw);
+      if (best < 0 || l < best) {
+        best = l;
+        a.ublocks = ub;
+      }
+    }
+  }
+  void* args[] = {&a};
   PINT_CUDA(cudaLaunchCooperativeKernel((const void*)k_g_sweep, dim3(blocks), dim3(GS_THREADS), args, 0, c->stream));
   c->launches++;
 }
@@ -977,8 +1031,7 @@ void solve_fp64(Ctx* c, const double* u0_nodes, const double* f_nodes, const dou
       g_sweep(c, H, H.Xu, H.Xw, H.amp, H.Fu, H.Fw, nullptr, nullptr, n_lo, false);
       g_sweep_check(c, H);
       PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
-      k_jump<double><<<dim3(N - n_lo, JS), 256, 0, c->stream>>>(H.Xu, H.Xw, H.Ou, H.Ow, c->CM, d1, d2, n_lo,
-                                                                 H.red + 8);
+      jumps_fp64(c, H.Xu, H.Xw, H.Ou, H.Ow, n_lo, H.red + 8);
       k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
       PINT_LAUNCH_CHECK();
       c->launches += 2;
@@ -1203,8 +1256,7 @@ void solve_carry(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
         c->launches += 4;
       }
       PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
-      k_jump<double><<<dim3(N - n_lo, JS), 256, 0, c->stream>>>(H.Xu, H.Xw, H.Ou, H.Ow, c->CM, d1, d2, n_lo,
-                                                                 H.red + 8);
+      jumps_fp64(c, H.Xu, H.Xw, H.Ou, H.Ow, n_lo, H.red + 8);
       k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
       PINT_LAUNCH_CHECK();
       c->launches += 2;
@@ -1880,8 +1932,7 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
     g_sweep_lp(c, H, M, r.Xu, r.Xw, r.amp, H.Fu, H.Fw, r.Cu, r.Cw, n_lo, false, r.g64);
     PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
     // the parareal jump and convergence norm of eq. (2.8) in FP64
-    k_jump<double><<<dim3(N - n_lo, JS), 256, 0, c->stream>>>(r.Xu, r.Xw, H.Ou, H.Ow, c->CM, d1, d2, n_lo,
-                                                               H.red + 8);
+    jumps_fp64(c, r.Xu, r.Xw, H.Ou, H.Ow, n_lo, H.red + 8);
     k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
     PINT_LAUNCH_CHECK();
     c->launches += 2;
@@ -1919,7 +1970,7 @@ static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw) {
   // k_jump measures rows 1..N against the zero rows of tmp1 (the scale of
   // the relative tolerances)
   PINT_CUDA(cudaMemsetAsync(H.red + 8, 0, (size_t)N * 8, c->stream));
-  k_jump<double><<<dim3(N, JS), 256, 0, c->stream>>>(Xu, Xw, H.tmp1, H.tmp1, c->CM, d1, d2, 0, H.red + 8);
+  jumps_fp64(c, Xu, Xw, H.tmp1, H.tmp1, 0, H.red + 8);
   k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
   PINT_LAUNCH_CHECK();
   double h[2];

@@ -452,27 +452,28 @@ __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, 
 // terms ah bl + al bh join the error term, and the running sum is kept as a
 // pair, Knuth's TwoSum on the high parts and the errors summed in FP32.
 // Same column maps as k_wr_gemm (FP64 path), operands pre-split into pairs.
-template <int MODE, int T>
+// Tiles of TM rows x TN columns, (TM / 16) x (TN / 16) outputs per thread.
+template <int MODE, int TM, int TN>
 __global__ void __launch_bounds__(256) k_wr_gemm_df(const float* __restrict__ Ah, const float* __restrict__ Al,
                                                     int M, int K, const float* __restrict__ Uh,
                                                     const float* __restrict__ Ul, const float* __restrict__ Wh,
                                                     const float* __restrict__ Wl, int d1, int d2, int P, int ncols,
                                                     double* __restrict__ out) {
-  constexpr int R = T / 16;
-  __shared__ float Ash[16][T + 1], Asl[16][T + 1], Bsh[16][T + 1], Bsl[16][T + 1];
-  const int i0 = blockIdx.y * T, j0 = blockIdx.x * T;
+  constexpr int RM = TM / 16, RN = TN / 16, TMAX = TM > TN ? TM : TN;
+  __shared__ float Ash[16][TM + 1], Asl[16][TM + 1], Bsh[16][TN + 1], Bsl[16][TN + 1];
+  const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
   const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
-  float sh[R][R] = {}, sl[R][R] = {};
+  float sh[RM][RN] = {}, sl[RM][RN] = {};
   for (int k0 = 0; k0 < K; k0 += 16) {
-    for (int e = threadIdx.x; e < 16 * T; e += 256) {
+    for (int e = threadIdx.x; e < 16 * TMAX; e += 256) {
       const int kk = e % 16, r = e / 16;
       const int kg = k0 + kk, ig = i0 + r, col = j0 + r;
       float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
-      if (kg < K && ig < M) {
+      if (r < TM && kg < K && ig < M) {
         ah = Ah[(size_t)ig * K + kg];
         al = Al[(size_t)ig * K + kg];
       }
-      if (kg < K && col < ncols) {
+      if (r < TN && kg < K && col < ncols) {
         const int n = col / P, p = col % P;
         if (MODE == 0) {  // [w_p ; w_{max(p-1,0)}]
           const size_t base = (size_t)n * (P + 1) * d2;
@@ -492,32 +493,39 @@ __global__ void __launch_bounds__(256) k_wr_gemm_df(const float* __restrict__ Ah
           }
         }
       }
-      Ash[kk][r] = ah;
-      Asl[kk][r] = al;
-      Bsh[kk][r] = bh;
-      Bsl[kk][r] = bl;
+      if (r < TM) {
+        Ash[kk][r] = ah;
+        Asl[kk][r] = al;
+      }
+      if (r < TN) {
+        Bsh[kk][r] = bh;
+        Bsl[kk][r] = bl;
+      }
     }
     __syncthreads();
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
-      float a_h[R], a_l[R], b_h[R], b_l[R];
+      float a_h[RM], a_l[RM], b_h[RN], b_l[RN];
 #pragma unroll
-      for (int q = 0; q < R; ++q) {
-        a_h[q] = Ash[kk][ty * R + q];
-        a_l[q] = Asl[kk][ty * R + q];
-        b_h[q] = Bsh[kk][tx * R + q];
-        b_l[q] = Bsl[kk][tx * R + q];
+      for (int q = 0; q < RM; ++q) {
+        a_h[q] = Ash[kk][ty * RM + q];
+        a_l[q] = Asl[kk][ty * RM + q];
       }
 #pragma unroll
-      for (int p = 0; p < R; ++p)
+      for (int q = 0; q < RN; ++q) {
+        b_h[q] = Bsh[kk][tx * RN + q];
+        b_l[q] = Bsl[kk][tx * RN + q];
+      }
 #pragma unroll
-        for (int q = 0; q < R; ++q) pintd::df_fma(a_h[p], a_l[p], b_h[q], b_l[q], sh[p][q], sl[p][q]);
+      for (int p = 0; p < RM; ++p)
+#pragma unroll
+        for (int q = 0; q < RN; ++q) pintd::df_fma(a_h[p], a_l[p], b_h[q], b_l[q], sh[p][q], sl[p][q]);
     }
     __syncthreads();
   }
-  for (int p = 0; p < R; ++p)
-    for (int q = 0; q < R; ++q) {
-      const int i = i0 + ty * R + p, col = j0 + tx * R + q;
+  for (int p = 0; p < RM; ++p)
+    for (int q = 0; q < RN; ++q) {
+      const int i = i0 + ty * RM + p, col = j0 + tx * RN + q;
       if (i < M && col < ncols) out[(size_t)col * M + i] = (double)sh[p][q] + (double)sl[p][q];
     }
 }
@@ -1273,25 +1281,31 @@ void mx_wr_gemm_df(Ctx* c, int mode, const float* Ah, const float* Al, int M, in
   cudaGetDevice(&dev);
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   sms = std::max(sms, 1);
-  auto eff = [&](int T) {
-    const long long t = (long long)nbl(M, T) * nbl(ncols, T);
-    const double waves = (double)((t + 3 * sms - 1) / (3 * sms));  // ~3 resident CTAs per SM
-    return ((double)t / (3 * sms) / waves) * ((double)M * ncols / ((double)t * T * T));
+  // 16 outputs per thread (64 x 64 or 32 x 128 tiles) keep the FP32 pipe busier
+  // than 32 x 32 tiles (4 per thread, bound by shared-memory loads): take the
+  // 16-output shape with the larger useful fraction of its tiles, and 32 x 32
+  // only when the larger tiles would leave SMs idle
+  auto useful = [&](int TM, int TN) {
+    const long long t = (long long)nbl(M, TM) * nbl(ncols, TN);
+    return (double)M * ncols / ((double)t * TM * TN);
   };
-  const int T = eff(64) >= eff(32) ? 64 : 32;
-  const dim3 grid(nbl(ncols, T), nbl(M, T));
+  const long long t64 = (long long)nbl(M, 64) * nbl(ncols, 64), t128 = (long long)nbl(M, 32) * nbl(ncols, 128);
+  int choice = useful(32, 128) > useful(64, 64) + 1e-9 ? 1 : 0;
+  if ((choice == 0 ? t64 : t128) < sms) choice = 2;
   const int d1 = c->d1, d2 = c->d2, P = c->P;
+#define PINT_DF_LAUNCH(MODE, TM, TN)                                                                        \
+  k_wr_gemm_df<MODE, TM, TN><<<dim3(nbl(ncols, TN), nbl(M, TM)), 256, 0, c->stream>>>(Ah, Al, M, K, Uh, Ul, Wh, \
+                                                                                     Wl, d1, d2, P, ncols, out)
   if (mode == 0) {
-    if (T == 64)
-      k_wr_gemm_df<0, 64><<<grid, 256, 0, c->stream>>>(Ah, Al, M, K, Uh, Ul, Wh, Wl, d1, d2, P, ncols, out);
-    else
-      k_wr_gemm_df<0, 32><<<grid, 256, 0, c->stream>>>(Ah, Al, M, K, Uh, Ul, Wh, Wl, d1, d2, P, ncols, out);
+    if (choice == 0) PINT_DF_LAUNCH(0, 64, 64);
+    else if (choice == 1) PINT_DF_LAUNCH(0, 32, 128);
+    else PINT_DF_LAUNCH(0, 32, 32);
   } else {
-    if (T == 64)
-      k_wr_gemm_df<1, 64><<<grid, 256, 0, c->stream>>>(Ah, Al, M, K, Uh, Ul, Wh, Wl, d1, d2, P, ncols, out);
-    else
-      k_wr_gemm_df<1, 32><<<grid, 256, 0, c->stream>>>(Ah, Al, M, K, Uh, Ul, Wh, Wl, d1, d2, P, ncols, out);
+    if (choice == 0) PINT_DF_LAUNCH(1, 64, 64);
+    else if (choice == 1) PINT_DF_LAUNCH(1, 32, 128);
+    else PINT_DF_LAUNCH(1, 32, 32);
   }
+#undef PINT_DF_LAUNCH
   PINT_LAUNCH_CHECK();
   c->launches++;
 }
