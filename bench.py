@@ -42,7 +42,7 @@ def parse():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c4", "c5"])
+    ap.add_argument("--config", default="c2", choices=["c1", "c2", "c3", "c4", "c5"])
     ap.add_argument("--no-autotune", action="store_true",
                     help="contraction tiles from the cost model instead of measured (mixed path)")
     ap.add_argument("--tuning", default=None,
@@ -461,6 +461,61 @@ def run_reference(args, rank, world):
                                         "d2h_bytes_per_step": 0}}
 
 
+def run_adjoint(args, rank, world):
+    """The 128x128 adjoint workload: one step = pint_adjoint (the forward solve,
+    the observation residuals, the backward parareal sweep and the gradients
+    with respect to u0 and the 32 per-interval amplitudes).  value = fine
+    unknowns x N P / time of the gradient call."""
+    import torch
+    from paper_2411_09244_gb300 import api, _lib, inputs
+    dev = torch.device("cuda", int(os.environ.get("LOCAL_RANK", "0")))
+    torch.cuda.set_device(dev)
+    prob = inputs.config_c3()
+    obs = inputs.observation_nodes(prob.n_f, 64, seed=prob.n_f)
+    data = np.random.default_rng(21).standard_normal((prob.N, obs.size))
+    prec = {"fp64": _lib.PINT_FP64, "mixed": _lib.PINT_MIXED, "mixed_f32": _lib.PINT_MIXED_F32}[args.precision]
+    t0 = time.perf_counter()
+    p = api.from_problem(prob, device=dev, precision=prec)
+    setup_s = time.perf_counter() - t0
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    u0 = torch.tensor(prob.u0, dtype=torch.float64, device=dev)
+    f = torch.tensor(prob.f, dtype=torch.float64, device=dev)
+    amp = torch.tensor(prob.amp, dtype=torch.float64, device=dev)
+    dd = torch.tensor(data, dtype=torch.float64, device=dev)
+    for _ in range(args.warmup):
+        p.adjoint(obs, dd, u0, f, amp, eps=prob.eps)
+    torch.cuda.synchronize()
+    times = []
+    barrier(world)
+    with ClockSampler(dev.index) as clk:
+        for _ in range(args.steps):
+            flush.zero_()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            J, gu, ga = p.adjoint(obs, dd, u0, f, amp, eps=prob.eps)
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1) / 1e3)
+    t = max_over_ranks(sum(times) / len(times), world)
+    work = (prob.n_f - 1) ** 2 * prob.N * prob.P
+    p.close()
+    if rank != 0:
+        return None
+    return {"metric": METRIC + " (adjoint: gradient of the observation misfit)", "value": world * work / t,
+            "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": t * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": {"fp64": "f64", "mixed": "tf32x3/f32 forward, f32 transposed sweeps",
+                      "mixed_f32": "f32"}[args.precision],
+            "data": "synthetic (seeded splitmix64 channels, Gaussian bumps, 64 seeded observation nodes)",
+            "config": {"workload": workload_desc(prob) + ", 64 observation nodes, gradient w.r.t. u0 and 32 "
+                                                       "per-interval amplitudes", "T": p.T, "misfit": J,
+                       "setup_s": setup_s, "l2": "512 MB buffer zeroed before every timed step",
+                       "amplitude_gradient": "fine adjoint recomputed inside each interval"},
+            "clocks": clk.summary()}
+
+
 def run_batch(args, rank, world):
     """Many independent uneven instances (the many-instance recipe) solved at
     once by pint_batch_solve: one context and CUDA stream per instance, the
@@ -598,6 +653,8 @@ def main():
         out = run_reference(args, rank, world)
     elif args.config == "c4":
         out = run_batch(args, rank, world)
+    elif args.config == "c3":
+        out = run_adjoint(args, rank, world)
     else:
         out = run_ours(args, rank, world)
     if args.tuning and args.impl != "reference" and rank == 0:

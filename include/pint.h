@@ -410,6 +410,19 @@ pint_status pint_tuning_clear(void);
  */
 int pint_set_wait_limit(int spins);
 
+/*
+ * pint_set_sweep_smem -- tuning control of the FP64 coarse sweep (the G step
+ * and update of Algorithm 1, eq. (2.7)): the most dynamic shared memory, in
+ * bytes, one block of the sweep may use to keep its rows of the coupling
+ * operators resident for the whole sweep (process-wide; bytes < 0 restores
+ * the default of 204800).  Couplings whose per-block share does not fit are
+ * read from global memory at every coarse step instead; both variants give
+ * the same products and sums, so results do not depend on this value.  0
+ * selects the streaming variant for every shape.  Returns the previous value.
+ * Touches no device state.
+ */
+int pint_set_sweep_smem(int bytes);
+
 /* pint_last_error -- message of the last failing call on this thread. */
 const char* pint_last_error(void);
 

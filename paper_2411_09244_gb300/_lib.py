@@ -96,6 +96,7 @@ SYMBOLS = {
     "pint_tuning_set": [C.c_void_p, C.c_void_p, C.c_int],
     "pint_tuning_clear": [],
     "pint_set_wait_limit": [C.c_int],
+    "pint_set_sweep_smem": [C.c_int],
 }
 
 

@@ -212,6 +212,8 @@ void step_source(Ctx* c, double* cu, double* cw);
 // polls of the coarse sweep's grid-barrier waits before they give up (k_hot64.cu)
 int wait_limit();
 void set_wait_limit(int spins);
+int sweep_smem();
+void set_sweep_smem(int bytes);
 
 // FP32 coarse sweep on one thread-block cluster (k_gcluster.cu)
 // WR stopping test fused into the last kernel of a WR iteration (k_mixed.cu):

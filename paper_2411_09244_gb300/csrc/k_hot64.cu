@@ -645,37 +645,58 @@ static void step_batch(Ctx* c, Hot& H, const double* u, const double* w, const d
 }
 
 // ---------------------------------------------------------------------------
-// The sequential coarse sweep of Algorithm 1 (G step + correction eq. (2.7) at
-// every coarse step) as one persistent cooperative kernel: per coarse step a
-// u-phase (rows of CA w, diagonal implicit solve), a grid barrier, a w-phase
-// (rows of CA^T u' and the update), a grid barrier.  The barrier spins are
-// bounded; on expiry the kernel records an error and returns.
+// The sequential coarse sweep of Algorithm 1 (the G step and the update of
+// eq. (2.7) at every coarse step) in FP64, as one persistent cooperative
+// kernel.  With D = (1 + Dt Lambda1)^-1, one step in spectral coordinates
+// (lags restarted) is
+//   u' = D (u - Dt CA w + Dt a b1)
+//   w' = (1 - Dt Lambda2) w - Dt CA^T u' + Dt a b2
+//      = (1 - Dt Lambda2) w + Dt^2 (CA^T D CA) w - Dt (CA^T D) u + Dt a (b2 - Dt CA^T D b1),
+// so both halves read only (u, w) of the step before and a step needs one
+// grid barrier.  The blocks split the rows: u-blocks own rows of CA (dotted
+// with w), w-blocks own rows of [Dt^2 CA^T D CA | -Dt CA^T D] (dotted with
+// [w ; u]), in the proportion that evens out the FP64 multiply-adds per SM,
+// the part of a step that scales with the coupling.  A block keeps its matrix
+// rows in shared memory for the whole sweep when they fit (otherwise it reads
+// them from global memory every step), stages the state of step n in shared
+// memory once after the barrier, and fetches what does not depend on the sweep
+// (F ends, old G values, jumps, the amplitude) for step n + 1 between its
+// arrival and its wait.  The barrier waits are bounded: on expiry the kernel
+// records an error and returns.
 namespace {
 
 constexpr int GS_THREADS = 512;
+constexpr int GS_WARPS = GS_THREADS / 32;
 constexpr int GS_SPIN = 1 << 22;
+constexpr int GS_SMEM_MAX = 200 * 1024;  // default: resident rows only below this per block
+constexpr size_t GS_SMEM_CAP = 220 * 1024;  // dynamic shared memory a block may take (static use is a few bytes)
+constexpr long long GS_MIN_FMA = 4096;      // fewer blocks for small couplings
 
 // Grid barrier on a counter that only grows within a launch (cleared before
 // each launch): barrier number b is passed once it reaches (b + 1) x blocks.
-// One arrival atomic per block and no reset or generation word; the wait
-// polls at most spin_limit times and then records the expiry and gives up.
-__device__ bool gs_barrier(unsigned* count, unsigned target, int* err, int spin_limit) {
+// Arrival and wait are separate so that a block can issue loads that do not
+// depend on the other blocks in between.
+__device__ __forceinline__ void gs_arrive(unsigned* count) {
   __syncthreads();
-  __shared__ int s_ok;
   if (threadIdx.x == 0) {
-    s_ok = 1;
     __threadfence();  // this block's writes are visible before its arrival
     atomicAdd(count, 1u);
+  }
+}
+// false (in every thread of the block) when the wait gave up: the other
+// blocks did not all arrive within spin_limit polls
+__device__ bool gs_wait(unsigned* count, unsigned target, int* err, int spin_limit) {
+  __shared__ int s_ok;
+  if (threadIdx.x == 0) {
     volatile unsigned* vc = count;
     int it = 0;
     while (*vc < target && it < spin_limit) {
       ++it;
       __nanosleep(20);
     }
-    if (*vc < target) {  // gave up: the other blocks did not all arrive within the limit
-      atomicExch(err, 1);
-      s_ok = 0;
-    }
+    const bool ok = *vc >= target;
+    if (!ok) atomicExch(err, 1);
+    s_ok = ok ? 1 : 0;
     __threadfence();
   }
   __syncthreads();
@@ -688,71 +709,184 @@ struct GSArgs {
   const double *Fu, *Fw, *Cu, *Cw;
   double *Xu, *Xw, *Gu, *Gw;
   int d1, d2, n_lo, n_hi, first;
-  int ublocks;  // blocks [0, ublocks) take the u rows, the others the w rows
+  int ublocks, ru, rw;  // blocks [0, ublocks) own ru rows of u each, the others rw rows of w each
   double Dt;
   unsigned* count;  // barrier arrivals, zero at launch
   int* err;
   int spin;  // polls before a barrier wait gives up
 };
 
-// One coarse step in spectral coordinates (lags restarted), D = (1 + Dt Lambda1)^-1:
-//   u' = D (u - Dt CA w + Dt a b1)
-//   w' = (1 - Dt Lambda2) w - Dt CA^T u' + Dt a b2
-//      = (1 - Dt Lambda2) w + Dt^2 (CA^T D CA) w - Dt (CA^T D) u + Dt a (b2 - Dt CA^T D b1),
-// so both halves depend on (u, w) only and the step needs one grid barrier:
-// blocks [0, ublocks) form u' a warp per row; the others form w' a block per
-// row, its 16 warps splitting the row of [Dt^2 CA^T D CA | -Dt CA^T D] against
-// [w ; u].  Each half applies eq. (2.7) to its rows at once.
+// shared-memory layout of k_g_sweep, in doubles
+struct GsLayout {
+  size_t xs, slot, pF, pG, pC, k1, k2, xown, pam, rows, n;
+};
+__host__ __device__ inline GsLayout gs_layout(int d1, int d2, int ru, int rw, bool resident) {
+  const size_t nrm = (size_t)(ru > rw ? ru : rw);
+  const size_t rowsz = (size_t)ru * d2 > (size_t)rw * (d1 + d2) ? (size_t)ru * d2 : (size_t)rw * (d1 + d2);
+  GsLayout L{};
+  size_t o = 0;
+  L.xs = o;  // [w ; u] of the current step
+  o += (size_t)d1 + d2;
+  L.slot = o;  // partial dot products
+  o += nrm > (size_t)GS_WARPS ? nrm : (size_t)GS_WARPS;
+  L.pF = o;  // F end, old G and jump of the own rows for the coming step
+  o += nrm;
+  L.pG = o;
+  o += nrm;
+  L.pC = o;
+  o += nrm;
+  L.k1 = o;  // per own row: b1 and 1 + Dt lambda1 (u), 1 - Dt lambda2 and b2 - Dt qb (w)
+  o += nrm;
+  L.k2 = o;
+  o += nrm;
+  L.xown = o;  // own u rows of the current state
+  o += nrm;
+  L.pam = o;  // the coming step's amplitude
+  o += 2;
+  L.rows = o;  // resident matrix rows
+  if (resident) o += rowsz;
+  L.n = o;
+  return L;
+}
+
+template <bool RES>
+__device__ __forceinline__ double gs_dot(const GSArgs& a, const double* rows, const double* xs, bool ub, int r0,
+                                         int r, int len, int k0, int k1, int lane) {
+  double acc = 0.0;
+  if (RES) {
+    const double* row = rows + (size_t)r * len;
+    for (int k = k0 + lane; k < k1; k += 32) acc = fma(row[k], xs[k], acc);
+  } else if (ub) {
+    const double* row = a.CA + (size_t)(r0 + r) * a.d2;
+    for (int k = k0 + lane; k < k1; k += 32) acc = fma(row[k], xs[k], acc);
+  } else {
+    const double s2 = a.Dt * a.Dt, s1 = -a.Dt;
+    const double* ge = a.GE + (size_t)(r0 + r) * a.d2;
+    const double* gc = a.GCD + (size_t)(r0 + r) * a.d1;
+    for (int k = k0 + lane; k < k1; k += 32) acc = fma(k < a.d2 ? s2 * ge[k] : s1 * gc[k - a.d2], xs[k], acc);
+  }
+  return pintd::warp_sum(acc);
+}
+
+template <bool RES>
 __global__ void __launch_bounds__(GS_THREADS) k_g_sweep(GSArgs a) {
-  __shared__ double s_part[GS_THREADS / 32];
-  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5;
-  const int d1 = a.d1, d2 = a.d2;
+  extern __shared__ __align__(16) double gs_sm[];
+  const int d1 = a.d1, d2 = a.d2, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double Dt = a.Dt;
-  const bool ublock = (int)blockIdx.x < a.ublocks;
-  const int uwarps = a.ublocks * (GS_THREADS / 32), uw = blockIdx.x * (GS_THREADS / 32) + wib;
-  const int wblocks = gridDim.x - a.ublocks, wb = blockIdx.x - a.ublocks;
-  const int kw = d2 + d1, piece = (kw + GS_THREADS / 32 - 1) / (GS_THREADS / 32);
-  unsigned target = 0;  // arrivals the next barrier waits for
-  for (int n = a.n_lo; n < a.n_hi; ++n) {
-    const double* xu = a.Xu + (size_t)n * d1;
-    const double* xw = a.Xw + (size_t)n * d2;
-    const double am = a.amp[n];
-    if (ublock) {
-      for (int i = uw; i < d1; i += uwarps) {
-        double acc = 0.0;
-        for (int j = lane; j < d2; j += 32) acc += a.CA[(size_t)i * d2 + j] * xw[j];
-        acc = pintd::warp_sum(acc);
-        if (lane == 0) {
-          const double g = (xu[i] - Dt * acc + Dt * am * a.b1[i]) / (1.0 + Dt * a.lam1[i]);
-          double v = a.first ? g : g + a.Fu[(size_t)n * d1 + i] - a.Gu[(size_t)n * d1 + i];
-          if (a.Cu) v += a.Cu[(size_t)(n + 1) * d1 + i];
-          a.Xu[(size_t)(n + 1) * d1 + i] = v;
-          a.Gu[(size_t)n * d1 + i] = g;
-        }
-      }
+  const bool ub = (int)blockIdx.x < a.ublocks;
+  const GsLayout L = gs_layout(d1, d2, a.ru, a.rw, RES);
+  double *xs = gs_sm + L.xs, *slot = gs_sm + L.slot, *pF = gs_sm + L.pF, *pG = gs_sm + L.pG, *pC = gs_sm + L.pC,
+         *k1 = gs_sm + L.k1, *k2 = gs_sm + L.k2, *xown = gs_sm + L.xown, *pam = gs_sm + L.pam,
+         *rows = gs_sm + L.rows;
+  int r0, nr, len;
+  if (ub) {
+    r0 = blockIdx.x * a.ru;
+    nr = max(0, min(d1, r0 + a.ru) - r0);
+    len = d2;
+  } else {
+    r0 = (blockIdx.x - a.ublocks) * a.rw;
+    nr = max(0, min(d2, r0 + a.rw) - r0);
+    len = d1 + d2;
+  }
+  const bool has_c = ub ? a.Cu != nullptr : a.Cw != nullptr;
+  if (RES) {
+    for (size_t e = tid; e < (size_t)nr * len; e += GS_THREADS) {
+      const int r = (int)(e / len), k = (int)(e - (size_t)r * len);
+      rows[e] = ub ? a.CA[(size_t)(r0 + r) * d2 + k]
+                   : (k < d2 ? (Dt * Dt) * a.GE[(size_t)(r0 + r) * d2 + k]
+                             : (-Dt) * a.GCD[(size_t)(r0 + r) * d1 + (k - d2)]);
+    }
+  }
+  for (int r = tid; r < nr; r += GS_THREADS) {
+    const int i = r0 + r;
+    if (ub) {
+      k1[r] = a.b1[i];
+      k2[r] = 1.0 + Dt * a.lam1[i];
+      xown[r] = a.Xu[(size_t)a.n_lo * d1 + i];
     } else {
-      for (int j = wb; j < d2; j += wblocks) {
-        const int k0 = wib * piece, k1 = min(kw, k0 + piece);
-        double acc = 0.0;
-        for (int k = k0 + lane; k < k1; k += 32)
-          acc += (k < d2) ? Dt * Dt * a.GE[(size_t)j * d2 + k] * xw[k] : -Dt * a.GCD[(size_t)j * d1 + (k - d2)] * xu[k - d2];
-        acc = pintd::warp_sum(acc);
-        if (lane == 0) s_part[wib] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-          double dot = 0.0;
-          for (int q = 0; q < GS_THREADS / 32; ++q) dot += s_part[q];
-          const double g = (1.0 - Dt * a.lam2[j]) * xw[j] + dot + Dt * am * (a.b2[j] - Dt * a.qb[j]);
-          double v = a.first ? g : g + a.Fw[(size_t)n * d2 + j] - a.Gw[(size_t)n * d2 + j];
-          if (a.Cw) v += a.Cw[(size_t)(n + 1) * d2 + j];
-          a.Xw[(size_t)(n + 1) * d2 + j] = v;
-          a.Gw[(size_t)n * d2 + j] = g;
+      k1[r] = 1.0 - Dt * a.lam2[i];
+      k2[r] = a.b2[i] - Dt * a.qb[i];
+    }
+  }
+  // inputs of step n that do not depend on the sweep; G_old of step n is read
+  // before this sweep rewrites it (at step n, by the same thread)
+  auto fetch = [&](int n) {
+    for (int r = tid; r < nr; r += GS_THREADS) {
+      const size_t i = (size_t)r0 + r;
+      double f = 0.0, g = 0.0, cc = 0.0;
+      if (ub) {
+        if (!a.first) {
+          f = a.Fu[(size_t)n * d1 + i];
+          g = a.Gu[(size_t)n * d1 + i];
         }
-        __syncthreads();
+        if (has_c) cc = a.Cu[(size_t)(n + 1) * d1 + i];
+      } else {
+        if (!a.first) {
+          f = a.Fw[(size_t)n * d2 + i];
+          g = a.Gw[(size_t)n * d2 + i];
+        }
+        if (has_c) cc = a.Cw[(size_t)(n + 1) * d2 + i];
+      }
+      pF[r] = f;
+      pG[r] = g;
+      pC[r] = cc;
+    }
+    if (tid == 0) pam[0] = a.amp[n];
+  };
+  fetch(a.n_lo);
+  // warps per row: whole rows round-robin when a block owns 16 rows or more,
+  // otherwise floor(16 / nr) warps split each row into contiguous pieces
+  const int g = nr >= GS_WARPS ? 1 : (nr > 0 ? GS_WARPS / nr : 1);
+  unsigned target = 0;  // arrivals the next wait needs
+  for (int n = a.n_lo; n < a.n_hi; ++n) {
+    if (nr > 0) {  // the state of step n, written by the other blocks (read past L1)
+      const double* xw = a.Xw + (size_t)n * d2;
+      for (int k = tid; k < d2; k += GS_THREADS) xs[k] = __ldcg(xw + k);
+      if (!ub) {
+        const double* xu = a.Xu + (size_t)n * d1;
+        for (int k = tid; k < d1; k += GS_THREADS) xs[d2 + k] = __ldcg(xu + k);
       }
     }
+    __syncthreads();
+    if (g == 1) {
+      for (int r = warp; r < nr; r += GS_WARPS) {
+        const double s = gs_dot<RES>(a, rows, xs, ub, r0, r, len, 0, len, lane);
+        if (lane == 0) slot[r] = s;
+      }
+    } else {
+      const int r = warp / g, sg = warp - r * g;
+      if (r < nr) {
+        const int kb = (int)((long long)len * sg / g), ke = (int)((long long)len * (sg + 1) / g);
+        const double s = gs_dot<RES>(a, rows, xs, ub, r0, r, len, kb, ke, lane);
+        if (lane == 0) slot[r * g + sg] = s;
+      }
+    }
+    __syncthreads();
+    const double am = pam[0];
+    for (int r = tid; r < nr; r += GS_THREADS) {
+      double dot = 0.0;
+      for (int q = 0; q < g; ++q) dot += slot[r * g + q];
+      const size_t i = (size_t)r0 + r;
+      if (ub) {
+        const double gv = (xown[r] - Dt * dot + Dt * am * k1[r]) / k2[r];
+        double v = a.first ? gv : gv + pF[r] - pG[r];
+        if (has_c) v += pC[r];
+        a.Xu[(size_t)(n + 1) * d1 + i] = v;
+        a.Gu[(size_t)n * d1 + i] = gv;
+        xown[r] = v;
+      } else {
+        const double gv = k1[r] * xs[i] + dot + Dt * am * k2[r];
+        double v = a.first ? gv : gv + pF[r] - pG[r];
+        if (has_c) v += pC[r];
+        a.Xw[(size_t)(n + 1) * d2 + i] = v;
+        a.Gw[(size_t)n * d2 + i] = gv;
+      }
+    }
+    if (n + 1 == a.n_hi) break;  // the kernel's end orders the last step's writes
     target += gridDim.x;
-    if (!gs_barrier(a.count, target, a.err, a.spin)) return;
+    gs_arrive(a.count);
+    fetch(n + 1);
+    if (!gs_wait(a.count, target, a.err, a.spin)) return;
   }
 }
 
@@ -762,26 +896,31 @@ __global__ void __launch_bounds__(GS_THREADS) k_g_sweep(GSArgs a) {
 static std::atomic<int> g_wait_limit{GS_SPIN};
 int wait_limit() { return g_wait_limit.load(); }
 void set_wait_limit(int spins) { g_wait_limit.store(spins < 0 ? GS_SPIN : spins); }
+// shared memory a sweep block may use for resident coupling rows (pint_set_sweep_smem)
+static std::atomic<int> g_sweep_smem{GS_SMEM_MAX};
+int sweep_smem() { return g_sweep_smem.load(); }
+void set_sweep_smem(int bytes) { g_sweep_smem.store(bytes < 0 ? GS_SMEM_MAX : bytes); }
 
 // one coarse sweep n = n_lo..N-1 (first: x_{n+1} = G(x_n) (+ c_{n+1}))
 static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, const double* Fu, const double* Fw,
                     const double* Cu, const double* Cw, int n_lo, bool first) {
-  static int blocks_per_sm = -1;
   static int num_sms = 0;
   {
-  std::lock_guard<std::mutex> lock(lazy_init_mutex());
-  if (blocks_per_sm < 0) {
-    int dev = 0;
-    PINT_CUDA(cudaGetDevice(&dev));
-    PINT_CUDA(cudaDeviceGetAttribute(&num_sms, cudaDevAttrMultiProcessorCount, dev));
-    PINT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&blocks_per_sm, k_g_sweep, GS_THREADS, 0));
-    PINT_REQUIRE(blocks_per_sm >= 1, PINT_ERR_CUDA, "coarse sweep kernel cannot be resident");
-  }
+    std::lock_guard<std::mutex> lock(lazy_init_mutex());
+    if (num_sms == 0) {
+      int dev = 0, sms = 0;
+      PINT_CUDA(cudaGetDevice(&dev));
+      PINT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+      PINT_CUDA(cudaFuncSetAttribute(k_g_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GS_SMEM_CAP));
+      PINT_CUDA(cudaFuncSetAttribute(k_g_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GS_SMEM_CAP));
+      num_sms = sms;  // set last: a failed attempt is retried by the next call
+    }
   }
   if (!H.gsync) {
     H.gsync = (unsigned*)dalloc(c, 64);
     PINT_CUDA(cudaMemsetAsync(H.gsync, 0, 64, c->stream));
   }
+  const int d1 = c->d1, d2 = c->d2;
   GSArgs a;
   a.CA = c->CA;
   a.GE = c->GE;
@@ -800,8 +939,8 @@ static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, c
   a.Xw = Xw;
   a.Gu = H.Gu;
   a.Gw = H.Gw;
-  a.d1 = c->d1;
-  a.d2 = c->d2;
+  a.d1 = d1;
+  a.d2 = d2;
   a.n_lo = n_lo;
   a.n_hi = c->N;
   a.first = first ? 1 : 0;
@@ -809,25 +948,34 @@ static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, c
   a.count = H.gsync;
   a.err = (int*)(H.gsync + 2);
   a.spin = wait_limit();
-  PINT_CUDA(cudaMemsetAsync(H.gsync, 0, 4, c->stream));  // the arrival counter
-  const int blocks = num_sms;  // one block per SM: fewest barrier arrivals
-  // split the blocks between u rows and w rows so that the longest per-warp
-  // dot product (the step's latency) is as short as possible
+  // blocks: one per SM at most, fewer for small couplings (each barrier costs
+  // every block's arrival); u-blocks vs w-blocks by the largest per-block
+  // count of multiply-adds
+  const long long fma_total = (long long)d1 * d2 + (long long)d2 * (d1 + d2);
+  const int blocks = (int)std::max<long long>(2, std::min<long long>(num_sms, fma_total / GS_MIN_FMA));
   {
-    const int W = GS_THREADS / 32, d1 = c->d1, d2 = c->d2;
     long long best = -1;
-    for (int ub = 1; ub < blocks; ++ub) {
-      const long long lu = (long long)((d1 + ub * W - 1) / (ub * W)) * ((d2 + 31) / 32);
-      const long long lw = (long long)((d2 + blocks - ub - 1) / (blocks - ub)) * (((d1 + d2 + W - 1) / W + 31) / 32);
-      const long long l = std::max(lu, lw);
+    for (int ubk = 1; ubk < blocks; ++ubk) {
+      const int ru = (d1 + ubk - 1) / ubk, rw = (d2 + blocks - ubk - 1) / (blocks - ubk);
+      const long long l = std::max((long long)ru * d2, (long long)rw * (d1 + d2));
       if (best < 0 || l < best) {
         best = l;
-        a.ublocks = ub;
+        a.ublocks = ubk;
+        a.ru = ru;
+        a.rw = rw;
       }
     }
   }
+  const bool resident = gs_layout(d1, d2, a.ru, a.rw, true).n * 8 <= (size_t)std::min<int>(sweep_smem(), GS_SMEM_CAP);
+  const size_t smem = gs_layout(d1, d2, a.ru, a.rw, resident).n * 8;
+  PINT_REQUIRE(smem <= GS_SMEM_CAP, PINT_ERR_CUDA, "coarse sweep: state does not fit in shared memory");
+  const void* fn = resident ? (const void*)k_g_sweep<true> : (const void*)k_g_sweep<false>;
+  int bps = 0;
+  PINT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, GS_THREADS, smem));
+  PINT_REQUIRE(bps >= 1, PINT_ERR_CUDA, "coarse sweep kernel cannot be resident");
+  PINT_CUDA(cudaMemsetAsync(H.gsync, 0, 4, c->stream));  // the arrival counter
   void* args[] = {&a};
-  PINT_CUDA(cudaLaunchCooperativeKernel((const void*)k_g_sweep, dim3(blocks), dim3(GS_THREADS), args, 0, c->stream));
+  PINT_CUDA(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(GS_THREADS), args, smem, c->stream));
   c->launches++;
 }
 

@@ -506,15 +506,17 @@ __global__ void __launch_bounds__(256) k_wr_gemm_df(const float* __restrict__ Ah
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
       float a_h[RM], a_l[RM], b_h[RN], b_l[RN];
+      // thread (tx, ty) owns rows ty + 16 p and columns tx + 16 q: the 16
+      // lanes of a half-warp read 16 consecutive words (no bank conflicts)
 #pragma unroll
       for (int q = 0; q < RM; ++q) {
-        a_h[q] = Ash[kk][ty * RM + q];
-        a_l[q] = Asl[kk][ty * RM + q];
+        a_h[q] = Ash[kk][ty + 16 * q];
+        a_l[q] = Asl[kk][ty + 16 * q];
       }
 #pragma unroll
       for (int q = 0; q < RN; ++q) {
-        b_h[q] = Bsh[kk][tx * RN + q];
-        b_l[q] = Bsl[kk][tx * RN + q];
+        b_h[q] = Bsh[kk][tx + 16 * q];
+        b_l[q] = Bsl[kk][tx + 16 * q];
       }
 #pragma unroll
       for (int p = 0; p < RM; ++p)
@@ -525,7 +527,7 @@ __global__ void __launch_bounds__(256) k_wr_gemm_df(const float* __restrict__ Ah
   }
   for (int p = 0; p < RM; ++p)
     for (int q = 0; q < RN; ++q) {
-      const int i = i0 + ty * RM + p, col = j0 + tx * RN + q;
+      const int i = i0 + ty + 16 * p, col = j0 + tx + 16 * q;
       if (i < M && col < ncols) out[(size_t)col * M + i] = (double)sh[p][q] + (double)sl[p][q];
     }
 }

@@ -586,6 +586,12 @@ int pint_set_wait_limit(int spins) {
   return old;
 }
 
+int pint_set_sweep_smem(int bytes) {
+  const int old = sweep_smem();
+  set_sweep_smem(bytes);
+  return old;
+}
+
 int pint_tuning_count(void) { return umma_tuning_count(); }
 
 pint_status pint_tuning_get(int* rows, float* us, int cap, int* count) {

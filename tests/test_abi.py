@@ -81,3 +81,11 @@ def test_wait_limit_control_without_gpu(libpint):
     assert libpint.pint_set_wait_limit(7) == default
     assert libpint.pint_set_wait_limit(-1) == 7
     assert libpint.pint_set_wait_limit(-1) == default
+
+
+def test_sweep_smem_control_without_gpu(libpint):
+    default = libpint.pint_set_sweep_smem(-1)
+    assert default == 200 * 1024
+    assert libpint.pint_set_sweep_smem(0) == default
+    assert libpint.pint_set_sweep_smem(-1) == 0
+    assert libpint.pint_set_sweep_smem(-1) == default

@@ -118,6 +118,24 @@ def test_parareal_solve_matches_oracle(pair):
     assert rel_t(fine.cpu().numpy(), ref_f) < 1e-10
 
 
+def test_streaming_coarse_sweep_matches_resident(pair):
+    """The FP64 coarse sweep keeps each block's coupling rows in shared
+    memory when they fit and reads them from global memory at every step
+    otherwise; both variants form the same products and sums, so a solve
+    with residency switched off agrees with the default one to rounding noise
+    (and so with the oracle)."""
+    _, prob, orc, p = pair
+    kw = dict(eps=1e-11, wr_tol=1e-14, wr_max=400, want_fine=False)
+    c0, _, s0 = p.parareal_solve(prob.u0, prob.f, prob.amp, **kw)
+    p.lib.pint_set_sweep_smem(0)
+    try:
+        c1, _, s1 = p.parareal_solve(prob.u0, prob.f, prob.amp, **kw)
+    finally:
+        p.lib.pint_set_sweep_smem(-1)
+    assert s1["K1"] == s0["K1"]
+    assert rel_t(c1.cpu().numpy(), c0.cpu().numpy()) < 1e-14
+
+
 def test_k_equals_N_matches_sequential(pair):
     _, prob, orc, p = pair
     c_seq, f_seq = p.sequential_solve(prob.u0, prob.f, prob.amp)
