@@ -453,56 +453,85 @@ __global__ void __launch_bounds__(128) k_w_sweep32(const float* __restrict__ S, 
 // pair, Knuth's TwoSum on the high parts and the errors summed in FP32.
 // Same column maps as k_wr_gemm (FP64 path), operands pre-split into pairs.
 // Tiles of TM rows x TN columns, (TM / 16) x (TN / 16) outputs per thread.
+// The next 16-wide K tile's operands are loaded into registers while the
+// current one is multiplied (its differences formed when they are stored to
+// shared memory), so the global loads' latency overlaps the arithmetic.
 template <int MODE, int TM, int TN>
 __global__ void __launch_bounds__(256) k_wr_gemm_df(const float* __restrict__ Ah, const float* __restrict__ Al,
                                                     int M, int K, const float* __restrict__ Uh,
                                                     const float* __restrict__ Ul, const float* __restrict__ Wh,
                                                     const float* __restrict__ Wl, int d1, int d2, int P, int ncols,
                                                     double* __restrict__ out) {
-  constexpr int RM = TM / 16, RN = TN / 16, TMAX = TM > TN ? TM : TN;
+  constexpr int RM = TM / 16, RN = TN / 16;
+  constexpr int NA = 16 * TM / 256, NB = 16 * TN / 256;  // staged elements per thread
   __shared__ float Ash[16][TM + 1], Asl[16][TM + 1], Bsh[16][TN + 1], Bsl[16][TN + 1];
   const int i0 = blockIdx.y * TM, j0 = blockIdx.x * TN;
-  const int tx = threadIdx.x % 16, ty = threadIdx.x / 16;
+  const int tid = threadIdx.x, tx = tid % 16, ty = tid / 16;
   float sh[RM][RN] = {}, sl[RM][RN] = {};
-  for (int k0 = 0; k0 < K; k0 += 16) {
-    for (int e = threadIdx.x; e < 16 * TMAX; e += 256) {
-      const int kk = e % 16, r = e / 16;
-      const int kg = k0 + kk, ig = i0 + r, col = j0 + r;
-      float ah = 0.f, al = 0.f, bh = 0.f, bl = 0.f;
-      if (r < TM && kg < K && ig < M) {
-        ah = Ah[(size_t)ig * K + kg];
-        al = Al[(size_t)ig * K + kg];
-      }
-      if (r < TN && kg < K && col < ncols) {
+  // element e = tid + 256 q of a stage: K offset e % 16, row / column e / 16.
+  // B values: x (the state) and, for a difference, y (the state before it)
+  float pah[NA], pal[NA], pxh[NB], pxl[NB], pyh[NB], pyl[NB];
+  bool pdf[NB];
+  auto load = [&](int k0) {
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int e = tid + 256 * q, kg = k0 + e % 16, ig = i0 + e / 16;
+      const bool in = kg < K && ig < M;
+      pah[q] = in ? Ah[(size_t)ig * K + kg] : 0.f;
+      pal[q] = in ? Al[(size_t)ig * K + kg] : 0.f;
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = tid + 256 * q, kg = k0 + e % 16, col = j0 + e / 16;
+      pxh[q] = pxl[q] = pyh[q] = pyl[q] = 0.f;
+      pdf[q] = false;
+      if (kg < K && col < ncols) {
         const int n = col / P, p = col % P;
         if (MODE == 0) {  // [w_p ; w_{max(p-1,0)}]
           const size_t base = (size_t)n * (P + 1) * d2;
           const size_t o = (kg < d2) ? base + (size_t)p * d2 + kg
                                      : base + (size_t)(p >= 1 ? p - 1 : 0) * d2 + (kg - d2);
-          bh = Wh[o];
-          bl = Wl[o];
+          pxh[q] = Wh[o];
+          pxl[q] = Wl[o];
         } else {  // [u_p - u_{max(p-1,0)} ; u_{p+1}]
           const size_t base = (size_t)n * (P + 1) * d1;
           if (kg < d1) {
             const size_t o1 = base + (size_t)p * d1 + kg, o0 = base + (size_t)(p >= 1 ? p - 1 : 0) * d1 + kg;
-            pintd::df_sub(Uh[o1], Ul[o1], Uh[o0], Ul[o0], bh, bl);
+            pxh[q] = Uh[o1];
+            pxl[q] = Ul[o1];
+            pyh[q] = Uh[o0];
+            pyl[q] = Ul[o0];
+            pdf[q] = true;
           } else {
             const size_t o = base + (size_t)(p + 1) * d1 + (kg - d1);
-            bh = Uh[o];
-            bl = Ul[o];
+            pxh[q] = Uh[o];
+            pxl[q] = Ul[o];
           }
         }
       }
-      if (r < TM) {
-        Ash[kk][r] = ah;
-        Asl[kk][r] = al;
-      }
-      if (r < TN) {
-        Bsh[kk][r] = bh;
-        Bsl[kk][r] = bl;
-      }
     }
+  };
+  auto store = [&]() {
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int e = tid + 256 * q;
+      Ash[e % 16][e / 16] = pah[q];
+      Asl[e % 16][e / 16] = pal[q];
+    }
+#pragma unroll
+    for (int q = 0; q < NB; ++q) {
+      const int e = tid + 256 * q;
+      float bh = pxh[q], bl = pxl[q];
+      if (pdf[q]) pintd::df_sub(pxh[q], pxl[q], pyh[q], pyl[q], bh, bl);
+      Bsh[e % 16][e / 16] = bh;
+      Bsl[e % 16][e / 16] = bl;
+    }
+  };
+  load(0);
+  for (int k0 = 0; k0 < K; k0 += 16) {
+    store();
     __syncthreads();
+    if (k0 + 16 < K) load(k0 + 16);
 #pragma unroll
     for (int kk = 0; kk < 16; ++kk) {
       float a_h[RM], a_l[RM], b_h[RN], b_l[RN];
@@ -692,8 +721,14 @@ __device__ __forceinline__ void cp_async4(float* sdst, const float* gsrc) {
 }
 __device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_all;" ::: "memory"); }
 
+// Eq. (4.7) for one mode over two intervals at once: every solved series is
+// real (the WR system is real), so intervals na (real part) and na + 1
+// (imaginary part) share one complex series through the forward DFT, the
+// shifted division (a complex scalar per frequency, the same for both) and
+// the inverse DFT, and come out as the real and imaginary parts: half the DFT
+// work of one series per interval.
 template <int R>
-__global__ void __launch_bounds__(256, 4) k_time_solve32_sq(const float* __restrict__ Rc, int d1, int ldu,
+__global__ void __launch_bounds__(256, 3) k_time_solve32_sq(const float* __restrict__ Rc, int d1, int ldu,
                                                          float* __restrict__ Ut, const float* __restrict__ lam1,
                                                          const float* __restrict__ src,
                                                          const float* __restrict__ b1,
@@ -701,46 +736,54 @@ __global__ void __launch_bounds__(256, 4) k_time_solve32_sq(const float* __restr
                                                          const float2* __restrict__ tw,
                                                          const float2* __restrict__ dsh,
                                                          const float* __restrict__ bpow, float* __restrict__ accU,
-                                                         float* __restrict__ B1h, float* __restrict__ B1l, const int* __restrict__ gate) {
+                                                         float* __restrict__ B1h, float* __restrict__ B1l,
+                                                         const int* __restrict__ gate, int nact) {
   if (gate && *gate) return;
   constexpr int P = R * R;       // steps per interval
   constexpr int NS = 256 / R;    // series (modes) per block
   constexpr int LD = NS + 1;     // tile row stride
   constexpr int PER = P * NS / 256;
-  __shared__ float sT[P * LD];   // right-hand sides, then the new states
-  __shared__ float sO[P * LD];   // previous iterate u_{p+1}
-  __shared__ float su0[NS];
-  const int nloc = blockIdx.y, i0 = blockIdx.x * NS;
+  __shared__ float sT[2][P * LD];  // right-hand sides, then the new states (per interval of the pair)
+  __shared__ float sO[2][P * LD];  // previous iterate u_{p+1}
+  __shared__ float su0[2][NS];
+  const int na = 2 * blockIdx.y, i0 = blockIdx.x * NS;
+  const int npair = (na + 1 < nact) ? 2 : 1;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  float* Un = Ut + (size_t)nloc * (P + 1) * ldu;
-  const float an = (float)amp[nloc];
   // every global read of the block is issued at once as asynchronous copies
   // into shared memory (the contraction output and the previous iterate)
+  for (int h = 0; h < npair; ++h) {
+    const int nloc = na + h;
+    const float* Un = Ut + (size_t)nloc * (P + 1) * ldu;
 #pragma unroll
-  for (int r = 0; r < PER; ++r) {
-    const int e = tid + 256 * r, p = e / NS, s = e % NS, i = i0 + s;
-    if (i < d1) {
-      cp_async4(&sT[p * LD + s], Rc + ((size_t)nloc * P + p) * d1 + i);
-      cp_async4(&sO[p * LD + s], Un + (size_t)(p + 1) * ldu + i);
-    } else {
-      sT[p * LD + s] = 0.f;
-      sO[p * LD + s] = 0.f;
+    for (int r = 0; r < PER; ++r) {
+      const int e = tid + 256 * r, p = e / NS, s = e % NS, i = i0 + s;
+      if (i < d1) {
+        cp_async4(&sT[h][p * LD + s], Rc + ((size_t)nloc * P + p) * d1 + i);
+        cp_async4(&sO[h][p * LD + s], Un + (size_t)(p + 1) * ldu + i);
+      } else {
+        sT[h][p * LD + s] = 0.f;
+        sO[h][p * LD + s] = 0.f;
+      }
     }
+    if (tid < NS) su0[h][tid] = (i0 + tid < d1) ? Un[i0 + tid] : 0.f;
   }
-  if (tid < NS) su0[tid] = (i0 + tid < d1) ? Un[i0 + tid] : 0.f;
   cp_async_wait_all();
   __syncthreads();
   // right-hand sides of eq. (4.7) scaled by beta^p, tile [p][mode]
+  for (int h = 0; h < npair; ++h) {
+    const int nloc = na + h;
+    const float an = (float)amp[nloc];
 #pragma unroll
-  for (int r = 0; r < PER; ++r) {
-    const int e = tid + 256 * r, p = e / NS, s = e % NS, i = i0 + s;
-    float y = 0.f;
-    if (i < d1) {
-      y = sT[p * LD + s] + (src ? src[((size_t)nloc * P + p) * d1 + i] : b1[i] * an);
-      if (p == 0) y += (su0[s] - alpha * sO[(P - 1) * LD + s]) / dt;  // u_P of the previous iterate
-      y *= bpow[p];
+    for (int r = 0; r < PER; ++r) {
+      const int e = tid + 256 * r, p = e / NS, s = e % NS, i = i0 + s;
+      float y = 0.f;
+      if (i < d1) {
+        y = sT[h][p * LD + s] + (src ? src[((size_t)nloc * P + p) * d1 + i] : b1[i] * an);
+        if (p == 0) y += (su0[h][s] - alpha * sO[h][(P - 1) * LD + s]) / dt;  // u_P of the previous iterate
+        y *= bpow[p];
+      }
+      sT[h][p * LD + s] = y;
     }
-    sT[p * LD + s] = y;
   }
   __syncthreads();
   // one series per R-lane group; series s = warp + 8 j keeps the tile reads
@@ -751,8 +794,8 @@ __global__ void __launch_bounds__(256, 4) k_time_solve32_sq(const float* __restr
   float re[R], im[R], twr[R], twi[R];
 #pragma unroll
   for (int m = 0; m < R; ++m) {
-    re[m] = sT[(g + R * m) * LD + s];
-    im[m] = 0.f;
+    re[m] = sT[0][(g + R * m) * LD + s];
+    im[m] = npair == 2 ? sT[1][(g + R * m) * LD + s] : 0.f;
   }
 #pragma unroll
   for (int a = 0; a < R; ++a) {
@@ -787,33 +830,42 @@ __global__ void __launch_bounds__(256, 4) k_time_solve32_sq(const float* __restr
   }
   group_transpose<R>(re, g, base);
   group_transpose<R>(im, g, base);
-  small_dft<R, 1>(re, im);  // lane g: P y[g + R m]
+  small_dft<R, 1>(re, im);  // lane g: P y[g + R m] (real part: interval na, imaginary part: na + 1)
   __syncthreads();          // every read of the right-hand sides is done
 #pragma unroll
-  for (int m = 0; m < R; ++m) sT[(g + R * m) * LD + s] = re[m] / ((float)P * bpow[g + R * m]);
+  for (int m = 0; m < R; ++m) {
+    const float sc = 1.f / ((float)P * bpow[g + R * m]);
+    sT[0][(g + R * m) * LD + s] = re[m] * sc;
+    sT[1][(g + R * m) * LD + s] = im[m] * sc;
+  }
   __syncthreads();
   // new states u_{p+1} (tile row p); the previous iterate is in sO.  Row r
   // of this thread is step p = (tid + 256 r) / NS: the warp's lanes share it
-  float dd[PER];
+  for (int h = 0; h < npair; ++h) {
+    const int nloc = na + h;
+    float* Un = Ut + (size_t)nloc * (P + 1) * ldu;
+    float dd[PER];
 #pragma unroll
-  for (int r = 0; r < PER; ++r) {
-    const int e = tid + 256 * r, p = e / NS, ss = e % NS, ii = i0 + ss;
-    dd[r] = 0.f;
-    if (ii < d1) {
-      const float uq = sT[p * LD + ss];
-      Un[(size_t)(p + 1) * ldu + ii] = uq;
-      if (B1h) {  // second-contraction column map [u_p - u_{p-1} ; u_{p+1}]
-        const size_t o = ((size_t)nloc * P + p) * 2 * ldu + ii;
-        const float dp = (p == 0) ? 0.f : sT[(p - 1) * LD + ss] - (p == 1 ? su0[ss] : sT[(p - 2) * LD + ss]);
-        put_split(B1h, B1l, o, dp);
-        put_split(B1h, B1l, o + ldu, uq);
+    for (int r = 0; r < PER; ++r) {
+      const int e = tid + 256 * r, p = e / NS, ss = e % NS, ii = i0 + ss;
+      dd[r] = 0.f;
+      if (ii < d1) {
+        const float uq = sT[h][p * LD + ss];
+        Un[(size_t)(p + 1) * ldu + ii] = uq;
+        if (B1h) {  // second-contraction column map [u_p - u_{p-1} ; u_{p+1}]
+          const size_t o = ((size_t)nloc * P + p) * 2 * ldu + ii;
+          const float dp =
+              (p == 0) ? 0.f : sT[h][(p - 1) * LD + ss] - (p == 1 ? su0[h][ss] : sT[h][(p - 2) * LD + ss]);
+          put_split(B1h, B1l, o, dp);
+          put_split(B1h, B1l, o + ldu, uq);
+        }
+        const float dv = uq - sO[h][p * LD + ss];
+        dd[r] = dv * dv;
       }
-      const float dv = uq - sO[p * LD + ss];
-      dd[r] = dv * dv;
     }
+    // one reduce-scatter over the warp for all PER rows (steps tid / NS + r 256 / NS)
+    warp_sum_scatter<PER>(dd, accU + (size_t)nloc * P + (tid - lane) / NS, 256 / NS);
   }
-  // one reduce-scatter over the warp for all PER rows (steps tid / NS + r 256 / NS)
-  warp_sum_scatter<PER>(dd, accU + (size_t)nloc * P + (tid - lane) / NS, 256 / NS);
 }
 
 // Register variant for P = 16, 32, 64: the contraction inputs and previous
@@ -1170,14 +1222,14 @@ void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const
   const dim3 grid(nbl(c->d1, 128), nact);
   const float al = (float)c->alpha, dt = (float)c->dt;
   if (P == 64)
-    k_time_solve32_sq<8><<<dim3(nbl(c->d1, 32), nact), 256, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al,
-                                                                           dt, tw, dsh, bpow, accU, B1h, B1l, gate);
+    k_time_solve32_sq<8><<<dim3(nbl(c->d1, 32), (nact + 1) / 2), 256, 0, c->stream>>>(
+        R, c->d1, ldu, Ut, lam1, src, b1, amp, al, dt, tw, dsh, bpow, accU, B1h, B1l, gate, nact);
   else if (P == 32)
     k_time_solve32_t<32><<<grid, 128, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al, dt, tw, dshbr, bpow,
                                                        accU, B1h, B1l, gate);
   else if (P == 16)
-    k_time_solve32_sq<4><<<dim3(nbl(c->d1, 64), nact), 256, 0, c->stream>>>(R, c->d1, ldu, Ut, lam1, src, b1, amp, al,
-                                                                           dt, tw, dsh, bpow, accU, B1h, B1l, gate);
+    k_time_solve32_sq<4><<<dim3(nbl(c->d1, 64), (nact + 1) / 2), 256, 0, c->stream>>>(
+        R, c->d1, ldu, Ut, lam1, src, b1, amp, al, dt, tw, dsh, bpow, accU, B1h, B1l, gate, nact);
   else  // other P: the DFTs as products with the DFT matrix
     k_time_solve32_mm<<<dim3(nbl(c->d1, MM_NS), nact), 256, 0, c->stream>>>(R, c->d1, ldu, P, Ut, lam1, src, b1,
                                                                            amp, al, dt, tw, dsh, bpow, accU, B1h,
