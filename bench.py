@@ -163,8 +163,8 @@ FP64_MEASURED_TFLOPS = 1.096
 # DRAM bytes (read + write) per launch of the tensor-core contraction on this
 # workload, averaged over its two launches, from the ncu capture summarised in
 # profiles/k_wr_umma_c2_mixed.md; only valid for the kernel source it was taken on.
-UMMA_TRAFFIC = {"sha1": "baabd2b174fd748f07bd009c310f300194b3a4c8",
-                "bytes": (25.104640e6 + 0.036864e6 + 93.659392e6 + 3.179264e6) / 2}
+UMMA_TRAFFIC = {"sha1": "c3188baec9826fb3cf93327189aa758ee4297bd4",
+                "bytes": (25.104384e6 + 0.021504e6 + 93.655040e6 + 2.986240e6) / 2}
 
 
 def umma_traffic():

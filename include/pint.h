@@ -185,10 +185,10 @@ pint_status pint_build_multiscale_spaces(pint_ctx* ctx, int nc, int J, int ell,
  *                    amplitude gradient from the interval's unit-source
  *                    response, <lambda_{n+1}, s>, instead of recomputing the
  *                    fine adjoint inside each interval (see pint_adjoint);
- *                    PINT_AUTOTUNE: on the PINT_MIXED path, the tile width
- *                    and K split of each tensor-core contraction shape are
- *                    measured (CUDA events, best of the cost model's top
- *                    candidates) the first time the shape is met, and kept
+ *                    PINT_AUTOTUNE: on the PINT_MIXED path, the tile width,
+ *                    K split and row pairing of each tensor-core contraction
+ *                    shape are measured (CUDA events, best of the cost
+ *                    model's top candidates) the first time the shape is met, and kept
  *                    in the process-wide table of pint_tuning_*; without
  *                    the flag the cost model's choice (or a loaded entry of
  *                    the table) is used
@@ -378,13 +378,16 @@ pint_status pint_batch_solve(pint_batch_item* items, int count, int workers);
 /*
  * Autotuner table (process-wide, shared by all contexts and host threads).
  * One row per contraction shape of the WR fine propagator's two tensor-core
- * contractions, as 6 ints: M (rows: d1 or d2), Kp (padded K), ncols (active
+ * contractions, as 7 ints: M (rows: d1 or d2), Kp (padded K), ncols (active
  * intervals x P), maxs (largest K split the consumer sums), tn (tile width,
- * 128..256, a multiple of 32), s (K split, 1..maxs, Kp a multiple of 16 s);
- * and the measured time of one launch in microseconds (0 when set by hand).
+ * 128..256, a multiple of 32), s (K split, 1..maxs, Kp a multiple of 16 s),
+ * pair (0 or 1: clusters of two CTAs take adjacent row tiles and share each
+ * B tile by multicast; a pair entry is ignored where such clusters cannot be
+ * resident); and the measured time of one launch in microseconds (0 when set
+ * by hand).
  * These calls touch no device state and need no GPU.
  *   pint_tuning_count  number of rows
- *   pint_tuning_get    copies up to cap rows (host int[cap][6], host
+ *   pint_tuning_get    copies up to cap rows (host int[cap][7], host
  *                      float[cap] or NULL) in key order; *count receives the
  *                      number copied.  Errors: BAD_ARG (NULL rows/count,
  *                      cap < 0)
@@ -404,9 +407,9 @@ pint_status pint_tuning_clear(void);
  * a grid-barrier wait of the FP64 coarse sweep makes before it gives up
  * (process-wide; spins < 0 restores the default of 4194304, about 0.1 s).
  * A wait that gives up records an error flag; the kernel returns, the solve
- * returns PINT_ERR_TIMEOUT and the context stays usable.  A small value
- * makes the wait run out on purpose, to exercise that path.  Returns the
- * previous limit.  Touches no device state.
+ * returns PINT_ERR_TIMEOUT and the context stays usable.  0 makes every
+ * such wait give up at once, to exercise that path.  Returns the previous
+ * limit.  Touches no device state.
  */
 int pint_set_wait_limit(int spins);
 

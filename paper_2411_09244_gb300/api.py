@@ -197,14 +197,14 @@ class ObservationMisfit(torch.autograd.Function):
 
 
 # -- autotuner table ----------------------------------------------------------
-TUNING_KEYS = ("M", "Kp", "ncols", "maxs", "tn", "s")
+TUNING_KEYS = ("M", "Kp", "ncols", "maxs", "tn", "s", "pair")
 
 
 def tuning_table() -> list[dict]:
     """Rows of the process-wide contraction tuning table (pint_tuning_get)."""
     lb = L.lib()
     n = lb.pint_tuning_count()
-    rows = np.zeros((max(n, 1), 6), dtype=np.int32)
+    rows = np.zeros((max(n, 1), len(TUNING_KEYS)), dtype=np.int32)
     us = np.zeros(max(n, 1), dtype=np.float32)
     got = C.c_int(0)
     L.check(lb.pint_tuning_get(rows.ctypes.data, us.ctypes.data, n, C.byref(got)))
@@ -214,7 +214,8 @@ def tuning_table() -> list[dict]:
 def set_tuning(entries) -> None:
     """Merge rows (dicts with TUNING_KEYS, optional "us") into the table."""
     entries = list(entries)
-    rows = np.array([[int(e[k]) for k in TUNING_KEYS] for e in entries], dtype=np.int32).reshape(-1, 6)
+    rows = np.array([[int(e.get(k, 0) if k == "pair" else e[k]) for k in TUNING_KEYS] for e in entries],
+                    dtype=np.int32).reshape(-1, len(TUNING_KEYS))
     us = np.array([float(e.get("us", 0.0)) for e in entries], dtype=np.float32)
     L.check(L.lib().pint_tuning_set(rows.ctypes.data if len(entries) else None,
                                     us.ctypes.data if len(entries) else None, len(entries)))
@@ -225,12 +226,12 @@ def clear_tuning() -> None:
 
 
 def save_tuning(path: str, device: str | None = None) -> None:
-    """Write the table as JSON: {"version": 1, "device": ..., "entries": [...]}."""
+    """Write the table as JSON: {"version": 2, "device": ..., "entries": [...]}."""
     import json
     if device is None and torch.cuda.is_available():
         device = torch.cuda.get_device_name()
     with open(path, "w") as fh:
-        json.dump({"version": 1, "device": device, "entries": tuning_table()}, fh, indent=1)
+        json.dump({"version": 2, "device": device, "entries": tuning_table()}, fh, indent=1)
 
 
 def load_tuning(path: str, device: str | None = None) -> int:
@@ -239,7 +240,7 @@ def load_tuning(path: str, device: str | None = None) -> int:
     import json
     with open(path) as fh:
         doc = json.load(fh)
-    if doc.get("version") != 1:
+    if doc.get("version") not in (1, 2):  # version 1 rows have no "pair" (unpaired)
         raise ValueError(f"{path}: unknown tuning table version {doc.get('version')!r}")
     if device is None and torch.cuda.is_available():
         device = torch.cuda.get_device_name()

@@ -684,7 +684,8 @@ __device__ __forceinline__ void gs_arrive(unsigned* count) {
   }
 }
 // false (in every thread of the block) when the wait gave up: the other
-// blocks did not all arrive within spin_limit polls
+// blocks did not all arrive within spin_limit polls (spin_limit <= 0: every
+// wait gives up at once, whatever has arrived)
 __device__ bool gs_wait(unsigned* count, unsigned target, int* err, int spin_limit) {
   __shared__ int s_ok;
   if (threadIdx.x == 0) {
@@ -694,7 +695,7 @@ __device__ bool gs_wait(unsigned* count, unsigned target, int* err, int spin_lim
       ++it;
       __nanosleep(20);
     }
-    const bool ok = *vc >= target;
+    const bool ok = spin_limit > 0 && *vc >= target;
     if (!ok) atomicExch(err, 1);
     s_ok = ok ? 1 : 0;
     __threadfence();
@@ -1556,11 +1557,11 @@ void apply_F_dev(Ctx* c, const double* in, int count, const double* f_nodes, con
 void mx_contract32(Ctx* c, int mode, const float* A, int M, int K, const float* Ut, const float* Wt, int ldu,
                    int ldw, int P, int ncols, float* out, const int* gate);
 void mx_contract_umma(Ctx* c, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
-                      const float* Blo, int ncols, int nsplit, int tn, float* out, int* err, const int* gate);
-void umma_plan(int M, int Kp, int ncols, int maxs, int* tn, int* s);
+                      const float* Blo, int ncols, int nsplit, int tn, int pair, float* out, int* err,
+                      const int* gate);
 void umma_prepare();
 void umma_choose(Ctx* c, bool tune, const float* Ahi, const float* Alo, int M, int Kp, const float* Bhi,
-                 const float* Blo, int ncols, int maxs, float* out, int* err, int* tn, int* s);
+                 const float* Blo, int ncols, int maxs, float* out, int* err, int* tn, int* s, int* pair);
 void mx_time_solve32(Ctx* c, const float* R, int nact, float* Ut, int ldu, const float* lam1, const float* src,
                      const float* b1, const double* amp, const float2* tw, const float2* dsh, const float2* dshbr,
                      const float* bpow, float* accU, float* B1h, float* B1l, const int* gate);
@@ -1827,7 +1828,7 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
   const bool tensor = (c->precision == PINT_MIXED);
   // tile widths and K splits of the two contractions (the time solve reads one
   // slice of the first; the W recurrence sums the slices of the second)
-  int tn0 = 128, tn1 = 128, nsl = 1, one = 1;
+  int tn0 = 128, tn1 = 128, nsl = 1, one = 1, pr0 = 0, pr1 = 0;
   float* acc32 = reinterpret_cast<float*>(H.acc);  // FP32 squared updates (2 nact P)
   wr_max = std::min(wr_max, PINT_MAX_ITERS);
   // column maps of the active window start at column 0 of B0 / B1
@@ -1835,9 +1836,9 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
   if (tensor) {
     // cost model, or the autotuner's measured choice (timing launches write
     // only the scratch outputs R and S, which the first iteration overwrites)
-    umma_choose(c, c->autotune, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, M.R, M.err, &tn0, &one);
+    umma_choose(c, c->autotune, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, M.R, M.err, &tn0, &one, &pr0);
     umma_choose(c, c->autotune, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, MX_MAX_SPLIT, M.S, M.err, &tn1,
-                &nsl);
+                &nsl, &pr1);
   }
   if (tensor) umma_prepare();  // before any capture
   PINT_CUDA(cudaMemsetAsync(M.gate, 0, 4, c->stream));
@@ -1857,14 +1858,14 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
       else PINT_CUDA(cudaEventRecord(e, c->stream));
     };
     rec(ev[0]);
-    if (tensor) mx_contract_umma(c, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, tn0, M.R, M.err, M.gate);
+    if (tensor) mx_contract_umma(c, M.Rhi, M.Rlo, d1, 2 * ldw, M.B0h, M.B0l, ncols, 1, tn0, pr0, M.R, M.err, M.gate);
     else mx_contract32(c, 0, M.AR32, d1, 2 * ldw, Ut, Wt, ldu, ldw, P, ncols, M.R, M.gate);
     rec(ev[1]);
     mx_time_solve32(c, M.R, nact, Ut, ldu, M.lam1f, srcU, M.b1f, amp_act, M.twf, M.dshf, M.dshbr, M.bpowf, acc32,
                     M.B1h, M.B1l, M.gate);
     rec(ev[2]);
     if (tensor)
-      mx_contract_umma(c, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, nsl, tn1, M.S, M.err, M.gate);
+      mx_contract_umma(c, M.Shi, M.Slo, d2, 2 * ldu, M.B1h, M.B1l, ncols, nsl, tn1, pr1, M.S, M.err, M.gate);
     else mx_contract32(c, 1, M.AS32, d2, 2 * ldu, Ut, Wt, ldu, ldw, P, ncols, M.S, M.gate);
     rec(ev[3]);
     mx_w_sweep32(c, M.S, tensor ? nsl : 1, (size_t)ncols * d2, nact, Wt, ldw, M.lam2f, srcW, M.b2f, amp_act,
@@ -1887,7 +1888,8 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
     }
     const std::array<uintptr_t, 9> key{(uintptr_t)Ut, (uintptr_t)Wt, (uintptr_t)srcU, (uintptr_t)srcW,
                                        (uintptr_t)amp_act, (uintptr_t)nact,
-                                       (uintptr_t)(tn0 | (tn1 << 10) | (nsl << 20) | ((tensor ? 1 : 0) << 24)),
+                                       (uintptr_t)(tn0 | (tn1 << 10) | (nsl << 20) | ((tensor ? 1 : 0) << 24) |
+                                                   (pr0 << 25) | (pr1 << 26)),
                                        (uintptr_t)tol_bits, (uintptr_t)par};
     auto f = M.graphs.find(key);
     if (f == M.graphs.end()) {

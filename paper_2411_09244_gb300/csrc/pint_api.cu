@@ -610,7 +610,7 @@ pint_status pint_tuning_set(const int* rows, const float* us, int count) {
   }
   const int bad = umma_tuning_set(rows, us, count);
   if (bad >= 0) {
-    set_error("tuning row " + std::to_string(bad) + " is not a valid (M, Kp, ncols, maxs, tn, s)");
+    set_error("tuning row " + std::to_string(bad) + " is not a valid (M, Kp, ncols, maxs, tn, s, pair)");
     return PINT_ERR_BAD_ARG;
   }
   return PINT_OK;

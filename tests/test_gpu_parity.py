@@ -314,9 +314,9 @@ def test_library_picks_the_stable_final_time():
 
 def test_bounded_wait_timeout_returns_status_and_context_recovers():
     """Failure detection without a device fault: with the grid-barrier wait
-    limit at zero every block but the last to arrive gives up at once, the
-    coarse sweep records the expiry and returns, and the solve returns
-    TIMEOUT; with the limit restored the same context solves as before."""
+    limit at zero every wait gives up at once, the coarse sweep records the
+    expiry and returns, and the solve returns TIMEOUT; with the limit
+    restored the same context solves as before."""
     from paper_2411_09244_gb300._lib import PintError
     prob = config_small(n_f=16, nc=4, J=2, ell=1, N=4, P=8)
     orc = OracleRun(prob)

@@ -19,11 +19,11 @@ def empty_table():
     api.clear_tuning()
 
 
-ROW = dict(M=1343, Kp=576, ncols=4096, maxs=1, tn=192, s=1, us=41.5)
+ROW = dict(M=1343, Kp=576, ncols=4096, maxs=1, tn=192, s=1, pair=0, us=41.5)
 
 
 def test_set_get_roundtrip_and_key_order():
-    rows = [dict(ROW), dict(ROW, M=257, Kp=2688, maxs=4, tn=256, s=3, us=0.0), dict(ROW, ncols=2048, tn=128)]
+    rows = [dict(ROW), dict(ROW, M=257, Kp=2688, maxs=4, tn=256, s=3, us=0.0), dict(ROW, ncols=2048, tn=128, pair=1)]
     api.set_tuning(rows)
     got = api.tuning_table()
     assert len(got) == 3 and _lib.lib().pint_tuning_count() == 3
@@ -37,7 +37,8 @@ def test_set_get_roundtrip_and_key_order():
 
 
 @pytest.mark.parametrize("bad", [dict(tn=96), dict(tn=288), dict(tn=200), dict(s=0), dict(s=2),
-                                 dict(maxs=4, s=3, Kp=584), dict(M=0), dict(ncols=-1)])
+                                 dict(maxs=4, s=3, Kp=584), dict(M=0), dict(ncols=-1), dict(pair=2),
+                                 dict(pair=-1)])
 def test_invalid_rows_are_rejected_atomically(bad):
     with pytest.raises(_lib.PintError) as ei:
         api.set_tuning([dict(ROW, M=64), dict(ROW, **bad)])
@@ -58,11 +59,17 @@ def test_json_save_load(tmp_path):
     path = tmp_path / "tune.json"
     api.save_tuning(str(path), device="GB300-test")
     doc = json.loads(path.read_text())
-    assert doc["version"] == 1 and doc["device"] == "GB300-test" and len(doc["entries"]) == 1
+    assert doc["version"] == 2 and doc["device"] == "GB300-test" and len(doc["entries"]) == 1
     api.clear_tuning()
     assert api.load_tuning(str(path), device="another") == 0 and api.tuning_table() == []
     assert api.load_tuning(str(path), device="GB300-test") == 1
     assert api.tuning_table()[0]["tn"] == 192
+    # a version-1 table (rows without the pairing column) loads as unpaired
+    api.clear_tuning()
+    old = {k: v for k, v in ROW.items() if k != "pair"}
+    path.write_text(json.dumps({"version": 1, "device": "GB300-test", "entries": [old]}))
+    assert api.load_tuning(str(path), device="GB300-test") == 1
+    assert api.tuning_table()[0]["pair"] == 0
 
 
 @pytest.mark.gpu
@@ -70,7 +77,9 @@ def test_autotuned_mixed_solve():
     """PINT_AUTOTUNE: the first mixed solve times each contraction shape and
     fills the table (one row per shape met, keyed by d1 / d2); the result
     stays within 1e-6 of the FP64 path, and a forced choice from the table
-    (every valid tile width) gives the same answer."""
+    (every valid tile width, unpaired and in cluster pairs sharing B tiles)
+    gives the same answer; pairing changes only which CTA loads which bytes,
+    so paired and unpaired solves agree bit for bit."""
     import numpy as np
     torch = pytest.importorskip("torch")
     from paper_2411_09244_gb300.inputs import config_small
@@ -88,9 +97,13 @@ def test_autotuned_mixed_solve():
         err = np.linalg.norm(fm.cpu().numpy() - ref) / np.linalg.norm(ref)
         assert err < 1e-6, err
         for tn in (128, 160, 192, 224, 256):
-            api.set_tuning([dict(r, tn=tn, s=1) for r in tab])
-            _, ft, _ = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-11)
-            e = np.linalg.norm(ft.cpu().numpy() - ref) / np.linalg.norm(ref)
-            assert e < 1e-6, (tn, e)
+            got = []
+            for pair in (0, 1):
+                api.set_tuning([dict(r, tn=tn, s=1, pair=pair) for r in tab])
+                _, ft, _ = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-11)
+                e = np.linalg.norm(ft.cpu().numpy() - ref) / np.linalg.norm(ref)
+                assert e < 1e-6, (tn, pair, e)
+                got.append(ft.cpu().numpy())
+            assert np.array_equal(got[0], got[1]), tn
     finally:
         p.close()
