@@ -1978,12 +1978,8 @@ static int wr_sweep_lp(Ctx* c, Hot& H, Mx& M, const double* xs_u, const double* 
   }
   if (it > wr_max) it = wr_max;
   mx_ends32(c, Ut, Wt, M.ldu, M.ldw, nact, fu, fw, fu32, fw32);
-  if (tensor) {
-    int herr = 0;
-    PINT_CUDA(cudaMemcpyAsync(&herr, M.err, 4, cudaMemcpyDeviceToHost, c->stream));
-    PINT_CUDA(cudaStreamSynchronize(c->stream));
-    PINT_REQUIRE(herr == 0, PINT_ERR_TIMEOUT, "tensor-core contraction: bounded mbarrier wait expired");
-  }
+  // the contractions' error flag (M.err) is read with the parareal jump at the
+  // end of the iteration: no host round trip here
   return it;
 }
 
@@ -2007,11 +2003,12 @@ struct LpRun {
 // coarse sweep of the low-precision path: FP32 couplings on one cluster when
 // they fit in its shared memory (and g64 is not asked), else the grid-wide
 // FP64 sweep (FP64 diagonal V_H1 solve, FP64 couplings and update)
+// (the grid-wide sweep's barrier error flag is read with the parareal jump at
+// the end of the iteration, lp_checks)
 static void g_sweep_lp(Ctx* c, Hot& H, Mx& M, double* Xu, double* Xw, const double* amp, const double* Fu,
                        const double* Fw, const double* Cu, const double* Cw, int n_lo, bool first, bool g64) {
   if (!M.gcl || g64) {
     g_sweep(c, H, Xu, Xw, amp, Fu, Fw, Cu, Cw, n_lo, first);
-    g_sweep_check(c, H);
     return;
   }
   GcArgs a;
@@ -2038,17 +2035,44 @@ static void g_sweep_lp(Ctx* c, Hot& H, Mx& M, double* Xu, double* Xw, const doub
   g_sweep_cluster(c, a, M.gcl);
 }
 
-// Algorithm 1 with the low-precision fine propagator (states FP64)
+// the device error flags of an iteration's bounded waits (contractions, grid
+// barrier), copied with the jump values before the iteration's one host sync
+// and raised after it
+static void lp_checks(Ctx* c, Hot& H, const int* herr) {
+  if (herr[1] != 0) {
+    // blocks that gave up left the counter mid-count: start the next sweep clean
+    PINT_CUDA(cudaMemsetAsync(H.gsync, 0, 64, c->stream));
+    PINT_CUDA(cudaStreamSynchronize(c->stream));
+    throw Fail{PINT_ERR_TIMEOUT, "coarse sweep: bounded grid barrier expired"};
+  }
+  PINT_REQUIRE(herr[0] == 0, PINT_ERR_TIMEOUT, "tensor-core contraction: bounded mbarrier wait expired");
+}
+
+// Algorithm 1 with the low-precision fine propagator (states FP64).  One
+// host synchronisation per iteration: the jump norm, read with the error
+// flags of the iteration's bounded waits.
 static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hist, double* jump_hist,
                         int hist_off) {
   const int N = c->N, d1 = c->d1, d2 = c->d2, P = c->P;
   if (!r.have_g0) {
     g_sweep_lp(c, H, M, r.Xu, r.Xw, r.amp, nullptr, nullptr, r.Cu, r.Cw, 0, true, r.g64);
   }
-  cudaEvent_t a0, a1;
-  PINT_CUDA(cudaEventCreate(&a0));
-  PINT_CUDA(cudaEventCreate(&a1));
+  struct Ev {  // released on every exit, including a thrown failure
+    cudaEvent_t e = nullptr;
+    ~Ev() {
+      if (e) cudaEventDestroy(e);
+    }
+  } e0, e1;
+  PINT_CUDA(cudaEventCreate(&e0.e));
+  PINT_CUDA(cudaEventCreate(&e1.e));
+  cudaEvent_t a0 = e0.e, a1 = e1.e;
   const int kcap = std::min(r.k_max, N);
+  if (kcap < 1) {  // no iteration: the initial sweep's flags are read here
+    int herr[2] = {0, 0};
+    if (H.gsync) PINT_CUDA(cudaMemcpyAsync(&herr[1], H.gsync + 2, 4, cudaMemcpyDeviceToHost, c->stream));
+    PINT_CUDA(cudaStreamSynchronize(c->stream));
+    lp_checks(c, H, herr);
+  }
   double best = 1e300;
   int stall = 0;
   for (int k = 1; k <= kcap; ++k) {
@@ -2067,10 +2091,6 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
                          H.Fw + (size_t)n_lo * d2, M.Fu32 ? M.Fu32 + (size_t)n_lo * d1 : nullptr,
                          M.Fw32 ? M.Fw32 + (size_t)n_lo * d2 : nullptr, &bad);
     PINT_CUDA(cudaEventRecord(a1, c->stream));
-    PINT_CUDA(cudaEventSynchronize(a1));
-    float ms = 0.f;
-    PINT_CUDA(cudaEventElapsedTime(&ms, a0, a1));
-    *f_ms += ms;
     if (bad) {
       r.nonfinite = true;
       break;
@@ -2087,8 +2107,15 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
     PINT_LAUNCH_CHECK();
     c->launches += 2;
     double h[2];
+    int herr[2] = {0, 0};
     PINT_CUDA(cudaMemcpyAsync(h, H.red, 16, cudaMemcpyDeviceToHost, c->stream));
+    if (M.tensor) PINT_CUDA(cudaMemcpyAsync(&herr[0], M.err, 4, cudaMemcpyDeviceToHost, c->stream));
+    if (H.gsync) PINT_CUDA(cudaMemcpyAsync(&herr[1], H.gsync + 2, 4, cudaMemcpyDeviceToHost, c->stream));
     PINT_CUDA(cudaStreamSynchronize(c->stream));
+    lp_checks(c, H, herr);
+    float ms = 0.f;
+    PINT_CUDA(cudaEventElapsedTime(&ms, a0, a1));
+    *f_ms += ms;
     r.K1 = k;
     r.last_jump = h[0];
     if (jump_hist && hist_off + k - 1 < PINT_MAX_ITERS) jump_hist[hist_off + k - 1] = h[0];
@@ -2109,8 +2136,6 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
     }
   }
   if (r.K1 == N) r.converged = true;
-  cudaEventDestroy(a0);
-  cudaEventDestroy(a1);
 }
 
 // max_n ||x_n||_{M_H} (n = 0..N) into *out (host)

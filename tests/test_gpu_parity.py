@@ -312,15 +312,18 @@ def test_library_picks_the_stable_final_time():
         p.close()
 
 
-def test_bounded_wait_timeout_returns_status_and_context_recovers():
+@pytest.mark.parametrize("mixed", [False, True])
+def test_bounded_wait_timeout_returns_status_and_context_recovers(mixed):
     """Failure detection without a device fault: with the grid-barrier wait
     limit at zero every wait gives up at once, the coarse sweep records the
-    expiry and returns, and the solve returns TIMEOUT; with the limit
-    restored the same context solves as before."""
-    from paper_2411_09244_gb300._lib import PintError
+    expiry and returns, and the solve returns TIMEOUT (on the mixed path the
+    FP64 sweeps of the correction solve, whose flag is read with the jump at
+    the end of the iteration); with the limit restored the same context
+    solves as before."""
+    from paper_2411_09244_gb300._lib import PintError, PINT_MIXED, PINT_FP64
     prob = config_small(n_f=16, nc=4, J=2, ell=1, N=4, P=8)
     orc = OracleRun(prob)
-    p = api.from_problem(prob, device="cuda", T=orc.T)
+    p = api.from_problem(prob, device="cuda", T=orc.T, precision=PINT_MIXED if mixed else PINT_FP64)
     try:
         c0, _, s0 = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-12, want_fine=False)
         p.lib.pint_set_wait_limit(0)
@@ -330,8 +333,10 @@ def test_bounded_wait_timeout_returns_status_and_context_recovers():
         finally:
             p.lib.pint_set_wait_limit(-1)
         c1, _, s1 = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-12, want_fine=False)
-        assert s1["converged"] and s1["K1"] == s0["K1"]
-        assert rel_t(c1.cpu().numpy(), c0.cpu().numpy()) < 1e-14
+        assert s1["converged"] == s0["converged"] and s1["K1"] == s0["K1"]
+        # FP64: the same arithmetic; mixed: FP32 atomics in the WR norms may
+        # reorder, so the same answer to well inside the mixed tolerance
+        assert rel_t(c1.cpu().numpy(), c0.cpu().numpy()) < (1e-9 if mixed else 1e-14)
     finally:
         p.close()
 
