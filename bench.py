@@ -408,7 +408,7 @@ def run_ours(args, rank, world):
                                                "spectral", "time_grid"), stages)),
                    "l2": "512 MB buffer zeroed before every timed step",
                    "contraction_tiles": ("cost model" if args.no_autotune or args.precision != "mixed" else
-                                         [{k: r[k] for k in ("M", "ncols", "tn", "s", "us")}
+                                         [{k: r[k] for k in ("M", "ncols", "tn", "s", "pair", "us")}
                                           for r in api.tuning_table()]),
                    "parallelism": "replicas" if world > 1 else "single GPU"},
         "roofline": roof,
