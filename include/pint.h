@@ -419,8 +419,9 @@ int pint_set_wait_limit(int spins);
  * bytes, one block of the sweep may use to keep its rows of the coupling
  * operators resident for the whole sweep (process-wide; bytes < 0 restores
  * the default of 204800).  Couplings whose per-block share does not fit are
- * read from global memory at every coarse step instead; both variants give
- * the same products and sums, so results do not depend on this value.  0
+ * read from global memory at every coarse step instead; both variants form
+ * the same products (summed in another order), so results agree to rounding
+ * whatever this value.  0
  * selects the streaming variant for every shape.  Returns the previous value.
  * Touches no device state.
  */

@@ -134,7 +134,8 @@ struct Ctx {
   double2* tw = nullptr;      // twiddles e^{-2 pi i k / P}, k < P
   double2* dshift = nullptr;  // d_k = (1 - beta w^k)/dt
   double* lampow = nullptr;   // beta^p, p = 0..P
-  double* GE = nullptr;       // CA^T D CA (d2 x d2), D = (1 + Dt Lambda1)^-1: the folded coarse step
+  double* GW = nullptr;       // [Dt^2 CA^T D CA | -Dt CA^T D] (d2 x (d2 + d1)), D = (1 + Dt Lambda1)^-1:
+                              // the w rows of the folded coarse step
   double* GCD = nullptr;      // CA^T D (d2 x d1)
 
   // mixed-path state lives in mixed.cu

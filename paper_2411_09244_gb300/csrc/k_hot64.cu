@@ -554,6 +554,16 @@ __global__ void k_scale_cols(const double* __restrict__ CAt, const double* __res
   out[e] = CAt[e] / (1.0 + Dt * lam1[e % d1]);
 }
 
+// GW = [Dt^2 GE | -Dt GCD], rows of d2 + d1
+__global__ void k_fold_rows(const double* __restrict__ GE, const double* __restrict__ GCD, double Dt, int d2, int d1,
+                            double* __restrict__ GW) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int w = d2 + d1;
+  if (e >= (long long)d2 * w) return;
+  const int j = (int)(e / w), k = (int)(e - (long long)j * w);
+  GW[e] = k < d2 ? (Dt * Dt) * GE[(size_t)j * d2 + k] : (-Dt) * GCD[(size_t)j * d1 + (k - d2)];
+}
+
 void hot_prepare(Ctx* c) {
   const int d1 = c->d1, d2 = c->d2, P = c->P;
   auto A = [&](size_t n) { return (double*)dalloc(c, n * 8); };
@@ -581,14 +591,22 @@ void hot_prepare(Ctx* c) {
   }
   PINT_CUDA(cudaMemcpyAsync(c->AR, AR.data(), AR.size() * 8, cudaMemcpyHostToDevice, c->stream));
   PINT_CUDA(cudaMemcpyAsync(c->AS, AS.data(), AS.size() * 8, cudaMemcpyHostToDevice, c->stream));
-  // the folded coarse step (k_g_sweep): GCD = CA^T D, GE = CA^T D CA, D = (1 + Dt Lambda1)^-1
-  if (!c->GE) {
-    c->GE = A((size_t)d2 * d2);
+  // the folded coarse step (k_g_sweep): GCD = CA^T D, GE = CA^T D CA, D = (1 + Dt Lambda1)^-1,
+  // and its w rows GW = [Dt^2 GE | -Dt GCD]
+  if (!c->GW) {
+    c->GW = A((size_t)d2 * (d2 + d1));
     c->GCD = A((size_t)d2 * d1);
   }
-  k_scale_cols<<<nb_((long long)d2 * d1, 256), 256, 0, c->stream>>>(c->CAt, c->lam1, c->Dt, d2, d1, c->GCD);
-  PINT_LAUNCH_CHECK();
-  dense_gemm(c, c->GCD, c->CA, c->GE, d2, d2, d1, false, false, 1.0, 0.0);
+  {
+    double* GE = A((size_t)d2 * d2);
+    k_scale_cols<<<nb_((long long)d2 * d1, 256), 256, 0, c->stream>>>(c->CAt, c->lam1, c->Dt, d2, d1, c->GCD);
+    PINT_LAUNCH_CHECK();
+    dense_gemm(c, c->GCD, c->CA, GE, d2, d2, d1, false, false, 1.0, 0.0);
+    k_fold_rows<<<nb_((long long)d2 * (d2 + d1), 256), 256, 0, c->stream>>>(GE, c->GCD, c->Dt, d2, d1, c->GW);
+    PINT_LAUNCH_CHECK();
+    PINT_CUDA(cudaStreamSynchronize(c->stream));
+    dfree(c, GE);
+  }
   std::vector<double2> tw(64), ds(64);
   std::vector<double> bp(65);
   const double beta = std::pow(c->alpha, 1.0 / P);
@@ -646,8 +664,9 @@ static void step_batch(Ctx* c, Hot& H, const double* u, const double* w, const d
 
 // ---------------------------------------------------------------------------
 // The sequential coarse sweep of Algorithm 1 (the G step and the update of
-// eq. (2.7) at every coarse step) in FP64, as one persistent cooperative
-// kernel.  With D = (1 + Dt Lambda1)^-1, one step in spectral coordinates
+// eq. (2.7) at every coarse step) as one persistent cooperative kernel, FP64
+// throughout or (the low-precision solve, where no cluster holds the
+// coupling) with FP32 couplings and dot products.  With D = (1 + Dt Lambda1)^-1, one step in spectral coordinates
 // (lags restarted) is
 //   u' = D (u - Dt CA w + Dt a b1)
 //   w' = (1 - Dt Lambda2) w - Dt CA^T u' + Dt a b2
@@ -655,14 +674,17 @@ static void step_batch(Ctx* c, Hot& H, const double* u, const double* w, const d
 // so both halves read only (u, w) of the step before and a step needs one
 // grid barrier.  The blocks split the rows: u-blocks own rows of CA (dotted
 // with w), w-blocks own rows of [Dt^2 CA^T D CA | -Dt CA^T D] (dotted with
-// [w ; u]), in the proportion that evens out the FP64 multiply-adds per SM,
-// the part of a step that scales with the coupling.  A block keeps its matrix
-// rows in shared memory for the whole sweep when they fit (otherwise it reads
-// them from global memory every step), stages the state of step n in shared
-// memory once after the barrier, and fetches what does not depend on the sweep
-// (F ends, old G values, jumps, the amplitude) for step n + 1 between its
-// arrival and its wait.  The barrier waits are bounded: on expiry the kernel
-// records an error and returns.
+// [w ; u]), in the proportion that evens out the multiply-adds per SM, the
+// part of a step that scales with the coupling; rows are cut into pieces
+// (as many as the warps of a block take in one round; at most GS_PIECE
+// entries when streamed), dealt out to the block's warps as tasks and summed
+// in a fixed order.  A block keeps its matrix rows in shared memory for
+// the whole sweep when they fit (otherwise it streams them from global memory
+// every step, four loads in flight per lane), stages the state of step n in
+// shared memory once after the barrier, and fetches what does not depend on
+// the sweep (F ends, old G values, jumps, the amplitude) for step n + 1
+// between its arrival and its wait.  The barrier waits are bounded: on expiry
+// the kernel records an error and returns.
 namespace {
 
 constexpr int GS_THREADS = 512;
@@ -671,6 +693,7 @@ constexpr int GS_SPIN = 1 << 22;
 constexpr int GS_SMEM_MAX = 200 * 1024;  // default: resident rows only below this per block
 constexpr size_t GS_SMEM_CAP = 220 * 1024;  // dynamic shared memory a block may take (static use is a few bytes)
 constexpr long long GS_MIN_FMA = 4096;      // fewer blocks for small couplings
+constexpr int GS_PIECE = 512;               // longest row piece one warp task streams
 
 // Grid barrier on a counter that only grows within a launch (cleared before
 // each launch): barrier number b is passed once it reaches (b + 1) x blocks.
@@ -704,100 +727,112 @@ __device__ bool gs_wait(unsigned* count, unsigned target, int* err, int spin_lim
   return s_ok != 0;
 }
 
+// Matrices of the sweep in MT (double: FP64 sweep; float: the low-precision
+// solve's sweep where no cluster holds the coupling); the dot products
+// accumulate in MT, everything else (states, updates, the diagonal solve) in
+// FP64.  A block's own rows of the state stay in shared memory in FP64.
+template <typename MT>
 struct GSArgs {
-  const double *CA, *lam1, *lam2, *b1, *b2, *qb, *amp;
-  const double *GE, *GCD;  // CA^T D CA (d2 x d2) and CA^T D (d2 x d1), D = (1 + Dt Lambda1)^-1
+  const MT *CA, *GW;  // u rows: CA (d1 x d2); w rows: [Dt^2 CA^T D CA | -Dt CA^T D] (d2 x (d2 + d1))
+  const double *lam1, *lam2, *b1, *b2, *qb, *amp;
   const double *Fu, *Fw, *Cu, *Cw;
   double *Xu, *Xw, *Gu, *Gw;
   int d1, d2, n_lo, n_hi, first;
   int ublocks, ru, rw;  // blocks [0, ublocks) own ru rows of u each, the others rw rows of w each
+  int nsu, nsw;         // pieces a u row / w row is split into (one warp task each)
   double Dt;
   unsigned* count;  // barrier arrivals, zero at launch
   int* err;
   int spin;  // polls before a barrier wait gives up
 };
 
-// shared-memory layout of k_g_sweep, in doubles
+// shared-memory layout of k_g_sweep, in bytes (16-byte aligned regions)
 struct GsLayout {
   size_t xs, slot, pF, pG, pC, k1, k2, xown, pam, rows, n;
 };
-__host__ __device__ inline GsLayout gs_layout(int d1, int d2, int ru, int rw, bool resident) {
+__host__ __device__ inline GsLayout gs_layout(int d1, int d2, int ru, int rw, int nsu, int nsw, int msz,
+                                              bool resident) {
   const size_t nrm = (size_t)(ru > rw ? ru : rw);
   const size_t rowsz = (size_t)ru * d2 > (size_t)rw * (d1 + d2) ? (size_t)ru * d2 : (size_t)rw * (d1 + d2);
+  const size_t tasks = (size_t)ru * nsu > (size_t)rw * nsw ? (size_t)ru * nsu : (size_t)rw * nsw;
   GsLayout L{};
   size_t o = 0;
-  L.xs = o;  // [w ; u] of the current step
-  o += (size_t)d1 + d2;
-  L.slot = o;  // partial dot products
-  o += nrm > (size_t)GS_WARPS ? nrm : (size_t)GS_WARPS;
-  L.pF = o;  // F end, old G and jump of the own rows for the coming step
-  o += nrm;
-  L.pG = o;
-  o += nrm;
-  L.pC = o;
-  o += nrm;
-  L.k1 = o;  // per own row: b1 and 1 + Dt lambda1 (u), 1 - Dt lambda2 and b2 - Dt qb (w)
-  o += nrm;
-  L.k2 = o;
-  o += nrm;
-  L.xown = o;  // own u rows of the current state
-  o += nrm;
-  L.pam = o;  // the coming step's amplitude
-  o += 2;
-  L.rows = o;  // resident matrix rows
-  if (resident) o += rowsz;
+  auto take = [&](size_t bytes) {
+    const size_t at = o;
+    o += (bytes + 15) / 16 * 16;
+    return at;
+  };
+  L.xs = take(((size_t)d1 + d2) * msz);  // [w ; u] of the current step (MT)
+  L.slot = take(tasks * 8);               // partial dot products of the warp tasks
+  L.pF = take(nrm * 8);                   // F end, old G and jump of the own rows for the coming step
+  L.pG = take(nrm * 8);
+  L.pC = take(nrm * 8);
+  L.k1 = take(nrm * 8);  // per own row: b1 and 1 + Dt lambda1 (u), 1 - Dt lambda2 and b2 - Dt qb (w)
+  L.k2 = take(nrm * 8);
+  L.xown = take(nrm * 8);  // own rows of the current state (FP64)
+  L.pam = take(16);        // the coming step's amplitude
+  L.rows = o;              // resident matrix rows (MT)
+  if (resident) take(rowsz * msz);
   L.n = o;
   return L;
 }
 
-template <bool RES>
-__device__ __forceinline__ double gs_dot(const GSArgs& a, const double* rows, const double* xs, bool ub, int r0,
-                                         int r, int len, int k0, int k1, int lane) {
-  double acc = 0.0;
-  if (RES) {
-    const double* row = rows + (size_t)r * len;
-    for (int k = k0 + lane; k < k1; k += 32) acc = fma(row[k], xs[k], acc);
-  } else if (ub) {
-    const double* row = a.CA + (size_t)(r0 + r) * a.d2;
-    for (int k = k0 + lane; k < k1; k += 32) acc = fma(row[k], xs[k], acc);
-  } else {
-    const double s2 = a.Dt * a.Dt, s1 = -a.Dt;
-    const double* ge = a.GE + (size_t)(r0 + r) * a.d2;
-    const double* gc = a.GCD + (size_t)(r0 + r) * a.d1;
-    for (int k = k0 + lane; k < k1; k += 32) acc = fma(k < a.d2 ? s2 * ge[k] : s1 * gc[k - a.d2], xs[k], acc);
+__device__ __forceinline__ float gs_warp_sum(float v) { return pintd::warp_sumf(v); }
+__device__ __forceinline__ double gs_warp_sum(double v) { return pintd::warp_sum(v); }
+
+// sum_k row[k] xs[k] over k = k0 + lane, k0 + lane + 32, ... < k1.
+// Streamed rows (STREAM): eight independent accumulators, eight loads in
+// flight per lane.  Rows in shared memory: one accumulator, since on GB300
+// an FP64 add costs an FP64 pipe slot like a multiply-add, and the resident
+// FP64 step is bound by that pipe, not by load latency.
+template <typename MT, bool STREAM>
+__device__ __forceinline__ MT gs_piece(const MT* row, const MT* xs, int k, int k1) {
+  if (!STREAM) {
+    MT acc = 0;
+    for (; k < k1; k += 32) acc = fma(row[k], xs[k], acc);
+    return acc;
   }
-  return pintd::warp_sum(acc);
+  MT acc[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (; k + 224 < k1; k += 256) {
+#pragma unroll
+    for (int u = 0; u < 8; ++u) acc[u] = fma(row[k + 32 * u], xs[k + 32 * u], acc[u]);
+  }
+#pragma unroll
+  for (int u = 0; u < 7; ++u)  // at most seven entries per lane are left
+    if (k + 32 * u < k1) acc[u] = fma(row[k + 32 * u], xs[k + 32 * u], acc[u]);
+  return ((acc[0] + acc[1]) + (acc[2] + acc[3])) + ((acc[4] + acc[5]) + (acc[6] + acc[7]));
 }
 
-template <bool RES>
-__global__ void __launch_bounds__(GS_THREADS) k_g_sweep(GSArgs a) {
-  extern __shared__ __align__(16) double gs_sm[];
+template <typename MT, bool RES>
+__global__ void __launch_bounds__(GS_THREADS, 1) k_g_sweep(GSArgs<MT> a) {
+  extern __shared__ __align__(16) unsigned char gs_raw[];
   const int d1 = a.d1, d2 = a.d2, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const double Dt = a.Dt;
   const bool ub = (int)blockIdx.x < a.ublocks;
-  const GsLayout L = gs_layout(d1, d2, a.ru, a.rw, RES);
-  double *xs = gs_sm + L.xs, *slot = gs_sm + L.slot, *pF = gs_sm + L.pF, *pG = gs_sm + L.pG, *pC = gs_sm + L.pC,
-         *k1 = gs_sm + L.k1, *k2 = gs_sm + L.k2, *xown = gs_sm + L.xown, *pam = gs_sm + L.pam,
-         *rows = gs_sm + L.rows;
-  int r0, nr, len;
+  const GsLayout L = gs_layout(d1, d2, a.ru, a.rw, a.nsu, a.nsw, (int)sizeof(MT), RES);
+  MT* xs = reinterpret_cast<MT*>(gs_raw + L.xs);
+  MT* rows = reinterpret_cast<MT*>(gs_raw + L.rows);
+  double *slot = reinterpret_cast<double*>(gs_raw + L.slot), *pF = reinterpret_cast<double*>(gs_raw + L.pF),
+         *pG = reinterpret_cast<double*>(gs_raw + L.pG), *pC = reinterpret_cast<double*>(gs_raw + L.pC),
+         *k1 = reinterpret_cast<double*>(gs_raw + L.k1), *k2 = reinterpret_cast<double*>(gs_raw + L.k2),
+         *xown = reinterpret_cast<double*>(gs_raw + L.xown), *pam = reinterpret_cast<double*>(gs_raw + L.pam);
+  int r0, nr, len, ns;
   if (ub) {
     r0 = blockIdx.x * a.ru;
     nr = max(0, min(d1, r0 + a.ru) - r0);
     len = d2;
+    ns = a.nsu;
   } else {
     r0 = (blockIdx.x - a.ublocks) * a.rw;
     nr = max(0, min(d2, r0 + a.rw) - r0);
     len = d1 + d2;
+    ns = a.nsw;
   }
+  const int seg = (len + ns - 1) / ns;  // length of a row piece
+  const MT* mat = ub ? a.CA : a.GW;     // rows of len entries
   const bool has_c = ub ? a.Cu != nullptr : a.Cw != nullptr;
-  if (RES) {
-    for (size_t e = tid; e < (size_t)nr * len; e += GS_THREADS) {
-      const int r = (int)(e / len), k = (int)(e - (size_t)r * len);
-      rows[e] = ub ? a.CA[(size_t)(r0 + r) * d2 + k]
-                   : (k < d2 ? (Dt * Dt) * a.GE[(size_t)(r0 + r) * d2 + k]
-                             : (-Dt) * a.GCD[(size_t)(r0 + r) * d1 + (k - d2)]);
-    }
-  }
+  if (RES)
+    for (size_t e = tid; e < (size_t)nr * len; e += GS_THREADS) rows[e] = mat[(size_t)r0 * len + e];
   for (int r = tid; r < nr; r += GS_THREADS) {
     const int i = r0 + r;
     if (ub) {
@@ -807,6 +842,7 @@ __global__ void __launch_bounds__(GS_THREADS) k_g_sweep(GSArgs a) {
     } else {
       k1[r] = 1.0 - Dt * a.lam2[i];
       k2[r] = a.b2[i] - Dt * a.qb[i];
+      xown[r] = a.Xw[(size_t)a.n_lo * d2 + i];
     }
   }
   // inputs of step n that do not depend on the sweep; G_old of step n is read
@@ -835,38 +871,29 @@ __global__ void __launch_bounds__(GS_THREADS) k_g_sweep(GSArgs a) {
     if (tid == 0) pam[0] = a.amp[n];
   };
   fetch(a.n_lo);
-  // warps per row: whole rows round-robin when a block owns 16 rows or more,
-  // otherwise floor(16 / nr) warps split each row into contiguous pieces
-  const int g = nr >= GS_WARPS ? 1 : (nr > 0 ? GS_WARPS / nr : 1);
-  unsigned target = 0;  // arrivals the next wait needs
+  const int ntask = nr * ns;  // (row, piece) tasks dealt out over the warps
+  unsigned target = 0;        // arrivals the next wait needs
   for (int n = a.n_lo; n < a.n_hi; ++n) {
     if (nr > 0) {  // the state of step n, written by the other blocks (read past L1)
       const double* xw = a.Xw + (size_t)n * d2;
-      for (int k = tid; k < d2; k += GS_THREADS) xs[k] = __ldcg(xw + k);
+      for (int k = tid; k < d2; k += GS_THREADS) xs[k] = (MT)__ldcg(xw + k);
       if (!ub) {
         const double* xu = a.Xu + (size_t)n * d1;
-        for (int k = tid; k < d1; k += GS_THREADS) xs[d2 + k] = __ldcg(xu + k);
+        for (int k = tid; k < d1; k += GS_THREADS) xs[d2 + k] = (MT)__ldcg(xu + k);
       }
     }
     __syncthreads();
-    if (g == 1) {
-      for (int r = warp; r < nr; r += GS_WARPS) {
-        const double s = gs_dot<RES>(a, rows, xs, ub, r0, r, len, 0, len, lane);
-        if (lane == 0) slot[r] = s;
-      }
-    } else {
-      const int r = warp / g, sg = warp - r * g;
-      if (r < nr) {
-        const int kb = (int)((long long)len * sg / g), ke = (int)((long long)len * (sg + 1) / g);
-        const double s = gs_dot<RES>(a, rows, xs, ub, r0, r, len, kb, ke, lane);
-        if (lane == 0) slot[r * g + sg] = s;
-      }
+    for (int t = warp; t < ntask; t += GS_WARPS) {
+      const int r = t / ns, pc = t - r * ns, kb = pc * seg, ke = min(len, kb + seg);
+      const MT* row = RES ? rows + (size_t)r * len : mat + (size_t)(r0 + r) * len;
+      const MT s = gs_warp_sum(gs_piece<MT, !RES>(row, xs, kb + lane, ke));
+      if (lane == 0) slot[t] = (double)s;
     }
     __syncthreads();
     const double am = pam[0];
     for (int r = tid; r < nr; r += GS_THREADS) {
       double dot = 0.0;
-      for (int q = 0; q < g; ++q) dot += slot[r * g + q];
+      for (int q = 0; q < ns; ++q) dot += slot[r * ns + q];
       const size_t i = (size_t)r0 + r;
       if (ub) {
         const double gv = (xown[r] - Dt * dot + Dt * am * k1[r]) / k2[r];
@@ -876,11 +903,12 @@ __global__ void __launch_bounds__(GS_THREADS) k_g_sweep(GSArgs a) {
         a.Gu[(size_t)n * d1 + i] = gv;
         xown[r] = v;
       } else {
-        const double gv = k1[r] * xs[i] + dot + Dt * am * k2[r];
+        const double gv = k1[r] * xown[r] + dot + Dt * am * k2[r];
         double v = a.first ? gv : gv + pF[r] - pG[r];
         if (has_c) v += pC[r];
         a.Xw[(size_t)(n + 1) * d2 + i] = v;
         a.Gw[(size_t)n * d2 + i] = gv;
+        xown[r] = v;
       }
     }
     if (n + 1 == a.n_hi) break;  // the kernel's end orders the last step's writes
@@ -902,9 +930,11 @@ static std::atomic<int> g_sweep_smem{GS_SMEM_MAX};
 int sweep_smem() { return g_sweep_smem.load(); }
 void set_sweep_smem(int bytes) { g_sweep_smem.store(bytes < 0 ? GS_SMEM_MAX : bytes); }
 
-// one coarse sweep n = n_lo..N-1 (first: x_{n+1} = G(x_n) (+ c_{n+1}))
-static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, const double* Fu, const double* Fw,
-                    const double* Cu, const double* Cw, int n_lo, bool first) {
+// one coarse sweep n = n_lo..N-1 (first: x_{n+1} = G(x_n) (+ c_{n+1})) with
+// the coupling rows CA, GW in MT
+template <typename MT>
+static void g_sweep_t(Ctx* c, Hot& H, const MT* CA, const MT* GW, double* Xu, double* Xw, const double* amp,
+                      const double* Fu, const double* Fw, const double* Cu, const double* Cw, int n_lo, bool first) {
   static int num_sms = 0;
   {
     std::lock_guard<std::mutex> lock(lazy_init_mutex());
@@ -912,8 +942,10 @@ static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, c
       int dev = 0, sms = 0;
       PINT_CUDA(cudaGetDevice(&dev));
       PINT_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-      PINT_CUDA(cudaFuncSetAttribute(k_g_sweep<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GS_SMEM_CAP));
-      PINT_CUDA(cudaFuncSetAttribute(k_g_sweep<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)GS_SMEM_CAP));
+      PINT_CUDA(cudaFuncSetAttribute(k_g_sweep<MT, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)GS_SMEM_CAP));
+      PINT_CUDA(cudaFuncSetAttribute(k_g_sweep<MT, false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)GS_SMEM_CAP));
       num_sms = sms;  // set last: a failed attempt is retried by the next call
     }
   }
@@ -922,10 +954,9 @@ static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, c
     PINT_CUDA(cudaMemsetAsync(H.gsync, 0, 64, c->stream));
   }
   const int d1 = c->d1, d2 = c->d2;
-  GSArgs a;
-  a.CA = c->CA;
-  a.GE = c->GE;
-  a.GCD = c->GCD;
+  GSArgs<MT> a;
+  a.CA = CA;
+  a.GW = GW;
   a.lam1 = c->lam1;
   a.lam2 = c->lam2;
   a.b1 = H.b1;
@@ -967,10 +998,26 @@ static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, c
       }
     }
   }
-  const bool resident = gs_layout(d1, d2, a.ru, a.rw, true).n * 8 <= (size_t)std::min<int>(sweep_smem(), GS_SMEM_CAP);
-  const size_t smem = gs_layout(d1, d2, a.ru, a.rw, resident).n * 8;
+  // rows split into as many pieces (one warp task each) as fit the warps of a
+  // block once (a second round of tasks would lengthen every step), and into
+  // pieces of at most GS_PIECE entries when streamed
+  auto pieces = [&](int rows, int len, bool stream) {
+    int ns = rows >= GS_WARPS ? 1 : GS_WARPS / std::max(rows, 1);
+    if (stream) ns = std::max(ns, (len + GS_PIECE - 1) / GS_PIECE);
+    return std::max(1, std::min(ns, len));
+  };
+  const int msz = (int)sizeof(MT);
+  a.nsu = pieces(a.ru, d2, false);
+  a.nsw = pieces(a.rw, d1 + d2, false);
+  const bool resident = gs_layout(d1, d2, a.ru, a.rw, a.nsu, a.nsw, msz, true).n <=
+                        (size_t)std::min<int>(sweep_smem(), (int)GS_SMEM_CAP);
+  if (!resident) {
+    a.nsu = pieces(a.ru, d2, true);
+    a.nsw = pieces(a.rw, d1 + d2, true);
+  }
+  const size_t smem = gs_layout(d1, d2, a.ru, a.rw, a.nsu, a.nsw, msz, resident).n;
   PINT_REQUIRE(smem <= GS_SMEM_CAP, PINT_ERR_CUDA, "coarse sweep: state does not fit in shared memory");
-  const void* fn = resident ? (const void*)k_g_sweep<true> : (const void*)k_g_sweep<false>;
+  const void* fn = resident ? (const void*)k_g_sweep<MT, true> : (const void*)k_g_sweep<MT, false>;
   int bps = 0;
   PINT_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bps, fn, GS_THREADS, smem));
   PINT_REQUIRE(bps >= 1, PINT_ERR_CUDA, "coarse sweep kernel cannot be resident");
@@ -978,6 +1025,12 @@ static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, c
   void* args[] = {&a};
   PINT_CUDA(cudaLaunchCooperativeKernel(fn, dim3(blocks), dim3(GS_THREADS), args, smem, c->stream));
   c->launches++;
+}
+
+// the FP64 sweep
+static void g_sweep(Ctx* c, Hot& H, double* Xu, double* Xw, const double* amp, const double* Fu, const double* Fw,
+                    const double* Cu, const double* Cw, int n_lo, bool first) {
+  g_sweep_t<double>(c, H, c->CA, c->GW, Xu, Xw, amp, Fu, Fw, Cu, Cw, n_lo, first);
 }
 
 static void g_sweep_check(Ctx* c, Hot& H) {
@@ -1626,7 +1679,8 @@ struct Mx {
   std::map<std::array<uintptr_t, 9>, std::pair<cudaGraphExec_t, int>> graphs;
   unsigned graph_epoch = 0;
   bool graphs_off = false;  // capture failed once: issue the iterations directly
-  float* CA32 = nullptr;  // FP32 coupling of the cluster coarse sweep
+  float* CA32 = nullptr;  // FP32 coupling of the low-precision coarse sweeps (cluster or grid-wide)
+  float* GW32 = nullptr;  // FP32 w rows of the folded coarse step (grid-wide low-precision sweep)
   // FP32 copies for the cluster coarse sweep: F ends, old G values, jumps
   float *Fu32 = nullptr, *Fw32 = nullptr, *Gu32 = nullptr, *Gw32 = nullptr, *Cu32 = nullptr, *Cw32 = nullptr;
   // double-float pairs of AR, AS and of the FP64 trajectory (refinement residual)
@@ -1683,8 +1737,9 @@ static Mx& mx_prepare(Ctx* c) {
   M.AR32 = Fa((size_t)d1 * 2 * ldw);
   M.AS32 = Fa((size_t)d2 * 2 * ldu);
   M.gcl = gc_cluster_size(d1, d2);
+  M.CA32 = Fa((size_t)d1 * d2);
+  if (!M.gcl) M.GW32 = Fa((size_t)d2 * (d2 + d1));  // the grid-wide FP32 sweep instead of the cluster
   if (M.gcl) {
-    M.CA32 = Fa((size_t)d1 * d2);
     M.Fu32 = Fa((size_t)N * d1);
     M.Fw32 = Fa((size_t)N * d2);
     M.Gu32 = Fa((size_t)N * d1);
@@ -1780,6 +1835,7 @@ static void mx_refresh(Ctx* c, Mx& M) {
   mx_ar_diff(c, M.ldw, M.AR32, M.Rhi, M.Rlo);  // [-CA | -CM/dt] against [w_p ; w_p - w_{p-1}]
   mx_pad_split(c, c->AS, d2, d1, M.ldu, M.AS32, M.Shi, M.Slo);
   if (M.CA32) mx_to_f32(c, c->CA, (long long)d1 * d2, M.CA32);
+  if (M.GW32) mx_to_f32(c, c->GW, (long long)d2 * (d2 + d1), M.GW32);
   mx_split_df(c, c->AR, (long long)d1 * 2 * d2, M.ARh, M.ARl);
   mx_split_df(c, c->AS, (long long)d2 * 2 * d1, M.ASh, M.ASl);
   mx_to_f32(c, c->lam1, d1, M.lam1f);
@@ -2000,15 +2056,20 @@ struct LpRun {
   double last_jump = 0;
 };
 
-// coarse sweep of the low-precision path: FP32 couplings on one cluster when
-// they fit in its shared memory (and g64 is not asked), else the grid-wide
-// FP64 sweep (FP64 diagonal V_H1 solve, FP64 couplings and update)
-// (the grid-wide sweep's barrier error flag is read with the parareal jump at
-// the end of the iteration, lp_checks)
+// coarse sweep of the low-precision path: g64 (the correction solve): the
+// grid-wide FP64 sweep; otherwise FP32 couplings on one cluster when they fit
+// in its shared memory, else the grid-wide sweep with FP32 couplings (FP64
+// states, diagonal solve and update either way).  The grid-wide sweep's
+// barrier error flag is read with the parareal jump at the end of the
+// iteration (lp_checks).
 static void g_sweep_lp(Ctx* c, Hot& H, Mx& M, double* Xu, double* Xw, const double* amp, const double* Fu,
                        const double* Fw, const double* Cu, const double* Cw, int n_lo, bool first, bool g64) {
-  if (!M.gcl || g64) {
+  if (g64) {
     g_sweep(c, H, Xu, Xw, amp, Fu, Fw, Cu, Cw, n_lo, first);
+    return;
+  }
+  if (!M.gcl) {
+    g_sweep_t<float>(c, H, M.CA32, M.GW32, Xu, Xw, amp, Fu, Fw, Cu, Cw, n_lo, first);
     return;
   }
   GcArgs a;
