@@ -183,6 +183,16 @@ def workload_desc(prob):
             f"ell={prob.ell}, N={prob.N} x P={prob.P}")
 
 
+def mixed_dtype(args):
+    """Arithmetic of the timed solve: the fine propagator's products and the
+    rest of the low-precision solve, then what runs in FP64 or double-float."""
+    if args.precision == "fp64":
+        return "f64"
+    lo = "tf32x3/f32" if args.precision == "mixed" else "f32"
+    ref = "f64" if getattr(args, "refine_fp64", False) else "double-float (f32 pairs)"
+    return f"{lo}; f64 jumps, states and correction coarse step; {ref} refinement residual"
+
+
 def problem(name):
     from paper_2411_09244_gb300 import inputs
     return {"c1": inputs.config_c1, "c2": inputs.config_c2, "c5": inputs.config_c5}[name]()
@@ -389,7 +399,7 @@ def run_ours(args, rank, world):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": t_step * 1e3, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None,
-        "dtype": {"fp64": "f64", "mixed": "tf32x3/f32 + f64 refinement", "mixed_f32": "f32 + f64 refinement"}[args.precision],
+        "dtype": mixed_dtype(args),
         "data": "synthetic (seeded splitmix64 high-contrast channels/inclusions; paper fields unavailable)",
         "config": {"workload": workload_desc(prob), "T": p.T,
                    "d1": info["d1"], "d2": info["d2"], "gamma": info["gamma"],
@@ -619,8 +629,7 @@ def run_batch(args, rank, world):
     return {"metric": METRIC, "value": world * work / t_conc, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": t_conc * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"fp64": "f64", "mixed": "tf32x3/f32 + f64 refinement",
-                      "mixed_f32": "f32 + f64 refinement"}[args.precision],
+            "dtype": mixed_dtype(args),
             "data": "synthetic (seeded splitmix64 high-contrast fields, many-instance recipe)",
             "config": {"workload": f"many-instance batch: {args.batch} instances per GPU, fine grids from {sizes}, "
                                    f"8-cell blocks, J 2-4, contrast 10^U(3,6), N in (16,32,64), P=32, ell=2",
