@@ -76,7 +76,8 @@ enum {
   PINT_COARSE_FP64 = 8,
   PINT_REFINE_FP64 = 16,
   PINT_CARRY_LAGS = 32,
-  PINT_ADJOINT_RESPONSE = 64
+  PINT_ADJOINT_RESPONSE = 64,
+  PINT_COARSE_GRID = 128
 };
 
 typedef struct {
@@ -156,15 +157,22 @@ pint_status pint_build_multiscale_spaces(pint_ctx* ctx, int nc, int J, int ell,
  *   precision        PINT_FP64 or PINT_MIXED
  *   flags            PINT_ALLOW_UNSTABLE: do not reject a Delta t above
  *                    dt_max (Section 3.2 condition);
- *                    PINT_FINE_SEQUENTIAL: on the FP64 path, the fine
- *                    propagator of Algorithm 1 is the fine scheme stepped
- *                    P times on all active intervals at once instead of the
- *                    WR all-at-once solve (same fixed point; a comparison
- *                    mode without the paper's counterpart);
+ *                    PINT_FINE_SEQUENTIAL (PINT_FP64 only; BAD_ARG with
+ *                    the mixed paths): the fine propagator of Algorithm 1
+ *                    is the fine scheme stepped P times on all active
+ *                    intervals at once instead of the WR all-at-once solve
+ *                    (same fixed point; a comparison mode without the
+ *                    paper's counterpart);
  *                    PINT_COARSE_FP64: on the mixed paths, the first
  *                    (low-precision) solve's coarse sweeps run in FP64 too
- *                    (by default they run in FP32 on one thread-block
- *                    cluster; the correction solve's are always FP64);
+ *                    (by default they run with FP32 couplings on one
+ *                    thread-block cluster, or grid-wide where no cluster
+ *                    holds the coupling; the correction solve's are always
+ *                    FP64);
+ *                    PINT_COARSE_GRID: on the mixed paths, the first
+ *                    solve's coarse sweeps run grid-wide with FP32
+ *                    couplings even where a cluster holds the coupling (the
+ *                    form otherwise used only for large couplings);
  *                    PINT_REFINE_FP64: on the mixed paths, the refinement
  *                    residual's two contractions run in FP64 (by default
  *                    in double-float arithmetic, about 48 bits, on the FP32

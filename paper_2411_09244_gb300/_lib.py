@@ -23,6 +23,7 @@ PINT_ALLOW_UNSTABLE = 1
 PINT_FINE_SEQUENTIAL = 2
 PINT_AUTOTUNE = 4
 PINT_COARSE_FP64 = 8
+PINT_COARSE_GRID = 128
 PINT_REFINE_FP64 = 16
 PINT_CARRY_LAGS = 32
 PINT_ADJOINT_RESPONSE = 64

@@ -64,7 +64,8 @@ class Pint:
     def assemble_reduced(self, T: float | None, N: int, P: int, alpha: float, precision: int = L.PINT_FP64,
                          allow_unstable: bool = False, fine_sequential: bool = False,
                          autotune: bool = False, coarse_fp64: bool = False, refine_fp64: bool = False,
-                         carry_lags: bool = False, adjoint_response: bool = False) -> dict:
+                         carry_lags: bool = False, adjoint_response: bool = False,
+                         coarse_grid: bool = False) -> dict:
         """T = None (passed as 0) lets the library pick the stable final time
         of Section 3.2; the T used is returned in info["T"].
         fine_sequential: PINT_FINE_SEQUENTIAL (FP64 path comparison mode).
@@ -72,12 +73,13 @@ class Pint:
         coarse_fp64: PINT_COARSE_FP64 (every coarse sweep of the mixed path in FP64).
         refine_fp64: PINT_REFINE_FP64 (refinement residual contractions in FP64).
         carry_lags: PINT_CARRY_LAGS (lag-carrying comparison variant, FP64).
-        adjoint_response: PINT_ADJOINT_RESPONSE (amplitude gradient by <lambda_{n+1}, s>)."""
+        adjoint_response: PINT_ADJOINT_RESPONSE (amplitude gradient by <lambda_{n+1}, s>).
+        coarse_grid: PINT_COARSE_GRID (the first solve's FP32 coarse sweeps grid-wide)."""
         info = L.SpaceInfo()
         flags = ((L.PINT_ALLOW_UNSTABLE if allow_unstable else 0) | (L.PINT_FINE_SEQUENTIAL if fine_sequential else 0)
                  | (L.PINT_AUTOTUNE if autotune else 0) | (L.PINT_COARSE_FP64 if coarse_fp64 else 0)
                  | (L.PINT_REFINE_FP64 if refine_fp64 else 0) | (L.PINT_CARRY_LAGS if carry_lags else 0)
-                 | (L.PINT_ADJOINT_RESPONSE if adjoint_response else 0))
+                 | (L.PINT_ADJOINT_RESPONSE if adjoint_response else 0) | (L.PINT_COARSE_GRID if coarse_grid else 0))
         st = self.lib.pint_assemble_reduced(self.h, 0.0 if T is None else T, N, P, alpha, precision, flags,
                                             C.byref(info))
         L.check(st)

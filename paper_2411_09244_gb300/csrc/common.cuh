@@ -123,6 +123,7 @@ struct Ctx {
   bool fine_seq = false;  // PINT_FINE_SEQUENTIAL
   bool autotune = false;  // PINT_AUTOTUNE: measured contraction tiles
   bool coarse64 = false;  // PINT_COARSE_FP64: every coarse sweep of the mixed path in FP64
+  bool coarse_grid = false;  // PINT_COARSE_GRID: the first solve's FP32 sweeps grid-wide, not on a cluster
   bool refine64 = false;  // PINT_REFINE_FP64: refinement residual contractions in FP64
   bool carry = false;     // PINT_CARRY_LAGS: lag-carrying variant (FP64, sequential fine steps)
   bool adj_response = false;  // PINT_ADJOINT_RESPONSE: amplitude gradient by <lambda_{n+1}, s>

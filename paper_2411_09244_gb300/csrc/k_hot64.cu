@@ -1738,7 +1738,7 @@ static Mx& mx_prepare(Ctx* c) {
   M.AS32 = Fa((size_t)d2 * 2 * ldu);
   M.gcl = gc_cluster_size(d1, d2);
   M.CA32 = Fa((size_t)d1 * d2);
-  if (!M.gcl) M.GW32 = Fa((size_t)d2 * (d2 + d1));  // the grid-wide FP32 sweep instead of the cluster
+  M.GW32 = Fa((size_t)d2 * (d2 + d1));  // the grid-wide FP32 sweep (no cluster, or PINT_COARSE_GRID)
   if (M.gcl) {
     M.Fu32 = Fa((size_t)N * d1);
     M.Fw32 = Fa((size_t)N * d2);
@@ -2068,7 +2068,7 @@ static void g_sweep_lp(Ctx* c, Hot& H, Mx& M, double* Xu, double* Xw, const doub
     g_sweep(c, H, Xu, Xw, amp, Fu, Fw, Cu, Cw, n_lo, first);
     return;
   }
-  if (!M.gcl) {
+  if (!M.gcl || c->coarse_grid) {
     g_sweep_t<float>(c, H, M.CA32, M.GW32, Xu, Xw, amp, Fu, Fw, Cu, Cw, n_lo, first);
     return;
   }

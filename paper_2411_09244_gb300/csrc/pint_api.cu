@@ -280,11 +280,14 @@ pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double 
     c->fine_seq = (flags & PINT_FINE_SEQUENTIAL) != 0;
     c->autotune = (flags & PINT_AUTOTUNE) != 0;
     c->coarse64 = (flags & PINT_COARSE_FP64) != 0;
+    c->coarse_grid = (flags & PINT_COARSE_GRID) != 0;
     c->refine64 = (flags & PINT_REFINE_FP64) != 0;
     c->carry = (flags & PINT_CARRY_LAGS) != 0;
     c->adj_response = (flags & PINT_ADJOINT_RESPONSE) != 0;
     PINT_REQUIRE(!c->carry || precision == PINT_FP64, PINT_ERR_BAD_ARG,
                  "PINT_CARRY_LAGS is an FP64 comparison mode");
+    PINT_REQUIRE(!c->fine_seq || precision == PINT_FP64, PINT_ERR_BAD_ARG,
+                 "PINT_FINE_SEQUENTIAL is an FP64 comparison mode");
     c->Dt = T / N;
     c->dt = c->Dt / P;
     timed_stage(c, 5, [&] { hot_prepare(c); });

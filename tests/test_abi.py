@@ -89,3 +89,16 @@ def test_sweep_smem_control_without_gpu(libpint):
     assert libpint.pint_set_sweep_smem(0) == default
     assert libpint.pint_set_sweep_smem(-1) == 0
     assert libpint.pint_set_sweep_smem(-1) == default
+
+
+def test_flag_and_status_constants_match_the_header():
+    """The binding's enum constants are the header's values."""
+    from paper_2411_09244_gb300 import _lib
+    src = re.sub(r"/\*.*?\*/", "", open(HEADER).read(), flags=re.S)
+    defined = {m.group(1): int(m.group(2)) for m in re.finditer(r"\b(PINT_[A-Z0-9_]+)\s*=\s*(-?\d+)", src)}
+    assert defined
+    for name, value in defined.items():
+        if hasattr(_lib, name):
+            assert getattr(_lib, name) == value, name
+    for name in ("PINT_FP64", "PINT_MIXED", "PINT_COARSE_FP64", "PINT_REFINE_FP64", "PINT_COARSE_GRID"):
+        assert name in defined and hasattr(_lib, name), name

@@ -183,19 +183,25 @@ def test_bad_arguments_return_codes():
         p.build_multiscale_spaces(5, 2, 1)   # 5 does not divide 16
     with pytest.raises(PintError, match="STATE"):
         p.assemble_reduced(1e-3, 4, 8, 0.1)
+    p.build_multiscale_spaces(4, 2, 1)
+    from paper_2411_09244_gb300._lib import PINT_MIXED
+    for bad in (dict(fine_sequential=True), dict(carry_lags=True)):  # FP64 comparison modes only
+        with pytest.raises(PintError, match="BAD_ARG"):
+            p.assemble_reduced(None, 4, 8, 0.1, precision=PINT_MIXED, **bad)
     p.close()
 
 
-@pytest.mark.parametrize("fp64_options", [False, True])
-def test_mixed_path_matches_oracle(pair, fp64_options):
+@pytest.mark.parametrize("options", ["default", "fp64", "grid"])
+def test_mixed_path_matches_oracle(pair, options):
     """Mixed path (FP32 WR + trajectory refinement) vs the FP64 oracle: max
-    over coarse times of the relative L2 error <= 1e-6; fp64_options also
-    runs every coarse sweep and the refinement residual in FP64
-    (PINT_COARSE_FP64 | PINT_REFINE_FP64)."""
+    over coarse times of the relative L2 error <= 1e-6; "fp64" also runs
+    every coarse sweep and the refinement residual in FP64 (PINT_COARSE_FP64
+    | PINT_REFINE_FP64); "grid" runs the first solve's FP32 coarse sweeps on
+    the grid-wide kernel instead of a cluster (PINT_COARSE_GRID)."""
     from paper_2411_09244_gb300._lib import PINT_MIXED, PINT_FP64
     _, prob, orc, p = pair
-    p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=PINT_MIXED, coarse_fp64=fp64_options,
-                       refine_fp64=fp64_options)
+    p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=PINT_MIXED, coarse_fp64=options == "fp64",
+                       refine_fp64=options == "fp64", coarse_grid=options == "grid")
     try:
         coarse, fine, st = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-11, wr_tol=1e-14, wr_max=400)
     finally:
