@@ -191,20 +191,25 @@ def test_bad_arguments_return_codes():
     p.close()
 
 
-@pytest.mark.parametrize("options", ["default", "fp64", "grid"])
+@pytest.mark.parametrize("options", ["default", "fp64", "grid", "grid_stream"])
 def test_mixed_path_matches_oracle(pair, options):
     """Mixed path (FP32 WR + trajectory refinement) vs the FP64 oracle: max
     over coarse times of the relative L2 error <= 1e-6; "fp64" also runs
     every coarse sweep and the refinement residual in FP64 (PINT_COARSE_FP64
     | PINT_REFINE_FP64); "grid" runs the first solve's FP32 coarse sweeps on
-    the grid-wide kernel instead of a cluster (PINT_COARSE_GRID)."""
+    the grid-wide kernel instead of a cluster (PINT_COARSE_GRID);
+    "grid_stream" also streams every grid-wide sweep's coupling rows from
+    global memory (pint_set_sweep_smem(0)), the form large couplings take."""
     from paper_2411_09244_gb300._lib import PINT_MIXED, PINT_FP64
     _, prob, orc, p = pair
     p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=PINT_MIXED, coarse_fp64=options == "fp64",
-                       refine_fp64=options == "fp64", coarse_grid=options == "grid")
+                       refine_fp64=options == "fp64", coarse_grid=options.startswith("grid"))
+    if options == "grid_stream":
+        p.lib.pint_set_sweep_smem(0)
     try:
         coarse, fine, st = p.parareal_solve(prob.u0, prob.f, prob.amp, eps=1e-11, wr_tol=1e-14, wr_max=400)
     finally:
+        p.lib.pint_set_sweep_smem(-1)
         p.assemble_reduced(orc.T, prob.N, prob.P, prob.alpha, precision=PINT_FP64)
     u, w = orc.sequential()
     ref = orc.fine_field(u, w)[1:]
