@@ -377,28 +377,32 @@ __global__ void k_step_w(const double* __restrict__ CMt, const double* __restric
 // ||du_n||^2 + ||dw_n||^2 + 2 du_n^T CM dw_n.  Coarse times n <= n_first are not
 // launched: in sweep k the states up to n = k - 1 do not change, so their
 // jumps are exactly zero.
-// One read of the coupling per launch: CTA (row tile,
-// group of JT_G coarse times) forms (CM dw_n)_i for its JT_R rows and JT_G
-// times at once, reading CM^T (d2 x d1) coalesced along the rows and reusing
-// each element for the JT_G times; dw_n is staged in shared memory in chunks
-// of JT_J columns.  Its partial sums of du_n^2 + 2 du_n (CM dw_n) over its rows,
-// plus ||dw_n||^2 from the first row tile, go to jump2[n-1] (zeroed by the
+// One read of the coupling per launch: CTA (row tile, group of JT_G coarse
+// times, column slice) forms the slice's part of (CM dw_n)_i for its JT_R rows
+// and JT_G times at once, reading CM^T (d2 x d1) coalesced along the rows and
+// reusing each element for the JT_G times; dw_n is staged in shared memory in
+// chunks of JT_J columns.  The column slices (blockIdx.z, jc columns each)
+// give the launch enough warps to hide the coupling's loads; the cross term
+// is a sum over columns, so each slice's part of du_n^2 + 2 du_n (CM dw_n)
+// over its rows (du_n^2 from the first slice, ||dw_n||^2 over the slice's
+// columns from the first row tile) is added to jump2[n-1] (zeroed by the
 // caller).  FP64 throughout.
 constexpr int JT_R = 128, JT_G = 4, JT_J = 512;
 __global__ void __launch_bounds__(JT_R) k_jump_tiled(const double* __restrict__ Xu, const double* __restrict__ Xw,
                                                      const double* __restrict__ Ou, const double* __restrict__ Ow,
                                                      const double* __restrict__ CMt, int d1, int d2, int n_first,
-                                                     int N, double* __restrict__ jump2) {
+                                                     int N, int jc, double* __restrict__ jump2) {
   __shared__ double sdw[JT_G][JT_J];
   __shared__ double sh[64];
   const int i = blockIdx.x * JT_R + threadIdx.x;
   const int n0 = n_first + 1 + blockIdx.y * JT_G;  // first coarse time of the group
   const int ng = min(JT_G, N + 1 - n0);
+  const int jb = blockIdx.z * jc, je = min(d2, jb + jc);  // this CTA's columns
   double acc[JT_G], w2[JT_G];
 #pragma unroll
   for (int g = 0; g < JT_G; ++g) acc[g] = w2[g] = 0.0;
-  for (int j0 = 0; j0 < d2; j0 += JT_J) {
-    const int nj = min(JT_J, d2 - j0);
+  for (int j0 = jb; j0 < je; j0 += JT_J) {
+    const int nj = min(JT_J, je - j0);
     __syncthreads();
     for (int e = threadIdx.x; e < JT_G * JT_J; e += JT_R) {
       const int g = e / JT_J, j = e % JT_J;
@@ -427,7 +431,7 @@ __global__ void __launch_bounds__(JT_R) k_jump_tiled(const double* __restrict__ 
     double v = w2[g];
     if (i < d1 && g < ng) {
       const double du = Xu[(size_t)(n0 + g) * d1 + i] - Ou[(size_t)(n0 + g) * d1 + i];
-      v += du * du + 2.0 * du * acc[g];
+      v += (blockIdx.z == 0 ? du * du : 0.0) + 2.0 * du * acc[g];
     }
     v = pintd::block_sum(v, sh);
     if (threadIdx.x == 0 && g < ng) atomicAdd(&jump2[n0 + g - 1], v);
@@ -438,8 +442,22 @@ static void jumps_fp64(Ctx* c, const double* Xu, const double* Xw, const double*
                        double* jump2) {
   const int N = c->N, nt = N - n_first;
   if (nt <= 0) return;
-  k_jump_tiled<<<dim3(nb_(c->d1, JT_R), nb_(nt, JT_G)), JT_R, 0, c->stream>>>(Xu, Xw, Ou, Ow, c->CMt, c->d1, c->d2,
-                                                                              n_first, N, jump2);
+  // column slices: about eight CTAs per SM in all, at least 32 columns each
+  static int sms = 0;
+  {
+    std::lock_guard<std::mutex> lock(lazy_init_mutex());
+    if (!sms) {
+      int dev = 0, n = 0;
+      PINT_CUDA(cudaGetDevice(&dev));
+      PINT_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+      sms = std::max(n, 1);
+    }
+  }
+  const int bx = nb_(c->d1, JT_R), by = nb_(nt, JT_G);
+  const int nz = std::max(1, std::min((8 * sms + bx * by - 1) / (bx * by), (c->d2 + 31) / 32));
+  const int jc = (c->d2 + nz - 1) / nz;
+  k_jump_tiled<<<dim3(bx, by, nb_(c->d2, jc)), JT_R, 0, c->stream>>>(Xu, Xw, Ou, Ow, c->CMt, c->d1, c->d2, n_first,
+                                                                      N, jc, jump2);
   PINT_LAUNCH_CHECK();
 }
 
