@@ -205,7 +205,10 @@ pint_status pint_build_multiscale_spaces(pint_ctx* ctx, int nc, int J, int ell,
  * Errors: BAD_ARG (also a non-finite T, or T <= 0 when no stable T exists),
  * STATE, UNSTABLE_DT (Delta t > dt_max without the flag; info is still
  * filled), SINGULAR, OOM, CUDA.  Every call replaces the time grid; work
- * cached for the previous one (captured WR iterations) is discarded.
+ * cached for the previous one (captured WR iterations, the low-precision
+ * operator copies) is discarded.  A call that fails with BAD_ARG, SINGULAR,
+ * OOM or CUDA after its argument checks leaves no time grid: solves return
+ * STATE until an assembly succeeds (UNSTABLE_DT keeps the new grid).
  */
 pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double alpha,
                                   int precision, int flags, pint_space_info* info);

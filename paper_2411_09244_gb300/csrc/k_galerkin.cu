@@ -109,7 +109,9 @@ __global__ void __launch_bounds__(256) k_pair(const GWin* __restrict__ gw, const
   }
 }
 
-// out[v][raw] = sum_nodes psi_raw(node) vec_v(node)
+// out[v][raw] = sum_nodes psi_raw(node) vec_v(node).  Vectors go two at a
+// time through one read of the basis function (the bases are the largest
+// array read); each vector's sum keeps the same order either way.
 __global__ void k_raw_dot(const GWin* __restrict__ gw, int n_f, const double* __restrict__ psi,
                           const double* __restrict__ vec, int count, int n_raw,
                           double* __restrict__ out) {
@@ -118,14 +120,23 @@ __global__ void k_raw_dot(const GWin* __restrict__ gw, int n_f, const double* __
   if (q >= W.kt) return;
   const int nn = (n_f + 1) * (n_f + 1);
   __shared__ double sh[64];
-  for (int v = 0; v < count; ++v) {
-    double acc = 0.0;
+  for (int v = 0; v < count; v += 2) {
+    const bool two = v + 1 < count;
+    const double* x0 = vec + (size_t)v * nn;
+    const double* x1 = two ? x0 + nn : x0;
+    double a0 = 0.0, a1 = 0.0;
     for (int l = threadIdx.x; l < W.nw; l += blockDim.x) {
-      int gx = W.X0 + l % W.wx, gy = W.Y0 + l / W.wx;
-      acc += psi[W.psi_off + (size_t)q * W.nw + l] * vec[(size_t)v * nn + gy * (n_f + 1) + gx];
+      const int gx = W.X0 + l % W.wx, gy = W.Y0 + l / W.wx, node = gy * (n_f + 1) + gx;
+      const double p = psi[W.psi_off + (size_t)q * W.nw + l];
+      a0 += p * x0[node];
+      if (two) a1 += p * x1[node];
     }
-    acc = pintd::block_sum(acc, sh);
-    if (threadIdx.x == 0) out[(size_t)v * n_raw + W.raw0 + q] = acc;
+    a0 = pintd::block_sum(a0, sh);
+    if (threadIdx.x == 0) out[(size_t)v * n_raw + W.raw0 + q] = a0;
+    if (two) {
+      a1 = pintd::block_sum(a1, sh);
+      if (threadIdx.x == 0) out[(size_t)(v + 1) * n_raw + W.raw0 + q] = a1;
+    }
   }
 }
 

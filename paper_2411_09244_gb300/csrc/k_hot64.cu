@@ -642,15 +642,24 @@ void hot_prepare(Ctx* c) {
 }
 
 // spectral load vectors of the source shape: b~1 = Q^T Psi1^T M f, b~2 = Q2^T Psi2^T M f
-static void spectral_load(Ctx* c, Hot& H, const double* f_nodes) {
+// With u0_nodes, the initial state's load vectors go through the same pass
+// over the bases (into Ou, Ow, spectral coordinates, before the projection
+// solve).
+static void spectral_load(Ctx* c, Hot& H, const double* f_nodes, const double* u0_nodes = nullptr) {
+  const int d1 = c->d1, d2 = c->d2, count = u0_nodes ? 2 : 1;
   apply_stencil(c, c->stM, f_nodes, H.nodes, 1);
-  raw_dot(c, H.nodes, 1, H.raw);
-  to_reduced(c, H.raw, 1, H.tmp1, H.tmp2);
-  dense_gemm(c, c->Q, H.tmp1, H.b1, c->d1, 1, c->d1, true, false, 1.0, 0.0);
-  dense_gemm(c, c->Q2, H.tmp2, H.b2, c->d2, 1, c->d2, true, false, 1.0, 0.0);
-  if (!H.qb) H.qb = (double*)dalloc(c, (size_t)c->d2 * 8);
-  dense_gemm(c, c->GCD, H.b1, H.qb, c->d2, 1, c->d1, false, false, 1.0, 0.0);
+  if (u0_nodes) apply_stencil(c, c->stM, u0_nodes, H.nodes + c->nn, 1);
+  raw_dot(c, H.nodes, count, H.raw);
+  to_reduced(c, H.raw, count, H.tmp1, H.tmp2);  // [count][d1], [count][d2]
+  dense_gemm(c, c->Q, H.tmp1, H.b1, d1, 1, d1, true, false, 1.0, 0.0);
+  dense_gemm(c, c->Q2, H.tmp2, H.b2, d2, 1, d2, true, false, 1.0, 0.0);
+  if (!H.qb) H.qb = (double*)dalloc(c, (size_t)d2 * 8);
+  dense_gemm(c, c->GCD, H.b1, H.qb, d2, 1, d1, false, false, 1.0, 0.0);
   c->launches += 3;
+  if (u0_nodes) {
+    dense_gemm(c, c->Q, H.tmp1 + d1, H.Ou, d1, 1, d1, true, false, 1.0, 0.0);
+    dense_gemm(c, c->Q2, H.tmp2 + d2, H.Ow, d2, 1, d2, true, false, 1.0, 0.0);
+  }
 }
 
 // original coordinates -> spectral: u~ = Q^T M11 u, w~ = Q2^T M22 w (count vectors)
@@ -1147,7 +1156,7 @@ static void stage_amp(Ctx* c, Hot& H, const double* amp_dev, int count) {
     k_fill<<<nb_(count, 256), 256, 0, c->stream>>>(H.amp, count, 1.0);
 }
 
-static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw);
+static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw, bool sweep_flag = false);
 
 // initial value (eq. (2.2)): L2 projection onto V_H through the joint Gram
 // matrix, in spectral coordinates, into H.Xu[0], H.Xw[0]
@@ -1697,6 +1706,10 @@ struct Mx {
   std::map<std::array<uintptr_t, 9>, std::pair<cudaGraphExec_t, int>> graphs;
   unsigned graph_epoch = 0;
   bool graphs_off = false;  // capture failed once: issue the iterations directly
+  // the context's graph_epoch when the FP32 / double-float operator copies
+  // were last made (every re-assembly or reallocation bumps it)
+  unsigned refresh_epoch = 0;
+  bool refreshed = false;
   float* CA32 = nullptr;  // FP32 coupling of the low-precision coarse sweeps (cluster or grid-wide)
   float* GW32 = nullptr;  // FP32 w rows of the folded coarse step (grid-wide low-precision sweep)
   // FP32 copies for the cluster coarse sweep: F ends, old G values, jumps
@@ -1837,8 +1850,12 @@ static Mx& mx_prepare(Ctx* c) {
   return M;
 }
 
-// FP32 copies of the time-grid dependent operators (refreshed every solve)
+// FP32 and double-float copies of the time-grid dependent operators.  Only
+// a re-assembly (or a reallocation of these buffers) changes what they are
+// made from, and both bump the context's graph_epoch: solves in between
+// reuse them.
 static void mx_refresh(Ctx* c, Mx& M) {
+  if (M.refreshed && M.refresh_epoch == c->graph_epoch) return;
   const int d1 = c->d1, d2 = c->d2;
   if (M.psi_src != c->psi) {  // bases rebuilt (or first solve): split them again
     if (!M.psih) {
@@ -1879,6 +1896,8 @@ static void mx_refresh(Ctx* c, Mx& M) {
     PINT_CUDA(cudaMemcpyAsync(M.dshbr, hb.data(), 64 * sizeof(float2), cudaMemcpyHostToDevice, c->stream));
     PINT_CUDA(cudaStreamSynchronize(c->stream));
   }
+  M.refresh_epoch = c->graph_epoch;
+  M.refreshed = true;
 }
 
 // Low-precision iterations stop at their precision floor: FP32 trajectories
@@ -2217,8 +2236,9 @@ static void parareal_lp(Ctx* c, Hot& H, Mx& M, LpRun& r, float* f_ms, int* wr_hi
   if (r.K1 == N) r.converged = true;
 }
 
-// max_n ||x_n||_{M_H} (n = 0..N) into *out (host)
-static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw) {
+// max_n ||x_n||_{M_H} (n = 0..N) into *out (host).  sweep_flag: the coarse
+// sweep just issued has its bounded-wait flag read in the same host sync.
+static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw, bool sweep_flag) {
   const int N = c->N, d1 = c->d1, d2 = c->d2;
   PINT_CUDA(cudaMemsetAsync(H.tmp1, 0, (size_t)(N + 1) * std::max(d1, d2) * 8, c->stream));
   // k_jump measures rows 1..N against the zero rows of tmp1 (the scale of
@@ -2228,8 +2248,12 @@ static double state_scale(Ctx* c, Hot& H, const double* Xu, const double* Xw) {
   k_max_fin<<<1, 256, 0, c->stream>>>(H.red + 8, N, H.red);
   PINT_LAUNCH_CHECK();
   double h[2];
+  int herr[2] = {0, 0};
   PINT_CUDA(cudaMemcpyAsync(h, H.red, 16, cudaMemcpyDeviceToHost, c->stream));
+  if (sweep_flag && H.gsync)
+    PINT_CUDA(cudaMemcpyAsync(&herr[1], H.gsync + 2, 4, cudaMemcpyDeviceToHost, c->stream));
   PINT_CUDA(cudaStreamSynchronize(c->stream));
+  if (sweep_flag) lp_checks(c, H, herr);
   return h[0];
 }
 
@@ -2280,15 +2304,10 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
   H.hot_launches = 0;
   PINT_CUDA(cudaEventRecord(e0, c->stream));
   stage_amp(c, H, amp_dev, N);
-  spectral_load(c, H, f_nodes);
+  spectral_load(c, H, f_nodes, u0_nodes);  // f and u0 in one pass over the bases
   mx_to_f32(c, H.b1, d1, M.b1f);
   mx_to_f32(c, H.b2, d2, M.b2f);
-  // initial projection (as in solve_fp64)
-  apply_stencil(c, c->stM, u0_nodes, H.nodes, 1);
-  raw_dot(c, H.nodes, 1, H.raw);
-  to_reduced(c, H.raw, 1, H.tmp1, H.tmp2);
-  dense_gemm(c, c->Q, H.tmp1, H.Ou, d1, 1, d1, true, false, 1.0, 0.0);
-  dense_gemm(c, c->Q2, H.tmp2, H.Ow, d2, 1, d2, true, false, 1.0, 0.0);
+  // initial projection (as in solve_fp64) from the u0 loads in Ou, Ow
   k_proj_rhs<<<nb_((long long)d2 * 32, 256), 256, 0, c->stream>>>(c->CMt, H.Ou, H.Ow, d1, d2, H.tmp2);
   dense_gemm(c, c->projInv, H.tmp2, H.Xw, d2, 1, d2, false, false, 1.0, 0.0);
   k_proj_u<<<nb_((long long)d1 * 32, 256), 256, 0, c->stream>>>(c->CM, H.Ou, H.Xw, d1, d2, H.Xu);
@@ -2311,11 +2330,10 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
   m.wr_tol = wr_tol;
   m.g64 = c->coarse64;  // PINT_COARSE_FP64: the main solve's coarse sweep in FP64 too
   {
-    // G sweep first to get the state scale for the relative tolerances
-    LpRun probe = m;
-    probe.k_max = 0;
-    parareal_lp(c, H, M, probe, &f_ms, nullptr, nullptr, 0);
-    double sc = state_scale(c, H, H.Xu, H.Xw);
+    // G sweep first to get the state scale for the relative tolerances (its
+    // bounded-wait flag read in the same host sync as the scale)
+    g_sweep_lp(c, H, M, m.Xu, m.Xw, m.amp, nullptr, nullptr, m.Cu, m.Cw, 0, true, m.g64);
+    double sc = state_scale(c, H, H.Xu, H.Xw, true);
     if (eps < 0) eps = -eps * sc;  // relative tolerances
     if (wr_tol < 0) wr_tol = -wr_tol * sc;
     // the refinement corrects what the low-precision solve leaves: loose tolerances
@@ -2377,10 +2395,8 @@ void solve_mixed(Ctx* c, const double* u0_nodes, const double* f_nodes, const do
     PINT_CUDA(cudaMemsetAsync(M.Yu, 0, (size_t)d1 * 8, c->stream));
     PINT_CUDA(cudaMemsetAsync(M.Yw, 0, (size_t)d2 * 8, c->stream));
     {
-      LpRun probe = y;
-      probe.k_max = 0;
-      parareal_lp(c, H, M, probe, &f_ms, nullptr, nullptr, 0);
-      double sc = state_scale(c, H, M.Yu, M.Yw);
+      g_sweep_lp(c, H, M, y.Xu, y.Xw, y.amp, nullptr, nullptr, y.Cu, y.Cw, 0, true, y.g64);
+      double sc = state_scale(c, H, M.Yu, M.Yw, true);
       y.eps = eps;  // the jumps stop at eps or at the precision floor
       // WR to 1e-6 of the correction's scale, but no tighter than a tenth of
       // the jump tolerance the correction solve stops at

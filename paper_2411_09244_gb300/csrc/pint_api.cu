@@ -258,6 +258,16 @@ pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double 
     PINT_REQUIRE(alpha > 0 && alpha < 1, PINT_ERR_BAD_ARG, "alpha must be in (0, 1)");
     PINT_REQUIRE(precision == PINT_FP64 || precision == PINT_MIXED || precision == PINT_MIXED_F32,
                  PINT_ERR_BAD_ARG, "unknown precision");
+    PINT_REQUIRE(!(flags & PINT_CARRY_LAGS) || precision == PINT_FP64, PINT_ERR_BAD_ARG,
+                 "PINT_CARRY_LAGS is an FP64 comparison mode");
+    PINT_REQUIRE(!(flags & PINT_FINE_SEQUENTIAL) || precision == PINT_FP64, PINT_ERR_BAD_ARG,
+                 "PINT_FINE_SEQUENTIAL is an FP64 comparison mode");
+    // from here on the context's operators and time grid change: until this
+    // call succeeds there is no time grid to solve on, and nothing derived
+    // from the previous one (captured graphs, low-precision operator copies)
+    // is reused
+    c->have_time = false;
+    c->graph_epoch++;
     cudaEvent_t e0, e1;
     PINT_CUDA(cudaEventCreate(&e0));
     PINT_CUDA(cudaEventCreate(&e1));
@@ -284,10 +294,6 @@ pint_status pint_assemble_reduced(pint_ctx* ctx, double T, int N, int P, double 
     c->refine64 = (flags & PINT_REFINE_FP64) != 0;
     c->carry = (flags & PINT_CARRY_LAGS) != 0;
     c->adj_response = (flags & PINT_ADJOINT_RESPONSE) != 0;
-    PINT_REQUIRE(!c->carry || precision == PINT_FP64, PINT_ERR_BAD_ARG,
-                 "PINT_CARRY_LAGS is an FP64 comparison mode");
-    PINT_REQUIRE(!c->fine_seq || precision == PINT_FP64, PINT_ERR_BAD_ARG,
-                 "PINT_FINE_SEQUENTIAL is an FP64 comparison mode");
     c->Dt = T / N;
     c->dt = c->Dt / P;
     timed_stage(c, 5, [&] { hot_prepare(c); });

@@ -185,9 +185,16 @@ def test_bad_arguments_return_codes():
         p.assemble_reduced(1e-3, 4, 8, 0.1)
     p.build_multiscale_spaces(4, 2, 1)
     from paper_2411_09244_gb300._lib import PINT_MIXED
+    p.assemble_reduced(None, 4, 8, 0.1)
+    nn = 17 * 17
+    ref, _, _ = p.parareal_solve(np.zeros(nn), np.ones(nn), eps=1e-10, want_fine=False)
     for bad in (dict(fine_sequential=True), dict(carry_lags=True)):  # FP64 comparison modes only
         with pytest.raises(PintError, match="BAD_ARG"):
             p.assemble_reduced(None, 4, 8, 0.1, precision=PINT_MIXED, **bad)
+    # a call refused in its argument checks leaves the assembled time grid in place
+    again, _, st = p.parareal_solve(np.zeros(nn), np.ones(nn), eps=1e-10, want_fine=False)
+    assert st["status"] == "OK"
+    assert float((again - ref).abs().max()) <= 1e-9 * float(ref.abs().max())
     p.close()
 
 
